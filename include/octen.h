@@ -1,0 +1,145 @@
+/*
+ * octen.h - C ABI of the GB300 OCTen online CP update.
+ *
+ * The library keeps the state of one online CP decomposition of a 3-mode
+ * tensor X (I x J x K) that grows along its third (time) mode, and updates it
+ * batch by batch as the paper's Algorithm 1 does: each batch of new slices is
+ * compressed into P small Q x Q x Q replicas (Sec. "Parallel Compression and
+ * Decomposition", Eq. 1-2), every replica is decomposed by CP-ALS, the replica
+ * factors are matched on their shared anchor rows (Sec. "Factor match for
+ * identifiability", Eq. 5) and lifted back into the global factors A, B, C
+ * (Sec. "Update results", Eq. 6-7).  The problem statement (Sec. "Problem
+ * Formulation") fixes the calls: start from existing summaries and factors,
+ * append a batch, read the factors and the fit.
+ *
+ * Conventions shared by every call:
+ *  - Every array is row-major and dense.  A slice batch X is laid out
+ *    [k][i][j] (t x I x J).  A is I x R, B is J x R, C is K x R.
+ *  - Projection matrices: U_all (I x Qd), V_all (J x Qd), W_all (t x Qd) with
+ *    Qd = S + P (Q - S).  Columns [0, S) are the anchors shared by every
+ *    replica (the paper's u, v, w of Eq. 1); replica p owns columns
+ *    [S + p (Q - S), S + (p + 1) (Q - S)).  The random draws are the caller's:
+ *    the library never generates them.
+ *  - Precision (octen_prec): FP32 computes everything in fp32 (fp32 FFMA, no
+ *    TF32).  BF16 takes bf16 slices, rounds U and V to bf16 once, and runs the
+ *    two large contractions in bf16 with fp32 accumulation.  FP8E4M3 takes
+ *    bf16 slices, quantises each slice to e4m3 with a per-slice absmax scale,
+ *    rounds V to e4m3 and U to bf16.  W stays fp32 in every mode.  The rounded
+ *    values are the matrices used by every later step.
+ *  - Pointers may be device memory or host memory (pageable or pinned); the
+ *    library detects which and copies host inputs to the device (and device
+ *    results to host outputs) on the context's stream.  The caller owns every
+ *    buffer it passes; the library copies what it keeps.
+ *  - Calls run on the stream given at creation and return once the work they
+ *    enqueued has finished (the status of device-side checks is known then).
+ *  - Errors are status codes; nothing is thrown across the ABI.  On a status
+ *    other than OCTEN_OK, octen_last_error() describes it.  A context is not
+ *    thread-safe.
+ */
+#ifndef OCTEN_H
+#define OCTEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct octen_ctx octen_ctx;
+
+typedef enum {
+  OCTEN_OK = 0,
+  OCTEN_EINVAL = 1,     /* bad argument or unsupported shape; state unchanged   */
+  OCTEN_ENOMEM = 2,     /* device allocation failed                             */
+  OCTEN_ECUDA = 3,      /* a CUDA runtime call failed                           */
+  OCTEN_ETIMEOUT = 4,   /* a bounded device-side wait ran out                   */
+  OCTEN_ENUMERIC = 5,   /* a Cholesky pivot was not positive even after loading */
+  OCTEN_ESTATE = 6      /* call out of order (e.g. append before init)          */
+} octen_status;
+
+typedef enum { OCTEN_FP32 = 0, OCTEN_BF16 = 1, OCTEN_FP8E4M3 = 2 } octen_prec;
+
+/* Shape of one online decomposition (Algorithm 1's REQUIRE line: R, p, Q,
+ * shared S; plus the fixed CP-ALS sweep count).  Limits: 1 <= R <= 32,
+ * 1 <= S <= Q <= 256, P >= 1, I, J >= 1, als_iters >= 1. */
+typedef struct {
+  int64_t I, J;
+  int32_t R, P, Q, S;
+  int32_t als_iters;
+  int32_t prec; /* octen_prec */
+} octen_config;
+
+/* Creates a context and allocates its device state (summaries P x Q^3 fp32,
+ * factors, lift operators).  `cuda_stream` is a cudaStream_t or NULL for the
+ * legacy default stream.  Returns EINVAL on limits above, ENOMEM on
+ * allocation failure.  *out is set only on success. */
+octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx **out);
+
+/* Existing summaries and decomposition (Sec. "Problem Formulation" (a)):
+ * compresses the existing tensor X_old (t_old x I x J; fp32 for FP32, bf16
+ * otherwise) into the P summaries Y_p with U_all, V_all and W_old (t_old x Qd),
+ * stores U_all, V_all (rounded per precision), takes A0 (I x R), B0 (J x R),
+ * C0 (t_old x R) as the existing factors, forms G_p = W_old,p^T C0 and
+ * precomputes the lift operators of Eq. 7.  All array arguments are required.
+ * May be called once per context (ESTATE otherwise). */
+octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
+                        const float *U_all, const float *V_all, const float *W_old,
+                        const float *A0, const float *B0, const float *C0);
+
+/* One pass of Algorithm 1's loop for a batch of t >= 1 new slices X_new
+ * (t x I x J, element type as in octen_init) with time projections W_new
+ * (t x Qd): Y_p += Z_p, CP-ALS of every replica warm-started from U_p^T A,
+ * V_p^T B, anchor matching, lift of A and B, t new rows of C.  Limit t <= 64. */
+octen_status octen_append(octen_ctx *ctx, const void *X_new, int64_t t, const float *W_new);
+
+/* Copies A (I x R), B (J x R) and C (K x R, K = rows so far) into caller
+ * buffers; any pointer may be NULL to skip it.  *K_out (if non-NULL) gets K. */
+octen_status octen_get_factors(const octen_ctx *ctx, float *A, float *B, float *C,
+                               int64_t *K_out);
+
+/* Number of rows of C so far. */
+int64_t octen_rows(const octen_ctx *ctx);
+
+/* Fitness of the current factors on K slices X_all (K x I x J, element type
+ * as in octen_init): 1 - ||X - [[A, B, C]]||_F / ||X||_F (Sec. "Evaluation
+ * Measures", as a fraction), with fp64 reductions.  K must equal octen_rows(). */
+octen_status octen_fit(octen_ctx *ctx, const void *X_all, int64_t K, double *fit_out);
+
+/* Copies the current summaries Y_p (P x Q x Q x Q, [p][a][b][c]) out. */
+octen_status octen_get_replicas(const octen_ctx *ctx, float *Y);
+
+/* Copies the last append's replica factors out, each P x Q x R ([p][q][r]):
+ * which = 0 gives the raw CP-ALS output, which = 1 the output of the anchor
+ * match (permuted and scaled).  perm (P x R int32, perm[p][s] = matched raw
+ * column) and scales (P x 2 x R fp64: d_a then d_b) may be NULL. */
+octen_status octen_get_replica_factors(const octen_ctx *ctx, int which, float *At,
+                                       float *Bt, float *Ct, int32_t *perm,
+                                       double *scales);
+
+/* Stateless compression of one slice batch (Sec. "Parallel Compression and
+ * Decomposition"): Z_p = X x1 U_p^T x2 V_p^T x3 W_p^T for every replica,
+ * written to Z (P x Q x Q x Q fp32, overwritten).  Same shapes, layouts,
+ * precisions and rounding as octen_init / octen_append; scratch space is
+ * allocated and freed inside the call.  cuda_stream as in octen_create. */
+octen_status octen_compress(const octen_config *cfg, void *cuda_stream, const void *X,
+                            int64_t t, const float *U_all, const float *V_all,
+                            const float *W_all, float *Z);
+
+/* Releases the context and its device memory (NULL is allowed). */
+void octen_destroy(octen_ctx *ctx);
+
+/* Human-readable description of the last error on this context (never NULL). */
+const char *octen_last_error(const octen_ctx *ctx);
+
+/* Short name of a status code (never NULL). */
+const char *octen_status_name(octen_status s);
+
+/* Number of kernel launches the library has issued in this process. */
+uint64_t octen_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCTEN_H */

@@ -1,0 +1,232 @@
+"""Python binding of the GB300 OCTen online CP update library.
+
+Argument marshalling only: every step of the update runs in the CUDA library
+(`_build/libocten.so`, C ABI in include/octen.h).  Arrays may be torch tensors
+(CUDA or CPU) or numpy arrays; CPU arrays are copied to the device by the
+library itself.  There is no fallback: if the library is missing or fails to
+load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Octen", "OctenError", "compress", "lib", "library_path", "PREC", "launch_count"]
+
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+_STATUS = {0: "OCTEN_OK", 1: "OCTEN_EINVAL", 2: "OCTEN_ENOMEM", 3: "OCTEN_ECUDA",
+           4: "OCTEN_ETIMEOUT", 5: "OCTEN_ENUMERIC", 6: "OCTEN_ESTATE"}
+
+
+class OctenError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_int64), ("J", ctypes.c_int64), ("R", ctypes.c_int32),
+                ("P", ctypes.c_int32), ("Q", ctypes.c_int32), ("S", ctypes.c_int32),
+                ("als_iters", ctypes.c_int32), ("prec", ctypes.c_int32)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (build it first with `build.build()`)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise OctenError(3, f"CUDA library not built: {path} is missing "
+                                "(run paper_1807_01350_gb300.build.build())")
+        L = ctypes.CDLL(path)
+        vp, i64, f32p = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p
+        L.octen_create.argtypes = [ctypes.POINTER(_Config), vp, ctypes.POINTER(vp)]
+        L.octen_init.argtypes = [vp, vp, i64, f32p, f32p, f32p, f32p, f32p, f32p]
+        L.octen_append.argtypes = [vp, vp, i64, f32p]
+        L.octen_get_factors.argtypes = [vp, f32p, f32p, f32p, ctypes.POINTER(i64)]
+        L.octen_rows.argtypes = [vp]
+        L.octen_rows.restype = i64
+        L.octen_fit.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
+        L.octen_get_replicas.argtypes = [vp, f32p]
+        L.octen_get_replica_factors.argtypes = [vp, ctypes.c_int, f32p, f32p, f32p, vp, vp]
+        L.octen_compress.argtypes = [ctypes.POINTER(_Config), vp, vp, i64, f32p, f32p, f32p, f32p]
+        L.octen_destroy.argtypes = [vp]
+        L.octen_destroy.restype = None
+        L.octen_last_error.argtypes = [vp]
+        L.octen_last_error.restype = ctypes.c_char_p
+        L.octen_status_name.argtypes = [ctypes.c_int]
+        L.octen_status_name.restype = ctypes.c_char_p
+        L.octen_launch_count.argtypes = []
+        L.octen_launch_count.restype = ctypes.c_uint64
+        for name in ("octen_create", "octen_init", "octen_append", "octen_get_factors",
+                     "octen_fit", "octen_get_replicas", "octen_get_replica_factors",
+                     "octen_compress"):
+            getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def launch_count() -> int:
+    return int(lib().octen_launch_count())
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(a, keep: list):
+    """Pointer to the data of a torch tensor or numpy array (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        keep.append(a)
+        return a.ctypes.data
+    if not a.is_contiguous():
+        a = a.contiguous()
+    keep.append(a)
+    return a.data_ptr()
+
+
+def _f32(a, keep: list):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return _ptr(np.ascontiguousarray(a, dtype=np.float32), keep)
+    import torch
+    return _ptr(a.to(torch.float32), keep)
+
+
+def _slices(a, prec: str, keep: list):
+    """Slice batch in the element type the precision takes (fp32 or bf16)."""
+    if isinstance(a, np.ndarray):
+        if prec == "fp32":
+            return _ptr(np.ascontiguousarray(a, dtype=np.float32), keep)
+        import torch
+        a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+    import torch
+    want = torch.float32 if prec == "fp32" else torch.bfloat16
+    return _ptr(a.to(want), keep)
+
+
+class Octen:
+    """One online CP decomposition (see include/octen.h)."""
+
+    def __init__(self, I, J, R, P, Q, S, als_iters, prec="fp32", stream=None):
+        self._lib = lib()
+        self.prec = prec
+        self.cfg = _Config(int(I), int(J), int(R), int(P), int(Q), int(S), int(als_iters),
+                           PREC[prec])
+        self.I, self.J, self.R, self.P, self.Q, self.S = I, J, R, P, Q, S
+        self.Qd = S + P * (Q - S)
+        h = ctypes.c_void_p()
+        st = self._lib.octen_create(ctypes.byref(self.cfg), _stream_handle(stream),
+                                    ctypes.byref(h))
+        if st != 0:
+            raise OctenError(st, "octen_create failed")
+        self._h = h
+
+    def _check(self, st: int):
+        if st != 0:
+            raise OctenError(st, self._lib.octen_last_error(self._h).decode())
+
+    def init(self, X_old, U_all, V_all, W_old, A0, B0, C0):
+        keep: list = []
+        t_old = int(X_old.shape[0])
+        self._check(self._lib.octen_init(
+            self._h, _slices(X_old, self.prec, keep), t_old, _f32(U_all, keep),
+            _f32(V_all, keep), _f32(W_old, keep), _f32(A0, keep), _f32(B0, keep),
+            _f32(C0, keep)))
+
+    def append(self, X_new, W_new):
+        keep: list = []
+        self._check(self._lib.octen_append(self._h, _slices(X_new, self.prec, keep),
+                                           int(X_new.shape[0]), _f32(W_new, keep)))
+
+    def append_ptr(self, x_ptr: int, t: int, w_ptr: int):
+        """Append from raw pointers (device or host) already in the right types."""
+        self._check(self._lib.octen_append(self._h, x_ptr, int(t), w_ptr))
+
+    @property
+    def rows(self) -> int:
+        return int(self._lib.octen_rows(self._h))
+
+    def factors(self):
+        K = self.rows
+        A = np.empty((self.I, self.R), np.float32)
+        B = np.empty((self.J, self.R), np.float32)
+        C = np.empty((K, self.R), np.float32)
+        k = ctypes.c_int64()
+        self._check(self._lib.octen_get_factors(self._h, A.ctypes.data, B.ctypes.data,
+                                                C.ctypes.data, ctypes.byref(k)))
+        return A, B, C
+
+    def factors_into(self, A, B, C):
+        """Copy the factors into caller buffers (torch device tensors allowed)."""
+        keep: list = []
+        k = ctypes.c_int64()
+        self._check(self._lib.octen_get_factors(self._h, _ptr(A, keep), _ptr(B, keep),
+                                                _ptr(C, keep), ctypes.byref(k)))
+        return int(k.value)
+
+    def fit(self, X_all) -> float:
+        keep: list = []
+        out = ctypes.c_double()
+        self._check(self._lib.octen_fit(self._h, _slices(X_all, self.prec, keep),
+                                        int(X_all.shape[0]), ctypes.byref(out)))
+        return float(out.value)
+
+    def replicas(self):
+        Y = np.empty((self.P, self.Q, self.Q, self.Q), np.float32)
+        self._check(self._lib.octen_get_replicas(self._h, Y.ctypes.data))
+        return Y
+
+    def replica_factors(self, which: int = 0):
+        shp = (self.P, self.Q, self.R)
+        At, Bt, Ct = (np.empty(shp, np.float32) for _ in range(3))
+        perm = np.empty((self.P, self.R), np.int32)
+        scales = np.empty((self.P, 2, self.R), np.float64)
+        self._check(self._lib.octen_get_replica_factors(
+            self._h, int(which), At.ctypes.data, Bt.ctypes.data, Ct.ctypes.data,
+            perm.ctypes.data, scales.ctypes.data))
+        return At, Bt, Ct, perm, scales
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.octen_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def compress(I, J, P, Q, S, X, U_all, V_all, W_all, prec="fp32", R=1, stream=None):
+    """Stateless compression of one batch into P summaries (P x Q x Q x Q)."""
+    L = lib()
+    cfg = _Config(int(I), int(J), int(R), int(P), int(Q), int(S), 1, PREC[prec])
+    keep: list = []
+    Z = np.empty((P, Q, Q, Q), np.float32)
+    st = L.octen_compress(ctypes.byref(cfg), _stream_handle(stream), _slices(X, prec, keep),
+                          int(X.shape[0]), _f32(U_all, keep), _f32(V_all, keep),
+                          _f32(W_all, keep), Z.ctypes.data)
+    if st != 0:
+        raise OctenError(st, "octen_compress failed")
+    return Z

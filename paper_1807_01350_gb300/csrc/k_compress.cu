@@ -1,0 +1,170 @@
+// Compression helpers (Sec. "Parallel Compression and Decomposition"):
+// layout/precision conversion of the projection matrices, per-slice e4m3
+// quantisation of the slice batch, and the time-mode contraction fused with the
+// summary update X_p = Y_p + Z_p (Eq. 2, Algorithm 1's second step).
+#include "octen_internal.cuh"
+
+namespace octen {
+
+__device__ __forceinline__ float round_as(float v, Elem te) {
+  if (te == Elem::BF16) return __bfloat162float(__float2bfloat16_rn(v));
+  if (te == Elem::E4M3) return float(__nv_fp8_e4m3(v));  // RNE, saturating to +-448
+  return v;
+}
+
+__device__ __forceinline__ void store_as(void *out, int64_t idx, float v, Elem te) {
+  if (te == Elem::F32) static_cast<float *>(out)[idx] = v;
+  else if (te == Elem::BF16) static_cast<__nv_bfloat16 *>(out)[idx] = __float2bfloat16_rn(v);
+  else static_cast<__nv_fp8_e4m3 *>(out)[idx] = __nv_fp8_e4m3(v);
+}
+
+// out[(p * Q + q) * rows + r] = M_all[r * Qd + col_p(q)] in type te, where
+// col_p(q) = q for anchors (q < S) and S + p (Q - S) + (q - S) otherwise.
+__global__ void replica_transpose_kernel(const float *__restrict__ M, int64_t rows, int P, int Q,
+                                         int S, int Qd, void *out, Elem te) {
+  __shared__ float tile[32][33];
+  const int p = blockIdx.z;
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int q0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t r = r0 + yy;
+    const int q = q0 + tx;
+    float v = 0.f;
+    if (r < rows && q < Q) {
+      const int c = q < S ? q : S + p * (Q - S) + (q - S);
+      v = M[r * Qd + c];
+    }
+    tile[yy][tx] = v;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int q = q0 + yy;
+    const int64_t r = r0 + tx;
+    if (q < Q && r < rows) store_as(out, ((int64_t)p * Q + q) * rows + r, tile[tx][yy], te);
+  }
+}
+
+void make_replica_transpose(const float *M_all, int64_t rows, int P, int Q, int S, int Qd,
+                            void *out, Elem te, cudaStream_t st) {
+  dim3 grid((unsigned)((rows + 31) / 32), (Q + 31) / 32, P);
+  replica_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(M_all, rows, P, Q, S, Qd, out, te);
+  count_launch();
+}
+
+void make_transpose(const float *M_all, int64_t rows, int Qd, void *out, Elem te,
+                    cudaStream_t st) {
+  make_replica_transpose(M_all, rows, 1, Qd, 0, Qd, out, te, st);
+}
+
+__global__ void round_copy_kernel(const float *__restrict__ in, float *__restrict__ out,
+                                  int64_t n, Elem te) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = round_as(in[i], te);
+}
+
+void round_copy(const float *in, float *out, int64_t n, Elem te, cudaStream_t st) {
+  if (n <= 0) return;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  round_copy_kernel<<<blocks, 256, 0, st>>>(in, out, n, te);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Per-slice absmax scaling to e4m3: s_k = max|X_k| / 448, X8 = rne(X / s_k).
+// ---------------------------------------------------------------------------
+__global__ void slice_absmax_kernel(const __nv_bfloat16 *__restrict__ X, int64_t IJ,
+                                    unsigned int *__restrict__ amax_bits) {
+  const int k = blockIdx.y;
+  const __nv_bfloat16 *x = X + (int64_t)k * IJ;
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < IJ;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(__bfloat162float(x[i])));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax_bits + k, __float_as_uint(m));
+}
+
+__global__ void slice_scale_kernel(const unsigned int *__restrict__ amax_bits, int64_t t,
+                                   float *__restrict__ scale) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < t) {
+    const float a = __uint_as_float(amax_bits[k]);
+    scale[k] = a > 0.f ? a / 448.f : 1.f;
+  }
+}
+
+__global__ void quantize_kernel(const __nv_bfloat16 *__restrict__ X, int64_t IJ,
+                                const float *__restrict__ scale,
+                                __nv_fp8_e4m3 *__restrict__ X8) {
+  const int k = blockIdx.y;
+  const float s = scale[k];
+  const __nv_bfloat16 *x = X + (int64_t)k * IJ;
+  __nv_fp8_e4m3 *y = X8 + (int64_t)k * IJ;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < IJ;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = __nv_fp8_e4m3(__fdiv_rn(__bfloat162float(x[i]), s));
+}
+
+void quantize_e4m3(const __nv_bfloat16 *X, int64_t t, int64_t IJ, __nv_fp8_e4m3 *X8,
+                   float *scale, cudaStream_t st) {
+  // the scale buffer doubles as the absmax bit store before it holds scales
+  unsigned int *bits = reinterpret_cast<unsigned int *>(scale);
+  cudaMemsetAsync(bits, 0, t * sizeof(unsigned int), st);
+  dim3 grid(64, (unsigned)t);
+  slice_absmax_kernel<<<grid, 256, 0, st>>>(X, IJ, bits);
+  count_launch();
+  slice_scale_kernel<<<(unsigned)((t + 127) / 128), 128, 0, st>>>(bits, t, scale);
+  count_launch();
+  quantize_kernel<<<dim3(256, (unsigned)t), 256, 0, st>>>(X, IJ, scale, X8);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Time-mode contraction + summary update:
+//   Y[p][a][b][c] += sum_k T2[p][k][a][b] * W[k][col_p(c)]
+// One CTA owns kRows consecutive (a, b) rows of one replica and every c.
+// ---------------------------------------------------------------------------
+constexpr int kRows = 32;
+
+__global__ void __launch_bounds__(256)
+    mode3_kernel(const float *__restrict__ T2, const float *__restrict__ W, float *__restrict__ Y,
+                 int t, int Q, int S, int Qd) {
+  extern __shared__ float sm[];
+  float *Ws = sm;                       // [t][Q]
+  float *Ts = sm + (size_t)t * Q;       // [t][kRows]
+  const int p = blockIdx.y;
+  const int64_t QQ = (int64_t)Q * Q;
+  const int64_t row0 = (int64_t)blockIdx.x * kRows;
+  const int nrows = (int)(QQ - row0 < kRows ? QQ - row0 : kRows);
+  for (int e = threadIdx.x; e < t * Q; e += blockDim.x) {
+    const int k = e / Q, c = e % Q;
+    const int col = c < S ? c : S + p * (Q - S) + (c - S);
+    Ws[e] = W[(int64_t)k * Qd + col];
+  }
+  for (int e = threadIdx.x; e < t * kRows; e += blockDim.x) {
+    const int k = e / kRows, r = e % kRows;
+    Ts[e] = r < nrows ? T2[((int64_t)p * t + k) * QQ + row0 + r] : 0.f;
+  }
+  __syncthreads();
+  float *Yp = Y + (int64_t)p * QQ * Q + row0 * Q;
+  for (int e = threadIdx.x; e < nrows * Q; e += blockDim.x) {
+    const int r = e / Q, c = e % Q;
+    float acc = 0.f;
+    for (int k = 0; k < t; ++k) acc = fmaf(Ts[k * kRows + r], Ws[k * Q + c], acc);
+    Yp[e] += acc;
+  }
+}
+
+void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
+                      int S, int Qd, cudaStream_t st) {
+  const size_t smem = ((size_t)t * Q + (size_t)t * kRows) * sizeof(float);
+  cudaFuncSetAttribute(mode3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  const int64_t QQ = (int64_t)Q * Q;
+  dim3 grid((unsigned)((QQ + kRows - 1) / kRows), P);
+  mode3_kernel<<<grid, 256, smem, st>>>(T2, W, Y, (int)t, Q, S, Qd);
+  count_launch();
+}
+
+}  // namespace octen

@@ -1,0 +1,486 @@
+// Merge of the replica factors: anchor match (Sec. "Factor match for
+// identifiability", Eq. 5, fp64), the lift of A and B through the stacked
+// projections (Sec. "Update results", Eq. 6-7), the least-squares solve of the
+// new rows of C, and the dense fp32 Cholesky / triangular solves that build the
+// lift operators once per stream.
+#include "octen_internal.cuh"
+
+namespace octen {
+
+// ---------------------------------------------------------------------------
+// Anchor match, one CTA per replica.  ref_a = PA rows [0, S) (= u^T A_prev).
+//   sim[r][s] = |cos(At[:S, r], ref_a[:, s])| + |cos(Bt[:S, r], ref_b[:, s])|
+// greedy: largest similarity among unmatched pairs, ties to lowest s then r;
+// d_a[s] = <At[:S, pi(s)], ref_a[:, s]> / ||ref_a[:, s]||^2 (0 -> 1), same for b.
+// ---------------------------------------------------------------------------
+template <int RT>
+__global__ void __launch_bounds__(256)
+    align_kernel(const float *__restrict__ At, const float *__restrict__ Bt,
+                 const float *__restrict__ Ct, const float *__restrict__ PA,
+                 const float *__restrict__ PB, int Q, int S, int R, float *__restrict__ Ah,
+                 float *__restrict__ Bh, float *__restrict__ Ch, int *__restrict__ perm_out,
+                 double *__restrict__ scales_out) {
+  __shared__ double dA[RT * RT], dB[RT * RT], sim[RT * RT];
+  __shared__ double nra[RT], nrb[RT], nta[RT], ntb[RT];
+  __shared__ double da[RT], db[RT];
+  __shared__ int perm[RT];
+  const int p = blockIdx.x;
+  const float *at = At + (int64_t)p * Q * RT, *bt = Bt + (int64_t)p * Q * RT;
+  const float *ct = Ct + (int64_t)p * Q * RT;
+  // dot products of anchor columns (fp64)
+  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
+    const int r = e / RT, s = e % RT;
+    double sa = 0.0, sb = 0.0;
+    if (r < R && s < R) {
+      for (int q = 0; q < S; ++q) {
+        sa += (double)at[q * RT + r] * (double)PA[(int64_t)q * R + s];
+        sb += (double)bt[q * RT + r] * (double)PB[(int64_t)q * R + s];
+      }
+    }
+    dA[e] = sa;
+    dB[e] = sb;
+  }
+  if (threadIdx.x < RT) {
+    const int r = threadIdx.x;
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
+    if (r < R) {
+      for (int q = 0; q < S; ++q) {
+        const double ra = PA[(int64_t)q * R + r], rb = PB[(int64_t)q * R + r];
+        const double ta = at[q * RT + r], tb = bt[q * RT + r];
+        a1 += ra * ra; a2 += rb * rb; a3 += ta * ta; a4 += tb * tb;
+      }
+    }
+    nra[r] = a1; nrb[r] = a2; nta[r] = a3; ntb[r] = a4;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
+    const int r = e / RT, s = e % RT;
+    double v = 0.0;
+    if (r < R && s < R) {
+      const double den_a = sqrt(nta[r]) * sqrt(nra[s]);
+      const double den_b = sqrt(ntb[r]) * sqrt(nrb[s]);
+      if (den_a > 0.0) v += fabs(dA[e]) / den_a;
+      if (den_b > 0.0) v += fabs(dB[e]) / den_b;
+      if (!isfinite(v)) v = 0.0;   // a diverged replica still gets a valid matching
+    }
+    sim[e] = v;
+  }
+  __syncthreads();
+  // greedy matching by warp 0: lane s scans its column for the best free r
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    unsigned used_r = 0u, used_s = 0u;
+    for (int round = 0; round < R; ++round) {
+      double best = -1.0;
+      int br = -1;
+      if (lane < R && !((used_s >> lane) & 1u)) {
+        for (int r = 0; r < R; ++r) {
+          if ((used_r >> r) & 1u) continue;
+          const double v = sim[r * RT + lane];
+          if (v > best || br < 0) { best = v; br = r; }
+        }
+      }
+      // warp argmax over lanes: larger value wins, ties to the lower lane (s)
+      int bs = lane;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int obr = __shfl_xor_sync(0xffffffffu, br, o);
+        const int obs = __shfl_xor_sync(0xffffffffu, bs, o);
+        if (ov > best || (ov == best && obs < bs)) { best = ov; br = obr; bs = obs; }
+      }
+      if (lane == 0) perm[bs] = br;
+      used_r |= 1u << br;
+      used_s |= 1u << bs;
+    }
+    __syncwarp();
+    if (lane < R) {
+      const int s = lane, r = perm[s];
+      double a = nra[s] > 0.0 ? dA[r * RT + s] / nra[s] : 0.0;
+      double b = nrb[s] > 0.0 ? dB[r * RT + s] / nrb[s] : 0.0;
+      if (a == 0.0) a = 1.0;
+      if (b == 0.0) b = 1.0;
+      da[s] = a;
+      db[s] = b;
+      perm_out[p * R + s] = r;
+      scales_out[(int64_t)p * 2 * R + s] = a;
+      scales_out[(int64_t)p * 2 * R + R + s] = b;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Q * RT; e += blockDim.x) {
+    const int q = e / RT, s = e % RT;
+    float va = 0.f, vb = 0.f, vc = 0.f;
+    if (s < R) {
+      const int r = perm[s];
+      va = (float)((double)at[q * RT + r] / da[s]);
+      vb = (float)((double)bt[q * RT + r] / db[s]);
+      vc = (float)((double)ct[q * RT + r] * (da[s] * db[s]));
+    }
+    const int64_t o = (int64_t)p * Q * RT + e;
+    Ah[o] = va;
+    Bh[o] = vb;
+    Ch[o] = vc;
+  }
+}
+
+void align_replicas(const float *At, const float *Bt, const float *Ct, const float *PA,
+                    const float *PB, int P, int Q, int S, int R, int RT, float *Ah,
+                    float *Bh, float *Ch, int *perm, double *scales, cudaStream_t st) {
+  if (RT == 8)
+    align_kernel<8><<<P, 256, 0, st>>>(At, Bt, Ct, PA, PB, Q, S, R, Ah, Bh, Ch, perm, scales);
+  else if (RT == 16)
+    align_kernel<16><<<P, 256, 0, st>>>(At, Bt, Ct, PA, PB, Q, S, R, Ah, Bh, Ch, perm, scales);
+  else
+    align_kernel<32><<<P, 256, 0, st>>>(At, Bt, Ct, PA, PB, Q, S, R, Ah, Bh, Ch, perm, scales);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side of the lift: residual of every replica block against the
+// projected previous factor, reduced to the Qd distinct rows of the stack.
+//   anchor row c < S:  sum_p (or mean_p) (Fh_p[c] - PF[c])
+//   private row c:     Fh_p[b] - PF[c] with p, b the owner of column c
+// ---------------------------------------------------------------------------
+__global__ void lift_rhs_kernel(const float *__restrict__ Fh, const float *__restrict__ PF,
+                                int P, int Q, int S, int R, int RT, int Qd, int sum_mode,
+                                float *__restrict__ e) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)Qd * R) return;
+  const int c = (int)(idx / R), r = (int)(idx % R);
+  const float pf = PF[idx];
+  float v;
+  if (c < S) {
+    float s = 0.f;
+    for (int p = 0; p < P; ++p) s += Fh[((int64_t)p * Q + c) * RT + r] - pf;
+    v = sum_mode ? s : s / (float)P;
+  } else {
+    const int p = (c - S) / (Q - S);
+    const int b = S + (c - S) - p * (Q - S);
+    v = Fh[((int64_t)p * Q + b) * RT + r] - pf;
+  }
+  e[idx] = v;
+}
+
+void lift_rhs(const float *Fh, const float *PF, int P, int Q, int S, int R, int RT, int Qd,
+              int sum_mode, float *e, cudaStream_t st) {
+  const int64_t n = (int64_t)Qd * R;
+  lift_rhs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Fh, PF, P, Q, S, R, RT, Qd,
+                                                                sum_mode, e);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// New rows of C.  The stacked system (W_new,p^T) C_new = Ch_p - G_p has normal
+// equations (sum_p W_p W_p^T) C_new = sum_p W_p (Ch_p - G_p).  Both sides are
+// reduced over the Qd distinct columns of W_all (anchor columns weighted P),
+// then factored by fp64 Cholesky (t x t, t <= 64) in one CTA.
+// ---------------------------------------------------------------------------
+__global__ void c_rhs_cols_kernel(const float *__restrict__ Ch, const float *__restrict__ G,
+                                  int P, int Q, int S, int R, int RT, int Qd,
+                                  float *__restrict__ E) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)Qd * R) return;
+  const int c = (int)(idx / R), r = (int)(idx % R);
+  float v = 0.f;
+  if (c < S) {
+    for (int p = 0; p < P; ++p)
+      v += Ch[((int64_t)p * Q + c) * RT + r] - G[((int64_t)p * Q + c) * R + r];
+  } else {
+    const int p = (c - S) / (Q - S);
+    const int b = S + (c - S) - p * (Q - S);
+    v = Ch[((int64_t)p * Q + b) * RT + r] - G[((int64_t)p * Q + b) * R + r];
+  }
+  E[idx] = v;
+}
+
+__global__ void __launch_bounds__(256)
+    c_solve_kernel(const float *__restrict__ Gram, const float *__restrict__ rhs, int t, int R,
+                   float *__restrict__ C_new, int *status) {
+  __shared__ double L[64 * 64];
+  __shared__ double X[64 * 32];
+  __shared__ int ok_s;
+  for (int e = threadIdx.x; e < t * t; e += blockDim.x) L[e] = Gram[e];
+  for (int e = threadIdx.x; e < t * R; e += blockDim.x) X[e] = rhs[e];
+  if (threadIdx.x == 0) ok_s = 1;
+  __syncthreads();
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    for (int j = 0; j < t; ++j) {
+      if (threadIdx.x == 0) {
+        double d = L[j * t + j];
+        for (int k = 0; k < j; ++k) d -= L[j * t + k] * L[j * t + k];
+        if (d > 0.0) L[j * t + j] = sqrt(d);
+        else ok_s = 0;
+      }
+      __syncthreads();
+      if (!ok_s) break;
+      const int i = j + 1 + threadIdx.x;
+      if (i < t) {
+        double s = L[i * t + j];
+        for (int k = 0; k < j; ++k) s -= L[i * t + k] * L[j * t + k];
+        L[i * t + j] = s / L[j * t + j];
+      }
+      __syncthreads();
+    }
+    if (ok_s || attempt == 1) break;
+    // reload, add 1e-12 * trace / t to the diagonal and retry once
+    __syncthreads();
+    for (int e = threadIdx.x; e < t * t; e += blockDim.x) L[e] = Gram[e];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tr = 0.0;
+      for (int k = 0; k < t; ++k) tr += L[k * t + k];
+      for (int k = 0; k < t; ++k) L[k * t + k] += 1e-12 * tr / t;
+      ok_s = 1;
+    }
+    __syncthreads();
+  }
+  if (!ok_s) {
+    if (threadIdx.x == 0) atomicOr(status, kDevCholesky);
+    for (int e = threadIdx.x; e < t * R; e += blockDim.x) C_new[e] = 0.f;
+    return;
+  }
+  const int r = threadIdx.x;
+  if (r < R) {
+    for (int i = 0; i < t; ++i) {
+      double s = X[i * R + r];
+      for (int k = 0; k < i; ++k) s -= L[i * t + k] * X[k * R + r];
+      X[i * R + r] = s / L[i * t + i];
+    }
+    for (int i = t - 1; i >= 0; --i) {
+      double s = X[i * R + r];
+      for (int k = i + 1; k < t; ++k) s -= L[k * t + i] * X[k * R + r];
+      X[i * R + r] = s / L[i * t + i];
+    }
+    for (int i = 0; i < t; ++i) C_new[i * R + r] = (float)X[i * R + r];
+  }
+}
+
+__global__ void scale_columns_kernel(const float *__restrict__ in, int64_t rows, int cols,
+                                     int S, float w, float *__restrict__ out) {
+  const int64_t n = rows * cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % cols);
+    out[i] = c < S ? in[i] * w : in[i];
+  }
+}
+
+void scale_columns(const float *in, int64_t rows, int cols, int S, float w_shared, float *out,
+                   cudaStream_t st) {
+  const int64_t n = rows * cols;
+  if (n <= 0) return;
+  const unsigned blocks = (unsigned)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+  scale_columns_kernel<<<blocks, 256, 0, st>>>(in, rows, cols, S, w_shared, out);
+  count_launch();
+}
+
+// scratch holds E (Qd x R), rhs (t x R), Ww (t x Qd) and Gram (t x t).
+void solve_c_new(const float *W, const float *Ch, const float *G, int64_t t, int P, int Q,
+                 int S, int Qd, int R, int RT, float *scratch, float *C_new, int *status,
+                 cudaStream_t st) {
+  float *E = scratch;
+  float *rhs = E + (int64_t)Qd * R;
+  float *Ww = rhs + t * R;
+  float *Gram = Ww + t * Qd;
+  const int64_t n = (int64_t)Qd * R;
+  c_rhs_cols_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Ch, G, P, Q, S, R, RT, Qd, E);
+  count_launch();
+  GemmArgs g{};
+  g.A = W; g.ta = Elem::F32; g.sAm = Qd; g.sAk = 1;
+  g.B = E; g.tb = Elem::F32; g.sBn = 1; g.sBk = R;
+  g.D = rhs; g.sDm = R; g.sDn = 1;
+  g.M = (int)t; g.N = R; g.K = Qd; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
+  gemm_strided(g, st);
+  scale_columns(W, t, Qd, S, (float)P, Ww, st);
+  GemmArgs h{};
+  h.A = Ww; h.ta = Elem::F32; h.sAm = Qd; h.sAk = 1;
+  h.B = W; h.tb = Elem::F32; h.sBn = Qd; h.sBk = 1;
+  h.D = Gram; h.sDm = t; h.sDn = 1;
+  h.M = (int)t; h.N = (int)t; h.K = Qd; h.batch = 1; h.alpha = 1.f; h.beta = 0.f;
+  gemm_strided(h, st);
+  c_solve_kernel<<<1, 256, 0, st>>>(Gram, rhs, (int)t, R, C_new, status);
+  count_launch();
+}
+
+// G[p][b][r] += sum_k W[k][col_p(b)] C_new[k][r]
+__global__ void update_g_kernel(const float *__restrict__ W, const float *__restrict__ Cn,
+                                int t, int P, int Q, int S, int Qd, int R,
+                                float *__restrict__ G) {
+  const int p = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Q * R) return;
+  const int b = e / R, r = e % R;
+  const int col = b < S ? b : S + p * (Q - S) + (b - S);
+  float acc = 0.f;
+  for (int k = 0; k < t; ++k) acc = fmaf(W[(int64_t)k * Qd + col], Cn[(int64_t)k * R + r], acc);
+  G[((int64_t)p * Q + b) * R + r] += acc;
+}
+
+void update_g(const float *W, const float *C_new, int64_t t, int P, int Q, int S, int Qd,
+              int R, float *G, cudaStream_t st) {
+  dim3 grid((Q * R + 255) / 256, P);
+  update_g_kernel<<<grid, 256, 0, st>>>(W, C_new, (int)t, P, Q, S, Qd, R, G);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Dense SPD factorisation A = L L^T (row-major n x n, lower triangle written,
+// fp32) by 32-wide column blocks: fp64 factor of the diagonal block, fp32
+// triangular solve of the panel below, fp32 trailing update by the SIMT GEMM.
+// ---------------------------------------------------------------------------
+constexpr int kNB = 32;
+
+__global__ void chol_diag_kernel(float *A, int n, int j0, int jb, int *status) {
+  __shared__ double Ls[kNB * kNB];
+  __shared__ int ok_s;
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+    const int r = e / jb, c = e % jb;
+    Ls[e] = A[(int64_t)(j0 + r) * n + j0 + c];
+  }
+  if (threadIdx.x == 0) ok_s = 1;
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    if (threadIdx.x == 0) {
+      double d = Ls[j * jb + j];
+      for (int k = 0; k < j; ++k) d -= Ls[j * jb + k] * Ls[j * jb + k];
+      if (d > 0.0) Ls[j * jb + j] = sqrt(d);
+      else { Ls[j * jb + j] = 1.0; ok_s = 0; }
+    }
+    __syncthreads();
+    const int i = j + 1 + threadIdx.x;
+    if (i < jb) {
+      double s = Ls[i * jb + j];
+      for (int k = 0; k < j; ++k) s -= Ls[i * jb + k] * Ls[j * jb + k];
+      Ls[i * jb + j] = s / Ls[j * jb + j];
+    }
+    __syncthreads();
+  }
+  if (!ok_s && threadIdx.x == 0) atomicOr(status, kDevCholesky);
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+    const int r = e / jb, c = e % jb;
+    A[(int64_t)(j0 + r) * n + j0 + c] = c <= r ? (float)Ls[e] : 0.f;
+  }
+}
+
+// rows i >= j0 + jb:  L[i][j0 : j0+jb] = A[i][j0 : j0+jb] L11^-T
+__global__ void chol_panel_kernel(float *A, int n, int j0, int jb) {
+  __shared__ float L11[kNB * kNB];
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x)
+    L11[e] = A[(int64_t)(j0 + e / jb) * n + j0 + e % jb];
+  __syncthreads();
+  const int64_t i = (int64_t)j0 + jb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x[kNB];
+  float *row = A + i * n + j0;
+  for (int k = 0; k < jb; ++k) {
+    float s = row[k];
+    for (int l = 0; l < k; ++l) s = fmaf(-x[l], L11[k * jb + l], s);
+    x[k] = s / L11[k * jb + k];
+  }
+  for (int k = 0; k < jb; ++k) row[k] = x[k];
+}
+
+void cholesky_f32(float *Gm, int n, int *status, cudaStream_t st) {
+  for (int j0 = 0; j0 < n; j0 += kNB) {
+    const int jb = n - j0 < kNB ? n - j0 : kNB;
+    chol_diag_kernel<<<1, 64, 0, st>>>(Gm, n, j0, jb, status);
+    count_launch();
+    const int rest = n - j0 - jb;
+    if (rest <= 0) continue;
+    chol_panel_kernel<<<(rest + 127) / 128, 128, 0, st>>>(Gm, n, j0, jb);
+    count_launch();
+    GemmArgs g{};
+    g.A = Gm + (int64_t)(j0 + jb) * n + j0; g.ta = Elem::F32; g.sAz = 0; g.sAm = n; g.sAk = 1;
+    g.B = g.A; g.tb = Elem::F32; g.sBz = 0; g.sBn = n; g.sBk = 1;
+    g.D = Gm + (int64_t)(j0 + jb) * n + j0 + jb; g.sDz = 0; g.sDm = n; g.sDn = 1;
+    g.M = rest; g.N = rest; g.K = jb; g.batch = 1; g.alpha = -1.f; g.beta = 1.f;
+    gemm_strided(g, st);
+  }
+}
+
+// Block triangular solves with m right-hand sides (row-major n x m, in place).
+__global__ void trsv_fwd_block_kernel(const float *L, int n, int j0, int jb, float *Bm, int m) {
+  __shared__ float L11[kNB * kNB];
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x)
+    L11[e] = L[(int64_t)(j0 + e / jb) * n + j0 + e % jb];
+  __syncthreads();
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  float x[kNB];
+  for (int k = 0; k < jb; ++k) {
+    float s = Bm[(int64_t)(j0 + k) * m + c];
+    for (int l = 0; l < k; ++l) s = fmaf(-L11[k * jb + l], x[l], s);
+    x[k] = s / L11[k * jb + k];
+  }
+  for (int k = 0; k < jb; ++k) Bm[(int64_t)(j0 + k) * m + c] = x[k];
+}
+
+__global__ void trsv_bwd_block_kernel(const float *L, int n, int j0, int jb, float *Bm, int m) {
+  __shared__ float L11[kNB * kNB];
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x)
+    L11[e] = L[(int64_t)(j0 + e / jb) * n + j0 + e % jb];
+  __syncthreads();
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  float x[kNB];
+  for (int k = jb - 1; k >= 0; --k) {
+    float s = Bm[(int64_t)(j0 + k) * m + c];
+    for (int l = k + 1; l < jb; ++l) s = fmaf(-L11[l * jb + k], x[l], s);
+    x[k] = s / L11[k * jb + k];
+  }
+  for (int k = 0; k < jb; ++k) Bm[(int64_t)(j0 + k) * m + c] = x[k];
+}
+
+void chol_solve_f32(const float *L, int n, float *Bm, int m, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((m + 127) / 128);
+  for (int j0 = 0; j0 < n; j0 += kNB) {          // L Y = B
+    const int jb = n - j0 < kNB ? n - j0 : kNB;
+    trsv_fwd_block_kernel<<<blocks, 128, 0, st>>>(L, n, j0, jb, Bm, m);
+    count_launch();
+    const int rest = n - j0 - jb;
+    if (rest <= 0) continue;
+    GemmArgs g{};
+    g.A = L + (int64_t)(j0 + jb) * n + j0; g.ta = Elem::F32; g.sAm = n; g.sAk = 1;
+    g.B = Bm + (int64_t)j0 * m; g.tb = Elem::F32; g.sBn = 1; g.sBk = m;
+    g.D = Bm + (int64_t)(j0 + jb) * m; g.sDm = m; g.sDn = 1;
+    g.M = rest; g.N = m; g.K = jb; g.batch = 1; g.alpha = -1.f; g.beta = 1.f;
+    gemm_strided(g, st);
+  }
+  const int last = ((n - 1) / kNB) * kNB;
+  for (int j0 = last; j0 >= 0; j0 -= kNB) {     // L^T X = Y
+    const int jb = n - j0 < kNB ? n - j0 : kNB;
+    trsv_bwd_block_kernel<<<blocks, 128, 0, st>>>(L, n, j0, jb, Bm, m);
+    count_launch();
+    if (j0 == 0) continue;
+    GemmArgs g{};
+    // Y[0:j0] -= L[j0:j0+jb, 0:j0]^T X[j0:j0+jb]
+    g.A = L + (int64_t)j0 * n; g.ta = Elem::F32; g.sAm = 1; g.sAk = n;
+    g.B = Bm + (int64_t)j0 * m; g.tb = Elem::F32; g.sBn = 1; g.sBk = m;
+    g.D = Bm; g.sDm = m; g.sDn = 1;
+    g.M = j0; g.N = m; g.K = jb; g.batch = 1; g.alpha = -1.f; g.beta = 1.f;
+    gemm_strided(g, st);
+  }
+}
+
+__global__ void transpose_kernel(const float *__restrict__ in, int64_t rows, int64_t cols,
+                                 float *__restrict__ out) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int64_t r = r0 + yy, c = c0 + threadIdx.x;
+    tile[yy][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : 0.f;
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int64_t c = c0 + yy, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) out[c * rows + r] = tile[threadIdx.x][yy];
+  }
+}
+
+void transpose_f32(const float *in, int64_t rows, int64_t cols, float *out, cudaStream_t st) {
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, out);
+  count_launch();
+}
+
+}  // namespace octen

@@ -1,0 +1,615 @@
+// C ABI of the library (include/octen.h): the context, its device state, and
+// the order of the stages of one online update (the loop body of the paper's
+// Algorithm 1: compress, X_p = Y_p + Z_p, CP of every replica, factor match,
+// lift of A, B and the new rows of C).
+#include <atomic>
+#include <cstdarg>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "octen_internal.cuh"
+
+using namespace octen;
+
+namespace octen {
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace octen
+
+namespace {
+
+// Device buffer owned by a context (freed in the destructor).
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+bool is_device_ptr(const void *p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int round_rt(int R) { return R <= 8 ? 8 : (R <= 16 ? 16 : 32); }
+
+}  // namespace
+
+struct octen_ctx {
+  octen_config cfg{};
+  int Qd = 0, RT = 8;
+  Elem xin = Elem::F32;    // slice element type at the boundary
+  Elem tu = Elem::F32;     // U rounding / mode-1 operand type
+  Elem tv = Elem::F32;     // V rounding / mode-2 operand type
+  Elem tmid = Elem::F32;   // mode-2 output (T_rep) type
+  cudaStream_t st = nullptr;
+  bool initialized = false;
+  std::string err;
+  int64_t K = 0, Kcap = 0;
+  int a_over = 0, b_over = 0;
+  std::vector<DevBuf> owned;
+
+  // persistent state
+  float *U32 = nullptr, *V32 = nullptr;   // rounded projections [rows][Qd]
+  void *Ut_rep = nullptr, *Vt = nullptr;  // contraction operands
+  float *La = nullptr, *Lb = nullptr;     // lift operators
+  float *Y = nullptr, *A = nullptr, *B = nullptr, *C = nullptr, *G = nullptr;
+  float *PA = nullptr, *PB = nullptr, *e = nullptr;
+  float *At = nullptr, *Bt = nullptr, *Ct = nullptr, *Ah = nullptr, *Bh = nullptr, *Ch = nullptr;
+  float *M = nullptr, *H = nullptr, *csolve = nullptr;
+  int *perm = nullptr;
+  double *scales = nullptr;
+  int *dstatus = nullptr;
+  double *dfit = nullptr;
+
+  // per-batch scratch, grown on demand
+  DevBuf Tbuf, T2buf, Wbuf, X8buf, xscale, stage[4], fitpart;
+
+  ~octen_ctx() {
+    if (st || true) cudaStreamSynchronize(st);
+    for (auto &b : owned) cudaFree(b.p);
+    DevBuf *extra[] = {&Tbuf, &T2buf, &Wbuf, &X8buf, &xscale, &stage[0], &stage[1], &stage[2],
+                       &stage[3], &fitpart};
+    for (DevBuf *b : extra) cudaFree(b->p);
+  }
+
+  octen_status fail(octen_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return s;
+  }
+
+  template <class T>
+  bool alloc(T *&ptr, size_t count) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, count * sizeof(T) + 16) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    owned.push_back({p, count * sizeof(T)});
+    ptr = static_cast<T *>(p);
+    return true;
+  }
+
+  bool grow(DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes) return true;
+    cudaStreamSynchronize(st);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes + 16) != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return false;
+    }
+    b.bytes = bytes;
+    return true;
+  }
+
+  // Device view of a caller buffer: the pointer itself if it is device
+  // memory, else a copy in staging slot `slot`.
+  const void *stage_in(const void *p, size_t bytes, int slot) {
+    if (is_device_ptr(p)) return p;
+    if (!grow(stage[slot], bytes)) return nullptr;
+    if (cudaMemcpyAsync(stage[slot].p, p, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return nullptr;
+    return stage[slot].p;
+  }
+
+  octen_status sync_check(const char *what) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(OCTEN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    int flags = 0;
+    cudaMemcpy(&flags, dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+    if (flags) {
+      cudaMemsetAsync(dstatus, 0, sizeof(int), st);
+      cudaStreamSynchronize(st);
+      if (flags & kDevTimeout) return fail(OCTEN_ETIMEOUT, "%s: a device wait ran out", what);
+      return fail(OCTEN_ENUMERIC, "%s: a Cholesky pivot was not positive", what);
+    }
+    return OCTEN_OK;
+  }
+};
+
+namespace {
+
+octen_status validate(const octen_config *c, std::string &why) {
+  char buf[256];
+  if (!c) { why = "config is NULL"; return OCTEN_EINVAL; }
+  if (c->I < 1 || c->J < 1 || c->R < 1 || c->R > 32 || c->P < 1 || c->Q < 2 || c->Q > 256 ||
+      c->S < 1 || c->S >= c->Q || c->als_iters < 1 || c->prec < 0 || c->prec > 2) {
+    snprintf(buf, sizeof buf,
+             "unsupported config I=%lld J=%lld R=%d P=%d Q=%d S=%d iters=%d prec=%d (limits: "
+             "1<=R<=32, 1<=S<Q<=256, P>=1, iters>=1)",
+             (long long)c->I, (long long)c->J, c->R, c->P, c->Q, c->S, c->als_iters, c->prec);
+    why = buf;
+    return OCTEN_EINVAL;
+  }
+  const int64_t Qd = (int64_t)c->S + (int64_t)c->P * (c->Q - c->S);
+  if (Qd > (1 << 20) || c->I > (1 << 24) || c->J > (1 << 24)) {
+    why = "dimensions too large";
+    return OCTEN_EINVAL;
+  }
+  return OCTEN_OK;
+}
+
+void set_types(octen_ctx *x) {
+  switch (x->cfg.prec) {
+    case OCTEN_FP32:
+      x->xin = Elem::F32; x->tu = Elem::F32; x->tv = Elem::F32; x->tmid = Elem::F32; break;
+    case OCTEN_BF16:
+      x->xin = Elem::BF16; x->tu = Elem::BF16; x->tv = Elem::BF16; x->tmid = Elem::BF16; break;
+    default:
+      x->xin = Elem::BF16; x->tu = Elem::BF16; x->tv = Elem::E4M3; x->tmid = Elem::BF16; break;
+  }
+}
+
+constexpr int64_t kChunk = 64;  // slices per compression pass
+
+// Z_p (+)= compression of t slices (t <= kChunk) into Yacc.
+octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float *Wd,
+                            float *Yacc) {
+  const octen_config &c = x->cfg;
+  const size_t tb = (size_t)t * c.P * c.Q * c.I * elem_size(x->tmid);
+  if (!x->grow(x->Tbuf, tb)) return x->fail(OCTEN_ENOMEM, "scratch T (%zu bytes)", tb);
+  const size_t t2b = (size_t)t * c.P * c.Q * c.Q * sizeof(float);
+  if (!x->grow(x->T2buf, t2b)) return x->fail(OCTEN_ENOMEM, "scratch T2 (%zu bytes)", t2b);
+  Mode2Args m2{};
+  m2.X = Xd; m2.tx = x->xin; m2.Vt = x->Vt; m2.tv = x->tv; m2.slice_scale = nullptr;
+  m2.T = x->Tbuf.p; m2.tt = x->tmid; m2.t = t; m2.I = c.I; m2.J = c.J;
+  m2.P = c.P; m2.Q = c.Q; m2.S = c.S; m2.Qd = x->Qd;
+  if (c.prec == OCTEN_FP8E4M3) {
+    const size_t xb = (size_t)t * c.I * c.J;
+    if (!x->grow(x->X8buf, xb) || !x->grow(x->xscale, (size_t)t * sizeof(float)))
+      return x->fail(OCTEN_ENOMEM, "scratch for e4m3 slices");
+    quantize_e4m3(static_cast<const __nv_bfloat16 *>(Xd), t, c.I * c.J,
+                  static_cast<__nv_fp8_e4m3 *>(x->X8buf.p), static_cast<float *>(x->xscale.p),
+                  x->st);
+    m2.X = x->X8buf.p; m2.tx = Elem::E4M3; m2.slice_scale = static_cast<float *>(x->xscale.p);
+  }
+  mode2_simt(m2, x->st);
+  Mode1Args m1{};
+  m1.Ut = x->Ut_rep; m1.T = x->Tbuf.p; m1.te = x->tmid; m1.T2 = static_cast<float *>(x->T2buf.p);
+  m1.t = t; m1.I = c.I; m1.P = c.P; m1.Q = c.Q;
+  mode1_simt(m1, x->st);
+  mode3_accumulate(static_cast<float *>(x->T2buf.p), Wd, Yacc, t, c.P, c.Q, c.S, x->Qd, x->st);
+  return OCTEN_OK;
+}
+
+octen_status compress_all(octen_ctx *x, const void *Xd, int64_t t, const float *Wd, float *Yacc) {
+  const size_t slice = (size_t)x->cfg.I * x->cfg.J * elem_size(x->xin);
+  for (int64_t k0 = 0; k0 < t; k0 += kChunk) {
+    const int64_t n = t - k0 < kChunk ? t - k0 : kChunk;
+    octen_status s = compress_chunk(x, static_cast<const char *>(Xd) + k0 * slice, n,
+                                    Wd + k0 * x->Qd, Yacc);
+    if (s != OCTEN_OK) return s;
+  }
+  return OCTEN_OK;
+}
+
+// Lift operator of one mode (Eq. 7 with P^-1 the pseudo-inverse).  With
+// Qd > rows the stack has full column rank: L = (U Omega U^T)^-1 U, shape
+// rows x Qd (Omega weights the anchor columns by P).  Otherwise the distinct
+// rows have full row rank: L = U (U^T U)^-1, stored transposed (Qd x rows).
+octen_status build_lift(octen_ctx *x, const float *Ur, int64_t rows, float *L, int &over) {
+  const int Qd = x->Qd;
+  over = Qd > rows ? 1 : 0;
+  const int n = over ? (int)rows : Qd;
+  float *Gm = nullptr;
+  if (cudaMalloc(&Gm, (size_t)n * n * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return x->fail(OCTEN_ENOMEM, "lift Gram (%d x %d)", n, n);
+  }
+  float *Uw = nullptr;
+  GemmArgs g{};
+  g.ta = Elem::F32; g.tb = Elem::F32; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
+  g.D = Gm; g.sDm = n; g.sDn = 1; g.M = n; g.N = n;
+  if (over) {
+    if (cudaMalloc(&Uw, (size_t)rows * Qd * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(Gm);
+      return x->fail(OCTEN_ENOMEM, "lift weights");
+    }
+    scale_columns(Ur, rows, Qd, x->cfg.S, (float)x->cfg.P, Uw, x->st);
+    g.A = Ur; g.sAm = Qd; g.sAk = 1;
+    g.B = Uw; g.sBn = Qd; g.sBk = 1;
+    g.K = Qd;
+    gemm_strided(g, x->st);
+    cholesky_f32(Gm, n, x->dstatus, x->st);
+    cudaMemcpyAsync(L, Ur, (size_t)rows * Qd * sizeof(float), cudaMemcpyDeviceToDevice, x->st);
+    chol_solve_f32(Gm, n, L, Qd, x->st);
+  } else {
+    g.A = Ur; g.sAm = 1; g.sAk = Qd;
+    g.B = Ur; g.sBn = 1; g.sBk = Qd;
+    g.K = (int)rows;
+    gemm_strided(g, x->st);
+    cholesky_f32(Gm, n, x->dstatus, x->st);
+    transpose_f32(Ur, rows, Qd, L, x->st);   // L <- U^T (Qd x rows)
+    chol_solve_f32(Gm, n, L, (int)rows, x->st);
+  }
+  octen_status s = x->sync_check("lift operator");
+  cudaFree(Gm);
+  if (Uw) cudaFree(Uw);
+  return s;
+}
+
+// Delta of one global factor: F += Lift * e (Qd x R rhs built from the
+// aligned replica blocks and the projected previous factor PF).
+void lift_mode(octen_ctx *x, const float *Fh, const float *PF, const float *L, int over,
+               int64_t rows, float *F) {
+  const octen_config &c = x->cfg;
+  lift_rhs(Fh, PF, c.P, c.Q, c.S, c.R, x->RT, x->Qd, over, x->e, x->st);
+  GemmArgs g{};
+  g.A = L; g.ta = Elem::F32;
+  if (over) { g.sAm = x->Qd; g.sAk = 1; } else { g.sAm = 1; g.sAk = rows; }
+  g.B = x->e; g.tb = Elem::F32; g.sBn = 1; g.sBk = c.R;
+  g.D = F; g.sDm = c.R; g.sDn = 1;
+  g.M = (int)rows; g.N = c.R; g.K = x->Qd; g.batch = 1; g.alpha = 1.f; g.beta = 1.f;
+  gemm_strided(g, x->st);
+}
+
+// PF = U_all^T F (Qd x R)
+void project(octen_ctx *x, const float *Ur, int64_t rows, const float *F, float *PF) {
+  const octen_config &c = x->cfg;
+  GemmArgs g{};
+  g.A = Ur; g.ta = Elem::F32; g.sAm = 1; g.sAk = x->Qd;
+  g.B = F; g.tb = Elem::F32; g.sBn = 1; g.sBk = c.R;
+  g.D = PF; g.sDm = c.R; g.sDn = 1;
+  g.M = x->Qd; g.N = c.R; g.K = (int)rows; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
+  gemm_strided(g, x->st);
+}
+
+bool ensure_c_capacity(octen_ctx *x, int64_t rows) {
+  if (rows <= x->Kcap) return true;
+  int64_t cap = x->Kcap > 0 ? x->Kcap : 64;
+  while (cap < rows) cap *= 2;
+  float *nc = nullptr;
+  if (cudaMalloc(&nc, (size_t)cap * x->cfg.R * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (x->C) {
+    cudaMemcpyAsync(nc, x->C, (size_t)x->K * x->cfg.R * sizeof(float), cudaMemcpyDeviceToDevice,
+                    x->st);
+    cudaStreamSynchronize(x->st);
+    for (auto &b : x->owned)
+      if (b.p == x->C) { cudaFree(b.p); b.p = nc; b.bytes = (size_t)cap * x->cfg.R * sizeof(float); }
+  } else {
+    x->owned.push_back({nc, (size_t)cap * x->cfg.R * sizeof(float)});
+  }
+  x->C = nc;
+  x->Kcap = cap;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx **out) {
+  if (!out) return OCTEN_EINVAL;
+  std::string why;
+  octen_status s = validate(cfg, why);
+  if (s != OCTEN_OK) {
+    fprintf(stderr, "octen_create: %s\n", why.c_str());
+    return s;
+  }
+  octen_ctx *x = new octen_ctx();
+  x->cfg = *cfg;
+  x->Qd = cfg->S + cfg->P * (cfg->Q - cfg->S);
+  x->RT = round_rt(cfg->R);
+  x->st = static_cast<cudaStream_t>(cuda_stream);
+  set_types(x);
+  const octen_config &c = x->cfg;
+  const size_t P = c.P, Q = c.Q, RT = x->RT, Qd = x->Qd;
+  bool ok = x->alloc(x->U32, (size_t)c.I * Qd) && x->alloc(x->V32, (size_t)c.J * Qd) &&
+            x->alloc(x->La, (size_t)c.I * Qd) && x->alloc(x->Lb, (size_t)c.J * Qd) &&
+            x->alloc(x->Y, P * Q * Q * Q) && x->alloc(x->A, (size_t)c.I * c.R) &&
+            x->alloc(x->B, (size_t)c.J * c.R) && x->alloc(x->G, P * Q * c.R) &&
+            x->alloc(x->PA, Qd * c.R) && x->alloc(x->PB, Qd * c.R) && x->alloc(x->e, Qd * c.R) &&
+            x->alloc(x->At, P * Q * RT) && x->alloc(x->Bt, P * Q * RT) &&
+            x->alloc(x->Ct, P * Q * RT) && x->alloc(x->Ah, P * Q * RT) &&
+            x->alloc(x->Bh, P * Q * RT) && x->alloc(x->Ch, P * Q * RT) &&
+            x->alloc(x->M, P * Q * RT) && x->alloc(x->H, P * Q * Q * RT) &&
+            x->alloc(x->perm, P * c.R) && x->alloc(x->scales, P * 2 * c.R) &&
+            x->alloc(x->dstatus, 1) && x->alloc(x->dfit, 2);
+  void *ut = nullptr, *vt = nullptr;
+  if (ok) {
+    ok = cudaMalloc(&ut, P * Q * c.I * elem_size(x->tu)) == cudaSuccess &&
+         cudaMalloc(&vt, Qd * c.J * elem_size(x->tv)) == cudaSuccess;
+    if (ut) x->owned.push_back({ut, 0});
+    if (vt) x->owned.push_back({vt, 0});
+    x->Ut_rep = ut;
+    x->Vt = vt;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    delete x;
+    return OCTEN_ENOMEM;
+  }
+  cudaMemsetAsync(x->Y, 0, P * Q * Q * Q * sizeof(float), x->st);
+  cudaMemsetAsync(x->G, 0, P * Q * c.R * sizeof(float), x->st);
+  cudaMemsetAsync(x->dstatus, 0, sizeof(int), x->st);
+  if (x->sync_check("create") != OCTEN_OK) {
+    delete x;
+    return OCTEN_ECUDA;
+  }
+  *out = x;
+  return OCTEN_OK;
+}
+
+octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const float *U_all,
+                        const float *V_all, const float *W_old, const float *A0,
+                        const float *B0, const float *C0) {
+  if (!x) return OCTEN_EINVAL;
+  if (x->initialized) return x->fail(OCTEN_ESTATE, "octen_init called twice");
+  if (!X_old || !U_all || !V_all || !W_old || !A0 || !B0 || !C0 || t_old < 1)
+    return x->fail(OCTEN_EINVAL, "octen_init: every array is required and t_old >= 1");
+  const octen_config &c = x->cfg;
+  const int Qd = x->Qd;
+  // projections: round once to the operand formats, build the operand layouts
+  const float *Ud = static_cast<const float *>(x->stage_in(U_all, (size_t)c.I * Qd * 4, 0));
+  if (!Ud) return x->fail(OCTEN_ENOMEM, "staging U");
+  round_copy(Ud, x->U32, (int64_t)c.I * Qd, x->tu, x->st);
+  const float *Vd = static_cast<const float *>(x->stage_in(V_all, (size_t)c.J * Qd * 4, 0));
+  if (!Vd) return x->fail(OCTEN_ENOMEM, "staging V");
+  round_copy(Vd, x->V32, (int64_t)c.J * Qd, x->tv, x->st);
+  make_replica_transpose(x->U32, c.I, c.P, c.Q, c.S, Qd, x->Ut_rep, x->tu, x->st);
+  make_transpose(x->V32, c.J, Qd, x->Vt, x->tv, x->st);
+  octen_status s = x->sync_check("projection setup");
+  if (s != OCTEN_OK) return s;
+  // summaries of the existing tensor, chunk by chunk
+  const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
+  const float *Wd = static_cast<const float *>(x->stage_in(W_old, (size_t)t_old * Qd * 4, 1));
+  if (!Wd) return x->fail(OCTEN_ENOMEM, "staging W_old");
+  if (is_device_ptr(X_old)) {
+    s = compress_all(x, X_old, t_old, Wd, x->Y);
+    if (s != OCTEN_OK) return s;
+  } else {
+    for (int64_t k0 = 0; k0 < t_old; k0 += kChunk) {
+      const int64_t n = t_old - k0 < kChunk ? t_old - k0 : kChunk;
+      const void *Xd = x->stage_in(static_cast<const char *>(X_old) + k0 * slice, n * slice, 2);
+      if (!Xd) return x->fail(OCTEN_ENOMEM, "staging X_old");
+      s = compress_chunk(x, Xd, n, Wd + k0 * Qd, x->Y);
+      if (s != OCTEN_OK) return s;
+      cudaStreamSynchronize(x->st);
+    }
+  }
+  // existing factors and G_p = W_old,p^T C_old
+  if (!ensure_c_capacity(x, t_old)) return x->fail(OCTEN_ENOMEM, "C");
+  cudaMemcpyAsync(x->A, A0, (size_t)c.I * c.R * 4, cudaMemcpyDefault, x->st);
+  cudaMemcpyAsync(x->B, B0, (size_t)c.J * c.R * 4, cudaMemcpyDefault, x->st);
+  cudaMemcpyAsync(x->C, C0, (size_t)t_old * c.R * 4, cudaMemcpyDefault, x->st);
+  update_g(Wd, x->C, t_old, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
+  s = x->sync_check("init summaries");
+  if (s != OCTEN_OK) return s;
+  x->K = t_old;
+  s = build_lift(x, x->U32, c.I, x->La, x->a_over);
+  if (s != OCTEN_OK) return s;
+  s = build_lift(x, x->V32, c.J, x->Lb, x->b_over);
+  if (s != OCTEN_OK) return s;
+  x->initialized = true;
+  return OCTEN_OK;
+}
+
+octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
+  if (!x) return OCTEN_EINVAL;
+  if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_append before octen_init");
+  if (!X_new || !W_new || t < 1 || t > kChunk)
+    return x->fail(OCTEN_EINVAL, "octen_append: need X_new, W_new and 1 <= t <= %d", (int)kChunk);
+  const octen_config &c = x->cfg;
+  const int Qd = x->Qd, RT = x->RT;
+  if (!ensure_c_capacity(x, x->K + t)) return x->fail(OCTEN_ENOMEM, "C");
+  const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
+  const void *Xd = x->stage_in(X_new, t * slice, 2);
+  const float *Wd = static_cast<const float *>(x->stage_in(W_new, (size_t)t * Qd * 4, 1));
+  if (!Xd || !Wd) return x->fail(OCTEN_ENOMEM, "staging the batch");
+  // 1. compress the batch and update the summaries
+  octen_status s = compress_chunk(x, Xd, t, Wd, x->Y);
+  if (s != OCTEN_OK) return s;
+  // 2. CP of every summary, warm-started from the projected previous factors
+  project(x, x->U32, c.I, x->A, x->PA);
+  project(x, x->V32, c.J, x->B, x->PB);
+  warm_start(x->PA, c.P, c.Q, c.S, c.R, RT, x->At, x->st);
+  warm_start(x->PB, c.P, c.Q, c.S, c.R, RT, x->Bt, x->st);
+  AlsBuffers ab{x->At, x->Bt, x->Ct, x->M, x->H, x->dstatus};
+  als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st);
+  // 3. anchor match against u^T A_prev, v^T B_prev
+  align_replicas(x->At, x->Bt, x->Ct, x->PA, x->PB, c.P, c.Q, c.S, c.R, RT, x->Ah, x->Bh,
+                 x->Ch, x->perm, x->scales, x->st);
+  // 4. lift A and B, solve the new rows of C, update G_p
+  lift_mode(x, x->Ah, x->PA, x->La, x->a_over, c.I, x->A);
+  lift_mode(x, x->Bh, x->PB, x->Lb, x->b_over, c.J, x->B);
+  const size_t cs = (size_t)Qd * c.R + t * c.R + t * Qd + t * t;
+  if (!x->grow(x->Wbuf, cs * sizeof(float))) return x->fail(OCTEN_ENOMEM, "C solve scratch");
+  float *C_new = x->C + x->K * c.R;
+  solve_c_new(Wd, x->Ch, x->G, t, c.P, c.Q, c.S, Qd, c.R, RT, static_cast<float *>(x->Wbuf.p),
+              C_new, x->dstatus, x->st);
+  update_g(Wd, C_new, t, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
+  s = x->sync_check("append");
+  if (s != OCTEN_OK) return s;
+  x->K += t;
+  return OCTEN_OK;
+}
+
+octen_status octen_get_factors(const octen_ctx *cx, float *A, float *B, float *C,
+                               int64_t *K_out) {
+  octen_ctx *x = const_cast<octen_ctx *>(cx);
+  if (!x) return OCTEN_EINVAL;
+  if (!x->initialized) return x->fail(OCTEN_ESTATE, "no factors before octen_init");
+  const octen_config &c = x->cfg;
+  if (A) cudaMemcpyAsync(A, x->A, (size_t)c.I * c.R * 4, cudaMemcpyDefault, x->st);
+  if (B) cudaMemcpyAsync(B, x->B, (size_t)c.J * c.R * 4, cudaMemcpyDefault, x->st);
+  if (C) cudaMemcpyAsync(C, x->C, (size_t)x->K * c.R * 4, cudaMemcpyDefault, x->st);
+  if (K_out) *K_out = x->K;
+  return x->sync_check("get_factors");
+}
+
+int64_t octen_rows(const octen_ctx *x) { return x ? x->K : 0; }
+
+octen_status octen_fit(octen_ctx *x, const void *X_all, int64_t K, double *fit_out) {
+  if (!x || !X_all || !fit_out) return OCTEN_EINVAL;
+  if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_fit before octen_init");
+  if (K != x->K || K > 65535) return x->fail(OCTEN_EINVAL, "octen_fit: K=%lld, rows=%lld",
+                                             (long long)K, (long long)x->K);
+  const octen_config &c = x->cfg;
+  const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
+  const int64_t np = fit_partial_count(1, c.I, c.J);
+  if (!x->grow(x->fitpart, (size_t)np * K * 2 * sizeof(double)))
+    return x->fail(OCTEN_ENOMEM, "fit scratch");
+  double total0 = 0.0, total1 = 0.0;
+  // slices are streamed in chunks (host inputs are staged chunk by chunk)
+  const int64_t chunk = is_device_ptr(X_all) ? K : 16;
+  for (int64_t k0 = 0; k0 < K; k0 += chunk) {
+    const int64_t n = K - k0 < chunk ? K - k0 : chunk;
+    const void *Xd = x->stage_in(static_cast<const char *>(X_all) + k0 * slice, n * slice, 3);
+    if (!Xd) return x->fail(OCTEN_ENOMEM, "staging X_all");
+    fit_sums(Xd, x->xin, n, c.I, c.J, x->A, x->B, x->C + k0 * c.R, c.R,
+             static_cast<double *>(x->fitpart.p), x->dfit, x->st);
+    double h[2];
+    cudaMemcpyAsync(h, x->dfit, sizeof h, cudaMemcpyDeviceToHost, x->st);
+    octen_status s = x->sync_check("fit");
+    if (s != OCTEN_OK) return s;
+    total0 += h[0];
+    total1 += h[1];
+  }
+  *fit_out = total0 > 0.0 ? 1.0 - sqrt(total1) / sqrt(total0) : 0.0;
+  return OCTEN_OK;
+}
+
+octen_status octen_get_replicas(const octen_ctx *cx, float *Y) {
+  octen_ctx *x = const_cast<octen_ctx *>(cx);
+  if (!x || !Y) return OCTEN_EINVAL;
+  const size_t n = (size_t)x->cfg.P * x->cfg.Q * x->cfg.Q * x->cfg.Q;
+  cudaMemcpyAsync(Y, x->Y, n * 4, cudaMemcpyDefault, x->st);
+  return x->sync_check("get_replicas");
+}
+
+octen_status octen_get_replica_factors(const octen_ctx *cx, int which, float *At, float *Bt,
+                                       float *Ct, int32_t *perm, double *scales) {
+  octen_ctx *x = const_cast<octen_ctx *>(cx);
+  if (!x || (which != 0 && which != 1)) return OCTEN_EINVAL;
+  const octen_config &c = x->cfg;
+  const float *src[3] = {which ? x->Ah : x->At, which ? x->Bh : x->Bt, which ? x->Ch : x->Ct};
+  float *dst[3] = {At, Bt, Ct};
+  for (int i = 0; i < 3; ++i) {
+    if (!dst[i]) continue;
+    cudaMemcpy2DAsync(dst[i], c.R * 4, src[i], x->RT * 4, c.R * 4, (size_t)c.P * c.Q,
+                      cudaMemcpyDefault, x->st);
+  }
+  if (perm) cudaMemcpyAsync(perm, x->perm, (size_t)c.P * c.R * 4, cudaMemcpyDefault, x->st);
+  if (scales)
+    cudaMemcpyAsync(scales, x->scales, (size_t)c.P * 2 * c.R * 8, cudaMemcpyDefault, x->st);
+  return x->sync_check("get_replica_factors");
+}
+
+octen_status octen_compress(const octen_config *cfg, void *cuda_stream, const void *X, int64_t t,
+                            const float *U_all, const float *V_all, const float *W_all,
+                            float *Z) {
+  std::string why;
+  if (validate(cfg, why) != OCTEN_OK || !X || !U_all || !V_all || !W_all || !Z || t < 1)
+    return OCTEN_EINVAL;
+  // a light context: projections, scratch and a summary buffer only
+  octen_ctx x;
+  x.cfg = *cfg;
+  x.Qd = cfg->S + cfg->P * (cfg->Q - cfg->S);
+  x.RT = round_rt(cfg->R);
+  x.st = static_cast<cudaStream_t>(cuda_stream);
+  set_types(&x);
+  const octen_config &c = x.cfg;
+  const size_t Qd = x.Qd, nz = (size_t)c.P * c.Q * c.Q * c.Q;
+  float *Zd = nullptr;
+  bool ok = x.alloc(x.U32, (size_t)c.I * Qd) && x.alloc(x.V32, (size_t)c.J * Qd) &&
+            x.alloc(x.dstatus, 1) && x.alloc(Zd, nz);
+  void *ut = nullptr, *vt = nullptr;
+  if (ok) {
+    ok = cudaMalloc(&ut, (size_t)c.P * c.Q * c.I * elem_size(x.tu)) == cudaSuccess &&
+         cudaMalloc(&vt, Qd * c.J * elem_size(x.tv)) == cudaSuccess;
+    if (ut) x.owned.push_back({ut, 0});
+    if (vt) x.owned.push_back({vt, 0});
+  }
+  if (!ok) { cudaGetLastError(); return OCTEN_ENOMEM; }
+  x.Ut_rep = ut;
+  x.Vt = vt;
+  cudaMemsetAsync(x.dstatus, 0, sizeof(int), x.st);
+  cudaMemsetAsync(Zd, 0, nz * 4, x.st);
+  const float *Ud = static_cast<const float *>(x.stage_in(U_all, (size_t)c.I * Qd * 4, 0));
+  if (!Ud) return OCTEN_ENOMEM;
+  round_copy(Ud, x.U32, (int64_t)c.I * Qd, x.tu, x.st);
+  const float *Vd = static_cast<const float *>(x.stage_in(V_all, (size_t)c.J * Qd * 4, 1));
+  if (!Vd) return OCTEN_ENOMEM;
+  round_copy(Vd, x.V32, (int64_t)c.J * Qd, x.tv, x.st);
+  make_replica_transpose(x.U32, c.I, c.P, c.Q, c.S, x.Qd, x.Ut_rep, x.tu, x.st);
+  make_transpose(x.V32, c.J, x.Qd, x.Vt, x.tv, x.st);
+  if (x.sync_check("compress setup") != OCTEN_OK) return OCTEN_ECUDA;
+  const float *Wd = static_cast<const float *>(x.stage_in(W_all, (size_t)t * Qd * 4, 3));
+  if (!Wd) return OCTEN_ENOMEM;
+  const size_t slice = (size_t)c.I * c.J * elem_size(x.xin);
+  octen_status s = OCTEN_OK;
+  if (is_device_ptr(X)) {
+    s = compress_all(&x, X, t, Wd, Zd);
+  } else {
+    for (int64_t k0 = 0; k0 < t && s == OCTEN_OK; k0 += kChunk) {
+      const int64_t n = t - k0 < kChunk ? t - k0 : kChunk;
+      const void *Xd = x.stage_in(static_cast<const char *>(X) + k0 * slice, n * slice, 2);
+      if (!Xd) return OCTEN_ENOMEM;
+      s = compress_chunk(&x, Xd, n, Wd + k0 * Qd, Zd);
+      cudaStreamSynchronize(x.st);
+    }
+  }
+  if (s != OCTEN_OK) return s;
+  cudaMemcpyAsync(Z, Zd, nz * 4, cudaMemcpyDefault, x.st);
+  return x.sync_check("compress");
+}
+
+void octen_destroy(octen_ctx *x) { delete x; }
+
+const char *octen_last_error(const octen_ctx *x) {
+  return x ? x->err.c_str() : "no context";
+}
+
+const char *octen_status_name(octen_status s) {
+  switch (s) {
+    case OCTEN_OK: return "OCTEN_OK";
+    case OCTEN_EINVAL: return "OCTEN_EINVAL";
+    case OCTEN_ENOMEM: return "OCTEN_ENOMEM";
+    case OCTEN_ECUDA: return "OCTEN_ECUDA";
+    case OCTEN_ETIMEOUT: return "OCTEN_ETIMEOUT";
+    case OCTEN_ENUMERIC: return "OCTEN_ENUMERIC";
+    case OCTEN_ESTATE: return "OCTEN_ESTATE";
+  }
+  return "OCTEN_UNKNOWN";
+}
+
+uint64_t octen_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

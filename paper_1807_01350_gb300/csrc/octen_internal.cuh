@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of the CUDA library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/octen.h"
+
+namespace octen {
+
+// Bit flags a kernel may raise in the context's device status word.
+enum DevFlag : int {
+  kDevCholesky = 1,   // a Cholesky pivot stayed non-positive after loading
+  kDevTimeout = 2,    // a bounded wait ran out
+};
+
+// Element types of the slice batch and of the contraction operands.
+enum class Elem : int { F32 = 0, BF16 = 1, E4M3 = 2 };
+
+inline size_t elem_size(Elem e) { return e == Elem::F32 ? 4 : (e == Elem::BF16 ? 2 : 1); }
+
+// Counts every kernel launch issued through the launch helpers below.
+void count_launch();
+
+// ---------------------------------------------------------------------------
+// Generic strided batched fp32-accumulate GEMM (SIMT FFMA):
+//   D[z](m, n) = alpha * sum_k A[z](m, k) * B[z](n, k) + beta * D[z](m, n)
+// with A(m, k) = A[z * sAz + m * sAm + k * sAk], and likewise for B and D.
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+  const void *A; Elem ta; int64_t sAz, sAm, sAk;
+  const void *B; Elem tb; int64_t sBz, sBn, sBk;
+  float *D; int64_t sDz, sDm, sDn;
+  int M, N, K, batch;
+  float alpha, beta;
+};
+void gemm_strided(const GemmArgs &g, cudaStream_t st);
+
+// Mode-2 contraction of the compression: T_rep[k][p][b][i] =
+//   sum_j X[k][i][j] * V_all[j][col_p(b)] for every replica p,
+// with Vt the transposed projection (Qd x J) in the operand type and T_rep in
+// `tt` (fp32 or bf16).  X element type `tx`, optional per-slice scales.
+struct Mode2Args {
+  const void *X; Elem tx;
+  const void *Vt; Elem tv;
+  const float *slice_scale;  // nullable: per-slice multiplier (fp8 path)
+  void *T; Elem tt;
+  int64_t t, I, J;
+  int P, Q, S, Qd;
+};
+void mode2_simt(const Mode2Args &a, cudaStream_t st);
+
+// Mode-1 contraction: T2[p][k][a][b] = sum_i Ut_rep[p][a][i] * T_rep[k][p][b][i].
+struct Mode1Args {
+  const void *Ut; const void *T; Elem te;
+  float *T2;
+  int64_t t, I;
+  int P, Q;
+};
+void mode1_simt(const Mode1Args &a, cudaStream_t st);
+
+// Mode-3 contraction and summary update: Y[p][a][b][c] +=
+//   sum_k T2[p][k][a][b] * W_all[k][col_p(c)].
+void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
+                      int S, int Qd, cudaStream_t st);
+
+// Layout / precision conversions of the projections.
+void make_replica_transpose(const float *M_all, int64_t rows, int P, int Q, int S, int Qd,
+                            void *out, Elem te, cudaStream_t st);   // [p][q][row]
+void make_transpose(const float *M_all, int64_t rows, int Qd, void *out, Elem te,
+                    cudaStream_t st);                                 // [c][row]
+void round_copy(const float *in, float *out, int64_t n, Elem te, cudaStream_t st);
+void convert_slices(const void *in, Elem tin, void *out, Elem tout, int64_t n,
+                    cudaStream_t st);
+void quantize_e4m3(const __nv_bfloat16 *X, int64_t t, int64_t IJ, __nv_fp8_e4m3 *X8,
+                   float *scale, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Replica CP-ALS (all P replicas in each launch).  Factors are P x Q x RT
+// (RT = R rounded up to 8, padded columns zero).
+// ---------------------------------------------------------------------------
+struct AlsBuffers {
+  float *Af, *Bf, *Cf;   // current factors
+  float *M;              // MTTKRP result
+  float *H;              // P x Q x Q x RT: H[a][c][r] = sum_b X[a][b][c] B[b][r]
+  int *status;
+};
+void als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
+             cudaStream_t st);
+
+// Warm start: F_p = unit columns of rows(p) of PF (Qd x R) into P x Q x RT.
+void warm_start(const float *PF, int P, int Q, int S, int R, int RT, float *F,
+                cudaStream_t st);
+
+// Anchor match (FP64).  ref rows = PA/PB rows [0, S).
+void align_replicas(const float *At, const float *Bt, const float *Ct, const float *PA,
+                    const float *PB, int P, int Q, int S, int R, int RT, float *Ah,
+                    float *Bh, float *Ch, int *perm, double *scales, cudaStream_t st);
+
+// e (Qd x R) for the lift: shared rows summed (sum_mode=1) or averaged.
+void lift_rhs(const float *Fh, const float *PF, int P, int Q, int S, int R, int RT, int Qd,
+              int sum_mode, float *e, cudaStream_t st);
+
+// C_new (t x R) from the stacked W_new,p^T system and G update.
+// scratch: Qd*R + t*R + t*Qd + t*t floats.
+void solve_c_new(const float *W, const float *Ch, const float *G, int64_t t, int P, int Q,
+                 int S, int Qd, int R, int RT, float *scratch, float *C_new, int *status,
+                 cudaStream_t st);
+void update_g(const float *W, const float *C_new, int64_t t, int P, int Q, int S, int Qd,
+              int R, float *G, cudaStream_t st);
+
+// Dense fp32 SPD factor / solve (init-time lift operators).
+void cholesky_f32(float *Gm, int n, int *status, cudaStream_t st);
+void chol_solve_f32(const float *L, int n, float *Bm, int m, cudaStream_t st);
+void scale_columns(const float *in, int64_t rows, int cols, int S, float w_shared,
+                   float *out, cudaStream_t st);
+void transpose_f32(const float *in, int64_t rows, int64_t cols, float *out, cudaStream_t st);
+
+// Fit: sums of ||X_k||^2 and ||X_k - A diag(C[k]) B^T||^2 over all slices,
+// written to out[0], out[1] (fp64).  partial: ceil(J/256)*ceil(I/32)*K*2 doubles.
+void fit_sums(const void *X, Elem tx, int64_t K, int64_t I, int64_t J, const float *A,
+              const float *B, const float *C, int R, double *partial, double *out,
+              cudaStream_t st);
+int64_t fit_partial_count(int64_t K, int64_t I, int64_t J);
+
+}  // namespace octen
+
+#define OCTEN_CUDA_TRY(expr)                                                         \
+  do {                                                                               \
+    cudaError_t _e = (expr);                                                         \
+    if (_e != cudaSuccess) {                                                         \
+      fprintf(stderr, "octen: %s failed: %s (%s:%d)\n", #expr, cudaGetErrorString(_e), \
+              __FILE__, __LINE__);                                                   \
+    }                                                                                \
+  } while (0)

@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, stage by stage (summaries, raw replica CP, anchor match,
+lifted factors, fit).
+
+Tolerances.  FP32: summaries within 1e-5 relative Frobenius error per
+replica (fp32 FFMA accumulation over J and I terms); replica factors and the
+lifted factors within 1e-3 (the lift operators are fp32 Cholesky solves whose
+error grows with cond(U^T U)); fit within 1e-4; factor-match
+score against the oracle's factors >= 0.999.  BF16: the mode-2 product is
+rounded to bf16 before the mode-1 contraction, a relative error of about
+2^-9 / sqrt(3) ~ 1.1e-3 per element that the two later contractions average but
+do not remove: summaries within 5e-3.  FP8: per-slice e4m3 quantisation of
+the slices (unit roundoff 2^-4): summaries within 6e-2.  For both reduced
+paths the fit stays within 1e-3 of the oracle's and the factor-match score
+>= 0.99.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests._cases import Case, rel
+from tests._metrics import fms
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1807_01350_gb300 as p
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    p.lib()
+    return p
+
+
+def dev(a, dtype=None):
+    t = torch.as_tensor(np.asarray(a, np.float32), device="cuda")
+    return t if dtype is None else t.to(dtype)
+
+
+def slices(a, prec):
+    return dev(a, torch.float32 if prec == "fp32" else torch.bfloat16)
+
+
+def run_gpu(pkg, case, d, upto=None):
+    g = pkg.Octen(case.I, case.J, case.R, case.P, case.Q, case.S, case.iters, case.prec)
+    g.init(slices(d["X"][:case.t_old], case.prec), dev(d["U"]), dev(d["V"]), dev(d["W"][0]),
+           dev(d["A0"]), dev(d["B0"]), dev(d["C0"]))
+    k = case.t_old
+    out = []
+    for b, t in enumerate(case.batches[:upto]):
+        g.append(slices(d["X"][k:k + t], case.prec), dev(d["W"][b + 1]))
+        k += t
+        A, B, C = g.factors()
+        out.append(dict(Y=g.replicas(), A=A, B=B, C=C, raw=g.replica_factors(0),
+                        hat=g.replica_factors(1),
+                        fit=g.fit(slices(d["X"][:k], case.prec))))
+    return g, out
+
+
+TOL = {"fp32": dict(Y=1e-5, F=1e-3, fit=1e-4, fms=0.999),
+       "bf16": dict(Y=5e-3, F=5e-2, fit=1e-3, fms=0.99),
+       "fp8": dict(Y=6e-2, F=2e-1, fit=1e-3, fms=0.99)}
+
+
+def check_update(case, d, gpu_states, ref_states):
+    tol = TOL[case.prec]
+    k = case.t_old
+    for b, (gs, rs) in enumerate(zip(gpu_states, ref_states)):
+        k += case.batches[b]
+        for p in range(case.P):
+            assert rel(gs["Y"][p], rs["Y"][p]) < tol["Y"], ("Y", b, p, rel(gs["Y"][p], rs["Y"][p]))
+        At, Bt, Ct, perm, scales = gs["raw"]
+        for p in range(case.P):
+            ra, rb, rc = rs["raw"][p]
+            for name, x, y in (("At", At[p], ra), ("Bt", Bt[p], rb), ("Ct", Ct[p], rc)):
+                assert rel(x, y) < tol["F"], (name, b, p, rel(x, y))
+        Ah, Bh, Ch, perm, scales = gs["hat"]
+        for p in range(case.P):
+            assert np.array_equal(perm[p], rs["hat"][p][3]), ("perm", b, p)
+        for name in ("A", "B", "C"):
+            assert rel(gs[name], rs[name]) < tol["F"], (name, b, rel(gs[name], rs[name]))
+        f_ref = oracle.fit(d["X"][:k], rs["A"], rs["B"], rs["C"])
+        assert abs(gs["fit"] - f_ref) < tol["fit"], ("fit", b, gs["fit"], f_ref)
+        assert fms((gs["A"], gs["B"], gs["C"]), (rs["A"], rs["B"], rs["C"])) > tol["fms"]
+
+
+CASES_FP32 = {
+    # the small dense workload: 100^3, rank 5, 80 old slices + 20 new, P=4, Q=20, S=5
+    "c1": Case(100, 100, 5, 4, 20, 5, 80, (20,), 50),
+    # ragged shapes (partial 64/128 tiles, R padded 7 -> 8), two batches
+    "ragged": Case(130, 70, 7, 3, 17, 4, 9, (9, 5), 20, seed=3),
+    # Qd = 52 > I = 40 and > J = 50: full-column-rank lift for both modes
+    "overdetermined": Case(40, 50, 4, 6, 12, 4, 20, (8,), 25, seed=4),
+    # one new slice per batch, R = 1
+    "single_slice_rank1": Case(30, 33, 1, 2, 6, 2, 10, (1, 1), 15, seed=5),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES_FP32))
+def test_update_parity_fp32(pkg, name):
+    case = CASES_FP32[name]
+    d = case.make()
+    _, ref = case.oracle_run(d)
+    g, gpu = run_gpu(pkg, case, d)
+    g.close()
+    check_update(case, d, gpu, ref)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_update_parity_reduced_precision(pkg, prec):
+    case = Case(100, 100, 5, 4, 20, 5, 80, (20,), 50, prec=prec, seed=7)
+    d = case.make()
+    _, ref = case.oracle_run(d)
+    g, gpu = run_gpu(pkg, case, d)
+    g.close()
+    check_update(case, d, gpu, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_stateless_compression_parity(pkg, prec):
+    I, J, P, Q, S, t = 150, 130, 3, 24, 4, 7
+    case = Case(I, J, 4, P, Q, S, t, (), 1, prec=prec, seed=11)
+    d = case.make()
+    Z = pkg.compress(I, J, P, Q, S, slices(d["X"], prec), dev(d["U"]), dev(d["V"]),
+                     dev(d["W"][0]), prec=prec)
+    for p in range(P):
+        ref = oracle.compress(d["X"], oracle.replica_block(d["U"], p, Q, S),
+                              oracle.replica_block(d["V"], p, Q, S),
+                              oracle.replica_block(d["W"][0], p, Q, S))
+        assert rel(Z[p], ref) < TOL[prec]["Y"], (p, rel(Z[p], ref))
+
+
+def test_host_inputs_give_the_device_result(pkg):
+    """The end-to-end path (host buffers copied by the library) is bitwise the
+    device path."""
+    case = CASES_FP32["ragged"]
+    d = case.make()
+    g1, out1 = run_gpu(pkg, case, d, upto=1)
+    g2 = pkg.Octen(case.I, case.J, case.R, case.P, case.Q, case.S, case.iters, case.prec)
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    g2.init(f32(d["X"][:case.t_old]), f32(d["U"]), f32(d["V"]), f32(d["W"][0]), f32(d["A0"]),
+            f32(d["B0"]), f32(d["C0"]))
+    t = case.batches[0]
+    g2.append(f32(d["X"][case.t_old:case.t_old + t]), f32(d["W"][1]))
+    A2, B2, C2 = g2.factors()
+    assert np.array_equal(A2, out1[0]["A"]) and np.array_equal(B2, out1[0]["B"])
+    assert np.array_equal(C2, out1[0]["C"])
+    g1.close()
+    g2.close()
+
+
+def test_fit_of_given_factors(pkg):
+    case = Case(64, 48, 3, 2, 8, 2, 12, (), 1, seed=9)
+    d = case.make()
+    g = pkg.Octen(case.I, case.J, case.R, case.P, case.Q, case.S, 1)
+    g.init(dev(d["X"][:12]), dev(d["U"]), dev(d["V"]), dev(d["W"][0]), dev(d["A0"]),
+           dev(d["B0"]), dev(d["C0"]))
+    f = g.fit(dev(d["X"][:12]))
+    g.close()
+    assert abs(f - oracle.fit(d["X"][:12], d["A0"], d["B0"], d["C0"])) < 1e-6
+
+
+def test_call_order_and_argument_errors(pkg):
+    g = pkg.Octen(20, 20, 2, 2, 6, 2, 3)
+    x = torch.zeros((2, 20, 20), device="cuda")
+    w = torch.zeros((2, 10), device="cuda")
+    with pytest.raises(pkg.OctenError) as e:
+        g.append(x, w)
+    assert e.value.status == 6          # ESTATE: append before init
+    with pytest.raises(pkg.OctenError) as e:
+        g.append_ptr(0, 1, 0)
+    assert e.value.status in (1, 6)
+    g.close()
