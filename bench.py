@@ -1,0 +1,455 @@
+#!/usr/bin/env python3
+"""Throughput of the OCTen online CP update on GB300: new slices per second.
+
+One step = one `octen_append` of a batch of new slices (compression into the
+P replicas, CP-ALS of every replica, anchor match, lift of A, B and the new
+rows of C), with the batch already resident in HBM.  The default workload is
+the 4000 x 4000-slice stream (rank 32, P = 16 replicas of 256^3, anchors
+S = 32, batches of 16 slices, 64 existing slices, 30 CP-ALS sweeps); the
+headline precision is bf16 (the precision whose fit stays within 1e-3 of the
+FP64 oracle), with fp32 and fp8 runs of the same stream reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own independent stream (weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and
+the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from synth import WORKLOADS, factors, init_factors, projections, slice_batch  # noqa: E402
+from synth import slice_batch_torch, time_projection  # noqa: E402
+
+METRIC = "new slices/sec (compress+CP update) at fit >= oracle-1e-3; BF16/FP8 vs FP32"
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max clock
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                    src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# ---------------------------------------------------------------------------
+# one stream on the GPU
+# ---------------------------------------------------------------------------
+def stream_inputs(wl, prec, seed, nbatch, device):
+    import torch
+
+    K = wl.t_old + nbatch * wl.batch
+    A, B, C = factors(wl.I, wl.J, K, wl.R, seed, cond=wl.cond, big_frac=wl.big_frac)
+    U, V = projections(wl.I, wl.J, wl.P, wl.Q, wl.S, seed, prec)
+    W = [time_projection(wl.t_old, wl.P, wl.Q, wl.S, seed, -1)]
+    W += [time_projection(wl.batch, wl.P, wl.Q, wl.S, seed, b) for b in range(nbatch)]
+    A0, B0, C0 = init_factors(A, B, C[:wl.t_old], 0.01, seed)
+    dt = torch.float32 if prec == "fp32" else torch.bfloat16
+    X = slice_batch_torch(A, B, C, 0, K, wl.noise, seed, device, dt)   # K x I x J in HBM
+    f32 = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=device)
+    return dict(X=X, U=f32(U), V=f32(V), W=[f32(w) for w in W], A0=f32(A0), B0=f32(B0),
+                C0=f32(C0))
+
+
+def stage_work(wl, prec):
+    """Algorithmic work per launch of each timed stage: (flops, bytes)."""
+    t, I, J, P, Q, R, Qd = wl.batch, wl.I, wl.J, wl.P, wl.Q, wl.R, wl.Qd
+    xb = 4 if prec == "fp32" else (1 if prec == "fp8" else 2)
+    return {
+        "mode2": (2.0 * t * I * J * Qd, t * I * J * xb + Qd * J * xb + t * I * P * Q * (4 if prec == "fp32" else 2)),
+        "mode1": (2.0 * t * P * Q * Q * I, t * P * Q * I * (4 if prec == "fp32" else 2) + P * Q * I * (4 if prec == "fp32" else 2)),
+        "mode3": (2.0 * t * P * Q ** 3, 2.0 * 4 * P * Q ** 3 + 4.0 * t * P * Q * Q),
+        "als_pass": (2.0 * P * Q ** 3 * R, 4.0 * P * Q ** 3),
+    }
+
+
+def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic):
+    flops, nbytes = stage_work(wl, prec)[stage]
+    sec = ms_per_launch / 1e3
+    if stage == "mode3":
+        bound, peak, unit, achieved = "hbm", pk["hbm"], "GB/s", nbytes / sec / 1e9
+    elif stage in ("mode2", "mode1") and prec in ("bf16", "fp8") and _tensor_core_path(stage):
+        peak = pk["bf16_sus"] * (2.0 if prec == "fp8" and stage == "mode2" else 1.0)
+        bound, unit, achieved = "tensor", "TFLOP/s", flops / sec / 1e12
+    else:
+        bound, peak, unit, achieved = "alu", FP32_ALU_TFLOPS, "TFLOP/s", flops / sec / 1e12
+    return {"kernel": stage, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1),
+            "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": pk["src"] if bound != "alu" else
+            "derived: 152 SMs x 128 fp32 lanes x 2 flop x 2070 MHz",
+            "ms_per_launch": round(ms_per_launch, 4)}
+
+
+def _tensor_core_path(stage):
+    import paper_1807_01350_gb300 as pkg
+    return bool(getattr(pkg, "TENSOR_CORE_STAGES", ())) and stage in pkg.TENSOR_CORE_STAGES
+
+
+def traffic_from_profiles(stage, prec):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        v = d.get(f"{stage}:{prec}")
+        return None if v is None else v.get("bytes_per_launch")
+    except Exception:
+        return None
+
+
+def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
+    import torch
+
+    import paper_1807_01350_gb300 as pkg
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nb = warmup + steps + (steps if time_e2e else 0)
+    d = stream_inputs(wl, prec, args.seed + 1000 * rank, nb, dev)
+    stream = torch.cuda.current_stream()
+    g = pkg.Octen(wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.als_iters, prec, stream=stream)
+    t_old, t = wl.t_old, wl.batch
+    g.init(d["X"][:t_old], d["U"], d["V"], d["W"][0], d["A0"], d["B0"], d["C0"])
+    k = t_old
+    for b in range(warmup):
+        g.append(d["X"][k:k + t], d["W"][1 + b])
+        k += t
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    g.reset_stage_times()
+    g.set_timing(True)
+    launches0 = pkg.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for s in range(steps):
+            g.append(d["X"][k:k + t], d["W"][1 + warmup + s])
+            k += t
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    g.set_timing(False)
+    launches = pkg.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+        torch.distributed.barrier()
+    stages = g.stage_times()
+    fit = g.fit(d["X"][:k])
+    out = dict(ms=ms, steps=steps, slices=steps * t, stages=stages, fit=fit,
+               launches=launches, clocks=clk.summary())
+    if time_e2e:
+        out["e2e"] = run_e2e(g, d, wl, prec, k, steps, warmup, rank, world)
+    g.close()
+    del d
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_e2e(g, d, wl, prec, k, steps, warmup, rank, world):
+    """Same appends through the public API with pinned HOST buffers: the
+    library copies each batch to the device and the factors come back."""
+    import torch
+
+    t = wl.batch
+    hostX = [d["X"][k + i * t:k + (i + 1) * t].to("cpu").pin_memory() for i in range(2)]
+    hostW = [d["W"][1 + warmup + i].to("cpu").pin_memory() for i in range(steps)]
+    K_end = k + steps * t
+    Ah = torch.empty((wl.I, wl.R), dtype=torch.float32).pin_memory()
+    Bh = torch.empty((wl.J, wl.R), dtype=torch.float32).pin_memory()
+    Ch = torch.empty((K_end, wl.R), dtype=torch.float32).pin_memory()
+    xb = hostX[0].numel() * hostX[0].element_size()
+    wb = hostW[0].numel() * 4
+    d2h = 0
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        g.append_ptr(hostX[s % 2].data_ptr(), t, hostW[s].data_ptr())
+        kk = g.factors_into(Ah, Bh, Ch)
+        d2h += (wl.I + wl.J + kk) * wl.R * 4
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([sec], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        sec = float(tt.item())
+    return {"value": round(world * steps * t / sec, 3), "unit": "slices/s",
+            "h2d_bytes_per_step": int(xb + wb), "d2h_bytes_per_step": int(d2h / steps),
+            "ms_per_step": round(1e3 * sec / steps, 3)}
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+class OracleSampler:
+    """The FP64 oracle on a bounded sample of one append of the workload.
+
+    Setup (untimed): the workload's factors, projections and a batch of new
+    slices, and the oracle's state from one existing slice.  Timed pieces:
+    `replica(p)` = compression of the batch into replica p + its CP-ALS +
+    anchor match; `lift()` = the lift of A and B and the solve of the new rows
+    of C.  One append costs P replica pieces plus one lift."""
+
+    def __init__(self, wl, seed=0):
+        import oracle
+
+        self.o_mod = oracle
+        self.wl = wl
+        I, J, R, P, Q, S, t = wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.batch
+        A, B, C = factors(I, J, 1 + t, R, seed, cond=wl.cond, big_frac=wl.big_frac)
+        self.X = slice_batch(A, B, C, 0, 1 + t, wl.noise, seed)
+        U, V = projections(I, J, P, Q, S, seed, wl.prec)
+        Wo = time_projection(1, P, Q, S, seed, -1)
+        Wn = time_projection(t, P, Q, S, seed, 0)
+        A0, B0, C0 = init_factors(A, B, C[:1], 0.01, seed)
+        self.o = oracle.OctenOracle(I, J, R, P, Q, S, wl.als_iters)
+        self.o.init(self.X[:1], U, V, Wo, A0, B0, C0)
+        self.Wp = [oracle.replica_block(Wn, p, Q, S) for p in range(P)]
+        self.ref_a = (self.o.U[0].T @ self.o.A)[:S]
+        self.ref_b = (self.o.V[0].T @ self.o.B)[:S]
+        self.hats = {}
+
+    def replica(self, p):
+        o, O, wl = self.o, self.o_mod, self.wl
+        t0 = time.perf_counter()
+        Yp = o.Y[p] + O.compress(self.X[1:], o.U[p], o.V[p], self.Wp[p])
+        At, Bt, Ct = O.cp_als(Yp, o.U[p].T @ o.A, o.V[p].T @ o.B, wl.als_iters)
+        self.hats[p] = O.align(At, Bt, Ct, self.ref_a, self.ref_b, wl.S)
+        return time.perf_counter() - t0
+
+    def lift(self):
+        o, O, P = self.o, self.o_mod, self.wl.P
+        if not self.hats:
+            self.replica(0)
+        hats = [self.hats.get(p, next(iter(self.hats.values()))) for p in range(P)]
+        t0 = time.perf_counter()
+        O.lift_factor(o.A, o.U, [h[0] for h in hats])
+        O.lift_factor(o.B, o.V, [h[1] for h in hats])
+        O.lift_C(self.Wp, [h[2] for h in hats], o.G)
+        return time.perf_counter() - t0
+
+    def describe(self, n_rep, t_rep, t_lift):
+        wl = self.wl
+        return (f"one append of {wl.batch} slices at {wl.name}: compression + CP-ALS + anchor "
+                f"match timed on {n_rep} of {wl.P} replicas ({t_rep:.2f} s each) and scaled to "
+                f"{wl.P}, plus the full lift of A, B and the new C rows ({t_lift:.2f} s)")
+
+
+def cpu_cores():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--beside", default="fp32,fp8", help="other precisions timed beside")
+    ap.add_argument("--beside-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        return main_reference(args, wl, world, rank)
+
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1807_01350_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_1807_01350_gb300  # noqa: F401  (fails loudly without the CUDA library)
+
+    main_run = run_stream(args, wl, args.prec, args.steps, args.warmup, rank, world,
+                          time_e2e=not args.no_e2e)
+    beside = {}
+    for prec in [p for p in args.beside.split(",") if p and p != args.prec]:
+        r = run_stream(args, wl, prec, args.beside_steps, 3, rank, world, time_e2e=False)
+        beside[prec] = {"value": round(world * r["slices"] / (r["ms"] / 1e3), 3),
+                        "ms_per_step": round(r["ms"] / r["steps"], 3), "fit": round(r["fit"], 6),
+                        "steps": r["steps"],
+                        "stage_ms_per_step": {k: round(v[0] / r["steps"], 3)
+                                              for k, v in r["stages"].items() if v[1]}}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return
+
+    pk = peaks()
+    st = main_run["stages"]
+    timed = {k: v for k, v in st.items() if v[1] > 0}
+    dominant = max(("mode2", "mode1", "mode3", "als_pass"), key=lambda s: st[s][0])
+    ms_launch = st[dominant][0] / st[dominant][1]
+    roof = roofline_for(dominant, ms_launch, wl, args.prec, pk,
+                        traffic_from_profiles(dominant, args.prec))
+    comp = {s: roofline_for(s, st[s][0] / st[s][1], wl, args.prec, pk,
+                            traffic_from_profiles(s, args.prec))
+            for s in ("mode2", "mode1", "mode3", "als_pass") if st[s][1]}
+    value = world * main_run["slices"] / (main_run["ms"] / 1e3)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "slices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(main_run["ms"] / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+        "data": "synthetic planted-CP slices (seeded), resident in HBM",
+        "config": {"workload": wl.name, "I": wl.I, "J": wl.J, "R": wl.R, "P": wl.P, "Q": wl.Q,
+                   "S": wl.S, "batch_slices": wl.batch, "existing_slices": wl.t_old,
+                   "als_iters": wl.als_iters, "noise": wl.noise,
+                   "l2": "inputs larger than L2 (each batch is a fresh "
+                         f"{wl.batch * wl.I * wl.J * (4 if args.prec == 'fp32' else 2) / 2**20:.0f} MiB)",
+                   "parallelism": f"independent stream per GPU x{world}"},
+        "fit": round(main_run["fit"], 6),
+        "clocks": main_run["clocks"],
+        "gpu_launches": main_run["launches"],
+        "roofline": roof,
+        "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in timed.items()},
+        "stage_roofline": comp,
+        "beside": beside,
+    }
+    if "e2e" in main_run:
+        line["e2e"] = main_run["e2e"]
+    if world == 1 and not args.no_cpu_baseline:
+        smp = OracleSampler(wl, args.seed)
+        t_rep = smp.replica(0)
+        t_lift = smp.lift()
+        sec = wl.P * t_rep + t_lift
+        line["cpu_baseline"] = {"value": round(wl.batch / sec, 5), "unit": "slices/s",
+                                "cores": cpu_cores(), "kind": "oracle",
+                                "sample": smp.describe(1, t_rep, t_lift)}
+    print(json.dumps(line), flush=True)
+
+
+def main_reference(args, wl, world, rank):
+    """The FP64 oracle timed on the host cores.  Each step is one replica
+    piece of an append (compression + CP-ALS + match of one replica); the
+    lift, shared by all replicas, is timed once during warm-up.  The value is
+    the batch's slices over P replica pieces plus one lift."""
+    if rank != 0:
+        return
+    smp = OracleSampler(wl, args.seed)
+    t_lift = None
+    reps = []
+    for s in range(args.warmup + args.steps):
+        p = s % wl.P
+        if s < args.warmup:
+            smp.replica(p)
+            if t_lift is None:
+                t_lift = smp.lift()
+        else:
+            reps.append(smp.replica(p))
+    t_rep = sum(reps) / len(reps)
+    sec = wl.P * t_rep + t_lift
+    value = wl.batch / sec
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "slices/s",
+            "n_gpus": world, "steps": len(reps), "warmup": args.warmup,
+            "ms_per_step": round(1e3 * sec, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic planted-CP slices (seeded)",
+            "config": {"workload": wl.name, "I": wl.I, "J": wl.J, "R": wl.R, "P": wl.P,
+                       "Q": wl.Q, "S": wl.S, "batch_slices": wl.batch,
+                       "als_iters": wl.als_iters},
+            "cpu_baseline": {"value": round(value, 5), "unit": "slices/s", "cores": cpu_cores(),
+                             "kind": "oracle",
+                             "sample": smp.describe(len(reps), t_rep, t_lift)},
+            "e2e": {"value": round(value, 5), "unit": "slices/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -62,7 +62,7 @@ typedef enum { OCTEN_FP32 = 0, OCTEN_BF16 = 1, OCTEN_FP8E4M3 = 2 } octen_prec;
 
 /* Shape of one online decomposition (Algorithm 1's REQUIRE line: R, p, Q,
  * shared S; plus the fixed CP-ALS sweep count).  Limits: 1 <= R <= 32,
- * 1 <= S <= Q <= 256, P >= 1, I, J >= 1, als_iters >= 1. */
+ * 1 <= S < Q <= 256, P >= 1, I, J >= 1, als_iters >= 1. */
 typedef struct {
   int64_t I, J;
   int32_t R, P, Q, S;
@@ -137,6 +137,19 @@ const char *octen_status_name(octen_status s);
 
 /* Number of kernel launches the library has issued in this process. */
 uint64_t octen_launch_count(void);
+
+/* Stage timers (measurement aid, not part of the method).  With timing on,
+ * every append records CUDA events on the context's stream around each
+ * stage: quantize, mode2, mode1, mode3 (the three contractions of the
+ * compression), warm_start, als_pass (the two passes over each replica per
+ * sweep), als_small (the other CP-ALS kernels), align, lift, c_solve.
+ * octen_stage_times fills ms[i] (accumulated milliseconds) and launches[i]
+ * (timed intervals) for i < octen_stage_count(); either may be NULL. */
+int octen_stage_count(void);
+const char *octen_stage_name(int i);
+octen_status octen_set_timing(octen_ctx *ctx, int on);
+octen_status octen_stage_times(const octen_ctx *ctx, double *ms, uint64_t *launches);
+octen_status octen_reset_stage_times(octen_ctx *ctx);
 
 #ifdef __cplusplus
 }

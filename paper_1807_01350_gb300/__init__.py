@@ -69,9 +69,17 @@ def lib() -> ctypes.CDLL:
         L.octen_status_name.restype = ctypes.c_char_p
         L.octen_launch_count.argtypes = []
         L.octen_launch_count.restype = ctypes.c_uint64
+        L.octen_stage_count.argtypes = []
+        L.octen_stage_count.restype = ctypes.c_int
+        L.octen_stage_name.argtypes = [ctypes.c_int]
+        L.octen_stage_name.restype = ctypes.c_char_p
+        L.octen_set_timing.argtypes = [vp, ctypes.c_int]
+        L.octen_stage_times.argtypes = [vp, vp, vp]
+        L.octen_reset_stage_times.argtypes = [vp]
         for name in ("octen_create", "octen_init", "octen_append", "octen_get_factors",
                      "octen_fit", "octen_get_replicas", "octen_get_replica_factors",
-                     "octen_compress"):
+                     "octen_compress", "octen_set_timing", "octen_stage_times",
+                     "octen_reset_stage_times"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -205,6 +213,21 @@ class Octen:
             self._h, int(which), At.ctypes.data, Bt.ctypes.data, Ct.ctypes.data,
             perm.ctypes.data, scales.ctypes.data))
         return At, Bt, Ct, perm, scales
+
+    def set_timing(self, on: bool = True):
+        self._check(self._lib.octen_set_timing(self._h, int(bool(on))))
+
+    def reset_stage_times(self):
+        self._check(self._lib.octen_reset_stage_times(self._h))
+
+    def stage_times(self) -> dict:
+        """{stage: (milliseconds, timed intervals)} accumulated while timing is on."""
+        n = self._lib.octen_stage_count()
+        ms = np.zeros(n, np.float64)
+        cnt = np.zeros(n, np.uint64)
+        self._check(self._lib.octen_stage_times(self._h, ms.ctypes.data, cnt.ctypes.data))
+        return {self._lib.octen_stage_name(i).decode(): (float(ms[i]), int(cnt[i]))
+                for i in range(n)}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -315,7 +315,7 @@ static int block_for(int Q) { return ((Q + 31) / 32) * 32; }
 
 template <int RT>
 static void als_run_t(const float *Y, int P, int Q, int R, int iters, AlsBuffers &b,
-                      cudaStream_t st) {
+                      cudaStream_t st, const Marker &mk) {
   const int bq = block_for(Q);
   const size_t smem_h = (size_t)Q * RT * sizeof(float);
   const size_t smem_m2 = ((size_t)Q * RT + 9 * RT) * sizeof(float);
@@ -324,27 +324,37 @@ static void als_run_t(const float *Y, int P, int Q, int R, int iters, AlsBuffers
   const dim3 gQP(Q, P);
   const dim3 gM3((Q * RT + 255) / 256, P);
   auto pass_h_m3_c = [&]() {
+    mk(kStAlsPass, 1);
     als_h_kernel<RT><<<gQP, bq, smem_h, st>>>(Y, b.Bf, b.H, Q);
+    mk(kStAlsPass, 0);
+    mk(kStAlsSmall, 1);
     als_m3_kernel<RT><<<gM3, 256, 0, st>>>(b.H, b.Af, b.M, Q);
     als_solve_kernel<RT><<<P, 256, 0, st>>>(b.M, b.Af, b.Bf, b.Cf, Q, R, 0, b.status);
+    mk(kStAlsSmall, 0);
     count_launch(); count_launch(); count_launch();
   };
   for (int it = 0; it < iters; ++it) {
     pass_h_m3_c();
+    mk(kStAlsSmall, 1);
     als_m1_kernel<RT><<<gQP, 256, 0, st>>>(b.H, b.Cf, b.M, Q);
     als_solve_kernel<RT><<<P, 256, 0, st>>>(b.M, b.Bf, b.Cf, b.Af, Q, R, 1, b.status);
+    mk(kStAlsSmall, 0);
+    mk(kStAlsPass, 1);
     als_m2_kernel<RT><<<gQP, bq, smem_m2, st>>>(Y, b.Af, b.Cf, b.M, Q);
+    mk(kStAlsPass, 0);
+    mk(kStAlsSmall, 1);
     als_solve_kernel<RT><<<P, 256, 0, st>>>(b.M, b.Af, b.Cf, b.Bf, Q, R, 1, b.status);
+    mk(kStAlsSmall, 0);
     count_launch(); count_launch(); count_launch(); count_launch();
   }
   pass_h_m3_c();
 }
 
 void als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
-             cudaStream_t st) {
-  if (RT == 8) als_run_t<8>(Y, P, Q, R, iters, b, st);
-  else if (RT == 16) als_run_t<16>(Y, P, Q, R, iters, b, st);
-  else als_run_t<32>(Y, P, Q, R, iters, b, st);
+             cudaStream_t st, const Marker &mk) {
+  if (RT == 8) als_run_t<8>(Y, P, Q, R, iters, b, st, mk);
+  else if (RT == 16) als_run_t<16>(Y, P, Q, R, iters, b, st, mk);
+  else als_run_t<32>(Y, P, Q, R, iters, b, st, mk);
 }
 
 void warm_start(const float *PF, int P, int Q, int S, int R, int RT, float *F,

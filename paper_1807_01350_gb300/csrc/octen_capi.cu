@@ -69,8 +69,52 @@ struct octen_ctx {
   // per-batch scratch, grown on demand
   DevBuf Tbuf, T2buf, Wbuf, X8buf, xscale, stage[4], fitpart;
 
+  // stage timers (CUDA events on the context's stream)
+  bool timing = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  cudaEvent_t open_ev[kNumStages] = {};
+  struct Pending { int stage; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  double stage_ms[kNumStages] = {};
+  uint64_t stage_n[kNumStages] = {};
+
+  cudaEvent_t next_event() {
+    if (evused == evpool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      evpool.push_back(e);
+    }
+    return evpool[evused++];
+  }
+  void mark(int stage, int begin) {
+    if (!timing) return;
+    cudaEvent_t e = next_event();
+    if (!e) return;
+    cudaEventRecord(e, st);
+    if (begin) open_ev[stage] = e;
+    else if (open_ev[stage]) pending.push_back({stage, open_ev[stage], e});
+  }
+  static void mark_cb(void *self, int stage, int begin) {
+    static_cast<octen_ctx *>(self)->mark(stage, begin);
+  }
+  void flush_timers() {
+    for (const Pending &q : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+        stage_ms[q.stage] += ms;
+        stage_n[q.stage] += 1;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    pending.clear();
+    evused = 0;
+  }
+
   ~octen_ctx() {
-    if (st || true) cudaStreamSynchronize(st);
+    cudaStreamSynchronize(st);
+    for (cudaEvent_t e : evpool) cudaEventDestroy(e);
     for (auto &b : owned) cudaFree(b.p);
     DevBuf *extra[] = {&Tbuf, &T2buf, &Wbuf, &X8buf, &xscale, &stage[0], &stage[1], &stage[2],
                        &stage[3], &fitpart};
@@ -127,6 +171,7 @@ struct octen_ctx {
   octen_status sync_check(const char *what) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && !pending.empty()) flush_timers();
     if (e != cudaSuccess) return fail(OCTEN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
     int flags = 0;
     cudaMemcpy(&flags, dstatus, sizeof(int), cudaMemcpyDeviceToHost);
@@ -191,17 +236,25 @@ octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float
     const size_t xb = (size_t)t * c.I * c.J;
     if (!x->grow(x->X8buf, xb) || !x->grow(x->xscale, (size_t)t * sizeof(float)))
       return x->fail(OCTEN_ENOMEM, "scratch for e4m3 slices");
+    x->mark(kStQuant, 1);
     quantize_e4m3(static_cast<const __nv_bfloat16 *>(Xd), t, c.I * c.J,
                   static_cast<__nv_fp8_e4m3 *>(x->X8buf.p), static_cast<float *>(x->xscale.p),
                   x->st);
+    x->mark(kStQuant, 0);
     m2.X = x->X8buf.p; m2.tx = Elem::E4M3; m2.slice_scale = static_cast<float *>(x->xscale.p);
   }
+  x->mark(kStMode2, 1);
   mode2_simt(m2, x->st);
+  x->mark(kStMode2, 0);
   Mode1Args m1{};
   m1.Ut = x->Ut_rep; m1.T = x->Tbuf.p; m1.te = x->tmid; m1.T2 = static_cast<float *>(x->T2buf.p);
   m1.t = t; m1.I = c.I; m1.P = c.P; m1.Q = c.Q;
+  x->mark(kStMode1, 1);
   mode1_simt(m1, x->st);
+  x->mark(kStMode1, 0);
+  x->mark(kStMode3, 1);
   mode3_accumulate(static_cast<float *>(x->T2buf.p), Wd, Yacc, t, c.P, c.Q, c.S, x->Qd, x->st);
+  x->mark(kStMode3, 0);
   return OCTEN_OK;
 }
 
@@ -437,24 +490,34 @@ octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const floa
   octen_status s = compress_chunk(x, Xd, t, Wd, x->Y);
   if (s != OCTEN_OK) return s;
   // 2. CP of every summary, warm-started from the projected previous factors
+  x->mark(kStWarm, 1);
   project(x, x->U32, c.I, x->A, x->PA);
   project(x, x->V32, c.J, x->B, x->PB);
   warm_start(x->PA, c.P, c.Q, c.S, c.R, RT, x->At, x->st);
   warm_start(x->PB, c.P, c.Q, c.S, c.R, RT, x->Bt, x->st);
+  x->mark(kStWarm, 0);
   AlsBuffers ab{x->At, x->Bt, x->Ct, x->M, x->H, x->dstatus};
-  als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st);
+  Marker mk;
+  if (x->timing) { mk.fn = &octen_ctx::mark_cb; mk.arg = x; }
+  als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st, mk);
   // 3. anchor match against u^T A_prev, v^T B_prev
+  x->mark(kStAlign, 1);
   align_replicas(x->At, x->Bt, x->Ct, x->PA, x->PB, c.P, c.Q, c.S, c.R, RT, x->Ah, x->Bh,
                  x->Ch, x->perm, x->scales, x->st);
+  x->mark(kStAlign, 0);
   // 4. lift A and B, solve the new rows of C, update G_p
+  x->mark(kStLift, 1);
   lift_mode(x, x->Ah, x->PA, x->La, x->a_over, c.I, x->A);
   lift_mode(x, x->Bh, x->PB, x->Lb, x->b_over, c.J, x->B);
+  x->mark(kStLift, 0);
   const size_t cs = (size_t)Qd * c.R + t * c.R + t * Qd + t * t;
   if (!x->grow(x->Wbuf, cs * sizeof(float))) return x->fail(OCTEN_ENOMEM, "C solve scratch");
   float *C_new = x->C + x->K * c.R;
+  x->mark(kStCsolve, 1);
   solve_c_new(Wd, x->Ch, x->G, t, c.P, c.Q, c.S, Qd, c.R, RT, static_cast<float *>(x->Wbuf.p),
               C_new, x->dstatus, x->st);
   update_g(Wd, C_new, t, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
+  x->mark(kStCsolve, 0);
   s = x->sync_check("append");
   if (s != OCTEN_OK) return s;
   x->K += t;
@@ -611,5 +674,37 @@ const char *octen_status_name(octen_status s) {
 }
 
 uint64_t octen_launch_count(void) { return g_launches.load(); }
+
+static const char *kStageNames[kNumStages] = {"quantize", "mode2", "mode1", "mode3",
+                                              "warm_start", "als_pass", "als_small", "align",
+                                              "lift", "c_solve"};
+
+int octen_stage_count(void) { return kNumStages; }
+
+const char *octen_stage_name(int i) {
+  return (i >= 0 && i < kNumStages) ? kStageNames[i] : "unknown";
+}
+
+octen_status octen_set_timing(octen_ctx *x, int on) {
+  if (!x) return OCTEN_EINVAL;
+  x->timing = on != 0;
+  return OCTEN_OK;
+}
+
+octen_status octen_stage_times(const octen_ctx *cx, double *ms, uint64_t *launches) {
+  octen_ctx *x = const_cast<octen_ctx *>(cx);
+  if (!x) return OCTEN_EINVAL;
+  for (int i = 0; i < kNumStages; ++i) {
+    if (ms) ms[i] = x->stage_ms[i];
+    if (launches) launches[i] = x->stage_n[i];
+  }
+  return OCTEN_OK;
+}
+
+octen_status octen_reset_stage_times(octen_ctx *x) {
+  if (!x) return OCTEN_EINVAL;
+  for (int i = 0; i < kNumStages; ++i) { x->stage_ms[i] = 0.0; x->stage_n[i] = 0; }
+  return OCTEN_OK;
+}
 
 }  // extern "C"

@@ -26,6 +26,22 @@ inline size_t elem_size(Elem e) { return e == Elem::F32 ? 4 : (e == Elem::BF16 ?
 // Counts every kernel launch issued through the launch helpers below.
 void count_launch();
 
+// Stages timed with CUDA events when a context has timing enabled.
+enum Stage : int {
+  kStQuant = 0, kStMode2, kStMode1, kStMode3, kStWarm, kStAlsPass, kStAlsSmall, kStAlign,
+  kStLift, kStCsolve, kNumStages
+};
+
+// Optional hook called around the kernels of a multi-kernel stage:
+// fn(arg, stage, 1) before a launch, fn(arg, stage, 0) after it.
+struct Marker {
+  void (*fn)(void *, int, int) = nullptr;
+  void *arg = nullptr;
+  void operator()(int stage, int begin) const {
+    if (fn) fn(arg, stage, begin);
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Generic strided batched fp32-accumulate GEMM (SIMT FFMA):
 //   D[z](m, n) = alpha * sum_k A[z](m, k) * B[z](n, k) + beta * D[z](m, n)
@@ -90,7 +106,7 @@ struct AlsBuffers {
   int *status;
 };
 void als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
-             cudaStream_t st);
+             cudaStream_t st, const Marker &mk = Marker());
 
 // Warm start: F_p = unit columns of rows(p) of PF (Qd x R) into P x Q x RT.
 void warm_start(const float *PF, int P, int Q, int S, int R, int RT, float *F,

@@ -9,10 +9,14 @@ error grows with cond(U^T U)); fit within 1e-4; factor-match
 score against the oracle's factors >= 0.999.  BF16: the mode-2 product is
 rounded to bf16 before the mode-1 contraction, a relative error of about
 2^-9 / sqrt(3) ~ 1.1e-3 per element that the two later contractions average but
-do not remove: summaries within 5e-3.  FP8: per-slice e4m3 quantisation of
-the slices (unit roundoff 2^-4): summaries within 6e-2.  For both reduced
-paths the fit stays within 1e-3 of the oracle's and the factor-match score
->= 0.99.
+do not remove: summaries within 5e-3, fit within 1e-3.  FP8: per-slice e4m3
+quantisation of the slices has unit roundoff 2^-4, an RMS relative error of
+about 3 % per element that random projections preserve (they keep norms, so
+they do not average independent errors away): summaries within 6e-2.  That
+error acts like three times the 1 % data noise, and an FP64 run of the
+oracle on e4m3-quantised slices loses 1.7e-3 to 2.0e-3 of fit against the
+unquantised oracle at every size tried (I = 100 .. 400): fit within 3e-3.
+Factor-match score against the oracle >= 0.99 for both reduced paths.
 """
 import numpy as np
 import pytest
@@ -62,7 +66,7 @@ def run_gpu(pkg, case, d, upto=None):
 
 TOL = {"fp32": dict(Y=1e-5, F=1e-3, fit=1e-4, fms=0.999),
        "bf16": dict(Y=5e-3, F=5e-2, fit=1e-3, fms=0.99),
-       "fp8": dict(Y=6e-2, F=2e-1, fit=1e-3, fms=0.99)}
+       "fp8": dict(Y=6e-2, F=2e-1, fit=3e-3, fms=0.99)}
 
 
 def check_update(case, d, gpu_states, ref_states):
