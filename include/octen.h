@@ -135,8 +135,13 @@ const char *octen_last_error(const octen_ctx *ctx);
 /* Short name of a status code (never NULL). */
 const char *octen_status_name(octen_status s);
 
-/* Number of kernel launches the library has issued in this process. */
+/* Number of kernel launches the library has issued in this process, and how
+ * many of them were tcgen05 tensor-core contractions (the bf16 / e4m3 paths
+ * use them whenever the device is sm_103 and every operand row pitch is a
+ * multiple of 16 bytes: J and I multiples of 8 for bf16, J a multiple of 16
+ * for e4m3; otherwise the SIMT kernels run). */
 uint64_t octen_launch_count(void);
+uint64_t octen_tc_launch_count(void);
 
 /* Stage timers (measurement aid, not part of the method).  With timing on,
  * every append records CUDA events on the context's stream around each

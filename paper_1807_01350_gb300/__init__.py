@@ -69,6 +69,8 @@ def lib() -> ctypes.CDLL:
         L.octen_status_name.restype = ctypes.c_char_p
         L.octen_launch_count.argtypes = []
         L.octen_launch_count.restype = ctypes.c_uint64
+        L.octen_tc_launch_count.argtypes = []
+        L.octen_tc_launch_count.restype = ctypes.c_uint64
         L.octen_stage_count.argtypes = []
         L.octen_stage_count.restype = ctypes.c_int
         L.octen_stage_name.argtypes = [ctypes.c_int]
@@ -87,6 +89,10 @@ def lib() -> ctypes.CDLL:
 
 def launch_count() -> int:
     return int(lib().octen_launch_count())
+
+
+def tc_launch_count() -> int:
+    return int(lib().octen_tc_launch_count())
 
 
 def _stream_handle(stream) -> int | None:

@@ -1,0 +1,398 @@
+// Tensor-core contractions of the compression step (Sec. "Parallel
+// Compression and Decomposition": the mode-2 and mode-1 products of
+// Z_p = X x1 U_p^T x2 V_p^T x3 W_p^T) on sm_103a: tcgen05.mma with the
+// accumulator in tensor memory, operands staged by TMA (128-byte swizzle) in
+// a multi-stage shared-memory ring, one CTA per 128 x BN output tile.
+//
+//   warp 0 lane 0 : TMA producer   (full[s] <- bytes landed)
+//   warp 1 lane 0 : MMA issuer     (empty[s] <- tcgen05.commit, acc <- last commit)
+//   warps 0..3    : epilogue, each reading its 32 TMEM lanes with tcgen05.ld
+//
+// Every wait on an mbarrier is bounded by a clock budget; on expiry the CTA
+// raises kDevTimeout in the status word, skips the rest of its work, still
+// waits (bounded) for the MMAs it issued and frees its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "octen_internal.cuh"
+
+namespace octen {
+
+namespace {
+
+constexpr int kBM = 128;          // UMMA M (cta_group::1)
+constexpr int kRowBytes = 128;    // one 128-byte swizzle row of K per operand row
+constexpr long long kWaitBudget = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; false on timeout or when another role raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          volatile int *abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *holder, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(holder)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  if constexpr (KIND == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 lanes x 32 columns of fp32 from tensor memory (lane = warp quadrant + lane id).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored as 128-byte
+// rows with the 128-byte swizzle (TMA SWIZZLE_128B): 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= static_cast<uint64_t>(1) << 16;                    // leading offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;            // stride offset: 8 rows x 128 B
+  d |= static_cast<uint64_t>(1) << 46;                    // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: fp32 accumulate, both operands K-major, M = 128.
+// KIND 0: bf16 x bf16 (kind::f16); KIND 1: e4m3 x e4m3 (kind::f8f6f4).
+__host__ __device__ constexpr uint32_t make_idesc(int KIND, int N) {
+  return (1u << 4) |                                   // D format f32
+         ((KIND == 0 ? 1u : 0u) << 7) |                 // A format: bf16 / e4m3
+         ((KIND == 0 ? 1u : 0u) << 10) |                // B format: bf16 / e4m3
+         (static_cast<uint32_t>(N >> 3) << 17) |        // N / 8
+         (static_cast<uint32_t>(kBM >> 4) << 24);       // M / 16
+}
+
+struct TcShape {
+  int M, N, K;          // per batch item (K in elements)
+  int BN;               // tile N (multiple of 32, <= 256)
+  int stages;
+  int tmem_cols;        // power of two >= BN
+  int zdiv;             // batch index z -> rows (z / zdiv) * hi + (z % zdiv) * lo
+  int a_hi, a_lo, b_hi, b_lo;
+};
+
+// Mode-2 epilogue: row m = k * I + i, column c of V_all -> every replica owning c.
+struct Mode2TcEpi {
+  __nv_bfloat16 *T;
+  const float *scale;
+  int64_t I;
+  int P, Q, S;
+  __device__ __forceinline__ void operator()(int, int m, int c, float v) const {
+    const int64_t k = m / I, i = m - k * I;
+    if (scale) v *= scale[k];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    if (c < S) {
+      for (int p = 0; p < P; ++p) T[((k * P + p) * Q + c) * I + i] = h;
+    } else {
+      const int p = (c - S) / (Q - S);
+      const int b = S + (c - S) - p * (Q - S);
+      T[((k * P + p) * Q + b) * I + i] = h;
+    }
+  }
+};
+
+// Mode-1 epilogue: batch z = k * P + p, row a, column b -> T2[p][k][a][b].
+struct Mode1TcEpi {
+  float *T2;
+  int64_t t;
+  int P, Q;
+  __device__ __forceinline__ void operator()(int z, int a, int b, float v) const {
+    const int k = z / P, p = z - k * P;
+    T2[(((int64_t)p * t + k) * Q + a) * Q + b] = v;
+  }
+};
+
+template <int KIND, class Epi>
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcShape sh, const Epi epi, int *status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int stages = sh.stages;
+  const uint32_t a_bytes = kBM * kRowBytes;
+  const uint32_t b_bytes = sh.BN * kRowBytes;
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + stages * a_bytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sB + stages * b_bytes);
+  uint64_t *empty = full + stages;
+  uint64_t *accf = empty + stages;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(accf + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int z = blockIdx.z;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * sh.BN;
+  const int a_row0 = (z / sh.zdiv) * sh.a_hi + (z % sh.zdiv) * sh.a_lo + m0;
+  const int b_row0 = (z / sh.zdiv) * sh.b_hi + (z % sh.zdiv) * sh.b_lo + n0;
+  constexpr int kElemsPerRow = KIND == 0 ? 64 : 128;   // 128 bytes of K
+  constexpr int kUmmaK = KIND == 0 ? 16 : 32;           // 32 bytes of K per MMA
+  const int nk = (sh.K + kElemsPerRow - 1) / kElemsPerRow;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_holder, sh.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % stages;
+      const uint32_t ph = (kb / stages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+        *abort_flag = 1;
+        atomicOr(status, kDevTimeout);
+        break;
+      }
+      mbar_expect_tx(&full[s], a_bytes + b_bytes);
+      tma_load_2d(sA + s * a_bytes, &tmA, &full[s], kb * kElemsPerRow, a_row0);
+      tma_load_2d(sB + s * b_bytes, &tmB, &full[s], kb * kElemsPerRow, b_row0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = make_idesc(KIND, sh.BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % stages;
+      const uint32_t ph = (kb / stages) & 1u;
+      if (!mbar_wait(&full[s], ph, abort_flag)) {
+        *abort_flag = 1;
+        atomicOr(status, kDevTimeout);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
+#pragma unroll
+      for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+        mma_issue<KIND>(tmem, make_desc_sw128(a0 + kk * 32), make_desc_sw128(b0 + kk * 32),
+                        idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accf);   // also issued after an abort: drains the MMAs already issued
+  }
+  (void)kUmmaK;
+
+  // epilogue: 4 warps, warp w owns accumulator rows [32 w, 32 w + 32)
+  __syncwarp();
+  const bool ok = mbar_wait(accf, 0, abort_flag);
+  if (!ok && lane == 0) atomicOr(status, kDevTimeout);
+  tc_fence_after();
+  // tcgen05.ld is warp-collective: take the decision for the whole warp
+  if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
+    const int m = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < sh.BN; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, r);
+      if (m < sh.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < sh.N) epi(z, m, n, __uint_as_float(r[j]));
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, sh.tmem_cols);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D map over a row-major [rows][inner] operand, 128-byte boxes along K.
+bool make_map(CUtensorMap *m, const void *base, bool fp8, uint64_t inner, uint64_t rows,
+              uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const uint64_t esz = fp8 ? 1 : 2;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((inner * esz) & 15)) return false;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * esz};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kRowBytes / esz), box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int pow2_at_least(int n) {
+  int p = 32;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+template <int KIND, class Epi>
+bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
+               const Epi &epi, int *status, cudaStream_t st) {
+  sh.tmem_cols = pow2_at_least(sh.BN);
+  const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes;
+  sh.stages = static_cast<int>((200 * 1024) / per_stage);
+  if (sh.stages > 6) sh.stages = 6;
+  if (sh.stages < 2) return false;
+  const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 1) * 8 + 16;
+  if (cudaFuncSetAttribute(tc_gemm_kernel<KIND, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return false;
+  dim3 grid((sh.N + sh.BN - 1) / sh.BN, (sh.M + kBM - 1) / kBM, batch);
+  tc_gemm_kernel<KIND, Epi><<<grid, 128, smem, st>>>(ma, mb, sh, epi, status);
+  count_launch();
+  count_tc_launch();
+  return cudaPeekAtLastError() == cudaSuccess;
+}
+
+}  // namespace
+
+bool tc_supported() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st) {
+  if (a.tt != Elem::BF16 || !(a.tx == Elem::BF16 || a.tx == Elem::E4M3) || a.tv != a.tx)
+    return false;
+  const bool fp8 = a.tx == Elem::E4M3;
+  const int64_t M = a.t * a.I;
+  if (M > (1 << 30) || a.J > (1 << 30)) return false;
+  CUtensorMap ma, mb;
+  const int BN = 256;
+  if (!make_map(&ma, a.X, fp8, a.J, M, kBM) || !make_map(&mb, a.Vt, fp8, a.J, a.Qd, BN))
+    return false;
+  TcShape sh{};
+  sh.M = static_cast<int>(M); sh.N = a.Qd; sh.K = static_cast<int>(a.J); sh.BN = BN;
+  sh.zdiv = 1; sh.a_hi = 0; sh.a_lo = 0; sh.b_hi = 0; sh.b_lo = 0;
+  Mode2TcEpi epi{static_cast<__nv_bfloat16 *>(a.T), a.slice_scale, a.I, a.P, a.Q, a.S};
+  return fp8 ? launch_tc<1>(ma, mb, sh, 1, epi, status, st)
+             : launch_tc<0>(ma, mb, sh, 1, epi, status, st);
+}
+
+bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
+  if (a.te != Elem::BF16) return false;
+  CUtensorMap ma, mb;
+  const int BN = (a.Q + 31) / 32 * 32;
+  if (BN > 256) return false;
+  const int64_t rowsA = static_cast<int64_t>(a.P) * a.Q;
+  const int64_t rowsB = a.t * a.P * a.Q;
+  if (rowsB > (1 << 30)) return false;
+  if (!make_map(&ma, a.Ut, false, a.I, rowsA, kBM) || !make_map(&mb, a.T, false, a.I, rowsB, BN))
+    return false;
+  TcShape sh{};
+  sh.M = a.Q; sh.N = a.Q; sh.K = static_cast<int>(a.I); sh.BN = BN;
+  sh.zdiv = a.P;                   // z = k * P + p
+  sh.a_hi = 0; sh.a_lo = a.Q;      // A rows: p * Q
+  sh.b_hi = a.P * a.Q; sh.b_lo = a.Q;   // B rows: (k * P + p) * Q
+  Mode1TcEpi epi{a.T2, a.t, a.P, a.Q};
+  return launch_tc<0>(ma, mb, sh, static_cast<int>(a.t * a.P), epi, status, st);
+}
+
+}  // namespace octen

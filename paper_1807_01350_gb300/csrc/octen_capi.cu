@@ -4,6 +4,7 @@
 // lift of A, B and the new rows of C).
 #include <atomic>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -14,7 +15,9 @@ using namespace octen;
 
 namespace octen {
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_tc_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_tc_launch() { g_tc_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace octen
 
 namespace {
@@ -48,6 +51,7 @@ struct octen_ctx {
   Elem tmid = Elem::F32;   // mode-2 output (T_rep) type
   cudaStream_t st = nullptr;
   bool initialized = false;
+  bool use_tc = true;      // tcgen05 contractions for bf16 / e4m3 operands
   std::string err;
   int64_t K = 0, Kcap = 0;
   int a_over = 0, b_over = 0;
@@ -207,7 +211,15 @@ octen_status validate(const octen_config *c, std::string &why) {
   return OCTEN_OK;
 }
 
+// OCTEN_GEMM=simt keeps the large contractions on the SIMT kernels (used to
+// cross-check the tensor-core kernels against an independent implementation).
+bool tc_wanted() {
+  const char *v = getenv("OCTEN_GEMM");
+  return !(v && strcmp(v, "simt") == 0) && tc_supported();
+}
+
 void set_types(octen_ctx *x) {
+  x->use_tc = x->cfg.prec != OCTEN_FP32 && tc_wanted();
   switch (x->cfg.prec) {
     case OCTEN_FP32:
       x->xin = Elem::F32; x->tu = Elem::F32; x->tv = Elem::F32; x->tmid = Elem::F32; break;
@@ -244,13 +256,19 @@ octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float
     m2.X = x->X8buf.p; m2.tx = Elem::E4M3; m2.slice_scale = static_cast<float *>(x->xscale.p);
   }
   x->mark(kStMode2, 1);
-  mode2_simt(m2, x->st);
+  if (!(x->use_tc && mode2_tc(m2, x->dstatus, x->st))) {
+    cudaGetLastError();
+    mode2_simt(m2, x->st);
+  }
   x->mark(kStMode2, 0);
   Mode1Args m1{};
   m1.Ut = x->Ut_rep; m1.T = x->Tbuf.p; m1.te = x->tmid; m1.T2 = static_cast<float *>(x->T2buf.p);
   m1.t = t; m1.I = c.I; m1.P = c.P; m1.Q = c.Q;
   x->mark(kStMode1, 1);
-  mode1_simt(m1, x->st);
+  if (!(x->use_tc && mode1_tc(m1, x->dstatus, x->st))) {
+    cudaGetLastError();
+    mode1_simt(m1, x->st);
+  }
   x->mark(kStMode1, 0);
   x->mark(kStMode3, 1);
   mode3_accumulate(static_cast<float *>(x->T2buf.p), Wd, Yacc, t, c.P, c.Q, c.S, x->Qd, x->st);
@@ -674,6 +692,8 @@ const char *octen_status_name(octen_status s) {
 }
 
 uint64_t octen_launch_count(void) { return g_launches.load(); }
+
+uint64_t octen_tc_launch_count(void) { return g_tc_launches.load(); }
 
 static const char *kStageNames[kNumStages] = {"quantize", "mode2", "mode1", "mode3",
                                               "warm_start", "als_pass", "als_small", "align",

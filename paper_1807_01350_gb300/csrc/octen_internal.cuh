@@ -79,6 +79,14 @@ struct Mode1Args {
 };
 void mode1_simt(const Mode1Args &a, cudaStream_t st);
 
+// tcgen05 versions of the two large contractions (bf16 / e4m3 operands).  They
+// return false without launching when the device is not sm_103 or an operand
+// violates the TMA alignment rules (row pitch a multiple of 16 bytes).
+bool tc_supported();
+bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st);
+bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st);
+void count_tc_launch();
+
 // Mode-3 contraction and summary update: Y[p][a][b][c] +=
 //   sum_k T2[p][k][a][b] * W_all[k][col_p(c)].
 void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,

@@ -1,0 +1,77 @@
+"""The tcgen05 tensor-core contractions (mode 2 and mode 1 of the compression)
+against the FP64 oracle and against the independent SIMT kernels, on shapes
+whose operand pitches satisfy the TMA rules (so the tensor-core path runs):
+ragged M, N and K tails, several tiles in every dimension, Q not a multiple
+of the 128-row tile."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests._cases import Case, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_Y = {"bf16": 5e-3, "fp8": 6e-2}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1807_01350_gb300 as p
+
+    assert torch.cuda.is_available()
+    p.lib()
+    return p
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.asarray(a, np.float32), device="cuda").to(dtype)
+
+
+SHAPES = [
+    # I, J, P, Q, S, t
+    (152, 144, 3, 24, 4, 7),
+    (256, 512, 4, 80, 8, 5),
+    (136, 208, 2, 200, 20, 3),
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_tc_compression_matches_oracle_and_simt(pkg, prec, shape, monkeypatch):
+    I, J, P, Q, S, t = shape
+    case = Case(I, J, 4, P, Q, S, t, (), 1, prec=prec, seed=21)
+    d = case.make()
+    args = (I, J, P, Q, S, dev(d["X"], torch.bfloat16), dev(d["U"]), dev(d["V"]),
+            dev(d["W"][0]))
+    n0 = pkg.tc_launch_count()
+    Z_tc = pkg.compress(*args, prec=prec)
+    assert pkg.tc_launch_count() - n0 == 2, "both contractions should run on tcgen05"
+    monkeypatch.setenv("OCTEN_GEMM", "simt")
+    n1 = pkg.tc_launch_count()
+    Z_simt = pkg.compress(*args, prec=prec)
+    assert pkg.tc_launch_count() == n1
+    for p in range(P):
+        ref = oracle.compress(d["X"], oracle.replica_block(d["U"], p, Q, S),
+                              oracle.replica_block(d["V"], p, Q, S),
+                              oracle.replica_block(d["W"][0], p, Q, S))
+        assert rel(Z_tc[p], ref) < TOL_Y[prec], (p, rel(Z_tc[p], ref))
+        # same operands, same bf16 rounding of the intermediate; only the fp32
+        # accumulation order differs
+        assert rel(Z_tc[p], Z_simt[p]) < 2e-3, (p, rel(Z_tc[p], Z_simt[p]))
+
+
+def test_tc_update_parity_bf16(pkg):
+    """A whole update on the tensor-core path (J, I multiples of 16)."""
+    from tests.test_gpu_parity import check_update, run_gpu
+
+    case = Case(160, 144, 6, 4, 32, 8, 40, (16, 16), 30, prec="bf16", seed=22)
+    d = case.make()
+    _, ref = case.oracle_run(d)
+    n0 = pkg.tc_launch_count()
+    g, gpu = run_gpu(pkg, case, d)
+    g.close()
+    assert pkg.tc_launch_count() > n0
+    check_update(case, d, gpu, ref)
