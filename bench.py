@@ -137,12 +137,12 @@ def stage_work(wl, prec):
     }
 
 
-def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic):
+def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic, tc_stages=()):
     flops, nbytes = stage_work(wl, prec)[stage]
     sec = ms_per_launch / 1e3
     if stage == "mode3":
         bound, peak, unit, achieved = "hbm", pk["hbm"], "GB/s", nbytes / sec / 1e9
-    elif stage in ("mode2", "mode1") and prec in ("bf16", "fp8") and _tensor_core_path(stage):
+    elif stage in tc_stages:
         peak = pk["bf16_sus"] * (2.0 if prec == "fp8" and stage == "mode2" else 1.0)
         bound, unit, achieved = "tensor", "TFLOP/s", flops / sec / 1e12
     else:
@@ -152,11 +152,6 @@ def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic):
             "peak_source": pk["src"] if bound != "alu" else
             "derived: 152 SMs x 128 fp32 lanes x 2 flop x 2070 MHz",
             "ms_per_launch": round(ms_per_launch, 4)}
-
-
-def _tensor_core_path(stage):
-    import paper_1807_01350_gb300 as pkg
-    return bool(getattr(pkg, "TENSOR_CORE_STAGES", ())) and stage in pkg.TENSOR_CORE_STAGES
 
 
 def traffic_from_profiles(stage, prec):
@@ -170,6 +165,27 @@ def traffic_from_profiles(stage, prec):
         return None
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Each rank runs its own independent stream (its own planted tensor)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's value (no-op for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
     import torch
 
@@ -177,7 +193,7 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
 
     dev = torch.device("cuda", torch.cuda.current_device())
     nb = warmup + steps + (steps if time_e2e else 0)
-    d = stream_inputs(wl, prec, args.seed + 1000 * rank, nb, dev)
+    d = stream_inputs(wl, prec, rank_seed(args.seed, rank), nb, dev)
     stream = torch.cuda.current_stream()
     g = pkg.Octen(wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.als_iters, prec, stream=stream)
     t_old, t = wl.t_old, wl.batch
@@ -192,6 +208,7 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
     g.reset_stage_times()
     g.set_timing(True)
     launches0 = pkg.launch_count()
+    tc0 = pkg.tc_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
@@ -203,16 +220,17 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
         torch.cuda.synchronize()
     g.set_timing(False)
     launches = pkg.launch_count() - launches0
-    ms = ev0.elapsed_time(ev1)
+    tc_launches = pkg.tc_launch_count() - tc0
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
         torch.distributed.barrier()
     stages = g.stage_times()
     fit = g.fit(d["X"][:k])
+    # the two tensor-core contractions run once per append when the path is taken
+    tc_stages = ("mode2", "mode1") if tc_launches >= 2 * steps else ()
     out = dict(ms=ms, steps=steps, slices=steps * t, stages=stages, fit=fit,
-               launches=launches, clocks=clk.summary())
+               launches=launches, tc_launches=tc_launches, tc_stages=tc_stages,
+               clocks=clk.summary())
     if time_e2e:
         out["e2e"] = run_e2e(g, d, wl, prec, k, steps, warmup, rank, world)
     g.close()
@@ -245,12 +263,8 @@ def run_e2e(g, d, wl, prec, k, steps, warmup, rank, world):
         kk = g.factors_into(Ah, Bh, Ch)
         d2h += (wl.I + wl.J + kk) * wl.R * 4
     torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([sec], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        sec = float(tt.item())
-    return {"value": round(world * steps * t / sec, 3), "unit": "slices/s",
+    sec = max_over_ranks(time.perf_counter() - t0, world, torch.device("cuda"))
+    return {"value": round(whole_job_rate(steps * t, sec, world), 3), "unit": "slices/s",
             "h2d_bytes_per_step": int(xb + wb), "d2h_bytes_per_step": int(d2h / steps),
             "ms_per_step": round(1e3 * sec / steps, 3)}
 
@@ -360,7 +374,7 @@ def main():
     beside = {}
     for prec in [p for p in args.beside.split(",") if p and p != args.prec]:
         r = run_stream(args, wl, prec, args.beside_steps, 3, rank, world, time_e2e=False)
-        beside[prec] = {"value": round(world * r["slices"] / (r["ms"] / 1e3), 3),
+        beside[prec] = {"value": round(whole_job_rate(r["slices"], r["ms"] / 1e3, world), 3),
                         "ms_per_step": round(r["ms"] / r["steps"], 3), "fit": round(r["fit"], 6),
                         "steps": r["steps"],
                         "stage_ms_per_step": {k: round(v[0] / r["steps"], 3)
@@ -375,12 +389,13 @@ def main():
     timed = {k: v for k, v in st.items() if v[1] > 0}
     dominant = max(("mode2", "mode1", "mode3", "als_pass"), key=lambda s: st[s][0])
     ms_launch = st[dominant][0] / st[dominant][1]
+    tcs = main_run["tc_stages"]
     roof = roofline_for(dominant, ms_launch, wl, args.prec, pk,
-                        traffic_from_profiles(dominant, args.prec))
+                        traffic_from_profiles(dominant, args.prec), tcs)
     comp = {s: roofline_for(s, st[s][0] / st[s][1], wl, args.prec, pk,
-                            traffic_from_profiles(s, args.prec))
+                            traffic_from_profiles(s, args.prec), tcs)
             for s in ("mode2", "mode1", "mode3", "als_pass") if st[s][1]}
-    value = world * main_run["slices"] / (main_run["ms"] / 1e3)
+    value = whole_job_rate(main_run["slices"], main_run["ms"] / 1e3, world)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "slices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -396,6 +411,7 @@ def main():
         "fit": round(main_run["fit"], 6),
         "clocks": main_run["clocks"],
         "gpu_launches": main_run["launches"],
+        "tcgen05_launches": main_run["tc_launches"],
         "roofline": roof,
         "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in timed.items()},
         "stage_roofline": comp,
