@@ -126,6 +126,31 @@ octen_status octen_compress(const octen_config *cfg, void *cuda_stream, const vo
                             int64_t t, const float *U_all, const float *V_all,
                             const float *W_all, float *Z);
 
+/* octen_compress without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (processes living inside a fixed device-memory budget handed out
+ * by a host framework, plugins whose host forbids the CUDA allocator, latency-
+ * critical code that must not pay for an allocation).  It computes what
+ * octen_compress computes, with the same arguments, but
+ *  - every array (X, U_all, V_all, W_all, Z) must already be device memory
+ *    (host buffers are rejected with OCTEN_EINVAL: staging them would
+ *    allocate);
+ *  - all scratch lives in one static device array of 64 MiB that every GPU
+ *    loading the library holds until the process exits; slices are processed
+ *    in chunks that fit it, and a shape whose projections alone do not fit is
+ *    rejected with OCTEN_EINVAL and a message on stderr;
+ *  - the first call on a device looks up the array's address on that device
+ *    (cudaGetSymbolAddress) and caches it: make that first call before any
+ *    stream capture;
+ *  - the array is shared by all calls and keeps the last call's contents
+ *    (each call clears what must start at zero); calls whose GPU work
+ *    overlaps (other streams or threads) race on it and must be serialised
+ *    by the caller.
+ * Returns after the work has finished on `cuda_stream`. */
+octen_status octen_compress_noalloc(const octen_config *cfg, void *cuda_stream, const void *X,
+                                    int64_t t, const float *U_all, const float *V_all,
+                                    const float *W_all, float *Z);
+
 /* Releases the context and its device memory (NULL is allowed). */
 void octen_destroy(octen_ctx *ctx);
 

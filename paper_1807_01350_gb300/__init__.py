@@ -61,6 +61,8 @@ def lib() -> ctypes.CDLL:
         L.octen_get_replicas.argtypes = [vp, f32p]
         L.octen_get_replica_factors.argtypes = [vp, ctypes.c_int, f32p, f32p, f32p, vp, vp]
         L.octen_compress.argtypes = [ctypes.POINTER(_Config), vp, vp, i64, f32p, f32p, f32p, f32p]
+        L.octen_compress_noalloc.argtypes = [ctypes.POINTER(_Config), vp, vp, i64, f32p, f32p,
+                                             f32p, f32p]
         L.octen_destroy.argtypes = [vp]
         L.octen_destroy.restype = None
         L.octen_last_error.argtypes = [vp]
@@ -80,7 +82,8 @@ def lib() -> ctypes.CDLL:
         L.octen_reset_stage_times.argtypes = [vp]
         for name in ("octen_create", "octen_init", "octen_append", "octen_get_factors",
                      "octen_fit", "octen_get_replicas", "octen_get_replica_factors",
-                     "octen_compress", "octen_set_timing", "octen_stage_times",
+                     "octen_compress", "octen_compress_noalloc", "octen_set_timing",
+                     "octen_stage_times",
                      "octen_reset_stage_times"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
