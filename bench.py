@@ -346,6 +346,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--compress-only", action="store_true",
+                    help="time octen_compress alone on --slices slices (profiling case)")
+    ap.add_argument("--slices", type=int, default=4)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -354,6 +357,8 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, wl, world, rank)
+    if args.compress_only:
+        return main_compress_only(args, wl)
 
     import torch
 
@@ -428,6 +433,39 @@ def main():
                                 "cores": cpu_cores(), "kind": "oracle",
                                 "sample": smp.describe(1, t_rep, t_lift)}
     print(json.dumps(line), flush=True)
+
+
+def main_compress_only(args, wl):
+    """Stateless compression of a few slices of the workload (a small, fixed
+    case for profiler captures): prints one JSON line with the time per call."""
+    import torch
+
+    from paper_1807_01350_gb300 import build as B
+    B.build()
+    import paper_1807_01350_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t = args.slices
+    A, B_, C = factors(wl.I, wl.J, t, wl.R, args.seed)
+    U, V = projections(wl.I, wl.J, wl.P, wl.Q, wl.S, args.seed, args.prec)
+    W = time_projection(t, wl.P, wl.Q, wl.S, args.seed, 0)
+    dt = torch.float32 if args.prec == "fp32" else torch.bfloat16
+    X = slice_batch_torch(A, B_, C, 0, t, wl.noise, args.seed, dev, dt)
+    f32 = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=dev)
+    Ud, Vd, Wd = f32(U), f32(V), f32(W)
+    ms = []
+    for s in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pkg.compress(wl.I, wl.J, wl.P, wl.Q, wl.S, X, Ud, Vd, Wd, prec=args.prec)
+        e1.record()
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"mode": "compress_only", "workload": wl.name, "prec": args.prec,
+                      "slices": t, "ms_per_call": round(sum(ms) / len(ms), 3),
+                      "tcgen05_launches": pkg.tc_launch_count()}), flush=True)
 
 
 def main_reference(args, wl, world, rank):

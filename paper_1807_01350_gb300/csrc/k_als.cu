@@ -147,84 +147,120 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x < RT) M[((int64_t)p * Q + b) * RT + threadIdx.x] = out[threadIdx.x];
 }
 
-// Cholesky of the R x R leading block of G (fp64, row-major [RT][RT]) by one
-// warp: lane i owns row i.  Returns false if a pivot is not positive.
+// Cholesky of an R x R SPD matrix held by one warp, lane i owning row i in
+// registers (a[k] = G[i][k] for k <= i): right-looking, the pivot column is
+// broadcast with shuffles and every lane updates its own row.  On return
+// a[k] = L[i][k].  Returns false if a pivot is not positive (uniform).
 template <int RT>
-__device__ bool warp_cholesky(double *G, double *L, int R) {
+__device__ __forceinline__ bool warp_chol_rows(double (&a)[RT], int R) {
   const int lane = threadIdx.x & 31;
   bool ok = true;
-  for (int j = 0; j < R; ++j) {
-    if (lane == j) {
-      double d = G[j * RT + j];
-      for (int k = 0; k < j; ++k) d -= L[j * RT + k] * L[j * RT + k];
-      L[j * RT + j] = d > 0.0 ? sqrt(d) : 0.0;
+#pragma unroll
+  for (int j = 0; j < RT; ++j) {
+    if (j < R) {
+      const double d = __shfl_sync(0xffffffffu, a[j], j);
+      const bool good = d > 0.0;
+      ok = ok && good;
+      const double piv = good ? sqrt(d) : 1.0;
+      const double inv = 1.0 / piv;
+      double l = 0.0;
+      if (lane == j) l = piv;
+      else if (lane > j && lane < R) l = a[j] * inv;
+      a[j] = l;
+#pragma unroll
+      for (int k = j + 1; k < RT; ++k) {
+        const double lk = __shfl_sync(0xffffffffu, l, k);
+        if (k < R && k <= lane && lane < R) a[k] = fma(-l, lk, a[k]);
+      }
     }
-    __syncwarp();
-    const double piv = L[j * RT + j];
-    if (!(piv > 0.0)) ok = false;
-    if (ok && lane > j && lane < R) {
-      double s = G[lane * RT + j];
-      for (int k = 0; k < j; ++k) s -= L[lane * RT + k] * L[j * RT + k];
-      L[lane * RT + j] = s / piv;
-    }
-    __syncwarp();
-    if (!ok) break;
   }
   return ok;
 }
 
-// F_p = M_p (F1_p^T F1_p * F2_p^T F2_p)^-1, optionally with unit-l2 columns.
-// grid P, 256 threads (Q <= 256: thread q owns row q).
+// Loads row `lane` of G1 * G2 (Hadamard, fp64) into a[], diagonal loaded by `add`.
 template <int RT>
-__global__ void __launch_bounds__(256)
-    als_solve_kernel(const float *__restrict__ M, const float *__restrict__ F1,
-                     const float *__restrict__ F2, float *__restrict__ F, int Q, int R,
-                     int normalize, int *status) {
-  __shared__ float g1[RT * RT], g2[RT * RT];
-  __shared__ double Gd[RT * RT], Ld[RT * RT];
-  __shared__ float Lf[RT * RT];
+__device__ __forceinline__ void load_gram_rows(const float *g1, const float *g2, int R,
+                                               double add, double (&a)[RT]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < RT; ++k) {
+    double v = 0.0;
+    if (lane < R && k <= lane) v = (double)g1[lane * RT + k] * (double)g2[lane * RT + k];
+    if (k == lane && lane < R) v += add;
+    a[k] = v;
+  }
+}
+
+// Warp 0: factor G1 * G2 (fp64) and leave L in Lf (fp32, identity on failure),
+// the reciprocal diagonal in invd and the success flag in *ok_out.  Kept out of
+// line so that its registers do not add to the substitution's.
+template <int RT>
+__device__ __noinline__ void chol_to_smem(const float *g1, const float *g2, int R, float *Lf,
+                                          float *invd, int *ok_out) {
+  double a[RT];
+  load_gram_rows<RT>(g1, g2, R, 0.0, a);
+  bool ok = warp_chol_rows<RT>(a, R);
+  if (!ok) {
+    // load the diagonal by 1e-12 * trace / R and retry once
+    double tr = threadIdx.x < R ? (double)g1[threadIdx.x * RT + threadIdx.x] *
+                                      (double)g2[threadIdx.x * RT + threadIdx.x]
+                                : 0.0;
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    load_gram_rows<RT>(g1, g2, R, 1e-12 * tr / R, a);
+    ok = warp_chol_rows<RT>(a, R);
+  }
+  const int i = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < RT; ++k)
+    if (i < RT) Lf[i * RT + k] = (ok && k <= i && i < R) ? (float)a[k] : (k == i ? 1.f : 0.f);
+  if (i < RT) invd[i] = (ok && i < R) ? (float)(1.0 / a[i]) : 1.f;
+  if (i == 0) *ok_out = ok ? 1 : 0;
+}
+
+// F_p = M_p (G1_p * G2_p)^-1 with G1, G2 the cached R x R Grams of the other two
+// factors (fp64 Cholesky, fp32 inverse from the factor, fp32 product with M_p);
+// M_p is the sum of `nsplit` partial MTTKRPs.  Optionally normalises
+// the columns to unit l2.  Writes F_p, its Gram F_p^T F_p and, if Ft is given,
+// a bf16 copy transposed to [NP][Q] (rows >= R zero) for the tensor-core passes.
+// grid P, 256 threads (thread q owns row q, Q <= 256); dynamic smem Q * RT floats.
+template <int RT>
+__global__ void __launch_bounds__(256, 1)
+    als_solve_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
+                     const float *__restrict__ G1, const float *__restrict__ G2,
+                     float *__restrict__ F, float *__restrict__ Gout,
+                     __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int R, int normalize,
+                     int *status) {
+  extern __shared__ __align__(16) float Fs[];   // [Q][RT]
+  __shared__ float Lf[RT * RT], invd[RT];
+  __shared__ __align__(16) float Li[RT * RT], Gi[RT * RT];
   __shared__ float red[8 * RT], out[RT];
   __shared__ int ok_s;
   const int p = blockIdx.x;
-  const float *f1 = F1 + (int64_t)p * Q * RT, *f2 = F2 + (int64_t)p * Q * RT;
-  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
-    const int r = e / RT, s = e % RT;
-    float a1 = 0.f, a2 = 0.f;
-    if (r < R && s < R) {
-      for (int q = 0; q < Q; ++q) {
-        a1 = fmaf(f1[q * RT + r], f1[q * RT + s], a1);
-        a2 = fmaf(f2[q * RT + r], f2[q * RT + s], a2);
+  const float *g1 = G1 + (int64_t)p * RT * RT, *g2 = G2 + (int64_t)p * RT * RT;
+  if (threadIdx.x < 32) chol_to_smem<RT>(g1, g2, R, Lf, invd, &ok_s);
+  __syncthreads();
+  if (!ok_s && threadIdx.x == 0) atomicOr(status, kDevCholesky);
+
+  // inverse of the Gram Hadamard product: Linv by warp 0 (lane j owns column j),
+  // then Ginv = Linv^T Linv by all threads
+  if (threadIdx.x < RT) {
+    const int j = threadIdx.x;
+    for (int i = 0; i < RT; ++i) Li[i * RT + j] = 0.f;
+    if (j < R) {
+      Li[j * RT + j] = invd[j];
+      for (int i = j + 1; i < R; ++i) {
+        float acc = 0.f;
+        for (int k = j; k < i; ++k) acc = fmaf(Lf[i * RT + k], Li[k * RT + j], acc);
+        Li[i * RT + j] = -acc * invd[i];
       }
     }
-    g1[e] = a1;
-    g2[e] = a2;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
-    Gd[e] = (double)g1[e] * (double)g2[e];
-    Ld[e] = 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    bool ok = warp_cholesky<RT>(Gd, Ld, R);
-    if (!ok) {
-      // load the diagonal by 1e-12 * trace / R and retry once
-      double tr = 0.0;
-      for (int r = 0; r < R; ++r) tr += Gd[r * RT + r];
-      const double add = 1e-12 * tr / R;
-      if (threadIdx.x < R) Gd[threadIdx.x * RT + threadIdx.x] += add;
-      for (int e = threadIdx.x; e < RT * RT; e += 32) Ld[e] = 0.0;
-      __syncwarp();
-      ok = warp_cholesky<RT>(Gd, Ld, R);
-    }
-    if (threadIdx.x == 0) ok_s = ok ? 1 : 0;
-  }
-  __syncthreads();
-  if (!ok_s) {
-    if (threadIdx.x == 0) atomicOr(status, kDevCholesky);
-    for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) Lf[e] = (e / RT == e % RT) ? 1.f : 0.f;
-  } else {
-    for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) Lf[e] = (float)Ld[e];
+    const int r = e / RT, c = e % RT;
+    float acc = 0.f;
+    for (int k = r > c ? r : c; k < R; ++k) acc = fmaf(Li[k * RT + r], Li[k * RT + c], acc);
+    Gi[e] = acc;
   }
   __syncthreads();
 
@@ -233,27 +269,28 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int r = 0; r < RT; ++r) f[r] = 0.f;
   if (q < Q) {
-    const float *m = M + ((int64_t)p * Q + q) * RT;
-    float y[RT];
+    float m[RT];
 #pragma unroll
-    for (int i = 0; i < RT; ++i) {
-      if (i < R) {
-        float s = m[i];
+    for (int r = 0; r < RT; ++r) m[r] = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const float4 *mp = reinterpret_cast<const float4 *>(M + sp * split_stride +
+                                                          ((int64_t)p * Q + q) * RT);
 #pragma unroll
-        for (int k = 0; k < i; ++k) s = fmaf(-Lf[i * RT + k], y[k], s);
-        y[i] = s / Lf[i * RT + i];
-      } else {
-        y[i] = 0.f;
+      for (int r4 = 0; r4 < RT / 4; ++r4) {
+        const float4 v = mp[r4];
+        m[4 * r4] += v.x; m[4 * r4 + 1] += v.y; m[4 * r4 + 2] += v.z; m[4 * r4 + 3] += v.w;
       }
     }
 #pragma unroll
-    for (int i = RT - 1; i >= 0; --i) {
-      if (i < R) {
-        float s = y[i];
+    for (int r = 0; r < RT; ++r) {
+      const float4 *gr = reinterpret_cast<const float4 *>(Gi + r * RT);
 #pragma unroll
-        for (int k = i + 1; k < RT; ++k)
-          if (k < R) s = fmaf(-Lf[k * RT + i], f[k], s);
-        f[i] = s / Lf[i * RT + i];
+      for (int c4 = 0; c4 < RT / 4; ++c4) {
+        const float4 g = gr[c4];
+        f[4 * c4] = fmaf(m[r], g.x, f[4 * c4]);
+        f[4 * c4 + 1] = fmaf(m[r], g.y, f[4 * c4 + 1]);
+        f[4 * c4 + 2] = fmaf(m[r], g.z, f[4 * c4 + 2]);
+        f[4 * c4 + 3] = fmaf(m[r], g.w, f[4 * c4 + 3]);
       }
     }
   }
@@ -270,16 +307,34 @@ __global__ void __launch_bounds__(256)
   }
   if (q < Q) {
     float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
+    float4 *os = reinterpret_cast<float4 *>(Fs + q * RT);
 #pragma unroll
-    for (int r4 = 0; r4 < RT / 4; ++r4)
-      o[r4] = make_float4(f[4 * r4], f[4 * r4 + 1], f[4 * r4 + 2], f[4 * r4 + 3]);
+    for (int r4 = 0; r4 < RT / 4; ++r4) {
+      const float4 v = make_float4(f[4 * r4], f[4 * r4 + 1], f[4 * r4 + 2], f[4 * r4 + 3]);
+      o[r4] = v;
+      os[r4] = v;
+    }
+  }
+  __syncthreads();
+  if (Ft && q < Q) {
+    for (int r = 0; r < NP; ++r)
+      Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(r < RT ? Fs[q * RT + r] : 0.f);
+  }
+  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
+    const int r = e / RT, c = e % RT;
+    float acc = 0.f;
+    for (int qq = 0; qq < Q; ++qq) acc = fmaf(Fs[qq * RT + r], Fs[qq * RT + c], acc);
+    Gout[(int64_t)p * RT * RT + e] = acc;
   }
 }
 
-// F_p = unit-l2 columns of the replica-p rows of PF (Qd x R), padded to RT.
+// F_p = unit-l2 columns of the replica-p rows of PF (Qd x R), padded to RT,
+// and its Gram.  grid P, 256 threads; dynamic smem Q * RT floats.
 template <int RT>
 __global__ void __launch_bounds__(256)
-    warm_start_kernel(const float *__restrict__ PF, int Q, int S, int R, float *__restrict__ F) {
+    warm_start_kernel(const float *__restrict__ PF, int Q, int S, int R, float *__restrict__ F,
+                      float *__restrict__ Gout) {
+  extern __shared__ __align__(16) float Fs[];
   __shared__ float red[8 * RT], out[RT];
   const int p = blockIdx.x, q = threadIdx.x;
   float f[RT];
@@ -295,73 +350,264 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int r = 0; r < RT; ++r) sq[r] = f[r] * f[r];
   block_sum_rows<RT>(sq, red, out);
+#pragma unroll
+  for (int r = 0; r < RT; ++r) {
+    const float n = sqrtf(out[r]);
+    if (n > 0.f) f[r] = f[r] / n;
+  }
   if (q < Q) {
     float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
+    float4 *os = reinterpret_cast<float4 *>(Fs + q * RT);
 #pragma unroll
     for (int r4 = 0; r4 < RT / 4; ++r4) {
-      float v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = 4 * r4 + u;
-        const float n = sqrtf(out[r]);
-        v[u] = n > 0.f ? f[r] / n : f[r];
-      }
-      o[r4] = make_float4(v[0], v[1], v[2], v[3]);
+      const float4 v = make_float4(f[4 * r4], f[4 * r4 + 1], f[4 * r4 + 2], f[4 * r4 + 3]);
+      o[r4] = v;
+      os[r4] = v;
     }
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
+    const int r = e / RT, c = e % RT;
+    float acc = 0.f;
+    for (int qq = 0; qq < Q; ++qq) acc = fmaf(Fs[qq * RT + r], Fs[qq * RT + c], acc);
+    Gout[(int64_t)p * RT * RT + e] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core path (bf16 / e4m3 modes): both passes of a sweep are GEMMs with
+// K-major bf16 operands.
+//   Xa[p][a][b][c] = bf16(X_p)          (rows (a, b), K = c)
+//   Xc[p][c][a][b] = bf16(X_p)          (rows c, K = (a, b))
+//   M3[c][r]  = sum_(a,b) Xc[c][(a,b)] KR[r][(a,b)],  KR[r][(a,b)] = A[a][r] B[b][r]
+//   Tc[(a,b)][r] = sum_c Xa[(a,b)][c] C[c][r]
+//   M1[a][r] = sum_b Tc[(a,b)][r] B[b][r],  M2[b][r] = sum_a Tc[(a,b)][r] A[a][r]
+// ---------------------------------------------------------------------------
+__global__ void bf16_layouts_kernel(const float *__restrict__ Y, int Q,
+                                    __nv_bfloat16 *__restrict__ Xa,
+                                    __nv_bfloat16 *__restrict__ Xc) {
+  __shared__ float tile[32][33];
+  const int p = blockIdx.z;
+  const int64_t QQ = (int64_t)Q * Q;
+  const int64_t ab0 = (int64_t)blockIdx.y * 32;
+  const int c0 = blockIdx.x * 32;
+  const float *y = Y + (int64_t)p * QQ * Q;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int64_t ab = ab0 + yy;
+    const int c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (ab < QQ && c < Q) {
+      v = y[ab * Q + c];
+      Xa[(int64_t)p * QQ * Q + ab * Q + c] = __float2bfloat16_rn(v);
+    }
+    tile[yy][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int c = c0 + yy;
+    const int64_t ab = ab0 + threadIdx.x;
+    if (ab < QQ && c < Q)
+      Xc[(int64_t)p * QQ * Q + (int64_t)c * QQ + ab] = __float2bfloat16_rn(tile[threadIdx.x][yy]);
+  }
+}
+
+// KR[p][r][(a,b)] = bf16(A[a][r] B[b][r]) for r < NP (zero beyond the rank).
+template <int RT>
+__global__ void kr_kernel(const float *__restrict__ Af, const float *__restrict__ Bf, int Q,
+                          int NP, __nv_bfloat16 *__restrict__ KR) {
+  const int p = blockIdx.y;
+  const int64_t QQ = (int64_t)Q * Q;
+  const int64_t ab = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ab >= QQ) return;
+  const int a = (int)(ab / Q), b = (int)(ab - (int64_t)a * Q);
+  const float *ar = Af + ((int64_t)p * Q + a) * RT, *br = Bf + ((int64_t)p * Q + b) * RT;
+  __nv_bfloat16 *kr = KR + (int64_t)p * NP * QQ + ab;
+#pragma unroll
+  for (int r = 0; r < RT; ++r) kr[r * QQ] = __float2bfloat16_rn(ar[r] * br[r]);
+  for (int r = RT; r < NP; ++r) kr[r * QQ] = __float2bfloat16_rn(0.f);
+}
+
+// M1[p][a][r] = sum_b Tc[p][(a,b)][r] B[p][b][r]     thread (a, r)
+template <int RT>
+__global__ void tc_m1_kernel(const float *__restrict__ Tc, const float *__restrict__ Bf, int Q,
+                             float *__restrict__ M) {
+  const int p = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Q * RT) return;
+  const int a = e / RT, r = e % RT;
+  const float *t = Tc + ((int64_t)p * Q + a) * Q * RT + r;
+  const float *bf = Bf + (int64_t)p * Q * RT + r;
+  float acc = 0.f;
+  for (int b = 0; b < Q; ++b) acc = fmaf(__ldg(t + (int64_t)b * RT), __ldg(bf + b * RT), acc);
+  M[(int64_t)p * Q * RT + e] = acc;
+}
+
+// M2[p][b][r] = sum_a Tc[p][(a,b)][r] A[p][a][r]     thread (b, r)
+template <int RT>
+__global__ void tc_m2_kernel(const float *__restrict__ Tc, const float *__restrict__ Af, int Q,
+                             float *__restrict__ M) {
+  const int p = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Q * RT) return;
+  const int r = e % RT;
+  const float *t = Tc + (int64_t)p * Q * Q * RT + e;
+  const float *af = Af + (int64_t)p * Q * RT + r;
+  float acc = 0.f;
+  for (int a = 0; a < Q; ++a)
+    acc = fmaf(__ldg(t + (int64_t)a * Q * RT), __ldg(af + a * RT), acc);
+  M[(int64_t)p * Q * RT + e] = acc;
 }
 
 static int block_for(int Q) { return ((Q + 31) / 32) * 32; }
 
 template <int RT>
-static void als_run_t(const float *Y, int P, int Q, int R, int iters, AlsBuffers &b,
-                      cudaStream_t st, const Marker &mk) {
+static void solve(const float *M, int nsplit, int64_t split_stride, const float *G1,
+                  const float *G2, float *F, float *Gout, __nv_bfloat16 *Ft, int NP, int P,
+                  int Q, int R, int normalize, int *status, cudaStream_t st) {
+  const size_t smem = (size_t)Q * RT * sizeof(float);
+  als_solve_kernel<RT><<<P, 256, smem, st>>>(M, nsplit, split_stride, G1, G2, F, Gout, Ft, NP, Q,
+                                             R, normalize, status);
+  count_launch();
+}
+
+// fp32 path: SIMT passes over X_p.
+template <int RT>
+static void als_run_simt(const float *Y, int P, int Q, int R, int iters, AlsBuffers &b,
+                         cudaStream_t st, const Marker &mk) {
   const int bq = block_for(Q);
   const size_t smem_h = (size_t)Q * RT * sizeof(float);
   const size_t smem_m2 = ((size_t)Q * RT + 9 * RT) * sizeof(float);
-  cudaFuncSetAttribute(als_h_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-  cudaFuncSetAttribute(als_m2_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
   const dim3 gQP(Q, P);
   const dim3 gM3((Q * RT + 255) / 256, P);
-  auto pass_h_m3_c = [&]() {
+  auto c_update = [&]() {
     mk(kStAlsPass, 1);
     als_h_kernel<RT><<<gQP, bq, smem_h, st>>>(Y, b.Bf, b.H, Q);
+    count_launch();
     mk(kStAlsPass, 0);
     mk(kStAlsSmall, 1);
     als_m3_kernel<RT><<<gM3, 256, 0, st>>>(b.H, b.Af, b.M, Q);
-    als_solve_kernel<RT><<<P, 256, 0, st>>>(b.M, b.Af, b.Bf, b.Cf, Q, R, 0, b.status);
+    count_launch();
+    solve<RT>(b.M, 1, 0, b.GA, b.GB, b.Cf, b.GC, nullptr, 0, P, Q, R, 0, b.status, st);
     mk(kStAlsSmall, 0);
-    count_launch(); count_launch(); count_launch();
   };
   for (int it = 0; it < iters; ++it) {
-    pass_h_m3_c();
+    c_update();
     mk(kStAlsSmall, 1);
     als_m1_kernel<RT><<<gQP, 256, 0, st>>>(b.H, b.Cf, b.M, Q);
-    als_solve_kernel<RT><<<P, 256, 0, st>>>(b.M, b.Bf, b.Cf, b.Af, Q, R, 1, b.status);
+    count_launch();
+    solve<RT>(b.M, 1, 0, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status, st);
     mk(kStAlsSmall, 0);
     mk(kStAlsPass, 1);
     als_m2_kernel<RT><<<gQP, bq, smem_m2, st>>>(Y, b.Af, b.Cf, b.M, Q);
+    count_launch();
     mk(kStAlsPass, 0);
     mk(kStAlsSmall, 1);
-    als_solve_kernel<RT><<<P, 256, 0, st>>>(b.M, b.Af, b.Cf, b.Bf, Q, R, 1, b.status);
+    solve<RT>(b.M, 1, 0, b.GA, b.GC, b.Bf, b.GB, nullptr, 0, P, Q, R, 1, b.status, st);
     mk(kStAlsSmall, 0);
-    count_launch(); count_launch(); count_launch(); count_launch();
   }
-  pass_h_m3_c();
+  c_update();
 }
 
-void als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
+// bf16 / e4m3 modes: both passes on tcgen05 (bf16 copies of X_p in two layouts).
+template <int RT>
+static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffers &b,
+                       cudaStream_t st, const Marker &mk) {
+  const int NP = kAlsNP;
+  const int64_t QQ = (int64_t)Q * Q;
+  mk(kStAlsPass, 1);
+  bf16_layouts_kernel<<<dim3((Q + 31) / 32, (unsigned)((QQ + 31) / 32), P), dim3(32, 8), 0, st>>>(
+      Y, Q, b.Xa, b.Xc);
+  count_launch();
+  mk(kStAlsPass, 0);
+  // M3 = Xc . KR^T (split over K = (a, b)), Tc = Xa . C
+  TcStoreArgs m3{};
+  m3.A = b.Xc; m3.a_inner = QQ; m3.a_rows = (int64_t)P * Q; m3.a_rows_per_z = Q;
+  m3.B = b.KR; m3.b_inner = QQ; m3.b_rows = (int64_t)P * NP; m3.b_rows_per_z = NP;
+  m3.M = Q; m3.N = RT; m3.K = (int)QQ; m3.BN = NP; m3.batch = P; m3.ksplit = b.ksplit;
+  m3.D = b.Mparts; m3.s_split = (int64_t)P * Q * RT; m3.s_z = (int64_t)Q * RT; m3.s_m = RT;
+  TcStoreArgs tc{};
+  tc.A = b.Xa; tc.a_inner = Q; tc.a_rows = (int64_t)P * QQ; tc.a_rows_per_z = (int)QQ;
+  tc.B = b.Ct; tc.b_inner = Q; tc.b_rows = (int64_t)P * NP; tc.b_rows_per_z = NP;
+  tc.M = (int)QQ; tc.N = RT; tc.K = Q; tc.BN = NP; tc.batch = P; tc.ksplit = 1;
+  tc.D = b.H; tc.s_split = 0; tc.s_z = QQ * RT; tc.s_m = RT;
+  const int ks = tc_gemm_splits(m3.K, b.ksplit);
+  const dim3 gKR((unsigned)((QQ + 255) / 256), P);
+  const dim3 gM((Q * RT + 255) / 256, P);
+  bool ok = true;
+  auto c_update = [&]() {
+    mk(kStAlsPass, 1);
+    kr_kernel<RT><<<gKR, 256, 0, st>>>(b.Af, b.Bf, Q, NP, b.KR);
+    count_launch();
+    ok = ok && tc_gemm_store(m3, b.status, st);
+    mk(kStAlsPass, 0);
+    mk(kStAlsSmall, 1);
+    solve<RT>(b.Mparts, ks, (int64_t)P * Q * RT, b.GA, b.GB, b.Cf, b.GC, b.Ct, NP, P, Q, R, 0,
+              b.status, st);
+    mk(kStAlsSmall, 0);
+  };
+  for (int it = 0; it < iters && ok; ++it) {
+    c_update();
+    mk(kStAlsPass, 1);
+    ok = ok && tc_gemm_store(tc, b.status, st);
+    mk(kStAlsPass, 0);
+    mk(kStAlsSmall, 1);
+    tc_m1_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Bf, Q, b.M);
+    count_launch();
+    solve<RT>(b.M, 1, 0, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status, st);
+    tc_m2_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Af, Q, b.M);
+    count_launch();
+    solve<RT>(b.M, 1, 0, b.GA, b.GC, b.Bf, b.GB, nullptr, 0, P, Q, R, 1, b.status, st);
+    mk(kStAlsSmall, 0);
+  }
+  if (ok) c_update();
+  return ok;
+}
+
+bool als_tc_eligible(int Q) { return Q % 8 == 0 && tc_supported(); }
+
+int als_tc_splits(int P, int Q, int desired) {
+  (void)P;
+  return tc_gemm_splits(Q * Q, desired);
+}
+
+bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
              cudaStream_t st, const Marker &mk) {
-  if (RT == 8) als_run_t<8>(Y, P, Q, R, iters, b, st, mk);
-  else if (RT == 16) als_run_t<16>(Y, P, Q, R, iters, b, st, mk);
-  else als_run_t<32>(Y, P, Q, R, iters, b, st, mk);
+  for (int RTi : {8, 16, 32}) {
+    if (RT != RTi) continue;
+    const size_t smem = (size_t)Q * RT * sizeof(float);
+    if (smem > 48 * 1024) {
+      if (RT == 8) cudaFuncSetAttribute(als_solve_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (RT == 16) cudaFuncSetAttribute(als_solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (RT == 32) cudaFuncSetAttribute(als_solve_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+  }
+  if (b.use_tc) {
+    if (RT == 8) return als_run_tc<8>(Y, P, Q, R, iters, b, st, mk);
+    if (RT == 16) return als_run_tc<16>(Y, P, Q, R, iters, b, st, mk);
+    return als_run_tc<32>(Y, P, Q, R, iters, b, st, mk);
+  }
+  cudaFuncSetAttribute(als_h_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(als_h_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(als_h_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(als_m2_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(als_m2_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(als_m2_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  if (RT == 8) als_run_simt<8>(Y, P, Q, R, iters, b, st, mk);
+  else if (RT == 16) als_run_simt<16>(Y, P, Q, R, iters, b, st, mk);
+  else als_run_simt<32>(Y, P, Q, R, iters, b, st, mk);
+  return true;
 }
 
-void warm_start(const float *PF, int P, int Q, int S, int R, int RT, float *F,
+void warm_start(const float *PF, int P, int Q, int S, int R, int RT, float *F, float *G,
                 cudaStream_t st) {
-  if (RT == 8) warm_start_kernel<8><<<P, 256, 0, st>>>(PF, Q, S, R, F);
-  else if (RT == 16) warm_start_kernel<16><<<P, 256, 0, st>>>(PF, Q, S, R, F);
-  else warm_start_kernel<32><<<P, 256, 0, st>>>(PF, Q, S, R, F);
+  const size_t smem = (size_t)Q * RT * sizeof(float);
+  if (RT == 8) warm_start_kernel<8><<<P, 256, smem, st>>>(PF, Q, S, R, F, G);
+  else if (RT == 16) warm_start_kernel<16><<<P, 256, smem, st>>>(PF, Q, S, R, F, G);
+  else {
+    cudaFuncSetAttribute(warm_start_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    warm_start_kernel<32><<<P, 256, smem, st>>>(PF, Q, S, R, F, G);
+  }
   count_launch();
 }
 

@@ -155,6 +155,16 @@ struct TcShape {
   int tmem_cols;        // power of two >= BN
   int zdiv;             // batch index z -> rows (z / zdiv) * hi + (z % zdiv) * lo
   int a_hi, a_lo, b_hi, b_lo;
+  int ksplit;           // > 1: blockIdx.x is the K split (a single N tile)
+};
+
+// Plain fp32 store: D[split * s_split + z * s_z + m * s_m + n] (split-K partials).
+struct TcStoreEpi {
+  float *D;
+  int64_t s_split, s_z, s_m;
+  __device__ __forceinline__ void operator()(int z, int m, int n, float v) const {
+    D[(int64_t)blockIdx.x * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n] = v;
+  }
 };
 
 // Mode-2 epilogue: row m = k * I + i, column c of V_all -> every replica owning c.
@@ -208,12 +218,18 @@ __global__ void __launch_bounds__(128, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int z = blockIdx.z;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * sh.BN;
+  const int m0 = blockIdx.y * kBM, n0 = sh.ksplit > 1 ? 0 : blockIdx.x * sh.BN;
   const int a_row0 = (z / sh.zdiv) * sh.a_hi + (z % sh.zdiv) * sh.a_lo + m0;
   const int b_row0 = (z / sh.zdiv) * sh.b_hi + (z % sh.zdiv) * sh.b_lo + n0;
   constexpr int kElemsPerRow = KIND == 0 ? 64 : 128;   // 128 bytes of K
   constexpr int kUmmaK = KIND == 0 ? 16 : 32;           // 32 bytes of K per MMA
-  const int nk = (sh.K + kElemsPerRow - 1) / kElemsPerRow;
+  const int nk_all = (sh.K + kElemsPerRow - 1) / kElemsPerRow;
+  int kb_begin = 0, nk = nk_all;
+  if (sh.ksplit > 1) {
+    const int per = (nk_all + sh.ksplit - 1) / sh.ksplit;
+    kb_begin = blockIdx.x * per;
+    nk = min(per, nk_all - kb_begin);   // the host makes every split non-empty
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -241,8 +257,8 @@ __global__ void __launch_bounds__(128, 1)
         break;
       }
       mbar_expect_tx(&full[s], a_bytes + b_bytes);
-      tma_load_2d(sA + s * a_bytes, &tmA, &full[s], kb * kElemsPerRow, a_row0);
-      tma_load_2d(sB + s * b_bytes, &tmB, &full[s], kb * kElemsPerRow, b_row0);
+      tma_load_2d(sA + s * a_bytes, &tmA, &full[s], (kb_begin + kb) * kElemsPerRow, a_row0);
+      tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb_begin + kb) * kElemsPerRow, b_row0);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -341,7 +357,8 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
   if (cudaFuncSetAttribute(tc_gemm_kernel<KIND, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return false;
-  dim3 grid((sh.N + sh.BN - 1) / sh.BN, (sh.M + kBM - 1) / kBM, batch);
+  dim3 grid(sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN, (sh.M + kBM - 1) / kBM,
+            batch);
   tc_gemm_kernel<KIND, Epi><<<grid, 128, smem, st>>>(ma, mb, sh, epi, status);
   count_launch();
   count_tc_launch();
@@ -369,6 +386,7 @@ bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st) {
   if (!make_map(&ma, a.X, fp8, a.J, M, kBM) || !make_map(&mb, a.Vt, fp8, a.J, a.Qd, BN))
     return false;
   TcShape sh{};
+  sh.ksplit = 1;
   sh.M = static_cast<int>(M); sh.N = a.Qd; sh.K = static_cast<int>(a.J); sh.BN = BN;
   sh.zdiv = 1; sh.a_hi = 0; sh.a_lo = 0; sh.b_hi = 0; sh.b_lo = 0;
   Mode2TcEpi epi{static_cast<__nv_bfloat16 *>(a.T), a.slice_scale, a.I, a.P, a.Q, a.S};
@@ -387,12 +405,39 @@ bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
   if (!make_map(&ma, a.Ut, false, a.I, rowsA, kBM) || !make_map(&mb, a.T, false, a.I, rowsB, BN))
     return false;
   TcShape sh{};
+  sh.ksplit = 1;
   sh.M = a.Q; sh.N = a.Q; sh.K = static_cast<int>(a.I); sh.BN = BN;
   sh.zdiv = a.P;                   // z = k * P + p
   sh.a_hi = 0; sh.a_lo = a.Q;      // A rows: p * Q
   sh.b_hi = a.P * a.Q; sh.b_lo = a.Q;   // B rows: (k * P + p) * Q
   Mode1TcEpi epi{a.T2, a.t, a.P, a.Q};
   return launch_tc<0>(ma, mb, sh, static_cast<int>(a.t * a.P), epi, status, st);
+}
+
+bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
+  if (g.BN % 32 || g.BN > 256 || g.BN < 32) return false;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, g.A, false, g.a_inner, g.a_rows, kBM) ||
+      !make_map(&mb, g.B, false, g.b_inner, g.b_rows, g.BN))
+    return false;
+  TcShape sh{};
+  sh.M = g.M; sh.N = g.N; sh.K = g.K; sh.BN = g.BN;
+  sh.zdiv = 1; sh.a_hi = g.a_rows_per_z; sh.a_lo = 0; sh.b_hi = g.b_rows_per_z; sh.b_lo = 0;
+  const int nk = (g.K + 63) / 64;
+  int ks = g.ksplit < 1 ? 1 : (g.ksplit > nk ? nk : g.ksplit);
+  const int per = (nk + ks - 1) / ks;
+  ks = (nk + per - 1) / per;            // every split gets at least one K block
+  sh.ksplit = ks;
+  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m};
+  if (ks > 1 && (g.N > g.BN)) return false;
+  return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st);
+}
+
+int tc_gemm_splits(int K, int ksplit) {
+  const int nk = (K + 63) / 64;
+  int ks = ksplit < 1 ? 1 : (ksplit > nk ? nk : ksplit);
+  const int per = (nk + ks - 1) / ks;
+  return (nk + per - 1) / per;
 }
 
 }  // namespace octen

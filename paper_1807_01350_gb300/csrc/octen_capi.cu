@@ -65,6 +65,12 @@ struct octen_ctx {
   float *PA = nullptr, *PB = nullptr, *e = nullptr;
   float *At = nullptr, *Bt = nullptr, *Ct = nullptr, *Ah = nullptr, *Bh = nullptr, *Ch = nullptr;
   float *M = nullptr, *H = nullptr, *csolve = nullptr;
+  float *GA = nullptr, *GB = nullptr, *GC = nullptr;
+  // tensor-core ALS (bf16 / e4m3 modes with Q % 8 == 0)
+  bool als_tc = false;
+  int als_ks = 1;
+  __nv_bfloat16 *Xa = nullptr, *Xc = nullptr, *KR = nullptr, *Ctb = nullptr;
+  float *Mparts = nullptr;
   int *perm = nullptr;
   double *scales = nullptr;
   int *dstatus = nullptr;
@@ -412,7 +418,17 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
             x->alloc(x->Bh, P * Q * RT) && x->alloc(x->Ch, P * Q * RT) &&
             x->alloc(x->M, P * Q * RT) && x->alloc(x->H, P * Q * Q * RT) &&
             x->alloc(x->perm, P * c.R) && x->alloc(x->scales, P * 2 * c.R) &&
-            x->alloc(x->dstatus, 1) && x->alloc(x->dfit, 2);
+            x->alloc(x->dstatus, 1) && x->alloc(x->dfit, 2) && x->alloc(x->GA, P * RT * RT) &&
+            x->alloc(x->GB, P * RT * RT) && x->alloc(x->GC, P * RT * RT);
+  if (ok && x->use_tc && als_tc_eligible(c.Q)) {
+    const int mt = (c.Q + 127) / 128;
+    const int want = (4 * 152 + mt * c.P - 1) / (mt * c.P);
+    x->als_ks = als_tc_splits(c.P, c.Q, want < 1 ? 1 : want);
+    ok = x->alloc(x->Xa, P * Q * Q * Q) && x->alloc(x->Xc, P * Q * Q * Q) &&
+         x->alloc(x->KR, P * kAlsNP * Q * Q) && x->alloc(x->Ctb, P * kAlsNP * Q) &&
+         x->alloc(x->Mparts, (size_t)x->als_ks * P * Q * RT);
+    x->als_tc = ok;
+  }
   void *ut = nullptr, *vt = nullptr;
   if (ok) {
     ok = cudaMalloc(&ut, P * Q * c.I * elem_size(x->tu)) == cudaSuccess &&
@@ -511,13 +527,25 @@ octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const floa
   x->mark(kStWarm, 1);
   project(x, x->U32, c.I, x->A, x->PA);
   project(x, x->V32, c.J, x->B, x->PB);
-  warm_start(x->PA, c.P, c.Q, c.S, c.R, RT, x->At, x->st);
-  warm_start(x->PB, c.P, c.Q, c.S, c.R, RT, x->Bt, x->st);
+  warm_start(x->PA, c.P, c.Q, c.S, c.R, RT, x->At, x->GA, x->st);
+  warm_start(x->PB, c.P, c.Q, c.S, c.R, RT, x->Bt, x->GB, x->st);
   x->mark(kStWarm, 0);
-  AlsBuffers ab{x->At, x->Bt, x->Ct, x->M, x->H, x->dstatus};
+  AlsBuffers ab;
+  ab.Af = x->At; ab.Bf = x->Bt; ab.Cf = x->Ct; ab.GA = x->GA; ab.GB = x->GB; ab.GC = x->GC;
+  ab.M = x->M; ab.H = x->H; ab.status = x->dstatus;
+  ab.use_tc = x->als_tc; ab.Xa = x->Xa; ab.Xc = x->Xc; ab.KR = x->KR; ab.Ct = x->Ctb;
+  ab.Mparts = x->Mparts; ab.ksplit = x->als_ks;
   Marker mk;
   if (x->timing) { mk.fn = &octen_ctx::mark_cb; mk.arg = x; }
-  als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st, mk);
+  if (!als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st, mk)) {
+    // a tensor-core launch was refused: redo the CP from the warm start on SIMT
+    cudaGetLastError();
+    x->als_tc = false;
+    ab.use_tc = false;
+    warm_start(x->PA, c.P, c.Q, c.S, c.R, RT, x->At, x->GA, x->st);
+    warm_start(x->PB, c.P, c.Q, c.S, c.R, RT, x->Bt, x->GB, x->st);
+    als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st, mk);
+  }
   // 3. anchor match against u^T A_prev, v^T B_prev
   x->mark(kStAlign, 1);
   align_replicas(x->At, x->Bt, x->Ct, x->PA, x->PB, c.P, c.Q, c.S, c.R, RT, x->Ah, x->Bh,

@@ -87,6 +87,20 @@ bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st);
 bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st);
 void count_tc_launch();
 
+// Generic bf16 tcgen05 GEMM with a plain fp32 store, used by the replica ALS:
+//   D[split][z](m, n) = sum_{k in split} A[z * a_rows_per_z + m][k] * B[z * b_rows_per_z + n][k]
+// A and B are row-major bf16 [rows][inner] (K contiguous).  Stored at
+// D + split * s_split + z * s_z + m * s_m + n for m < M, n < N.  With ksplit > 1
+// the K blocks are divided among that many CTAs per tile (N <= BN then).
+struct TcStoreArgs {
+  const void *A; int64_t a_inner, a_rows; int a_rows_per_z;
+  const void *B; int64_t b_inner, b_rows; int b_rows_per_z;
+  int M, N, K, BN, batch, ksplit;
+  float *D; int64_t s_split, s_z, s_m;
+};
+bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st);
+int tc_gemm_splits(int K, int ksplit);   // the split count tc_gemm_store will use
+
 // Mode-3 contraction and summary update: Y[p][a][b][c] +=
 //   sum_k T2[p][k][a][b] * W_all[k][col_p(c)].
 void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
@@ -107,17 +121,32 @@ void quantize_e4m3(const __nv_bfloat16 *X, int64_t t, int64_t IJ, __nv_fp8_e4m3 
 // Replica CP-ALS (all P replicas in each launch).  Factors are P x Q x RT
 // (RT = R rounded up to 8, padded columns zero).
 // ---------------------------------------------------------------------------
-struct AlsBuffers {
-  float *Af, *Bf, *Cf;   // current factors
-  float *M;              // MTTKRP result
-  float *H;              // P x Q x Q x RT: H[a][c][r] = sum_b X[a][b][c] B[b][r]
-  int *status;
-};
-void als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
-             cudaStream_t st, const Marker &mk = Marker());
+constexpr int kAlsNP = 32;   // padded rank rows of the tensor-core ALS operands
 
-// Warm start: F_p = unit columns of rows(p) of PF (Qd x R) into P x Q x RT.
-void warm_start(const float *PF, int P, int Q, int S, int R, int RT, float *F,
+struct AlsBuffers {
+  float *Af, *Bf, *Cf;   // current factors, P x Q x RT
+  float *GA, *GB, *GC;   // their Grams, P x RT x RT
+  float *M;              // MTTKRP result, P x Q x RT
+  float *H;              // P x Q x Q x RT: SIMT pass-1 product or the Tc GEMM output
+  int *status;
+  // tensor-core path (bf16 / e4m3 modes, Q % 8 == 0)
+  bool use_tc = false;
+  __nv_bfloat16 *Xa = nullptr, *Xc = nullptr;   // P x Q^3 each
+  __nv_bfloat16 *KR = nullptr;                  // P x kAlsNP x Q^2
+  __nv_bfloat16 *Ct = nullptr;                  // P x kAlsNP x Q
+  float *Mparts = nullptr;                      // ksplit x P x Q x RT
+  int ksplit = 1;
+};
+// Returns false if a tensor-core launch was refused (the caller then reruns
+// the SIMT path).
+bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
+             cudaStream_t st, const Marker &mk = Marker());
+bool als_tc_eligible(int Q);
+int als_tc_splits(int P, int Q, int desired);
+
+// Warm start: F_p = unit columns of rows(p) of PF (Qd x R) into P x Q x RT, and
+// the Gram of each F_p into G (P x RT x RT).
+void warm_start(const float *PF, int P, int Q, int S, int R, int RT, float *F, float *G,
                 cudaStream_t st);
 
 // Anchor match (FP64).  ref rows = PA/PB rows [0, S).
