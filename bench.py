@@ -133,8 +133,20 @@ def stage_work(wl, prec):
         "mode2": (2.0 * t * I * J * Qd, t * I * J * xb + Qd * J * xb + t * I * P * Q * (4 if prec == "fp32" else 2)),
         "mode1": (2.0 * t * P * Q * Q * I, t * P * Q * I * (4 if prec == "fp32" else 2) + P * Q * I * (4 if prec == "fp32" else 2)),
         "mode3": (2.0 * t * P * Q ** 3, 2.0 * 4 * P * Q ** 3 + 4.0 * t * P * Q * Q),
-        "als_pass": (2.0 * P * Q ** 3 * R, 4.0 * P * Q ** 3),
+        "als_gemm": (2.0 * P * Q ** 3 * R, 4.0 * P * Q ** 3),
     }
+
+
+def als_gemm_tc_bytes(wl):
+    """Algorithmic bytes per tensor-core ALS GEMM launch, averaged over an
+    append: the M3 GEMM reads the bf16 copy Xc and the Khatri-Rao operand, the
+    Tc GEMM reads the bf16 copy Xa and writes Tc (fp32, rank padded to RT)."""
+    P, Q, R, it = wl.P, wl.Q, wl.R, wl.als_iters
+    RT = 8 if R <= 8 else (16 if R <= 16 else 32)
+    NP = 32
+    m3 = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q * Q
+    tc = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q + 4.0 * P * Q * Q * RT
+    return ((it + 1) * m3 + it * tc) / (2 * it + 1)
 
 
 def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic, tc_stages=()):
@@ -142,6 +154,9 @@ def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic, tc_stages=()):
     sec = ms_per_launch / 1e3
     if stage == "mode3":
         bound, peak, unit, achieved = "hbm", pk["hbm"], "GB/s", nbytes / sec / 1e9
+    elif stage == "als_gemm" and stage in tc_stages:
+        bound, peak, unit = "hbm", pk["hbm"], "GB/s"
+        achieved = als_gemm_tc_bytes(wl) / sec / 1e9
     elif stage in tc_stages:
         peak = pk["bf16_sus"] * (2.0 if prec == "fp8" and stage == "mode2" else 1.0)
         bound, unit, achieved = "tensor", "TFLOP/s", flops / sec / 1e12
@@ -228,6 +243,8 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
     fit = g.fit(d["X"][:k])
     # the two tensor-core contractions run once per append when the path is taken
     tc_stages = ("mode2", "mode1") if tc_launches >= 2 * steps else ()
+    if tc_launches >= (2 + 2 * wl.als_iters + 1) * steps:
+        tc_stages = tc_stages + ("als_gemm",)
     out = dict(ms=ms, steps=steps, slices=steps * t, stages=stages, fit=fit,
                launches=launches, tc_launches=tc_launches, tc_stages=tc_stages,
                clocks=clk.summary())
@@ -349,8 +366,13 @@ def main():
     ap.add_argument("--compress-only", action="store_true",
                     help="time octen_compress alone on --slices slices (profiling case)")
     ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--existing", type=int, default=0,
+                    help="override the number of existing slices (small profiling cases)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.existing > 0:
+        import dataclasses
+        wl = dataclasses.replace(wl, t_old=args.existing)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     args.warmup = max(args.warmup, 3)
@@ -392,14 +414,14 @@ def main():
     pk = peaks()
     st = main_run["stages"]
     timed = {k: v for k, v in st.items() if v[1] > 0}
-    dominant = max(("mode2", "mode1", "mode3", "als_pass"), key=lambda s: st[s][0])
+    dominant = max(("mode2", "mode1", "mode3", "als_gemm"), key=lambda s: st[s][0])
     ms_launch = st[dominant][0] / st[dominant][1]
     tcs = main_run["tc_stages"]
     roof = roofline_for(dominant, ms_launch, wl, args.prec, pk,
                         traffic_from_profiles(dominant, args.prec), tcs)
     comp = {s: roofline_for(s, st[s][0] / st[s][1], wl, args.prec, pk,
                             traffic_from_profiles(s, args.prec), tcs)
-            for s in ("mode2", "mode1", "mode3", "als_pass") if st[s][1]}
+            for s in ("mode2", "mode1", "mode3", "als_gemm") if st[s][1]}
     value = whole_job_rate(main_run["slices"], main_run["ms"] / 1e3, world)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "slices/s", "n_gpus": world,

@@ -151,6 +151,15 @@ octen_status octen_compress_noalloc(const octen_config *cfg, void *cuda_stream, 
                                     int64_t t, const float *U_all, const float *V_all,
                                     const float *W_all, float *Z);
 
+/* Checkpoint and resume (not in the paper; the state is what its complexity
+ * analysis says OCTen keeps: summaries, projections, factors).  octen_save
+ * writes the full state of an initialised context to a file; octen_load
+ * creates a new context on `cuda_stream` from such a file.  A loaded context
+ * continues the stream exactly as the saved one would (same results, bit for
+ * bit, on the same GPU and library build).  EINVAL on a bad path or file. */
+octen_status octen_save(const octen_ctx *ctx, const char *path);
+octen_status octen_load(const char *path, void *cuda_stream, octen_ctx **out);
+
 /* Releases the context and its device memory (NULL is allowed). */
 void octen_destroy(octen_ctx *ctx);
 
@@ -171,8 +180,10 @@ uint64_t octen_tc_launch_count(void);
 /* Stage timers (measurement aid, not part of the method).  With timing on,
  * every append records CUDA events on the context's stream around each
  * stage: quantize, mode2, mode1, mode3 (the three contractions of the
- * compression), warm_start, als_pass (the two passes over each replica per
- * sweep), als_small (the other CP-ALS kernels), align, lift, c_solve.
+ * compression), warm_start, als_gemm (the two passes over each replica per
+ * sweep: tcgen05 GEMMs in bf16 / e4m3 mode, SIMT kernels in fp32 mode),
+ * als_aux (the other CP-ALS data kernels), als_solve (the R x R normal-equation
+ * solves), align, lift, c_solve.
  * octen_stage_times fills ms[i] (accumulated milliseconds) and launches[i]
  * (timed intervals) for i < octen_stage_count(); either may be NULL. */
 int octen_stage_count(void);

@@ -63,6 +63,8 @@ def lib() -> ctypes.CDLL:
         L.octen_compress.argtypes = [ctypes.POINTER(_Config), vp, vp, i64, f32p, f32p, f32p, f32p]
         L.octen_compress_noalloc.argtypes = [ctypes.POINTER(_Config), vp, vp, i64, f32p, f32p,
                                              f32p, f32p]
+        L.octen_save.argtypes = [vp, ctypes.c_char_p]
+        L.octen_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
         L.octen_destroy.argtypes = [vp]
         L.octen_destroy.restype = None
         L.octen_last_error.argtypes = [vp]
@@ -83,6 +85,7 @@ def lib() -> ctypes.CDLL:
         for name in ("octen_create", "octen_init", "octen_append", "octen_get_factors",
                      "octen_fit", "octen_get_replicas", "octen_get_replica_factors",
                      "octen_compress", "octen_compress_noalloc", "octen_set_timing",
+                     "octen_save", "octen_load",
                      "octen_stage_times",
                      "octen_reset_stage_times"):
             getattr(L, name).restype = ctypes.c_int
@@ -222,6 +225,31 @@ class Octen:
             self._h, int(which), At.ctypes.data, Bt.ctypes.data, Ct.ctypes.data,
             perm.ctypes.data, scales.ctypes.data))
         return At, Bt, Ct, perm, scales
+
+    def save(self, path: str):
+        """Checkpoint the whole state to `path`."""
+        self._check(self._lib.octen_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Octen":
+        """A context resumed from a checkpoint written by `save`."""
+        L = lib()
+        h = ctypes.c_void_p()
+        st = L.octen_load(os.fsencode(path), _stream_handle(stream), ctypes.byref(h))
+        if st != 0:
+            raise OctenError(st, f"octen_load({path!r}) failed")
+        self = cls.__new__(cls)
+        self._lib = L
+        self._h = h
+        # read the shape back from the file header (magic, then octen_config)
+        with open(path, "rb") as f:
+            f.read(8)
+            cfg = _Config.from_buffer_copy(f.read(ctypes.sizeof(_Config)))
+        self.cfg = cfg
+        self.prec = {v: k for k, v in PREC.items()}[cfg.prec]
+        self.I, self.J, self.R, self.P, self.Q, self.S = cfg.I, cfg.J, cfg.R, cfg.P, cfg.Q, cfg.S
+        self.Qd = cfg.S + cfg.P * (cfg.Q - cfg.S)
+        return self
 
     def set_timing(self, on: bool = True):
         self._check(self._lib.octen_set_timing(self._h, int(bool(on))))

@@ -147,74 +147,124 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x < RT) M[((int64_t)p * Q + b) * RT + threadIdx.x] = out[threadIdx.x];
 }
 
-// Cholesky of an R x R SPD matrix held by one warp, lane i owning row i in
-// registers (a[k] = G[i][k] for k <= i): right-looking, the pivot column is
-// broadcast with shuffles and every lane updates its own row.  On return
-// a[k] = L[i][k].  Returns false if a pivot is not positive (uniform).
+// 1/sqrt(d) in fp64 by two Newton-Raphson steps y <- y (3 - d y^2) / 2 on
+// f(y) = y^-2 - d, seeded with the fp32 estimate (each step squares the
+// relative error: ~2^-22 -> 2^-44 -> below fp64 rounding).  Only fp64 multiplies
+// and adds on the pivot's critical path; outside the fp32 exponent range the
+// plain sqrt / division are used.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  y = y * fma(-0.5 * d, y * y, 1.5);
+  y = y * fma(-0.5 * d, y * y, 1.5);
+  return y;
+}
+
+// Warp 0: factor G1 * G2 = L L^T in fp64 and write L^-1 (fp32, lower
+// triangular; identity on failure) to Li ([RT][RT + 1]).  *ok_out gets the
+// success flag.  The matrix lives in shared memory (Ad, fp64, padded rows) and
+// lane i owns row i; the loops are kept rolled so that the code stays in the
+// instruction cache (this runs once per launch on a single warp).
+//   right-looking Cholesky: for each pivot j, lane j forms L[j][j] (Newton
+//   rsqrt), lanes i > j scale their L[i][j] and update a[i][k] for j < k <= i;
+//   then L^-1 row by row: lane k finishes its row, lanes below subtract
+//   L[i][k] times it.
 template <int RT>
-__device__ __forceinline__ bool warp_chol_rows(double (&a)[RT], int R) {
+__device__ void chol_inverse_to_smem(const float *g1, const float *g2, int R, double *Ad,
+                                     double *dinv, float *Li, int *ok_out) {
+  constexpr int LD = RT + 1;
   const int lane = threadIdx.x & 31;
   bool ok = true;
-#pragma unroll
-  for (int j = 0; j < RT; ++j) {
-    if (j < R) {
-      const double d = __shfl_sync(0xffffffffu, a[j], j);
-      const bool good = d > 0.0;
-      ok = ok && good;
-      const double piv = good ? sqrt(d) : 1.0;
-      const double inv = 1.0 / piv;
-      double l = 0.0;
-      if (lane == j) l = piv;
-      else if (lane > j && lane < R) l = a[j] * inv;
-      a[j] = l;
-#pragma unroll
-      for (int k = j + 1; k < RT; ++k) {
-        const double lk = __shfl_sync(0xffffffffu, l, k);
-        if (k < R && k <= lane && lane < R) a[k] = fma(-l, lk, a[k]);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    double add = 0.0;
+    if (attempt == 1) {
+      // load the diagonal by 1e-12 * trace / R and retry once
+      double tr = lane < R ? (double)g1[lane * RT + lane] * (double)g2[lane * RT + lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      add = 1e-12 * tr / R;
+    }
+    if (lane < R) {
+      for (int k = 0; k <= lane; ++k)
+        Ad[lane * LD + k] = (double)g1[lane * RT + k] * (double)g2[lane * RT + k] +
+                            (k == lane ? add : 0.0);
+    }
+    ok = true;
+    for (int j = 0; j < R; ++j) {
+      __syncwarp();
+      if (lane == j) {
+        const double d = Ad[j * LD + j];
+        const double inv = d > 0.0 ? rsqrt_nr(d) : 0.0;
+        Ad[j * LD + j] = d > 0.0 ? d * inv : 1.0;
+        dinv[j] = inv;
+      }
+      __syncwarp();
+      const double inv = dinv[j];
+      if (!(inv > 0.0)) { ok = false; break; }
+      if (lane > j && lane < R) Ad[lane * LD + j] *= inv;
+      __syncwarp();   // every L[k][j] is scaled before any lane reads it
+      if (lane > j && lane < R) {
+        const double l = Ad[lane * LD + j];
+        int k = j + 1;
+        for (; k + 3 <= lane; k += 4) {
+          const double l0 = Ad[k * LD + j], l1 = Ad[(k + 1) * LD + j];
+          const double l2 = Ad[(k + 2) * LD + j], l3 = Ad[(k + 3) * LD + j];
+          Ad[lane * LD + k] = fma(-l, l0, Ad[lane * LD + k]);
+          Ad[lane * LD + k + 1] = fma(-l, l1, Ad[lane * LD + k + 1]);
+          Ad[lane * LD + k + 2] = fma(-l, l2, Ad[lane * LD + k + 2]);
+          Ad[lane * LD + k + 3] = fma(-l, l3, Ad[lane * LD + k + 3]);
+        }
+        for (; k <= lane; ++k) Ad[lane * LD + k] = fma(-l, Ad[k * LD + j], Ad[lane * LD + k]);
       }
     }
+    if (ok) break;
   }
-  return ok;
+  __syncwarp();
+  // L^-1 (fp32): Li rows accumulate -sum_{k<i} L[i][k] X[k][.] until row i is finished
+  if (lane < RT)
+    for (int j = 0; j < RT; ++j) Li[lane * LD + j] = 0.f;
+  __syncwarp();
+  for (int k = 0; k < R && ok; ++k) {
+    if (lane == k) {
+      const float inv = (float)dinv[k];
+      for (int j = 0; j <= k; ++j) Li[k * LD + j] = ((j == k ? 1.f : 0.f) + Li[k * LD + j]) * inv;
+    }
+    __syncwarp();
+    if (lane > k && lane < R) {
+      const float lik = (float)Ad[lane * LD + k];
+      for (int j = 0; j <= k; ++j) Li[lane * LD + j] = fmaf(-lik, Li[k * LD + j], Li[lane * LD + j]);
+    }
+    __syncwarp();
+  }
+  if (!ok && lane < RT) {
+    for (int j = 0; j < RT; ++j) Li[lane * LD + j] = (j == lane) ? 1.f : 0.f;
+  }
+  if (lane == 0) *ok_out = ok ? 1 : 0;
 }
 
-// Loads row `lane` of G1 * G2 (Hadamard, fp64) into a[], diagonal loaded by `add`.
+// Gram of the Q x RT factor held in shared memory: Gout[r][s] = sum_q F[q][r] F[q][s].
+// Each thread accumulates its entries over q with independent chains.
 template <int RT>
-__device__ __forceinline__ void load_gram_rows(const float *g1, const float *g2, int R,
-                                               double add, double (&a)[RT]) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void smem_gram(const float *Fs, int Q, float *Gout) {
+  constexpr int kPer = (RT * RT + 255) / 256;
+  float acc[kPer];
+  int rr[kPer], cc[kPer];
 #pragma unroll
-  for (int k = 0; k < RT; ++k) {
-    double v = 0.0;
-    if (lane < R && k <= lane) v = (double)g1[lane * RT + k] * (double)g2[lane * RT + k];
-    if (k == lane && lane < R) v += add;
-    a[k] = v;
+  for (int u = 0; u < kPer; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    rr[u] = e < RT * RT ? e / RT : 0;
+    cc[u] = e < RT * RT ? e % RT : 0;
+    acc[u] = 0.f;
   }
-}
-
-// Warp 0: factor G1 * G2 (fp64) and leave L in Lf (fp32, identity on failure),
-// the reciprocal diagonal in invd and the success flag in *ok_out.  Kept out of
-// line so that its registers do not add to the substitution's.
-template <int RT>
-__device__ __noinline__ void chol_to_smem(const float *g1, const float *g2, int R, float *Lf,
-                                          float *invd, int *ok_out) {
-  double a[RT];
-  load_gram_rows<RT>(g1, g2, R, 0.0, a);
-  bool ok = warp_chol_rows<RT>(a, R);
-  if (!ok) {
-    // load the diagonal by 1e-12 * trace / R and retry once
-    double tr = threadIdx.x < R ? (double)g1[threadIdx.x * RT + threadIdx.x] *
-                                      (double)g2[threadIdx.x * RT + threadIdx.x]
-                                : 0.0;
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-    load_gram_rows<RT>(g1, g2, R, 1e-12 * tr / R, a);
-    ok = warp_chol_rows<RT>(a, R);
-  }
-  const int i = threadIdx.x;
+#pragma unroll 4
+  for (int q = 0; q < Q; ++q) {
 #pragma unroll
-  for (int k = 0; k < RT; ++k)
-    if (i < RT) Lf[i * RT + k] = (ok && k <= i && i < R) ? (float)a[k] : (k == i ? 1.f : 0.f);
-  if (i < RT) invd[i] = (ok && i < R) ? (float)(1.0 / a[i]) : 1.f;
-  if (i == 0) *ok_out = ok ? 1 : 0;
+    for (int u = 0; u < kPer; ++u) acc[u] = fmaf(Fs[q * RT + rr[u]], Fs[q * RT + cc[u]], acc[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    if (e < RT * RT) Gout[e] = acc[u];
+  }
 }
 
 // F_p = M_p (G1_p * G2_p)^-1 with G1, G2 the cached R x R Grams of the other two
@@ -231,35 +281,23 @@ __global__ void __launch_bounds__(256, 1)
                      __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int R, int normalize,
                      int *status) {
   extern __shared__ __align__(16) float Fs[];   // [Q][RT]
-  __shared__ float Lf[RT * RT], invd[RT];
-  __shared__ __align__(16) float Li[RT * RT], Gi[RT * RT];
+  __shared__ __align__(16) float Gi[RT * RT];
+  __shared__ float Li[RT * (RT + 1)];
+  __shared__ double Ad[RT * (RT + 1)], dinv[RT];
   __shared__ float red[8 * RT], out[RT];
   __shared__ int ok_s;
   const int p = blockIdx.x;
   const float *g1 = G1 + (int64_t)p * RT * RT, *g2 = G2 + (int64_t)p * RT * RT;
-  if (threadIdx.x < 32) chol_to_smem<RT>(g1, g2, R, Lf, invd, &ok_s);
+  if (threadIdx.x < 32) chol_inverse_to_smem<RT>(g1, g2, R, Ad, dinv, Li, &ok_s);
   __syncthreads();
   if (!ok_s && threadIdx.x == 0) atomicOr(status, kDevCholesky);
 
-  // inverse of the Gram Hadamard product: Linv by warp 0 (lane j owns column j),
-  // then Ginv = Linv^T Linv by all threads
-  if (threadIdx.x < RT) {
-    const int j = threadIdx.x;
-    for (int i = 0; i < RT; ++i) Li[i * RT + j] = 0.f;
-    if (j < R) {
-      Li[j * RT + j] = invd[j];
-      for (int i = j + 1; i < R; ++i) {
-        float acc = 0.f;
-        for (int k = j; k < i; ++k) acc = fmaf(Lf[i * RT + k], Li[k * RT + j], acc);
-        Li[i * RT + j] = -acc * invd[i];
-      }
-    }
-  }
-  __syncthreads();
+  // inverse of the Gram Hadamard product: Ginv = L^-T L^-1 by all threads
   for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
     const int r = e / RT, c = e % RT;
     float acc = 0.f;
-    for (int k = r > c ? r : c; k < R; ++k) acc = fmaf(Li[k * RT + r], Li[k * RT + c], acc);
+    for (int k = r > c ? r : c; k < R; ++k)
+      acc = fmaf(Li[k * (RT + 1) + r], Li[k * (RT + 1) + c], acc);
     Gi[e] = acc;
   }
   __syncthreads();
@@ -320,12 +358,7 @@ __global__ void __launch_bounds__(256, 1)
     for (int r = 0; r < NP; ++r)
       Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(r < RT ? Fs[q * RT + r] : 0.f);
   }
-  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
-    const int r = e / RT, c = e % RT;
-    float acc = 0.f;
-    for (int qq = 0; qq < Q; ++qq) acc = fmaf(Fs[qq * RT + r], Fs[qq * RT + c], acc);
-    Gout[(int64_t)p * RT * RT + e] = acc;
-  }
+  smem_gram<RT>(Fs, Q, Gout + (int64_t)p * RT * RT);
 }
 
 // F_p = unit-l2 columns of the replica-p rows of PF (Qd x R), padded to RT,
@@ -366,12 +399,7 @@ __global__ void __launch_bounds__(256)
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
-    const int r = e / RT, c = e % RT;
-    float acc = 0.f;
-    for (int qq = 0; qq < Q; ++qq) acc = fmaf(Fs[qq * RT + r], Fs[qq * RT + c], acc);
-    Gout[(int64_t)p * RT * RT + e] = acc;
-  }
+  smem_gram<RT>(Fs, Q, Gout + (int64_t)p * RT * RT);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,19 +440,25 @@ __global__ void bf16_layouts_kernel(const float *__restrict__ Y, int Q,
 }
 
 // KR[p][r][(a,b)] = bf16(A[a][r] B[b][r]) for r < NP (zero beyond the rank).
+// One CTA per (a, replica): the A row and the B factor are staged in shared
+// memory; thread b writes the NP values of column (a, b), coalesced over b.
 template <int RT>
-__global__ void kr_kernel(const float *__restrict__ Af, const float *__restrict__ Bf, int Q,
-                          int NP, __nv_bfloat16 *__restrict__ KR) {
-  const int p = blockIdx.y;
+__global__ void __launch_bounds__(256)
+    kr_kernel(const float *__restrict__ Af, const float *__restrict__ Bf, int Q, int NP,
+              __nv_bfloat16 *__restrict__ KR) {
+  extern __shared__ __align__(16) float Bs[];   // [Q][RT]
+  __shared__ float arow[RT];
+  const int a = blockIdx.x, p = blockIdx.y;
   const int64_t QQ = (int64_t)Q * Q;
-  const int64_t ab = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (ab >= QQ) return;
-  const int a = (int)(ab / Q), b = (int)(ab - (int64_t)a * Q);
-  const float *ar = Af + ((int64_t)p * Q + a) * RT, *br = Bf + ((int64_t)p * Q + b) * RT;
-  __nv_bfloat16 *kr = KR + (int64_t)p * NP * QQ + ab;
+  for (int e = threadIdx.x; e < Q * RT; e += blockDim.x) Bs[e] = Bf[(int64_t)p * Q * RT + e];
+  if (threadIdx.x < RT) arow[threadIdx.x] = Af[((int64_t)p * Q + a) * RT + threadIdx.x];
+  __syncthreads();
+  __nv_bfloat16 *kr = KR + (int64_t)p * NP * QQ + (int64_t)a * Q;
+  for (int b = threadIdx.x; b < Q; b += blockDim.x) {
 #pragma unroll
-  for (int r = 0; r < RT; ++r) kr[r * QQ] = __float2bfloat16_rn(ar[r] * br[r]);
-  for (int r = RT; r < NP; ++r) kr[r * QQ] = __float2bfloat16_rn(0.f);
+    for (int r = 0; r < RT; ++r) kr[r * QQ + b] = __float2bfloat16_rn(arow[r] * Bs[b * RT + r]);
+    for (int r = RT; r < NP; ++r) kr[r * QQ + b] = __float2bfloat16_rn(0.f);
+  }
 }
 
 // M1[p][a][r] = sum_b Tc[p][(a,b)][r] B[p][b][r]     thread (a, r)
@@ -480,30 +514,34 @@ static void als_run_simt(const float *Y, int P, int Q, int R, int iters, AlsBuff
   const dim3 gQP(Q, P);
   const dim3 gM3((Q * RT + 255) / 256, P);
   auto c_update = [&]() {
-    mk(kStAlsPass, 1);
+    mk(kStAlsGemm, 1);
     als_h_kernel<RT><<<gQP, bq, smem_h, st>>>(Y, b.Bf, b.H, Q);
     count_launch();
-    mk(kStAlsPass, 0);
-    mk(kStAlsSmall, 1);
+    mk(kStAlsGemm, 0);
+    mk(kStAlsAux, 1);
     als_m3_kernel<RT><<<gM3, 256, 0, st>>>(b.H, b.Af, b.M, Q);
     count_launch();
+    mk(kStAlsAux, 0);
+    mk(kStAlsSolve, 1);
     solve<RT>(b.M, 1, 0, b.GA, b.GB, b.Cf, b.GC, nullptr, 0, P, Q, R, 0, b.status, st);
-    mk(kStAlsSmall, 0);
+    mk(kStAlsSolve, 0);
   };
   for (int it = 0; it < iters; ++it) {
     c_update();
-    mk(kStAlsSmall, 1);
+    mk(kStAlsAux, 1);
     als_m1_kernel<RT><<<gQP, 256, 0, st>>>(b.H, b.Cf, b.M, Q);
     count_launch();
+    mk(kStAlsAux, 0);
+    mk(kStAlsSolve, 1);
     solve<RT>(b.M, 1, 0, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status, st);
-    mk(kStAlsSmall, 0);
-    mk(kStAlsPass, 1);
+    mk(kStAlsSolve, 0);
+    mk(kStAlsGemm, 1);
     als_m2_kernel<RT><<<gQP, bq, smem_m2, st>>>(Y, b.Af, b.Cf, b.M, Q);
     count_launch();
-    mk(kStAlsPass, 0);
-    mk(kStAlsSmall, 1);
+    mk(kStAlsGemm, 0);
+    mk(kStAlsSolve, 1);
     solve<RT>(b.M, 1, 0, b.GA, b.GC, b.Bf, b.GB, nullptr, 0, P, Q, R, 1, b.status, st);
-    mk(kStAlsSmall, 0);
+    mk(kStAlsSolve, 0);
   }
   c_update();
 }
@@ -514,11 +552,11 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
                        cudaStream_t st, const Marker &mk) {
   const int NP = kAlsNP;
   const int64_t QQ = (int64_t)Q * Q;
-  mk(kStAlsPass, 1);
+  mk(kStAlsAux, 1);
   bf16_layouts_kernel<<<dim3((Q + 31) / 32, (unsigned)((QQ + 31) / 32), P), dim3(32, 8), 0, st>>>(
       Y, Q, b.Xa, b.Xc);
   count_launch();
-  mk(kStAlsPass, 0);
+  mk(kStAlsAux, 0);
   // M3 = Xc . KR^T (split over K = (a, b)), Tc = Xa . C
   TcStoreArgs m3{};
   m3.A = b.Xc; m3.a_inner = QQ; m3.a_rows = (int64_t)P * Q; m3.a_rows_per_z = Q;
@@ -531,33 +569,42 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   tc.M = (int)QQ; tc.N = RT; tc.K = Q; tc.BN = NP; tc.batch = P; tc.ksplit = 1;
   tc.D = b.H; tc.s_split = 0; tc.s_z = QQ * RT; tc.s_m = RT;
   const int ks = tc_gemm_splits(m3.K, b.ksplit);
-  const dim3 gKR((unsigned)((QQ + 255) / 256), P);
+  const dim3 gKR(Q, P);
+  const size_t smem_kr = (size_t)Q * RT * sizeof(float);
   const dim3 gM((Q * RT + 255) / 256, P);
   bool ok = true;
   auto c_update = [&]() {
-    mk(kStAlsPass, 1);
-    kr_kernel<RT><<<gKR, 256, 0, st>>>(b.Af, b.Bf, Q, NP, b.KR);
+    mk(kStAlsAux, 1);
+    kr_kernel<RT><<<gKR, 256, smem_kr, st>>>(b.Af, b.Bf, Q, NP, b.KR);
     count_launch();
+    mk(kStAlsAux, 0);
+    mk(kStAlsGemm, 1);
     ok = ok && tc_gemm_store(m3, b.status, st);
-    mk(kStAlsPass, 0);
-    mk(kStAlsSmall, 1);
+    mk(kStAlsGemm, 0);
+    mk(kStAlsSolve, 1);
     solve<RT>(b.Mparts, ks, (int64_t)P * Q * RT, b.GA, b.GB, b.Cf, b.GC, b.Ct, NP, P, Q, R, 0,
               b.status, st);
-    mk(kStAlsSmall, 0);
+    mk(kStAlsSolve, 0);
   };
   for (int it = 0; it < iters && ok; ++it) {
     c_update();
-    mk(kStAlsPass, 1);
+    mk(kStAlsGemm, 1);
     ok = ok && tc_gemm_store(tc, b.status, st);
-    mk(kStAlsPass, 0);
-    mk(kStAlsSmall, 1);
+    mk(kStAlsGemm, 0);
+    mk(kStAlsAux, 1);
     tc_m1_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Bf, Q, b.M);
     count_launch();
+    mk(kStAlsAux, 0);
+    mk(kStAlsSolve, 1);
     solve<RT>(b.M, 1, 0, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status, st);
+    mk(kStAlsSolve, 0);
+    mk(kStAlsAux, 1);
     tc_m2_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Af, Q, b.M);
     count_launch();
+    mk(kStAlsAux, 0);
+    mk(kStAlsSolve, 1);
     solve<RT>(b.M, 1, 0, b.GA, b.GC, b.Bf, b.GB, nullptr, 0, P, Q, R, 1, b.status, st);
-    mk(kStAlsSmall, 0);
+    mk(kStAlsSolve, 0);
   }
   if (ok) c_update();
   return ok;
@@ -572,15 +619,10 @@ int als_tc_splits(int P, int Q, int desired) {
 
 bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
              cudaStream_t st, const Marker &mk) {
-  for (int RTi : {8, 16, 32}) {
-    if (RT != RTi) continue;
-    const size_t smem = (size_t)Q * RT * sizeof(float);
-    if (smem > 48 * 1024) {
-      if (RT == 8) cudaFuncSetAttribute(als_solve_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (RT == 16) cudaFuncSetAttribute(als_solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (RT == 32) cudaFuncSetAttribute(als_solve_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
-  }
+  const int smem = (int)((size_t)Q * RT * sizeof(float));
+  if (RT == 8) cudaFuncSetAttribute(als_solve_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (RT == 16) cudaFuncSetAttribute(als_solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (RT == 32) cudaFuncSetAttribute(als_solve_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (b.use_tc) {
     if (RT == 8) return als_run_tc<8>(Y, P, Q, R, iters, b, st, mk);
     if (RT == 16) return als_run_tc<16>(Y, P, Q, R, iters, b, st, mk);

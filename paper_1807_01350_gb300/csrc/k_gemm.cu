@@ -71,18 +71,22 @@ constexpr int kBK = 16;
 
 // 256 threads as 16 x 16; each thread owns TM consecutive rows and TN columns
 // strided by 16 (conflict-free shared reads of the B tile).
+// kc > 0 splits K: batch index z covers k in [z * kc, min(z * kc + kc, K)) and the
+// operands take no batch offset (the epilogue writes partial z).
 template <Elem EA, Elem EB, int BM, int BN, class Epi>
 __global__ void __launch_bounds__(kThreads)
-    gemm_kernel(Operand A, Operand B, int M, int N, int K, int zdiv, Epi epi) {
+    gemm_kernel(Operand A, Operand B, int M, int N, int K, int zdiv, int kc, Epi epi) {
   constexpr int TM = BM / 16, TN = BN / 16;
   __shared__ __align__(16) float As[kBK][BM + 4];
   __shared__ __align__(16) float Bs[kBK][BN + 1];
   const int z = blockIdx.z;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t offA = (int64_t)(z / zdiv) * A.s_hi + (int64_t)(z % zdiv) * A.s_lo;
-  const int64_t offB = (int64_t)(z / zdiv) * B.s_hi + (int64_t)(z % zdiv) * B.s_lo;
+  const int64_t offA = kc ? 0 : (int64_t)(z / zdiv) * A.s_hi + (int64_t)(z % zdiv) * A.s_lo;
+  const int64_t offB = kc ? 0 : (int64_t)(z / zdiv) * B.s_hi + (int64_t)(z % zdiv) * B.s_lo;
   const bool a_kfast = A.s_k == 1, b_kfast = B.s_k == 1;
+  const int kbeg = kc ? z * kc : 0;
+  const int kend = kc ? min(K, kbeg + kc) : K;
 
   float acc[TM][TN];
 #pragma unroll
@@ -90,13 +94,13 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
 
-  for (int k0 = 0; k0 < K; k0 += kBK) {
+  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
     for (int e = tid; e < BM * kBK; e += kThreads) {
       int mm, kk;
       if (a_kfast) { mm = e / kBK; kk = e % kBK; } else { mm = e % BM; kk = e / BM; }
       const int m = m0 + mm, k = k0 + kk;
       float v = 0.f;
-      if (m < M && k < K) v = ld_elem<EA>(A.p, offA + (int64_t)m * A.s_row + (int64_t)k * A.s_k);
+      if (m < M && k < kend) v = ld_elem<EA>(A.p, offA + (int64_t)m * A.s_row + (int64_t)k * A.s_k);
       As[kk][mm] = v;
     }
     for (int e = tid; e < BN * kBK; e += kThreads) {
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(kThreads)
       if (b_kfast) { nn = e / kBK; kk = e % kBK; } else { nn = e % BN; kk = e / BN; }
       const int n = n0 + nn, k = k0 + kk;
       float v = 0.f;
-      if (n < N && k < K) v = ld_elem<EB>(B.p, offB + (int64_t)n * B.s_row + (int64_t)k * B.s_k);
+      if (n < N && k < kend) v = ld_elem<EB>(B.p, offB + (int64_t)n * B.s_row + (int64_t)k * B.s_k);
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -139,11 +143,24 @@ __global__ void __launch_bounds__(kThreads)
 
 template <Elem EA, Elem EB, int BM, int BN, class Epi>
 static void launch_gemm(const Operand &A, const Operand &B, int M, int N, int K, int batch,
-                        int zdiv, const Epi &epi, cudaStream_t st) {
+                        int zdiv, const Epi &epi, cudaStream_t st, int kc = 0) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-  gemm_kernel<EA, EB, BM, BN, Epi><<<grid, kThreads, 0, st>>>(A, B, M, N, K, zdiv, epi);
+  gemm_kernel<EA, EB, BM, BN, Epi><<<grid, kThreads, 0, st>>>(A, B, M, N, K, zdiv, kc, epi);
   count_launch();
+}
+
+// D(m, n) = alpha * sum_z part[z](m, n) + beta * D(m, n)
+__global__ void splitk_reduce_kernel(const float *__restrict__ part, int splits, int M, int N,
+                                     float *D, int64_t s_m, int64_t s_n, float alpha, float beta) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t MN = (int64_t)M * N;
+  if (idx >= MN) return;
+  float acc = 0.f;
+  for (int z = 0; z < splits; ++z) acc += part[z * MN + idx];
+  const int m = (int)(idx / N), n = (int)(idx % N);
+  float *d = D + m * s_m + n * s_n;
+  *d = beta == 0.f ? alpha * acc : fmaf(beta, *d, alpha * acc);
 }
 
 template <Elem EA, Elem EB>
@@ -161,6 +178,26 @@ void gemm_strided(const GemmArgs &g, cudaStream_t st) {
   // zdiv = 1: the whole batch index goes through the s_hi strides
   Operand A{g.A, g.sAz, 0, g.sAm, g.sAk};
   Operand B{g.B, g.sBz, 0, g.sBn, g.sBk};
+  // few output tiles and a long K: split K over CTAs into the caller's scratch
+  const int64_t tiles64 = (int64_t)((g.M + 63) / 64) * ((g.N + 63) / 64);
+  if (g.batch == 1 && g.split_scratch && tiles64 < 76 && g.K >= 1024 &&
+      g.ta == Elem::F32 && g.tb == Elem::F32) {
+    int splits = (int)(304 / tiles64);
+    if (splits > g.K / 256) splits = g.K / 256;
+    const int64_t MN = (int64_t)g.M * g.N;
+    if ((int64_t)splits * MN > (int64_t)g.split_scratch_floats)
+      splits = (int)(g.split_scratch_floats / MN);
+    if (splits >= 2) {
+      const int kc = ((g.K + splits - 1) / splits + kBK - 1) / kBK * kBK;
+      splits = (g.K + kc - 1) / kc;
+      StridedEpi pe{g.split_scratch, MN, 0, g.N, 1, 1.f, 0.f};
+      launch_gemm<Elem::F32, Elem::F32, 64, 64>(A, B, g.M, g.N, g.K, splits, 1, pe, st, kc);
+      splitk_reduce_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(
+          g.split_scratch, splits, g.M, g.N, g.D, g.sDm, g.sDn, g.alpha, g.beta);
+      count_launch();
+      return;
+    }
+  }
   StridedEpi epi{g.D, g.sDz, 0, g.sDm, g.sDn, g.alpha, g.beta};
   if (g.ta == Elem::F32 && g.tb == Elem::F32)
     gemm_dispatch_tile<Elem::F32, Elem::F32>(A, B, g, epi, st);

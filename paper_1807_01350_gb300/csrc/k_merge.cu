@@ -276,8 +276,8 @@ void scale_columns(const float *in, int64_t rows, int cols, int S, float w_share
 
 // scratch holds E (Qd x R), rhs (t x R), Ww (t x Qd) and Gram (t x t).
 void solve_c_new(const float *W, const float *Ch, const float *G, int64_t t, int P, int Q,
-                 int S, int Qd, int R, int RT, float *scratch, float *C_new, int *status,
-                 cudaStream_t st) {
+                 int S, int Qd, int R, int RT, float *scratch, float *splitk,
+                 size_t splitk_floats, float *C_new, int *status, cudaStream_t st) {
   float *E = scratch;
   float *rhs = E + (int64_t)Qd * R;
   float *Ww = rhs + t * R;
@@ -290,6 +290,7 @@ void solve_c_new(const float *W, const float *Ch, const float *G, int64_t t, int
   g.B = E; g.tb = Elem::F32; g.sBn = 1; g.sBk = R;
   g.D = rhs; g.sDm = R; g.sDn = 1;
   g.M = (int)t; g.N = R; g.K = Qd; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
+  g.split_scratch = splitk; g.split_scratch_floats = splitk_floats;
   gemm_strided(g, st);
   scale_columns(W, t, Qd, S, (float)P, Ww, st);
   GemmArgs h{};
@@ -297,6 +298,7 @@ void solve_c_new(const float *W, const float *Ch, const float *G, int64_t t, int
   h.B = W; h.tb = Elem::F32; h.sBn = Qd; h.sBk = 1;
   h.D = Gram; h.sDm = t; h.sDn = 1;
   h.M = (int)t; h.N = (int)t; h.K = Qd; h.batch = 1; h.alpha = 1.f; h.beta = 0.f;
+  h.split_scratch = splitk; h.split_scratch_floats = splitk_floats;
   gemm_strided(h, st);
   c_solve_kernel<<<1, 256, 0, st>>>(Gram, rhs, (int)t, R, C_new, status);
   count_launch();

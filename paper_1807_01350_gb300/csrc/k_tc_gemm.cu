@@ -162,8 +162,8 @@ struct TcShape {
 struct TcStoreEpi {
   float *D;
   int64_t s_split, s_z, s_m;
-  __device__ __forceinline__ void operator()(int z, int m, int n, float v) const {
-    D[(int64_t)blockIdx.x * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n] = v;
+  __device__ __forceinline__ void operator()(int z, int split, int m, int n, float v) const {
+    D[(int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n] = v;
   }
 };
 
@@ -173,7 +173,7 @@ struct Mode2TcEpi {
   const float *scale;
   int64_t I;
   int P, Q, S;
-  __device__ __forceinline__ void operator()(int, int m, int c, float v) const {
+  __device__ __forceinline__ void operator()(int, int, int m, int c, float v) const {
     const int64_t k = m / I, i = m - k * I;
     if (scale) v *= scale[k];
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -192,16 +192,26 @@ struct Mode1TcEpi {
   float *T2;
   int64_t t;
   int P, Q;
-  __device__ __forceinline__ void operator()(int z, int a, int b, float v) const {
+  __device__ __forceinline__ void operator()(int z, int, int a, int b, float v) const {
     const int k = z / P, p = z - k * P;
     T2[(((int64_t)p * t + k) * Q + a) * Q + b] = v;
   }
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent GEMM: one CTA per SM walks the tiles (N fastest, then M, then the
+// batch index); tensor memory holds two accumulators so the epilogue of one
+// tile overlaps the main loop of the next.
+//   warp 0 lane 0 : TMA producer        full[s]  <- TMA bytes,  waits empty[s]
+//   warp 1 lane 0 : MMA issuer          empty[s] <- commit,     acc_full[b] <- commit
+//   warps 2..5    : epilogue (lane quadrant = warp % 4), acc_empty[b] <- 4 arrivals
 template <int KIND, class Epi>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const TcShape sh, const Epi epi, int *status) {
+                   const TcShape sh, const Epi epi, int batch, int *status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -212,31 +222,30 @@ __global__ void __launch_bounds__(128, 1)
   uint8_t *sB = smem + stages * a_bytes;
   uint64_t *full = reinterpret_cast<uint64_t *>(sB + stages * b_bytes);
   uint64_t *empty = full + stages;
-  uint64_t *accf = empty + stages;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(accf + 1);
+  uint64_t *acc_full = empty + stages;     // [2]
+  uint64_t *acc_empty = acc_full + 2;      // [2]
+  uint64_t *drain = acc_empty + 2;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int z = blockIdx.z;
-  const int m0 = blockIdx.y * kBM, n0 = sh.ksplit > 1 ? 0 : blockIdx.x * sh.BN;
-  const int a_row0 = (z / sh.zdiv) * sh.a_hi + (z % sh.zdiv) * sh.a_lo + m0;
-  const int b_row0 = (z / sh.zdiv) * sh.b_hi + (z % sh.zdiv) * sh.b_lo + n0;
   constexpr int kElemsPerRow = KIND == 0 ? 64 : 128;   // 128 bytes of K
-  constexpr int kUmmaK = KIND == 0 ? 16 : 32;           // 32 bytes of K per MMA
   const int nk_all = (sh.K + kElemsPerRow - 1) / kElemsPerRow;
-  int kb_begin = 0, nk = nk_all;
-  if (sh.ksplit > 1) {
-    const int per = (nk_all + sh.ksplit - 1) / sh.ksplit;
-    kb_begin = blockIdx.x * per;
-    nk = min(per, nk_all - kb_begin);   // the host makes every split non-empty
-  }
+  const int tiles_n = sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN;
+  const int tiles_m = (sh.M + kBM - 1) / kBM;
+  const int total = tiles_n * tiles_m * batch;
+  const int per_split = sh.ksplit > 1 ? (nk_all + sh.ksplit - 1) / sh.ksplit : nk_all;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -246,62 +255,125 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
+  // tile -> (z, m0, n0 or split, first K block, K blocks)
+  auto decode = [&](int tile, int &z, int &m0, int &n0, int &split, int &kb0, int &nk) {
+    const int nt = tile % tiles_n;
+    const int rest = tile / tiles_n;
+    m0 = (rest % tiles_m) * kBM;
+    z = rest / tiles_m;
+    if (sh.ksplit > 1) {
+      split = nt; n0 = 0; kb0 = nt * per_split; nk = min(per_split, nk_all - kb0);
+    } else {
+      split = 0; n0 = nt * sh.BN; kb0 = 0; nk = nk_all;
+    }
+  };
+
   if (warp == 0 && lane == 0) {
     // TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % stages;
-      const uint32_t ph = (kb / stages) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
-        *abort_flag = 1;
-        atomicOr(status, kDevTimeout);
-        break;
+    uint32_t it = 0;
+    bool aborted = false;
+    for (int tile = blockIdx.x; tile < total && !aborted; tile += gridDim.x) {
+      int z, m0, n0, split, kb0, nk;
+      decode(tile, z, m0, n0, split, kb0, nk);
+      const int a_row = (z / sh.zdiv) * sh.a_hi + (z % sh.zdiv) * sh.a_lo + m0;
+      const int b_row = (z / sh.zdiv) * sh.b_hi + (z % sh.zdiv) * sh.b_lo + n0;
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (it / stages) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(status, kDevTimeout);
+          aborted = true;
+          break;
+        }
+        mbar_expect_tx(&full[s], a_bytes + b_bytes);
+        tma_load_2d(sA + s * a_bytes, &tmA, &full[s], (kb0 + kb) * kElemsPerRow, a_row);
+        tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb0 + kb) * kElemsPerRow, b_row);
       }
-      mbar_expect_tx(&full[s], a_bytes + b_bytes);
-      tma_load_2d(sA + s * a_bytes, &tmA, &full[s], (kb_begin + kb) * kElemsPerRow, a_row0);
-      tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb_begin + kb) * kElemsPerRow, b_row0);
+    }
+    if (aborted) {
+      // wait (bounded) for the copies still in flight before the CTA can exit
+      const uint32_t first = it > (uint32_t)stages ? it - stages : 0u;
+      for (uint32_t j = first; j < it; ++j) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&full[j % stages], (j / stages) & 1u) &&
+               clock64() - t0 < kWaitBudget) {
+        }
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     const uint32_t idesc = make_idesc(KIND, sh.BN);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % stages;
-      const uint32_t ph = (kb / stages) & 1u;
-      if (!mbar_wait(&full[s], ph, abort_flag)) {
+    uint32_t it = 0, local = 0;
+    bool aborted = false;
+    for (int tile = blockIdx.x; tile < total && !aborted; tile += gridDim.x, ++local) {
+      int z, m0, n0, split, kb0, nk;
+      decode(tile, z, m0, n0, split, kb0, nk);
+      const uint32_t buf = local & 1u, use = local >> 1;
+      if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u, abort_flag)) {
         *abort_flag = 1;
         atomicOr(status, kDevTimeout);
         break;
       }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
+      const uint32_t d = tmem + buf * static_cast<uint32_t>(sh.BN);
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (it / stages) & 1u;
+        if (!mbar_wait(&full[s], ph, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(status, kDevTimeout);
+          aborted = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
 #pragma unroll
-      for (int kk = 0; kk < kRowBytes / 32; ++kk) {
-        mma_issue<KIND>(tmem, make_desc_sw128(a0 + kk * 32), make_desc_sw128(b0 + kk * 32),
-                        idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+          mma_issue<KIND>(d, make_desc_sw128(a0 + kk * 32), make_desc_sw128(b0 + kk * 32), idesc,
+                          (kb > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&empty[s]);
+      mma_commit(&acc_full[buf]);
     }
-    mma_commit(accf);   // also issued after an abort: drains the MMAs already issued
-  }
-  (void)kUmmaK;
-
-  // epilogue: 4 warps, warp w owns accumulator rows [32 w, 32 w + 32)
-  __syncwarp();
-  const bool ok = mbar_wait(accf, 0, abort_flag);
-  if (!ok && lane == 0) atomicOr(status, kDevTimeout);
-  tc_fence_after();
-  // tcgen05.ld is warp-collective: take the decision for the whole warp
-  if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
-    const int m = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < sh.BN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, r);
-      if (m < sh.M) {
+    // every MMA this thread issued has completed once the drain barrier flips
+    mma_commit(drain);
+    const long long t0 = clock64();
+    while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitBudget) {
+    }
+  } else if (warp >= 2) {
+    // epilogue
+    const int quad = warp & 3;
+    uint32_t local = 0;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++local) {
+      int z, m0, n0, split, kb0, nk;
+      decode(tile, z, m0, n0, split, kb0, nk);
+      const uint32_t buf = local & 1u, use = local >> 1;
+      const bool ok = mbar_wait(&acc_full[buf], use & 1u, abort_flag);
+      if (!__all_sync(0xffffffffu, ok && !*abort_flag)) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          atomicOr(status, kDevTimeout);
+        }
+        break;
+      }
+      tc_fence_after();
+      const int m = m0 + quad * 32 + lane;
+      for (int c0 = 0; c0 < sh.BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + buf * sh.BN + c0, r);
+        if (m < sh.M) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          if (n < sh.N) epi(z, m, n, __uint_as_float(r[j]));
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < sh.N) epi(z, split, m, n, __uint_as_float(r[j]));
+          }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
   }
   tc_fence_before();
@@ -345,21 +417,35 @@ int pow2_at_least(int n) {
   return p;
 }
 
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
 template <int KIND, class Epi>
 bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
                const Epi &epi, int *status, cudaStream_t st) {
-  sh.tmem_cols = pow2_at_least(sh.BN);
+  sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
+  if (sh.tmem_cols > 512) return false;
   const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes;
   sh.stages = static_cast<int>((200 * 1024) / per_stage);
-  if (sh.stages > 6) sh.stages = 6;
+  if (sh.stages > 8) sh.stages = 8;
   if (sh.stages < 2) return false;
-  const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 1) * 8 + 16;
+  const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 5) * 8 + 16;
   if (cudaFuncSetAttribute(tc_gemm_kernel<KIND, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return false;
-  dim3 grid(sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN, (sh.M + kBM - 1) / kBM,
-            batch);
-  tc_gemm_kernel<KIND, Epi><<<grid, 128, smem, st>>>(ma, mb, sh, epi, status);
+  const int tiles_n = sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN;
+  const int64_t tiles = (int64_t)tiles_n * ((sh.M + kBM - 1) / kBM) * batch;
+  if (tiles <= 0 || tiles > (int64_t)1 << 30) return false;
+  const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
+  tc_gemm_kernel<KIND, Epi><<<grid, 192, smem, st>>>(ma, mb, sh, epi, batch, status);
   count_launch();
   count_tc_launch();
   return cudaPeekAtLastError() == cudaSuccess;

@@ -66,6 +66,8 @@ struct octen_ctx {
   float *At = nullptr, *Bt = nullptr, *Ct = nullptr, *Ah = nullptr, *Bh = nullptr, *Ch = nullptr;
   float *M = nullptr, *H = nullptr, *csolve = nullptr;
   float *GA = nullptr, *GB = nullptr, *GC = nullptr;
+  float *splitk = nullptr;                 // split-K partials of the small GEMMs
+  static constexpr size_t kSplitkFloats = size_t(4) << 20;
   // tensor-core ALS (bf16 / e4m3 modes with Q % 8 == 0)
   bool als_tc = false;
   int als_ks = 1;
@@ -351,6 +353,7 @@ void lift_mode(octen_ctx *x, const float *Fh, const float *PF, const float *L, i
   g.B = x->e; g.tb = Elem::F32; g.sBn = 1; g.sBk = c.R;
   g.D = F; g.sDm = c.R; g.sDn = 1;
   g.M = (int)rows; g.N = c.R; g.K = x->Qd; g.batch = 1; g.alpha = 1.f; g.beta = 1.f;
+  g.split_scratch = x->splitk; g.split_scratch_floats = octen_ctx::kSplitkFloats;
   gemm_strided(g, x->st);
 }
 
@@ -362,6 +365,7 @@ void project(octen_ctx *x, const float *Ur, int64_t rows, const float *F, float 
   g.B = F; g.tb = Elem::F32; g.sBn = 1; g.sBk = c.R;
   g.D = PF; g.sDm = c.R; g.sDn = 1;
   g.M = x->Qd; g.N = c.R; g.K = (int)rows; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
+  g.split_scratch = x->splitk; g.split_scratch_floats = octen_ctx::kSplitkFloats;
   gemm_strided(g, x->st);
 }
 
@@ -419,7 +423,8 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
             x->alloc(x->M, P * Q * RT) && x->alloc(x->H, P * Q * Q * RT) &&
             x->alloc(x->perm, P * c.R) && x->alloc(x->scales, P * 2 * c.R) &&
             x->alloc(x->dstatus, 1) && x->alloc(x->dfit, 2) && x->alloc(x->GA, P * RT * RT) &&
-            x->alloc(x->GB, P * RT * RT) && x->alloc(x->GC, P * RT * RT);
+            x->alloc(x->GB, P * RT * RT) && x->alloc(x->GC, P * RT * RT) &&
+            x->alloc(x->splitk, octen_ctx::kSplitkFloats);
   if (ok && x->use_tc && als_tc_eligible(c.Q)) {
     const int mt = (c.Q + 127) / 128;
     const int want = (4 * 152 + mt * c.P - 1) / (mt * c.P);
@@ -561,7 +566,7 @@ octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const floa
   float *C_new = x->C + x->K * c.R;
   x->mark(kStCsolve, 1);
   solve_c_new(Wd, x->Ch, x->G, t, c.P, c.Q, c.S, Qd, c.R, RT, static_cast<float *>(x->Wbuf.p),
-              C_new, x->dstatus, x->st);
+              x->splitk, octen_ctx::kSplitkFloats, C_new, x->dstatus, x->st);
   update_g(Wd, C_new, t, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
   x->mark(kStCsolve, 0);
   s = x->sync_check("append");
@@ -612,6 +617,101 @@ octen_status octen_fit(octen_ctx *x, const void *X_all, int64_t K, double *fit_o
     total1 += h[1];
   }
   *fit_out = total0 > 0.0 ? 1.0 - sqrt(total1) / sqrt(total0) : 0.0;
+  return OCTEN_OK;
+}
+
+namespace {
+
+// Device arrays that make up the state of an initialised context, in file order.
+struct StateArray {
+  void *p;
+  size_t bytes;
+};
+
+std::vector<StateArray> state_arrays(octen_ctx *x) {
+  const octen_config &c = x->cfg;
+  const size_t P = c.P, Q = c.Q, Qd = x->Qd;
+  return {
+      {x->U32, (size_t)c.I * Qd * 4},
+      {x->V32, (size_t)c.J * Qd * 4},
+      {x->Ut_rep, P * Q * c.I * elem_size(x->tu)},
+      {x->Vt, Qd * c.J * elem_size(x->tv)},
+      {x->La, (size_t)c.I * Qd * 4},
+      {x->Lb, (size_t)c.J * Qd * 4},
+      {x->Y, P * Q * Q * Q * 4},
+      {x->A, (size_t)c.I * c.R * 4},
+      {x->B, (size_t)c.J * c.R * 4},
+      {x->G, P * Q * c.R * 4},
+      {x->C, (size_t)x->K * c.R * 4},
+  };
+}
+
+const char kMagic[8] = {'O', 'C', 'T', 'E', 'N', 'S', 'T', '1'};
+
+}  // namespace
+
+octen_status octen_save(const octen_ctx *cx, const char *path) {
+  octen_ctx *x = const_cast<octen_ctx *>(cx);
+  if (!x || !path) return OCTEN_EINVAL;
+  if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_save before octen_init");
+  if (x->sync_check("save") != OCTEN_OK) return OCTEN_ECUDA;
+  FILE *f = fopen(path, "wb");
+  if (!f) return x->fail(OCTEN_EINVAL, "octen_save: cannot open %s", path);
+  int64_t hdr[4] = {x->K, x->a_over, x->b_over, 0};
+  bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(&x->cfg, sizeof x->cfg, 1, f) == 1 &&
+            fwrite(hdr, sizeof hdr, 1, f) == 1;
+  std::vector<char> host;
+  for (const StateArray &a : state_arrays(x)) {
+    if (!ok) break;
+    host.resize(a.bytes);
+    ok = cudaMemcpy(host.data(), a.p, a.bytes, cudaMemcpyDeviceToHost) == cudaSuccess &&
+         fwrite(host.data(), 1, a.bytes, f) == a.bytes;
+  }
+  ok = (fclose(f) == 0) && ok;
+  return ok ? OCTEN_OK : x->fail(OCTEN_ECUDA, "octen_save: writing %s failed", path);
+}
+
+octen_status octen_load(const char *path, void *cuda_stream, octen_ctx **out) {
+  if (!path || !out) return OCTEN_EINVAL;
+  FILE *f = fopen(path, "rb");
+  if (!f) return OCTEN_EINVAL;
+  char magic[8];
+  octen_config cfg{};
+  int64_t hdr[4];
+  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 ||
+      fread(&cfg, sizeof cfg, 1, f) != 1 || fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] < 1) {
+    fclose(f);
+    return OCTEN_EINVAL;
+  }
+  octen_ctx *x = nullptr;
+  octen_status s = octen_create(&cfg, cuda_stream, &x);
+  if (s != OCTEN_OK) {
+    fclose(f);
+    return s;
+  }
+  if (!ensure_c_capacity(x, hdr[0])) {
+    fclose(f);
+    delete x;
+    return OCTEN_ENOMEM;
+  }
+  x->K = hdr[0];
+  x->a_over = (int)hdr[1];
+  x->b_over = (int)hdr[2];
+  bool ok = true;
+  std::vector<char> host;
+  for (const StateArray &a : state_arrays(x)) {
+    host.resize(a.bytes);
+    ok = fread(host.data(), 1, a.bytes, f) == a.bytes &&
+         cudaMemcpy(a.p, host.data(), a.bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) break;
+  }
+  fclose(f);
+  if (!ok) {
+    delete x;
+    return OCTEN_EINVAL;
+  }
+  x->initialized = true;
+  *out = x;
   return OCTEN_OK;
 }
 
@@ -724,8 +824,8 @@ uint64_t octen_launch_count(void) { return g_launches.load(); }
 uint64_t octen_tc_launch_count(void) { return g_tc_launches.load(); }
 
 static const char *kStageNames[kNumStages] = {"quantize", "mode2", "mode1", "mode3",
-                                              "warm_start", "als_pass", "als_small", "align",
-                                              "lift", "c_solve"};
+                                              "warm_start", "als_gemm", "als_aux", "als_solve",
+                                              "align", "lift", "c_solve"};
 
 int octen_stage_count(void) { return kNumStages; }
 

@@ -28,8 +28,8 @@ void count_launch();
 
 // Stages timed with CUDA events when a context has timing enabled.
 enum Stage : int {
-  kStQuant = 0, kStMode2, kStMode1, kStMode3, kStWarm, kStAlsPass, kStAlsSmall, kStAlign,
-  kStLift, kStCsolve, kNumStages
+  kStQuant = 0, kStMode2, kStMode1, kStMode3, kStWarm, kStAlsGemm, kStAlsAux, kStAlsSolve,
+  kStAlign, kStLift, kStCsolve, kNumStages
 };
 
 // Optional hook called around the kernels of a multi-kernel stage:
@@ -53,6 +53,10 @@ struct GemmArgs {
   float *D; int64_t sDz, sDm, sDn;
   int M, N, K, batch;
   float alpha, beta;
+  // optional scratch: lets a GEMM with few output tiles and a long K split K
+  // over CTAs (partials reduced by a second kernel)
+  float *split_scratch = nullptr;
+  size_t split_scratch_floats = 0;
 };
 void gemm_strided(const GemmArgs &g, cudaStream_t st);
 
@@ -161,8 +165,8 @@ void lift_rhs(const float *Fh, const float *PF, int P, int Q, int S, int R, int 
 // C_new (t x R) from the stacked W_new,p^T system and G update.
 // scratch: Qd*R + t*R + t*Qd + t*t floats.
 void solve_c_new(const float *W, const float *Ch, const float *G, int64_t t, int P, int Q,
-                 int S, int Qd, int R, int RT, float *scratch, float *C_new, int *status,
-                 cudaStream_t st);
+                 int S, int Qd, int R, int RT, float *scratch, float *splitk,
+                 size_t splitk_floats, float *C_new, int *status, cudaStream_t st);
 void update_g(const float *W, const float *C_new, int64_t t, int P, int Q, int S, int Qd,
               int R, float *G, cudaStream_t st);
 

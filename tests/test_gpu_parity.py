@@ -178,3 +178,27 @@ def test_call_order_and_argument_errors(pkg):
         g.append_ptr(0, 1, 0)
     assert e.value.status in (1, 6)
     g.close()
+
+
+def test_checkpoint_resume_is_bit_identical(pkg, tmp_path):
+    """Save after one batch, load into a new context, append the next batch on
+    both: identical summaries and factors."""
+    case = CASES_FP32["ragged"]
+    d = case.make()
+    g = pkg.Octen(case.I, case.J, case.R, case.P, case.Q, case.S, case.iters, case.prec)
+    g.init(slices(d["X"][:case.t_old], case.prec), dev(d["U"]), dev(d["V"]), dev(d["W"][0]),
+           dev(d["A0"]), dev(d["B0"]), dev(d["C0"]))
+    k = case.t_old
+    t0, t1 = case.batches
+    g.append(slices(d["X"][k:k + t0], case.prec), dev(d["W"][1]))
+    path = str(tmp_path / "state.octen")
+    g.save(path)
+    h = pkg.Octen.load(path)
+    xs = slices(d["X"][k + t0:k + t0 + t1], case.prec)
+    g.append(xs, dev(d["W"][2]))
+    h.append(xs, dev(d["W"][2]))
+    for a, b in zip(g.factors(), h.factors()):
+        assert np.array_equal(a, b)
+    assert np.array_equal(g.replicas(), h.replicas())
+    g.close()
+    h.close()
