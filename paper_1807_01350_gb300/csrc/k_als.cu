@@ -162,16 +162,16 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
 
 // Warp 0: factor G1 * G2 = L L^T in fp64 and write L^-1 (fp32, lower
 // triangular; identity on failure) to Li ([RT][RT + 1]).  *ok_out gets the
-// success flag.  The matrix lives in shared memory (Ad, fp64, padded rows) and
-// lane i owns row i; the loops are kept rolled so that the code stays in the
-// instruction cache (this runs once per launch on a single warp).
-//   right-looking Cholesky: for each pivot j, lane j forms L[j][j] (Newton
-//   rsqrt), lanes i > j scale their L[i][j] and update a[i][k] for j < k <= i;
-//   then L^-1 row by row: lane k finishes its row, lanes below subtract
-//   L[i][k] times it.
+// success flag.  The matrix lives in shared memory (Ad, fp64, padded rows); the
+// loops are kept rolled so that the code stays in the instruction cache (this
+// runs once per launch on a single warp).
+//   right-looking Cholesky: for each pivot j, lane 0 forms L[j][j] (Newton
+//   rsqrt), the lanes scale column j and share the trailing update of the
+//   entries (i, k), j < k <= i; then L^-1 row by row: row k is finished and
+//   L[i][k] times it is subtracted from every row i > k, spread over the lanes.
 template <int RT>
-__device__ void chol_inverse_to_smem(const float *g1, const float *g2, int R, double *Ad,
-                                     double *dinv, float *Li, int *ok_out) {
+__device__ void chol_inverse_to_smem(const double *Gd, int R, double *Ad, double *dinv, float *Li,
+                                     int *ok_out) {
   constexpr int LD = RT + 1;
   const int lane = threadIdx.x & 31;
   bool ok = true;
@@ -179,19 +179,17 @@ __device__ void chol_inverse_to_smem(const float *g1, const float *g2, int R, do
     double add = 0.0;
     if (attempt == 1) {
       // load the diagonal by 1e-12 * trace / R and retry once
-      double tr = lane < R ? (double)g1[lane * RT + lane] * (double)g2[lane * RT + lane] : 0.0;
+      double tr = lane < R ? Gd[lane * LD + lane] : 0.0;
       for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
       add = 1e-12 * tr / R;
     }
     if (lane < R) {
-      for (int k = 0; k <= lane; ++k)
-        Ad[lane * LD + k] = (double)g1[lane * RT + k] * (double)g2[lane * RT + k] +
-                            (k == lane ? add : 0.0);
+      for (int k = 0; k <= lane; ++k) Ad[lane * LD + k] = Gd[lane * LD + k] + (k == lane ? add : 0.0);
     }
     ok = true;
     for (int j = 0; j < R; ++j) {
       __syncwarp();
-      if (lane == j) {
+      if (lane == 0) {
         const double d = Ad[j * LD + j];
         const double inv = d > 0.0 ? rsqrt_nr(d) : 0.0;
         Ad[j * LD + j] = d > 0.0 ? d * inv : 1.0;
@@ -200,20 +198,19 @@ __device__ void chol_inverse_to_smem(const float *g1, const float *g2, int R, do
       __syncwarp();
       const double inv = dinv[j];
       if (!(inv > 0.0)) { ok = false; break; }
-      if (lane > j && lane < R) Ad[lane * LD + j] *= inv;
+      const int n = R - 1 - j;   // rows below the pivot
+      if (lane < n) Ad[(j + 1 + lane) * LD + j] *= inv;
       __syncwarp();   // every L[k][j] is scaled before any lane reads it
-      if (lane > j && lane < R) {
-        const double l = Ad[lane * LD + j];
-        int k = j + 1;
-        for (; k + 3 <= lane; k += 4) {
-          const double l0 = Ad[k * LD + j], l1 = Ad[(k + 1) * LD + j];
-          const double l2 = Ad[(k + 2) * LD + j], l3 = Ad[(k + 3) * LD + j];
-          Ad[lane * LD + k] = fma(-l, l0, Ad[lane * LD + k]);
-          Ad[lane * LD + k + 1] = fma(-l, l1, Ad[lane * LD + k + 1]);
-          Ad[lane * LD + k + 2] = fma(-l, l2, Ad[lane * LD + k + 2]);
-          Ad[lane * LD + k + 3] = fma(-l, l3, Ad[lane * LD + k + 3]);
-        }
-        for (; k <= lane; ++k) Ad[lane * LD + k] = fma(-l, Ad[k * LD + j], Ad[lane * LD + k]);
+      // trailing update of the n(n+1)/2 entries (i, k), j < k <= i < R, spread
+      // over the lanes in row-major triangular order
+      const int T = n * (n + 1) / 2;
+      int ii = 0, kk = lane;
+      while (kk > ii) { kk -= ii + 1; ++ii; }
+      for (int e = lane; e < T; e += 32) {
+        const int i = j + 1 + ii, k = j + 1 + kk;
+        Ad[i * LD + k] = fma(-Ad[i * LD + j], Ad[k * LD + j], Ad[i * LD + k]);
+        kk += 32;
+        while (kk > ii) { kk -= ii + 1; ++ii; }
       }
     }
     if (ok) break;
@@ -224,14 +221,20 @@ __device__ void chol_inverse_to_smem(const float *g1, const float *g2, int R, do
     for (int j = 0; j < RT; ++j) Li[lane * LD + j] = 0.f;
   __syncwarp();
   for (int k = 0; k < R && ok; ++k) {
-    if (lane == k) {
-      const float inv = (float)dinv[k];
-      for (int j = 0; j <= k; ++j) Li[k * LD + j] = ((j == k ? 1.f : 0.f) + Li[k * LD + j]) * inv;
-    }
+    // finish row k of L^-1 (one column per lane), then subtract L[i][k] times it
+    // from every row i > k: the (R-1-k) x (k+1) updates spread over the lanes
+    const float inv = (float)dinv[k];
+    if (lane <= k) Li[k * LD + lane] = ((lane == k ? 1.f : 0.f) + Li[k * LD + lane]) * inv;
     __syncwarp();
-    if (lane > k && lane < R) {
-      const float lik = (float)Ad[lane * LD + k];
-      for (int j = 0; j <= k; ++j) Li[lane * LD + j] = fmaf(-lik, Li[k * LD + j], Li[lane * LD + j]);
+    const int rows = R - 1 - k, cols = k + 1;
+    int ii = lane / cols, jj = lane - (lane / cols) * cols;   // walk e = lane, lane + 32, ...
+    const int step_i = 32 / cols, step_j = 32 - step_i * cols;
+    for (int e = lane; e < rows * cols; e += 32) {
+      const int i = k + 1 + ii;
+      Li[i * LD + jj] = fmaf(-(float)Ad[i * LD + k], Li[k * LD + jj], Li[i * LD + jj]);
+      ii += step_i;
+      jj += step_j;
+      if (jj >= cols) { jj -= cols; ++ii; }
     }
     __syncwarp();
   }
@@ -276,19 +279,26 @@ __device__ __forceinline__ void smem_gram(const float *Fs, int Q, float *Gout) {
 template <int RT>
 __global__ void __launch_bounds__(256, 1)
     als_solve_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
-                     const float *__restrict__ G1, const float *__restrict__ G2,
+                     int64_t row_stride, const float *__restrict__ G1,
+                     const float *__restrict__ G2,
                      float *__restrict__ F, float *__restrict__ Gout,
                      __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int R, int normalize,
                      int *status) {
   extern __shared__ __align__(16) float Fs[];   // [Q][RT]
   __shared__ __align__(16) float Gi[RT * RT];
   __shared__ float Li[RT * (RT + 1)];
-  __shared__ double Ad[RT * (RT + 1)], dinv[RT];
+  __shared__ double Ad[RT * (RT + 1)], Gd[RT * (RT + 1)], dinv[RT];
   __shared__ float red[8 * RT], out[RT];
   __shared__ int ok_s;
   const int p = blockIdx.x;
   const float *g1 = G1 + (int64_t)p * RT * RT, *g2 = G2 + (int64_t)p * RT * RT;
-  if (threadIdx.x < 32) chol_inverse_to_smem<RT>(g1, g2, R, Ad, dinv, Li, &ok_s);
+  // Hadamard product of the Grams in fp64, loaded by every thread at once
+  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
+    const int i = e / RT, k = e % RT;
+    Gd[i * (RT + 1) + k] = (double)g1[e] * (double)g2[e];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) chol_inverse_to_smem<RT>(Gd, R, Ad, dinv, Li, &ok_s);
   __syncthreads();
   if (!ok_s && threadIdx.x == 0) atomicOr(status, kDevCholesky);
 
@@ -312,7 +322,7 @@ __global__ void __launch_bounds__(256, 1)
     for (int r = 0; r < RT; ++r) m[r] = 0.f;
     for (int sp = 0; sp < nsplit; ++sp) {
       const float4 *mp = reinterpret_cast<const float4 *>(M + sp * split_stride +
-                                                          ((int64_t)p * Q + q) * RT);
+                                                          ((int64_t)p * Q + q) * row_stride);
 #pragma unroll
       for (int r4 = 0; r4 < RT / 4; ++r4) {
         const float4 v = mp[r4];
@@ -494,13 +504,17 @@ __global__ void tc_m2_kernel(const float *__restrict__ Tc, const float *__restri
 
 static int block_for(int Q) { return ((Q + 31) / 32) * 32; }
 
+// M row q of replica p is sum_{s < nsplit} M[s * split_stride + (p * Q + q) * row_stride]
+// (row_stride 0 means RT).
 template <int RT>
 static void solve(const float *M, int nsplit, int64_t split_stride, const float *G1,
                   const float *G2, float *F, float *Gout, __nv_bfloat16 *Ft, int NP, int P,
-                  int Q, int R, int normalize, int *status, cudaStream_t st) {
+                  int Q, int R, int normalize, int *status, cudaStream_t st,
+                  int64_t row_stride = 0) {
   const size_t smem = (size_t)Q * RT * sizeof(float);
-  als_solve_kernel<RT><<<P, 256, smem, st>>>(M, nsplit, split_stride, G1, G2, F, Gout, Ft, NP, Q,
-                                             R, normalize, status);
+  als_solve_kernel<RT><<<P, 256, smem, st>>>(M, nsplit, split_stride,
+                                             row_stride ? row_stride : RT, G1, G2, F, Gout, Ft,
+                                             NP, Q, R, normalize, status);
   count_launch();
 }
 
@@ -568,6 +582,9 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   tc.B = b.Ct; tc.b_inner = Q; tc.b_rows = (int64_t)P * NP; tc.b_rows_per_z = NP;
   tc.M = (int)QQ; tc.N = RT; tc.K = Q; tc.BN = NP; tc.batch = P; tc.ksplit = 1;
   tc.D = b.H; tc.s_split = 0; tc.s_z = QQ * RT; tc.s_m = RT;
+  // M1 fused into the Tc GEMM: per-warp partials over 32 consecutive b
+  const bool fuse_m1 = Q % 32 == 0;
+  if (fuse_m1) { tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; }
   const int ks = tc_gemm_splits(m3.K, b.ksplit);
   const dim3 gKR(Q, P);
   const size_t smem_kr = (size_t)Q * RT * sizeof(float);
@@ -591,13 +608,20 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     mk(kStAlsGemm, 1);
     ok = ok && tc_gemm_store(tc, b.status, st);
     mk(kStAlsGemm, 0);
-    mk(kStAlsAux, 1);
-    tc_m1_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Bf, Q, b.M);
-    count_launch();
-    mk(kStAlsAux, 0);
-    mk(kStAlsSolve, 1);
-    solve<RT>(b.M, 1, 0, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status, st);
-    mk(kStAlsSolve, 0);
+    if (fuse_m1) {
+      mk(kStAlsSolve, 1);
+      solve<RT>(b.Mparts, Q / 32, RT, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status,
+                st, (int64_t)(Q / 32) * RT);
+      mk(kStAlsSolve, 0);
+    } else {
+      mk(kStAlsAux, 1);
+      tc_m1_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Bf, Q, b.M);
+      count_launch();
+      mk(kStAlsAux, 0);
+      mk(kStAlsSolve, 1);
+      solve<RT>(b.M, 1, 0, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status, st);
+      mk(kStAlsSolve, 0);
+    }
     mk(kStAlsAux, 1);
     tc_m2_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Af, Q, b.M);
     count_launch();

@@ -160,15 +160,23 @@ struct TcShape {
 
 // Plain fp32 store: D[split * s_split + z * s_z + m * s_m + n] (split-K partials).
 struct TcStoreEpi {
+  static constexpr bool kRowMajor = true;   // rows are contiguous in n
   float *D;
   int64_t s_split, s_z, s_m;
-  __device__ __forceinline__ void operator()(int z, int split, int m, int n, float v) const {
-    D[(int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n] = v;
+  // optional fused reduction (replica ALS): with rows m = a * Q + b, every warp
+  // block of 32 rows (one a, 32 consecutive b) also writes
+  //   part[z][m / 32][n] = sum_{i < 32} D(m + i, n) * Bfac[z][b + i][n]
+  const float *Bfac;
+  float *part;
+  int Q, RT;
+  __device__ __forceinline__ float *row(int z, int split, int m) const {
+    return D + (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m;
   }
 };
 
 // Mode-2 epilogue: row m = k * I + i, column c of V_all -> every replica owning c.
 struct Mode2TcEpi {
+  static constexpr bool kRowMajor = false;
   __nv_bfloat16 *T;
   const float *scale;
   int64_t I;
@@ -189,14 +197,50 @@ struct Mode2TcEpi {
 
 // Mode-1 epilogue: batch z = k * P + p, row a, column b -> T2[p][k][a][b].
 struct Mode1TcEpi {
+  static constexpr bool kRowMajor = true;
   float *T2;
   int64_t t;
   int P, Q;
-  __device__ __forceinline__ void operator()(int z, int, int a, int b, float v) const {
+  const float *Bfac = nullptr;   // no fused reduction
+  float *part = nullptr;
+  int RT = 0;
+  __device__ __forceinline__ float *row(int z, int, int a) const {
     const int k = z / P, p = z - k * P;
-    T2[(((int64_t)p * t + k) * Q + a) * Q + b] = v;
+    return T2 + (((int64_t)p * t + k) * Q + a) * Q;
   }
 };
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+// TMA load multicast to the CTAs of `mask` (same shared-memory offset and
+// mbarrier offset in each of them).
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                               int x, int y, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+// Arrives (once MMAs issued so far complete) on the mbarrier at this offset in
+// every CTA of `mask`.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -204,11 +248,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // Persistent GEMM: one CTA per SM walks the tiles (N fastest, then M, then the
 // batch index); tensor memory holds two accumulators so the epilogue of one
-// tile overlaps the main loop of the next.
+// tile overlaps the main loop of the next.  With CL > 1 the CTAs form clusters
+// of CL along M that work on CL vertically adjacent tiles of the same N range:
+// each CTA loads its own A tile and 1/CL of the shared B tile, multicast to the
+// whole cluster, so B crosses the L2 once per cluster instead of once per CTA;
+// a stage is refilled only after the MMAs of every CTA in the cluster released it.
 //   warp 0 lane 0 : TMA producer        full[s]  <- TMA bytes,  waits empty[s]
 //   warp 1 lane 0 : MMA issuer          empty[s] <- commit,     acc_full[b] <- commit
 //   warps 2..5    : epilogue (lane quadrant = warp % 4), acc_empty[b] <- 4 arrivals
-template <int KIND, class Epi>
+template <int KIND, int CL, class Epi>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcShape sh, const Epi epi, int batch, int *status) {
@@ -227,19 +275,27 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t *drain = acc_empty + 2;
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+  // row-major epilogues stage each warp's 32 x 32 block here to store whole rows
+  float *stage_all = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(tmem_holder + 2) + 15) & ~static_cast<uintptr_t>(15));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kElemsPerRow = KIND == 0 ? 64 : 128;   // 128 bytes of K
   const int nk_all = (sh.K + kElemsPerRow - 1) / kElemsPerRow;
   const int tiles_n = sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN;
   const int tiles_m = (sh.M + kBM - 1) / kBM;
-  const int total = tiles_n * tiles_m * batch;
+  const int groups_m = (tiles_m + CL - 1) / CL;        // CL vertically adjacent tiles
+  const int total = tiles_n * groups_m * batch;        // work items (tile groups)
   const int per_split = sh.ksplit > 1 ? (nk_all + sh.ksplit - 1) / sh.ksplit : nk_all;
+  const int crank = CL > 1 ? (int)cluster_ctarank() : 0;
+  const int item0 = CL > 1 ? (int)blockIdx.x / CL : (int)blockIdx.x;
+  const int nitems = CL > 1 ? (int)gridDim.x / CL : (int)gridDim.x;
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);   // released by the MMAs of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -252,15 +308,16 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 1) tmem_alloc(tmem_holder, sh.tmem_cols);
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync_all();   // peers' barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  // tile -> (z, m0, n0 or split, first K block, K blocks)
+  // work item -> (z, m0, n0 or split, first K block, K blocks)
   auto decode = [&](int tile, int &z, int &m0, int &n0, int &split, int &kb0, int &nk) {
     const int nt = tile % tiles_n;
     const int rest = tile / tiles_n;
-    m0 = (rest % tiles_m) * kBM;
-    z = rest / tiles_m;
+    m0 = ((rest % groups_m) * CL + crank) * kBM;
+    z = rest / groups_m;
     if (sh.ksplit > 1) {
       split = nt; n0 = 0; kb0 = nt * per_split; nk = min(per_split, nk_all - kb0);
     } else {
@@ -272,11 +329,12 @@ __global__ void __launch_bounds__(192, 1)
     // TMA producer
     uint32_t it = 0;
     bool aborted = false;
-    for (int tile = blockIdx.x; tile < total && !aborted; tile += gridDim.x) {
+    for (int tile = item0; tile < total && !aborted; tile += nitems) {
       int z, m0, n0, split, kb0, nk;
       decode(tile, z, m0, n0, split, kb0, nk);
       const int a_row = (z / sh.zdiv) * sh.a_hi + (z % sh.zdiv) * sh.a_lo + m0;
       const int b_row = (z / sh.zdiv) * sh.b_hi + (z % sh.zdiv) * sh.b_lo + n0;
+      const int b_part = sh.BN / CL;   // rows of B this CTA loads for the cluster
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = it % stages;
         const uint32_t ph = (it / stages) & 1u;
@@ -288,7 +346,12 @@ __global__ void __launch_bounds__(192, 1)
         }
         mbar_expect_tx(&full[s], a_bytes + b_bytes);
         tma_load_2d(sA + s * a_bytes, &tmA, &full[s], (kb0 + kb) * kElemsPerRow, a_row);
-        tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb0 + kb) * kElemsPerRow, b_row);
+        if constexpr (CL > 1) {
+          tma_load_2d_mc(sB + s * b_bytes + crank * b_part * kRowBytes, &tmB, &full[s],
+                         (kb0 + kb) * kElemsPerRow, b_row + crank * b_part, kMask);
+        } else {
+          tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb0 + kb) * kElemsPerRow, b_row);
+        }
       }
     }
     if (aborted) {
@@ -306,7 +369,7 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t idesc = make_idesc(KIND, sh.BN);
     uint32_t it = 0, local = 0;
     bool aborted = false;
-    for (int tile = blockIdx.x; tile < total && !aborted; tile += gridDim.x, ++local) {
+    for (int tile = item0; tile < total && !aborted; tile += nitems, ++local) {
       int z, m0, n0, split, kb0, nk;
       decode(tile, z, m0, n0, split, kb0, nk);
       const uint32_t buf = local & 1u, use = local >> 1;
@@ -333,7 +396,8 @@ __global__ void __launch_bounds__(192, 1)
           mma_issue<KIND>(d, make_desc_sw128(a0 + kk * 32), make_desc_sw128(b0 + kk * 32), idesc,
                           (kb > 0 || kk > 0) ? 1u : 0u);
         }
-        mma_commit(&empty[s]);
+        if constexpr (CL > 1) mma_commit_mc(&empty[s], kMask);
+        else mma_commit(&empty[s]);
       }
       mma_commit(&acc_full[buf]);
     }
@@ -346,7 +410,7 @@ __global__ void __launch_bounds__(192, 1)
     // epilogue
     const int quad = warp & 3;
     uint32_t local = 0;
-    for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++local) {
+    for (int tile = item0; tile < total; tile += nitems, ++local) {
       int z, m0, n0, split, kb0, nk;
       decode(tile, z, m0, n0, split, kb0, nk);
       const uint32_t buf = local & 1u, use = local >> 1;
@@ -363,11 +427,36 @@ __global__ void __launch_bounds__(192, 1)
       for (int c0 = 0; c0 < sh.BN; c0 += 32) {
         uint32_t r[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + buf * sh.BN + c0, r);
-        if (m < sh.M) {
+        if constexpr (Epi::kRowMajor) {
+          // transpose through shared memory: instruction `i` stores row i of the
+          // warp's block, lanes covering 32 consecutive columns
+          float *stg = stage_all + (warp - 2) * 32 * 33;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
-            if (n < sh.N) epi(z, split, m, n, __uint_as_float(r[j]));
+          for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(r[j]);
+          __syncwarp();
+          const int n = n0 + c0 + lane;
+          for (int i = 0; i < 32; ++i) {
+            const int mi = m0 + quad * 32 + i;
+            if (mi < sh.M && n < sh.N) epi.row(z, split, mi)[n] = stg[i * 33 + lane];
+          }
+          if (epi.part != nullptr) {
+            const int mb = m0 + quad * 32;   // 32 rows of one a when 32 divides Q
+            if (mb < sh.M && n < sh.N) {
+              const int b0 = mb % epi.Q;
+              const float *bf = epi.Bfac + ((int64_t)z * epi.Q + b0) * epi.RT + n;
+              float acc = 0.f;
+              for (int i = 0; i < 32; ++i) acc = fmaf(stg[i * 33 + lane], bf[i * epi.RT], acc);
+              epi.part[((int64_t)z * (sh.M / 32) + mb / 32) * epi.RT + n] = acc;
+            }
+          }
+          __syncwarp();
+        } else {
+          if (m < sh.M) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + c0 + j;
+              if (n < sh.N) epi(z, split, m, n, __uint_as_float(r[j]));
+            }
           }
         }
       }
@@ -378,6 +467,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync_all();   // no peer still writes into this CTA's memory
   if (warp == 1) tmem_dealloc(tmem, sh.tmem_cols);
 }
 
@@ -428,27 +518,59 @@ int sm_count() {
   return n;
 }
 
-template <int KIND, class Epi>
+template <int KIND, int CL, class Epi>
 bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
                const Epi &epi, int *status, cudaStream_t st) {
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
   const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes;
-  sh.stages = static_cast<int>((200 * 1024) / per_stage);
+  const size_t stage_bytes = Epi::kRowMajor ? 4 * 32 * 33 * sizeof(float) + 16 : 0;
+  sh.stages = static_cast<int>((200 * 1024 - stage_bytes) / per_stage);
   if (sh.stages > 8) sh.stages = 8;
   if (sh.stages < 2) return false;
-  const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 5) * 8 + 16;
-  if (cudaFuncSetAttribute(tc_gemm_kernel<KIND, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 5) * 8 + 16 + stage_bytes;
+  auto kern = tc_gemm_kernel<KIND, CL, Epi>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return false;
   const int tiles_n = sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN;
-  const int64_t tiles = (int64_t)tiles_n * ((sh.M + kBM - 1) / kBM) * batch;
-  if (tiles <= 0 || tiles > (int64_t)1 << 30) return false;
-  const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-  tc_gemm_kernel<KIND, Epi><<<grid, 192, smem, st>>>(ma, mb, sh, epi, batch, status);
+  const int64_t items =
+      (int64_t)tiles_n * ((((sh.M + kBM - 1) / kBM) + CL - 1) / CL) * batch;
+  if (items <= 0 || items > (int64_t)1 << 30) return false;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(192);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  int slots = sm_count();
+  if (CL > 1) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) !=
+        cudaSuccess)
+      cudaGetLastError();
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(CL * 1024);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess ||
+        nclusters < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    slots = nclusters;   // co-resident clusters
+  }
+  const int grid_items = (int)(items < slots ? items : slots);
+  cfg.gridDim = dim3(grid_items * CL);
+  if (cudaLaunchKernelEx(&cfg, kern, ma, mb, sh, epi, batch, status) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   count_launch();
   count_tc_launch();
-  return cudaPeekAtLastError() == cudaSuccess;
+  return true;
 }
 
 }  // namespace
@@ -467,17 +589,24 @@ bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st) {
   const bool fp8 = a.tx == Elem::E4M3;
   const int64_t M = a.t * a.I;
   if (M > (1 << 30) || a.J > (1 << 30)) return false;
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mb4;
   const int BN = 256;
-  if (!make_map(&ma, a.X, fp8, a.J, M, kBM) || !make_map(&mb, a.Vt, fp8, a.J, a.Qd, BN))
+  if (!make_map(&ma, a.X, fp8, a.J, M, kBM) || !make_map(&mb, a.Vt, fp8, a.J, a.Qd, BN) ||
+      !make_map(&mb4, a.Vt, fp8, a.J, a.Qd, BN / 4))
     return false;
   TcShape sh{};
   sh.ksplit = 1;
   sh.M = static_cast<int>(M); sh.N = a.Qd; sh.K = static_cast<int>(a.J); sh.BN = BN;
   sh.zdiv = 1; sh.a_hi = 0; sh.a_lo = 0; sh.b_hi = 0; sh.b_lo = 0;
   Mode2TcEpi epi{static_cast<__nv_bfloat16 *>(a.T), a.slice_scale, a.I, a.P, a.Q, a.S};
-  return fp8 ? launch_tc<1>(ma, mb, sh, 1, epi, status, st)
-             : launch_tc<0>(ma, mb, sh, 1, epi, status, st);
+  // clusters of 4 along M share the 256-row V tile (multicast); plain
+  // persistent launch if the cluster launch is refused
+  if (fp8) {
+    if (launch_tc<1, 4>(ma, mb4, sh, 1, epi, status, st)) return true;
+    return launch_tc<1, 1>(ma, mb, sh, 1, epi, status, st);
+  }
+  if (launch_tc<0, 4>(ma, mb4, sh, 1, epi, status, st)) return true;
+  return launch_tc<0, 1>(ma, mb, sh, 1, epi, status, st);
 }
 
 bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
@@ -497,7 +626,7 @@ bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
   sh.a_hi = 0; sh.a_lo = a.Q;      // A rows: p * Q
   sh.b_hi = a.P * a.Q; sh.b_lo = a.Q;   // B rows: (k * P + p) * Q
   Mode1TcEpi epi{a.T2, a.t, a.P, a.Q};
-  return launch_tc<0>(ma, mb, sh, static_cast<int>(a.t * a.P), epi, status, st);
+  return launch_tc<0, 1>(ma, mb, sh, static_cast<int>(a.t * a.P), epi, status, st);
 }
 
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
@@ -514,9 +643,10 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   const int per = (nk + ks - 1) / ks;
   ks = (nk + per - 1) / per;            // every split gets at least one K block
   sh.ksplit = ks;
-  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m};
+  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT};
+  if (g.m1_part && (g.BN != 32 || g.Q % 32 || ks > 1)) return false;
   if (ks > 1 && (g.N > g.BN)) return false;
-  return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st);
+  return launch_tc<0, 1>(ma, mb, sh, g.batch, epi, status, st);
 }
 
 int tc_gemm_splits(int K, int ksplit) {

@@ -429,9 +429,10 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     const int mt = (c.Q + 127) / 128;
     const int want = (4 * 152 + mt * c.P - 1) / (mt * c.P);
     x->als_ks = als_tc_splits(c.P, c.Q, want < 1 ? 1 : want);
+    const size_t nparts = (size_t)(x->als_ks > (c.Q / 32) ? x->als_ks : (c.Q / 32));
     ok = x->alloc(x->Xa, P * Q * Q * Q) && x->alloc(x->Xc, P * Q * Q * Q) &&
          x->alloc(x->KR, P * kAlsNP * Q * Q) && x->alloc(x->Ctb, P * kAlsNP * Q) &&
-         x->alloc(x->Mparts, (size_t)x->als_ks * P * Q * RT);
+         x->alloc(x->Mparts, nparts * P * Q * RT);
     x->als_tc = ok;
   }
   void *ut = nullptr, *vt = nullptr;

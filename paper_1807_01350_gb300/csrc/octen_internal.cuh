@@ -101,6 +101,11 @@ struct TcStoreArgs {
   const void *B; int64_t b_inner, b_rows; int b_rows_per_z;
   int M, N, K, BN, batch, ksplit;
   float *D; int64_t s_split, s_z, s_m;
+  // optional fused reduction for rows m = a * Q + b (needs BN == 32, Q % 32 == 0):
+  // m1_part[z][m / 32][n] = sum over the 32 rows of D(m, n) * m1_B[z][b][n]
+  const float *m1_B = nullptr;
+  float *m1_part = nullptr;
+  int Q = 0, RT = 0;
 };
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st);
 int tc_gemm_splits(int K, int ksplit);   // the split count tc_gemm_store will use
