@@ -93,6 +93,16 @@ octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
  * V_p^T B, anchor matching, lift of A and B, t new rows of C.  Limit t <= 64. */
 octen_status octen_append(octen_ctx *ctx, const void *X_new, int64_t t, const float *W_new);
 
+/* One append on each of n independent decompositions (many streams with
+ * uneven shapes, ranks and batch sizes): the work of every context is enqueued
+ * on that context's own stream before any of them is waited for, so streams
+ * created on different CUDA streams run concurrently.  Arguments per stream as
+ * in octen_append.  Every context whose work was enqueued without error is
+ * advanced; the first error is returned (details via octen_last_error of that
+ * context). */
+octen_status octen_append_many(octen_ctx *const *ctxs, int n, const void *const *X_new,
+                               const int64_t *t, const float *const *W_new);
+
 /* Copies A (I x R), B (J x R) and C (K x R, K = rows so far) into caller
  * buffers; any pointer may be NULL to skip it.  *K_out (if non-NULL) gets K. */
 octen_status octen_get_factors(const octen_ctx *ctx, float *A, float *B, float *C,

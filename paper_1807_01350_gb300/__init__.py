@@ -15,7 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Octen", "OctenError", "compress", "lib", "library_path", "PREC", "launch_count"]
+__all__ = ["Octen", "OctenError", "append_many", "compress", "lib", "library_path", "PREC",
+           "launch_count"]
 
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 _STATUS = {0: "OCTEN_OK", 1: "OCTEN_EINVAL", 2: "OCTEN_ENOMEM", 3: "OCTEN_ECUDA",
@@ -54,6 +55,7 @@ def lib() -> ctypes.CDLL:
         L.octen_create.argtypes = [ctypes.POINTER(_Config), vp, ctypes.POINTER(vp)]
         L.octen_init.argtypes = [vp, vp, i64, f32p, f32p, f32p, f32p, f32p, f32p]
         L.octen_append.argtypes = [vp, vp, i64, f32p]
+        L.octen_append_many.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         L.octen_get_factors.argtypes = [vp, f32p, f32p, f32p, ctypes.POINTER(i64)]
         L.octen_rows.argtypes = [vp]
         L.octen_rows.restype = i64
@@ -82,7 +84,8 @@ def lib() -> ctypes.CDLL:
         L.octen_set_timing.argtypes = [vp, ctypes.c_int]
         L.octen_stage_times.argtypes = [vp, vp, vp]
         L.octen_reset_stage_times.argtypes = [vp]
-        for name in ("octen_create", "octen_init", "octen_append", "octen_get_factors",
+        for name in ("octen_create", "octen_init", "octen_append", "octen_append_many",
+                     "octen_get_factors",
                      "octen_fit", "octen_get_replicas", "octen_get_replica_factors",
                      "octen_compress", "octen_compress_noalloc", "octen_set_timing",
                      "octen_save", "octen_load",
@@ -276,6 +279,21 @@ class Octen:
             self.close()
         except Exception:
             pass
+
+
+def append_many(streams, batches, ws):
+    """One append on each of several Octen contexts (see octen_append_many)."""
+    L = lib()
+    keep: list = []
+    n = len(streams)
+    hs = (ctypes.c_void_p * n)(*[s._h.value for s in streams])
+    xs = (ctypes.c_void_p * n)(*[_slices(x, s.prec, keep) for x, s in zip(batches, streams)])
+    ts = (ctypes.c_int64 * n)(*[int(x.shape[0]) for x in batches])
+    wp = (ctypes.c_void_p * n)(*[_f32(w, keep) for w in ws])
+    st = L.octen_append_many(hs, n, xs, ts, wp)
+    if st != 0:
+        msgs = "; ".join(L.octen_last_error(s._h).decode() for s in streams)
+        raise OctenError(st, msgs)
 
 
 def compress(I, J, P, Q, S, X, U_all, V_all, W_all, prec="fp32", R=1, stream=None):

@@ -171,7 +171,7 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
 //   L[i][k] times it is subtracted from every row i > k, spread over the lanes.
 template <int RT>
 __device__ void chol_inverse_to_smem(const double *Gd, int R, double *Ad, double *dinv, float *Li,
-                                     int *ok_out) {
+                                     float *Lf, float *invf, int *ok_out) {
   constexpr int LD = RT + 1;
   const int lane = threadIdx.x & 31;
   bool ok = true;
@@ -206,16 +206,35 @@ __device__ void chol_inverse_to_smem(const double *Gd, int R, double *Ad, double
       const int T = n * (n + 1) / 2;
       int ii = 0, kk = lane;
       while (kk > ii) { kk -= ii + 1; ++ii; }
-      for (int e = lane; e < T; e += 32) {
-        const int i = j + 1 + ii, k = j + 1 + kk;
-        Ad[i * LD + k] = fma(-Ad[i * LD + j], Ad[k * LD + j], Ad[i * LD + k]);
-        kk += 32;
-        while (kk > ii) { kk -= ii + 1; ++ii; }
+      // up to four independent updates per round: all operands are loaded
+      // before the fused multiply-adds so their fp64 latencies overlap
+      for (int e = lane; e < T; e += 128) {
+        int idx[4];
+        double x[4], y[4], z[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool live = e + 32 * u < T;
+          const int i = j + 1 + ii, k = j + 1 + kk;
+          idx[u] = live ? i * LD + k : -1;
+          x[u] = live ? Ad[i * LD + j] : 0.0;
+          y[u] = live ? Ad[k * LD + j] : 0.0;
+          z[u] = live ? Ad[i * LD + k] : 0.0;
+          kk += 32;
+          while (kk > ii) { kk -= ii + 1; ++ii; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (idx[u] >= 0) Ad[idx[u]] = fma(-x[u], y[u], z[u]);
       }
     }
     if (ok) break;
   }
   __syncwarp();
+  // L in fp32 (Lf) and its reciprocal diagonal, converted once
+  if (ok && lane < R) {
+    for (int k = 0; k < lane; ++k) Lf[lane * LD + k] = (float)Ad[lane * LD + k];
+    invf[lane] = (float)dinv[lane];
+  }
   // L^-1 (fp32): Li rows accumulate -sum_{k<i} L[i][k] X[k][.] until row i is finished
   if (lane < RT)
     for (int j = 0; j < RT; ++j) Li[lane * LD + j] = 0.f;
@@ -223,18 +242,24 @@ __device__ void chol_inverse_to_smem(const double *Gd, int R, double *Ad, double
   for (int k = 0; k < R && ok; ++k) {
     // finish row k of L^-1 (one column per lane), then subtract L[i][k] times it
     // from every row i > k: the (R-1-k) x (k+1) updates spread over the lanes
-    const float inv = (float)dinv[k];
-    if (lane <= k) Li[k * LD + lane] = ((lane == k ? 1.f : 0.f) + Li[k * LD + lane]) * inv;
+    if (lane <= k) Li[k * LD + lane] = ((lane == k ? 1.f : 0.f) + Li[k * LD + lane]) * invf[k];
     __syncwarp();
     const int rows = R - 1 - k, cols = k + 1;
     int ii = lane / cols, jj = lane - (lane / cols) * cols;   // walk e = lane, lane + 32, ...
     const int step_i = 32 / cols, step_j = 32 - step_i * cols;
-    for (int e = lane; e < rows * cols; e += 32) {
-      const int i = k + 1 + ii;
-      Li[i * LD + jj] = fmaf(-(float)Ad[i * LD + k], Li[k * LD + jj], Li[i * LD + jj]);
-      ii += step_i;
-      jj += step_j;
+    for (int e = lane; e < rows * cols; e += 64) {
+      int i0 = k + 1 + ii, j0 = jj;
+      ii += step_i; jj += step_j;
       if (jj >= cols) { jj -= cols; ++ii; }
+      const bool live1 = e + 32 < rows * cols;
+      const int i1 = k + 1 + ii, j1 = jj;
+      ii += step_i; jj += step_j;
+      if (jj >= cols) { jj -= cols; ++ii; }
+      const float a0 = Lf[i0 * LD + k], b0 = Li[k * LD + j0], c0 = Li[i0 * LD + j0];
+      const float a1 = live1 ? Lf[i1 * LD + k] : 0.f, b1 = live1 ? Li[k * LD + j1] : 0.f;
+      const float c1 = live1 ? Li[i1 * LD + j1] : 0.f;
+      Li[i0 * LD + j0] = fmaf(-a0, b0, c0);
+      if (live1) Li[i1 * LD + j1] = fmaf(-a1, b1, c1);
     }
     __syncwarp();
   }
@@ -288,6 +313,7 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ __align__(16) float Gi[RT * RT];
   __shared__ float Li[RT * (RT + 1)];
   __shared__ double Ad[RT * (RT + 1)], Gd[RT * (RT + 1)], dinv[RT];
+  __shared__ float Lf[RT * (RT + 1)], invf[RT];
   __shared__ float red[8 * RT], out[RT];
   __shared__ int ok_s;
   const int p = blockIdx.x;
@@ -298,7 +324,7 @@ __global__ void __launch_bounds__(256, 1)
     Gd[i * (RT + 1) + k] = (double)g1[e] * (double)g2[e];
   }
   __syncthreads();
-  if (threadIdx.x < 32) chol_inverse_to_smem<RT>(Gd, R, Ad, dinv, Li, &ok_s);
+  if (threadIdx.x < 32) chol_inverse_to_smem<RT>(Gd, R, Ad, dinv, Li, Lf, invf, &ok_s);
   __syncthreads();
   if (!ok_s && threadIdx.x == 0) atomicOr(status, kDevCholesky);
 
@@ -456,17 +482,19 @@ template <int RT>
 __global__ void __launch_bounds__(256)
     kr_kernel(const float *__restrict__ Af, const float *__restrict__ Bf, int Q, int NP,
               __nv_bfloat16 *__restrict__ KR) {
-  extern __shared__ __align__(16) float Bs[];   // [Q][RT]
+  extern __shared__ __align__(16) float Bs[];   // [Q][RT + 1] (padded: lanes b hit distinct banks)
   __shared__ float arow[RT];
   const int a = blockIdx.x, p = blockIdx.y;
   const int64_t QQ = (int64_t)Q * Q;
-  for (int e = threadIdx.x; e < Q * RT; e += blockDim.x) Bs[e] = Bf[(int64_t)p * Q * RT + e];
+  for (int e = threadIdx.x; e < Q * RT; e += blockDim.x)
+    Bs[(e / RT) * (RT + 1) + e % RT] = Bf[(int64_t)p * Q * RT + e];
   if (threadIdx.x < RT) arow[threadIdx.x] = Af[((int64_t)p * Q + a) * RT + threadIdx.x];
   __syncthreads();
   __nv_bfloat16 *kr = KR + (int64_t)p * NP * QQ + (int64_t)a * Q;
   for (int b = threadIdx.x; b < Q; b += blockDim.x) {
 #pragma unroll
-    for (int r = 0; r < RT; ++r) kr[r * QQ + b] = __float2bfloat16_rn(arow[r] * Bs[b * RT + r]);
+    for (int r = 0; r < RT; ++r)
+      kr[r * QQ + b] = __float2bfloat16_rn(arow[r] * Bs[b * (RT + 1) + r]);
     for (int r = RT; r < NP; ++r) kr[r * QQ + b] = __float2bfloat16_rn(0.f);
   }
 }
@@ -587,7 +615,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   if (fuse_m1) { tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; }
   const int ks = tc_gemm_splits(m3.K, b.ksplit);
   const dim3 gKR(Q, P);
-  const size_t smem_kr = (size_t)Q * RT * sizeof(float);
+  const size_t smem_kr = (size_t)Q * (RT + 1) * sizeof(float);
   const dim3 gM((Q * RT + 255) / 256, P);
   bool ok = true;
   auto c_update = [&]() {

@@ -514,7 +514,13 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
   return OCTEN_OK;
 }
 
-octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
+}  // extern "C"
+
+namespace {
+
+// Enqueues one append on the context's stream (no final synchronisation; K is
+// advanced by the caller once the stream has finished without error).
+octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
   if (!x) return OCTEN_EINVAL;
   if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_append before octen_init");
   if (!X_new || !W_new || t < 1 || t > kChunk)
@@ -570,10 +576,39 @@ octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const floa
               x->splitk, octen_ctx::kSplitkFloats, C_new, x->dstatus, x->st);
   update_g(Wd, C_new, t, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
   x->mark(kStCsolve, 0);
+  return OCTEN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
+  octen_status s = append_enqueue(x, X_new, t, W_new);
+  if (s != OCTEN_OK) return s;
   s = x->sync_check("append");
   if (s != OCTEN_OK) return s;
   x->K += t;
   return OCTEN_OK;
+}
+
+octen_status octen_append_many(octen_ctx *const *ctxs, int n, const void *const *X_new,
+                               const int64_t *t, const float *const *W_new) {
+  if (!ctxs || !X_new || !t || !W_new || n < 1) return OCTEN_EINVAL;
+  octen_status first = OCTEN_OK;
+  std::vector<char> enqueued(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const octen_status s = append_enqueue(ctxs[i], X_new[i], t[i], W_new[i]);
+    enqueued[i] = s == OCTEN_OK;
+    if (s != OCTEN_OK && first == OCTEN_OK) first = s;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!enqueued[i]) continue;
+    const octen_status s = ctxs[i]->sync_check("append_many");
+    if (s == OCTEN_OK) ctxs[i]->K += t[i];
+    else if (first == OCTEN_OK) first = s;
+  }
+  return first;
 }
 
 octen_status octen_get_factors(const octen_ctx *cx, float *A, float *B, float *C,

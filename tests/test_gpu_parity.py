@@ -202,3 +202,48 @@ def test_checkpoint_resume_is_bit_identical(pkg, tmp_path):
     assert np.array_equal(g.replicas(), h.replicas())
     g.close()
     h.close()
+
+
+def test_append_many_uneven_streams(pkg):
+    """Several independent streams with uneven shapes, ranks and batch sizes,
+    each on its own CUDA stream, appended in one octen_append_many call: each
+    matches the oracle (bf16 tolerances) and equals its own single-stream
+    octen_append bit for bit."""
+    rng = np.random.default_rng(41)
+    cases = []
+    for i in range(4):
+        R = int(rng.integers(2, 7))
+        Q = int(rng.choice([12, 16, 20, 24]))
+        S = min(R, Q // 2)
+        cases.append(Case(int(rng.integers(40, 130)), int(rng.integers(40, 130)), R, 3, Q, S,
+                          int(rng.integers(8, 20)), (int(rng.integers(3, 12)),), 20,
+                          prec="bf16", seed=100 + i))
+    datas = [c.make() for c in cases]
+    streams = [torch.cuda.Stream() for _ in cases]
+
+    def start(case, d, stream):
+        g = pkg.Octen(case.I, case.J, case.R, case.P, case.Q, case.S, case.iters, case.prec,
+                      stream=stream)
+        g.init(slices(d["X"][:case.t_old], case.prec), dev(d["U"]), dev(d["V"]), dev(d["W"][0]),
+               dev(d["A0"]), dev(d["B0"]), dev(d["C0"]))
+        return g
+
+    many = [start(c, d, s) for c, d, s in zip(cases, datas, streams)]
+    torch.cuda.synchronize()
+    xs = [slices(d["X"][c.t_old:c.t_old + c.batches[0]], c.prec) for c, d in zip(cases, datas)]
+    ws = [dev(d["W"][1]) for d in datas]
+    pkg.append_many(many, xs, ws)
+    for c, d, g, x, w in zip(cases, datas, many, xs, ws):
+        single = start(c, d, None)
+        single.append(x, w)
+        for a, b in zip(g.factors(), single.factors()):
+            assert np.array_equal(a, b)
+        _, ref = c.oracle_run(d)
+        k = c.t_old + c.batches[0]
+        A, B, C = g.factors()
+        f = g.fit(slices(d["X"][:k], c.prec))
+        f_ref = oracle.fit(d["X"][:k], ref[0]["A"], ref[0]["B"], ref[0]["C"])
+        assert abs(f - f_ref) < TOL["bf16"]["fit"], (f, f_ref)
+        assert fms((A, B, C), (ref[0]["A"], ref[0]["B"], ref[0]["C"])) > TOL["bf16"]["fms"]
+        single.close()
+        g.close()
