@@ -147,17 +147,15 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x < RT) M[((int64_t)p * Q + b) * RT + threadIdx.x] = out[threadIdx.x];
 }
 
-// 1/sqrt(d) in fp64 by two Newton-Raphson steps y <- y (3 - d y^2) / 2 on
-// f(y) = y^-2 - d, seeded with the fp32 estimate (each step squares the
-// relative error: ~2^-22 -> 2^-44 -> below fp64 rounding).  Only fp64 multiplies
-// and adds on the pivot's critical path; outside the fp32 exponent range the
-// plain sqrt / division are used.
+// 1/sqrt(d) in fp64: the fp32 estimate refined by one Newton-Raphson step
+// y <- y (3 - d y^2) / 2 on f(y) = y^-2 - d, which squares its relative error
+// (~2^-22 -> ~2^-44).  Every fp64 operation on this GPU has a long latency and
+// this sits on the critical path of the factorisation, so the chain is kept
+// short; outside the fp32 exponent range the plain sqrt / division are used.
 __device__ __forceinline__ double rsqrt_nr(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  double y = (double)rsqrtf((float)d);
-  y = y * fma(-0.5 * d, y * y, 1.5);
-  y = y * fma(-0.5 * d, y * y, 1.5);
-  return y;
+  const double y = (double)rsqrtf((float)d);
+  return y * fma(-0.5 * d, y * y, 1.5);
 }
 
 // Warp 0: factor G1 * G2 = L L^T in fp64 and write L^-1 (fp32, lower
@@ -165,10 +163,11 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
 // success flag.  The matrix lives in shared memory (Ad, fp64, padded rows); the
 // loops are kept rolled so that the code stays in the instruction cache (this
 // runs once per launch on a single warp).
-//   right-looking Cholesky: for each pivot j, lane 0 forms L[j][j] (Newton
-//   rsqrt), the lanes scale column j and share the trailing update of the
-//   entries (i, k), j < k <= i; then L^-1 row by row: row k is finished and
-//   L[i][k] times it is subtracted from every row i > k, spread over the lanes.
+//   right-looking Cholesky: the lanes scale column j by the pivot's reciprocal,
+//   lane 0 finishes diagonal entry j+1 and forms the next pivot (look-ahead)
+//   while lanes 1..31 share the rest of the trailing update; then L^-1 row by
+//   row: row k is finished and L[i][k] times it is subtracted from every row
+//   i > k, spread over the lanes.
 template <int RT>
 __device__ void chol_inverse_to_smem(const double *Gd, int R, double *Ad, double *dinv, float *Li,
                                      float *Lf, float *invf, int *ok_out) {
@@ -187,44 +186,53 @@ __device__ void chol_inverse_to_smem(const double *Gd, int R, double *Ad, double
       for (int k = 0; k <= lane; ++k) Ad[lane * LD + k] = Gd[lane * LD + k] + (k == lane ? add : 0.0);
     }
     ok = true;
+    // pivot 0; every later pivot is formed one step ahead (look-ahead below)
+    if (lane == 0) {
+      const double d = Ad[0];
+      const double inv = d > 0.0 ? rsqrt_nr(d) : 0.0;
+      Ad[0] = d > 0.0 ? d * inv : 1.0;
+      dinv[0] = inv;
+    }
     for (int j = 0; j < R; ++j) {
-      __syncwarp();
-      if (lane == 0) {
-        const double d = Ad[j * LD + j];
-        const double inv = d > 0.0 ? rsqrt_nr(d) : 0.0;
-        Ad[j * LD + j] = d > 0.0 ? d * inv : 1.0;
-        dinv[j] = inv;
-      }
       __syncwarp();
       const double inv = dinv[j];
       if (!(inv > 0.0)) { ok = false; break; }
       const int n = R - 1 - j;   // rows below the pivot
       if (lane < n) Ad[(j + 1 + lane) * LD + j] *= inv;
       __syncwarp();   // every L[k][j] is scaled before any lane reads it
-      // trailing update of the n(n+1)/2 entries (i, k), j < k <= i < R, spread
-      // over the lanes in row-major triangular order
-      const int T = n * (n + 1) / 2;
-      int ii = 0, kk = lane;
-      while (kk > ii) { kk -= ii + 1; ++ii; }
-      // up to four independent updates per round: all operands are loaded
-      // before the fused multiply-adds so their fp64 latencies overlap
-      for (int e = lane; e < T; e += 128) {
-        int idx[4];
-        double x[4], y[4], z[4];
+      if (n == 0) break;
+      if (lane == 0) {
+        // look-ahead: finish diagonal entry j+1 and form the next pivot now, so
+        // its fp64 chain overlaps the rest of this step's trailing update
+        const double l = Ad[(j + 1) * LD + j];
+        const double d = fma(-l, l, Ad[(j + 1) * LD + j + 1]);
+        const double inv1 = d > 0.0 ? rsqrt_nr(d) : 0.0;
+        Ad[(j + 1) * LD + j + 1] = d > 0.0 ? d * inv1 : 1.0;
+        dinv[j + 1] = inv1;
+      } else {
+        // the other n(n+1)/2 - 1 entries (i, k), j < k <= i < R, (i, k) != (j+1, j+1),
+        // in row-major triangular order, entry e to lane 1 + (e - 1) % 31
+        const int T = n * (n + 1) / 2;
+        int ii = 0, kk = lane;   // triangular index of e = lane
+        while (kk > ii) { kk -= ii + 1; ++ii; }
+        for (int e = lane; e < T; e += 62) {
+          int idx[2];
+          double x[2], y[2], z[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool live = e + 32 * u < T;
-          const int i = j + 1 + ii, k = j + 1 + kk;
-          idx[u] = live ? i * LD + k : -1;
-          x[u] = live ? Ad[i * LD + j] : 0.0;
-          y[u] = live ? Ad[k * LD + j] : 0.0;
-          z[u] = live ? Ad[i * LD + k] : 0.0;
-          kk += 32;
-          while (kk > ii) { kk -= ii + 1; ++ii; }
+          for (int u = 0; u < 2; ++u) {
+            const bool live = e + 31 * u < T;
+            const int i = j + 1 + ii, k = j + 1 + kk;
+            idx[u] = live ? i * LD + k : -1;
+            x[u] = live ? Ad[i * LD + j] : 0.0;
+            y[u] = live ? Ad[k * LD + j] : 0.0;
+            z[u] = live ? Ad[i * LD + k] : 0.0;
+            kk += 31;
+            while (kk > ii) { kk -= ii + 1; ++ii; }
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (idx[u] >= 0) Ad[idx[u]] = fma(-x[u], y[u], z[u]);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (idx[u] >= 0) Ad[idx[u]] = fma(-x[u], y[u], z[u]);
       }
     }
     if (ok) break;
@@ -270,29 +278,28 @@ __device__ void chol_inverse_to_smem(const double *Gd, int R, double *Ad, double
 }
 
 // Gram of the Q x RT factor held in shared memory: Gout[r][s] = sum_q F[q][r] F[q][s].
-// Each thread accumulates its entries over q with independent chains.
+// Thread t < (RT/2)^2 accumulates the 2 x 2 block at rows 2 (t / (RT/2)), columns
+// 2 (t % (RT/2)) with two 8-byte shared loads per row of F.
 template <int RT>
 __device__ __forceinline__ void smem_gram(const float *Fs, int Q, float *Gout) {
-  constexpr int kPer = (RT * RT + 255) / 256;
-  float acc[kPer];
-  int rr[kPer], cc[kPer];
-#pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int e = threadIdx.x + 256 * u;
-    rr[u] = e < RT * RT ? e / RT : 0;
-    cc[u] = e < RT * RT ? e % RT : 0;
-    acc[u] = 0.f;
-  }
+  constexpr int H = RT / 2;
+  const int t = threadIdx.x;
+  if (t >= H * H) return;
+  const int r0 = 2 * (t / H), c0 = 2 * (t % H);
+  float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
 #pragma unroll 4
   for (int q = 0; q < Q; ++q) {
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) acc[u] = fmaf(Fs[q * RT + rr[u]], Fs[q * RT + cc[u]], acc[u]);
+    const float2 x = *reinterpret_cast<const float2 *>(Fs + q * RT + r0);
+    const float2 y = *reinterpret_cast<const float2 *>(Fs + q * RT + c0);
+    a00 = fmaf(x.x, y.x, a00);
+    a01 = fmaf(x.x, y.y, a01);
+    a10 = fmaf(x.y, y.x, a10);
+    a11 = fmaf(x.y, y.y, a11);
   }
-#pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int e = threadIdx.x + 256 * u;
-    if (e < RT * RT) Gout[e] = acc[u];
-  }
+  Gout[r0 * RT + c0] = a00;
+  Gout[r0 * RT + c0 + 1] = a01;
+  Gout[(r0 + 1) * RT + c0] = a10;
+  Gout[(r0 + 1) * RT + c0 + 1] = a11;
 }
 
 // F_p = M_p (G1_p * G2_p)^-1 with G1, G2 the cached R x R Grams of the other two
@@ -324,9 +331,41 @@ __global__ void __launch_bounds__(256, 1)
     Gd[i * (RT + 1) + k] = (double)g1[e] * (double)g2[e];
   }
   __syncthreads();
+  const int q = threadIdx.x;
+  float m[RT];
+#pragma unroll
+  for (int r = 0; r < RT; ++r) m[r] = 0.f;
+  // row q of the MTTKRP: sum of the partials (independent loads, 4 at a time)
+  auto load_m = [&]() {
+    if (q >= Q) return;
+    const float *base = M + ((int64_t)p * Q + q) * row_stride;
+    int sp = 0;
+    for (; sp + 4 <= nsplit; sp += 4) {
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4) {
+        const float4 v0 = reinterpret_cast<const float4 *>(base + (sp + 0) * split_stride)[r4];
+        const float4 v1 = reinterpret_cast<const float4 *>(base + (sp + 1) * split_stride)[r4];
+        const float4 v2 = reinterpret_cast<const float4 *>(base + (sp + 2) * split_stride)[r4];
+        const float4 v3 = reinterpret_cast<const float4 *>(base + (sp + 3) * split_stride)[r4];
+        m[4 * r4] += (v0.x + v1.x) + (v2.x + v3.x);
+        m[4 * r4 + 1] += (v0.y + v1.y) + (v2.y + v3.y);
+        m[4 * r4 + 2] += (v0.z + v1.z) + (v2.z + v3.z);
+        m[4 * r4 + 3] += (v0.w + v1.w) + (v2.w + v3.w);
+      }
+    }
+    for (; sp < nsplit; ++sp) {
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4) {
+        const float4 v = reinterpret_cast<const float4 *>(base + sp * split_stride)[r4];
+        m[4 * r4] += v.x; m[4 * r4 + 1] += v.y; m[4 * r4 + 2] += v.z; m[4 * r4 + 3] += v.w;
+      }
+    }
+  };
   if (threadIdx.x < 32) chol_inverse_to_smem<RT>(Gd, R, Ad, dinv, Li, Lf, invf, &ok_s);
+  else load_m();   // the other warps fetch their rows of M meanwhile
   __syncthreads();
   if (!ok_s && threadIdx.x == 0) atomicOr(status, kDevCholesky);
+  if (threadIdx.x < 32) load_m();
 
   // inverse of the Gram Hadamard product: Ginv = L^-T L^-1 by all threads
   for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
@@ -338,23 +377,10 @@ __global__ void __launch_bounds__(256, 1)
   }
   __syncthreads();
 
-  const int q = threadIdx.x;
   float f[RT];
 #pragma unroll
   for (int r = 0; r < RT; ++r) f[r] = 0.f;
   if (q < Q) {
-    float m[RT];
-#pragma unroll
-    for (int r = 0; r < RT; ++r) m[r] = 0.f;
-    for (int sp = 0; sp < nsplit; ++sp) {
-      const float4 *mp = reinterpret_cast<const float4 *>(M + sp * split_stride +
-                                                          ((int64_t)p * Q + q) * row_stride);
-#pragma unroll
-      for (int r4 = 0; r4 < RT / 4; ++r4) {
-        const float4 v = mp[r4];
-        m[4 * r4] += v.x; m[4 * r4 + 1] += v.y; m[4 * r4 + 2] += v.z; m[4 * r4 + 3] += v.w;
-      }
-    }
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
       const float4 *gr = reinterpret_cast<const float4 *>(Gi + r * RT);
@@ -373,11 +399,13 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
     for (int r = 0; r < RT; ++r) sq[r] = f[r] * f[r];
     block_sum_rows<RT>(sq, red, out);
-#pragma unroll
-    for (int r = 0; r < RT; ++r) {
-      const float n = sqrtf(out[r]);
-      if (n > 0.f) f[r] = f[r] / n;
+    if (threadIdx.x < RT) {
+      const float n = sqrtf(out[threadIdx.x]);
+      red[threadIdx.x] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
     }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RT; ++r) f[r] *= red[r];
   }
   if (q < Q) {
     float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
