@@ -8,36 +8,11 @@
 //   H[a][c][r] = sum_b X[a][b][c] B[b][r]
 // from which M3[c][r] = sum_a A[a][r] H[a][c][r] and (after C is updated)
 // M1[a][r] = sum_c C[c][r] H[a][c][r]; a second pass over X_p forms M2.
-// The R x R Gram Hadamard products are factored by Cholesky in fp64 (one warp),
-// the Grams and the triangular substitutions run in fp32.
-#include "octen_internal.cuh"
+// The R x R Gram Hadamard products are factored (L D L^T) in fp64 over four
+// warps, the Grams and the triangular substitutions run in fp32 (k_solve.cuh).
+#include "k_solve.cuh"
 
 namespace octen {
-
-// Block-wide sum of v[0..RT) held per thread; the result lands in out[RT]
-// (shared) for every thread after the call.  blockDim.x must be a multiple of 32.
-template <int RT>
-__device__ __forceinline__ void block_sum_rows(float (&v)[RT], float *red /*[32][RT]*/,
-                                               float *out /*[RT]*/) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int r = 0; r < RT; ++r) {
-    float x = v[r];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    v[r] = x;
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int r = 0; r < RT; ++r) red[warp * RT + r] = v[r];
-  }
-  __syncthreads();
-  if (threadIdx.x < RT) {
-    float s = 0.f;
-    for (int w = 0; w < nw; ++w) s += red[w * RT + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
 
 // H[p][a][c][:] = sum_b X_p[a][b][c] B_p[b][:]      grid (Q, P), thread c
 template <int RT>
@@ -145,284 +120,6 @@ __global__ void __launch_bounds__(256)
   }
   block_sum_rows<RT>(acc, red, out);
   if (threadIdx.x < RT) M[((int64_t)p * Q + b) * RT + threadIdx.x] = out[threadIdx.x];
-}
-
-// 1/sqrt(d) in fp64: the fp32 estimate refined by one Newton-Raphson step
-// y <- y (3 - d y^2) / 2 on f(y) = y^-2 - d, which squares its relative error
-// (~2^-22 -> ~2^-44).  Every fp64 operation on this GPU has a long latency and
-// this sits on the critical path of the factorisation, so the chain is kept
-// short; outside the fp32 exponent range the plain sqrt / division are used.
-__device__ __forceinline__ double rsqrt_nr(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  const double y = (double)rsqrtf((float)d);
-  return y * fma(-0.5 * d, y * y, 1.5);
-}
-
-// Warp 0: factor G1 * G2 = L L^T in fp64 and write L^-1 (fp32, lower
-// triangular; identity on failure) to Li ([RT][RT + 1]).  *ok_out gets the
-// success flag.  The matrix lives in shared memory (Ad, fp64, padded rows); the
-// loops are kept rolled so that the code stays in the instruction cache (this
-// runs once per launch on a single warp).
-//   right-looking Cholesky: the lanes scale column j by the pivot's reciprocal,
-//   lane 0 finishes diagonal entry j+1 and forms the next pivot (look-ahead)
-//   while lanes 1..31 share the rest of the trailing update; then L^-1 row by
-//   row: row k is finished and L[i][k] times it is subtracted from every row
-//   i > k, spread over the lanes.
-template <int RT>
-__device__ void chol_inverse_to_smem(const double *Gd, int R, double *Ad, double *dinv, float *Li,
-                                     float *Lf, float *invf, int *ok_out) {
-  constexpr int LD = RT + 1;
-  const int lane = threadIdx.x & 31;
-  bool ok = true;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    double add = 0.0;
-    if (attempt == 1) {
-      // load the diagonal by 1e-12 * trace / R and retry once
-      double tr = lane < R ? Gd[lane * LD + lane] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-      add = 1e-12 * tr / R;
-    }
-    if (lane < R) {
-      for (int k = 0; k <= lane; ++k) Ad[lane * LD + k] = Gd[lane * LD + k] + (k == lane ? add : 0.0);
-    }
-    ok = true;
-    // pivot 0; every later pivot is formed one step ahead (look-ahead below)
-    if (lane == 0) {
-      const double d = Ad[0];
-      const double inv = d > 0.0 ? rsqrt_nr(d) : 0.0;
-      Ad[0] = d > 0.0 ? d * inv : 1.0;
-      dinv[0] = inv;
-    }
-    for (int j = 0; j < R; ++j) {
-      __syncwarp();
-      const double inv = dinv[j];
-      if (!(inv > 0.0)) { ok = false; break; }
-      const int n = R - 1 - j;   // rows below the pivot
-      if (lane < n) Ad[(j + 1 + lane) * LD + j] *= inv;
-      __syncwarp();   // every L[k][j] is scaled before any lane reads it
-      if (n == 0) break;
-      if (lane == 0) {
-        // look-ahead: finish diagonal entry j+1 and form the next pivot now, so
-        // its fp64 chain overlaps the rest of this step's trailing update
-        const double l = Ad[(j + 1) * LD + j];
-        const double d = fma(-l, l, Ad[(j + 1) * LD + j + 1]);
-        const double inv1 = d > 0.0 ? rsqrt_nr(d) : 0.0;
-        Ad[(j + 1) * LD + j + 1] = d > 0.0 ? d * inv1 : 1.0;
-        dinv[j + 1] = inv1;
-      } else {
-        // the other n(n+1)/2 - 1 entries (i, k), j < k <= i < R, (i, k) != (j+1, j+1),
-        // in row-major triangular order, entry e to lane 1 + (e - 1) % 31
-        const int T = n * (n + 1) / 2;
-        int ii = 0, kk = lane;   // triangular index of e = lane
-        while (kk > ii) { kk -= ii + 1; ++ii; }
-        for (int e = lane; e < T; e += 62) {
-          int idx[2];
-          double x[2], y[2], z[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const bool live = e + 31 * u < T;
-            const int i = j + 1 + ii, k = j + 1 + kk;
-            idx[u] = live ? i * LD + k : -1;
-            x[u] = live ? Ad[i * LD + j] : 0.0;
-            y[u] = live ? Ad[k * LD + j] : 0.0;
-            z[u] = live ? Ad[i * LD + k] : 0.0;
-            kk += 31;
-            while (kk > ii) { kk -= ii + 1; ++ii; }
-          }
-#pragma unroll
-          for (int u = 0; u < 2; ++u)
-            if (idx[u] >= 0) Ad[idx[u]] = fma(-x[u], y[u], z[u]);
-        }
-      }
-    }
-    if (ok) break;
-  }
-  __syncwarp();
-  // L in fp32 (Lf) and its reciprocal diagonal, converted once
-  if (ok && lane < R) {
-    for (int k = 0; k < lane; ++k) Lf[lane * LD + k] = (float)Ad[lane * LD + k];
-    invf[lane] = (float)dinv[lane];
-  }
-  // L^-1 (fp32): Li rows accumulate -sum_{k<i} L[i][k] X[k][.] until row i is finished
-  if (lane < RT)
-    for (int j = 0; j < RT; ++j) Li[lane * LD + j] = 0.f;
-  __syncwarp();
-  for (int k = 0; k < R && ok; ++k) {
-    // finish row k of L^-1 (one column per lane), then subtract L[i][k] times it
-    // from every row i > k: the (R-1-k) x (k+1) updates spread over the lanes
-    if (lane <= k) Li[k * LD + lane] = ((lane == k ? 1.f : 0.f) + Li[k * LD + lane]) * invf[k];
-    __syncwarp();
-    const int rows = R - 1 - k, cols = k + 1;
-    int ii = lane / cols, jj = lane - (lane / cols) * cols;   // walk e = lane, lane + 32, ...
-    const int step_i = 32 / cols, step_j = 32 - step_i * cols;
-    for (int e = lane; e < rows * cols; e += 64) {
-      int i0 = k + 1 + ii, j0 = jj;
-      ii += step_i; jj += step_j;
-      if (jj >= cols) { jj -= cols; ++ii; }
-      const bool live1 = e + 32 < rows * cols;
-      const int i1 = k + 1 + ii, j1 = jj;
-      ii += step_i; jj += step_j;
-      if (jj >= cols) { jj -= cols; ++ii; }
-      const float a0 = Lf[i0 * LD + k], b0 = Li[k * LD + j0], c0 = Li[i0 * LD + j0];
-      const float a1 = live1 ? Lf[i1 * LD + k] : 0.f, b1 = live1 ? Li[k * LD + j1] : 0.f;
-      const float c1 = live1 ? Li[i1 * LD + j1] : 0.f;
-      Li[i0 * LD + j0] = fmaf(-a0, b0, c0);
-      if (live1) Li[i1 * LD + j1] = fmaf(-a1, b1, c1);
-    }
-    __syncwarp();
-  }
-  if (!ok && lane < RT) {
-    for (int j = 0; j < RT; ++j) Li[lane * LD + j] = (j == lane) ? 1.f : 0.f;
-  }
-  if (lane == 0) *ok_out = ok ? 1 : 0;
-}
-
-// Gram of the Q x RT factor held in shared memory: Gout[r][s] = sum_q F[q][r] F[q][s].
-// Thread t < (RT/2)^2 accumulates the 2 x 2 block at rows 2 (t / (RT/2)), columns
-// 2 (t % (RT/2)) with two 8-byte shared loads per row of F.
-template <int RT>
-__device__ __forceinline__ void smem_gram(const float *Fs, int Q, float *Gout) {
-  constexpr int H = RT / 2;
-  const int t = threadIdx.x;
-  if (t >= H * H) return;
-  const int r0 = 2 * (t / H), c0 = 2 * (t % H);
-  float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
-#pragma unroll 4
-  for (int q = 0; q < Q; ++q) {
-    const float2 x = *reinterpret_cast<const float2 *>(Fs + q * RT + r0);
-    const float2 y = *reinterpret_cast<const float2 *>(Fs + q * RT + c0);
-    a00 = fmaf(x.x, y.x, a00);
-    a01 = fmaf(x.x, y.y, a01);
-    a10 = fmaf(x.y, y.x, a10);
-    a11 = fmaf(x.y, y.y, a11);
-  }
-  Gout[r0 * RT + c0] = a00;
-  Gout[r0 * RT + c0 + 1] = a01;
-  Gout[(r0 + 1) * RT + c0] = a10;
-  Gout[(r0 + 1) * RT + c0 + 1] = a11;
-}
-
-// F_p = M_p (G1_p * G2_p)^-1 with G1, G2 the cached R x R Grams of the other two
-// factors (fp64 Cholesky, fp32 inverse from the factor, fp32 product with M_p);
-// M_p is the sum of `nsplit` partial MTTKRPs.  Optionally normalises
-// the columns to unit l2.  Writes F_p, its Gram F_p^T F_p and, if Ft is given,
-// a bf16 copy transposed to [NP][Q] (rows >= R zero) for the tensor-core passes.
-// grid P, 256 threads (thread q owns row q, Q <= 256); dynamic smem Q * RT floats.
-template <int RT>
-__global__ void __launch_bounds__(256, 1)
-    als_solve_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
-                     int64_t row_stride, const float *__restrict__ G1,
-                     const float *__restrict__ G2,
-                     float *__restrict__ F, float *__restrict__ Gout,
-                     __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int R, int normalize,
-                     int *status) {
-  extern __shared__ __align__(16) float Fs[];   // [Q][RT]
-  __shared__ __align__(16) float Gi[RT * RT];
-  __shared__ float Li[RT * (RT + 1)];
-  __shared__ double Ad[RT * (RT + 1)], Gd[RT * (RT + 1)], dinv[RT];
-  __shared__ float Lf[RT * (RT + 1)], invf[RT];
-  __shared__ float red[8 * RT], out[RT];
-  __shared__ int ok_s;
-  const int p = blockIdx.x;
-  const float *g1 = G1 + (int64_t)p * RT * RT, *g2 = G2 + (int64_t)p * RT * RT;
-  // Hadamard product of the Grams in fp64, loaded by every thread at once
-  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
-    const int i = e / RT, k = e % RT;
-    Gd[i * (RT + 1) + k] = (double)g1[e] * (double)g2[e];
-  }
-  __syncthreads();
-  const int q = threadIdx.x;
-  float m[RT];
-#pragma unroll
-  for (int r = 0; r < RT; ++r) m[r] = 0.f;
-  // row q of the MTTKRP: sum of the partials (independent loads, 4 at a time)
-  auto load_m = [&]() {
-    if (q >= Q) return;
-    const float *base = M + ((int64_t)p * Q + q) * row_stride;
-    int sp = 0;
-    for (; sp + 4 <= nsplit; sp += 4) {
-#pragma unroll
-      for (int r4 = 0; r4 < RT / 4; ++r4) {
-        const float4 v0 = reinterpret_cast<const float4 *>(base + (sp + 0) * split_stride)[r4];
-        const float4 v1 = reinterpret_cast<const float4 *>(base + (sp + 1) * split_stride)[r4];
-        const float4 v2 = reinterpret_cast<const float4 *>(base + (sp + 2) * split_stride)[r4];
-        const float4 v3 = reinterpret_cast<const float4 *>(base + (sp + 3) * split_stride)[r4];
-        m[4 * r4] += (v0.x + v1.x) + (v2.x + v3.x);
-        m[4 * r4 + 1] += (v0.y + v1.y) + (v2.y + v3.y);
-        m[4 * r4 + 2] += (v0.z + v1.z) + (v2.z + v3.z);
-        m[4 * r4 + 3] += (v0.w + v1.w) + (v2.w + v3.w);
-      }
-    }
-    for (; sp < nsplit; ++sp) {
-#pragma unroll
-      for (int r4 = 0; r4 < RT / 4; ++r4) {
-        const float4 v = reinterpret_cast<const float4 *>(base + sp * split_stride)[r4];
-        m[4 * r4] += v.x; m[4 * r4 + 1] += v.y; m[4 * r4 + 2] += v.z; m[4 * r4 + 3] += v.w;
-      }
-    }
-  };
-  if (threadIdx.x < 32) chol_inverse_to_smem<RT>(Gd, R, Ad, dinv, Li, Lf, invf, &ok_s);
-  else load_m();   // the other warps fetch their rows of M meanwhile
-  __syncthreads();
-  if (!ok_s && threadIdx.x == 0) atomicOr(status, kDevCholesky);
-  if (threadIdx.x < 32) load_m();
-
-  // inverse of the Gram Hadamard product: Ginv = L^-T L^-1 by all threads
-  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
-    const int r = e / RT, c = e % RT;
-    float acc = 0.f;
-    for (int k = r > c ? r : c; k < R; ++k)
-      acc = fmaf(Li[k * (RT + 1) + r], Li[k * (RT + 1) + c], acc);
-    Gi[e] = acc;
-  }
-  __syncthreads();
-
-  float f[RT];
-#pragma unroll
-  for (int r = 0; r < RT; ++r) f[r] = 0.f;
-  if (q < Q) {
-#pragma unroll
-    for (int r = 0; r < RT; ++r) {
-      const float4 *gr = reinterpret_cast<const float4 *>(Gi + r * RT);
-#pragma unroll
-      for (int c4 = 0; c4 < RT / 4; ++c4) {
-        const float4 g = gr[c4];
-        f[4 * c4] = fmaf(m[r], g.x, f[4 * c4]);
-        f[4 * c4 + 1] = fmaf(m[r], g.y, f[4 * c4 + 1]);
-        f[4 * c4 + 2] = fmaf(m[r], g.z, f[4 * c4 + 2]);
-        f[4 * c4 + 3] = fmaf(m[r], g.w, f[4 * c4 + 3]);
-      }
-    }
-  }
-  if (normalize) {
-    float sq[RT];
-#pragma unroll
-    for (int r = 0; r < RT; ++r) sq[r] = f[r] * f[r];
-    block_sum_rows<RT>(sq, red, out);
-    if (threadIdx.x < RT) {
-      const float n = sqrtf(out[threadIdx.x]);
-      red[threadIdx.x] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < RT; ++r) f[r] *= red[r];
-  }
-  if (q < Q) {
-    float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
-    float4 *os = reinterpret_cast<float4 *>(Fs + q * RT);
-#pragma unroll
-    for (int r4 = 0; r4 < RT / 4; ++r4) {
-      const float4 v = make_float4(f[4 * r4], f[4 * r4 + 1], f[4 * r4 + 2], f[4 * r4 + 3]);
-      o[r4] = v;
-      os[r4] = v;
-    }
-  }
-  __syncthreads();
-  if (Ft && q < Q) {
-    for (int r = 0; r < NP; ++r)
-      Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(r < RT ? Fs[q * RT + r] : 0.f);
-  }
-  smem_gram<RT>(Fs, Q, Gout + (int64_t)p * RT * RT);
 }
 
 // F_p = unit-l2 columns of the replica-p rows of PF (Qd x R), padded to RT,

@@ -1,0 +1,353 @@
+// The R x R normal-equation solve of the replica ALS (Algorithm 1's CP(X_p, R)
+// step): F_p = M_p (G1_p * G2_p)^-1, with G1, G2 the Grams of the two factors
+// that stay fixed in the update and M_p the MTTKRP.
+//
+// The Hadamard product G = G1 * G2 is factored as G = L D L^T (L unit lower
+// triangular) in fp64, then every row of M is solved by fp32 forward and
+// backward substitution with L and D^-1 rounded to fp32.
+//
+// fp64 arithmetic on this GPU issues one warp instruction per ~64 cycles per
+// warp (its latency is the same), while the SM as a whole sustains about one
+// fp64 warp instruction per ~19 cycles.  The factorisation is therefore spread
+// over four warps, one per SM sub-partition, with the dependent chain kept
+// apart from the bulk of the arithmetic:
+//   warp 0 (pivot warp) owns the diagonal.  At step j it applies column j to
+//     the diagonal and forms the next pivot's reciprocal r_{j+1} = 1 / D_{j+1}
+//     (fp32 estimate from the bits of D, one Newton step in fp64);
+//   warps 1..3 (update warps) own the strictly lower entries, 96 threads with a
+//     fixed set of entries each, kept in registers.  At step j every owner of an
+//     entry (i, k), k > j, subtracts c_ij c_kj r_j from it; the owners of
+//     column j + 1 publish its final (unscaled) values c_{i,j+1} to shared memory.
+// One named barrier over the four warps closes each step.  Warps 4..7 sum the
+// MTTKRP's partial products into shared memory meanwhile.
+#pragma once
+
+#include "octen_internal.cuh"
+
+namespace octen {
+
+// Block-wide sum of v[0..RT) held per thread; the result lands in out[RT]
+// (shared) for every thread after the call.  blockDim.x must be a multiple of 32.
+template <int RT>
+__device__ __forceinline__ void block_sum_rows(float (&v)[RT], float *red /*[32][RT]*/,
+                                               float *out /*[RT]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int r = 0; r < RT; ++r) {
+    float x = v[r];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[r] = x;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int r = 0; r < RT; ++r) red[warp * RT + r] = v[r];
+  }
+  __syncthreads();
+  if (threadIdx.x < RT) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += red[w * RT + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Gram of the Q x RT factor held in shared memory: Gout[r][s] = sum_q F[q][r] F[q][s].
+// Thread t < (RT/2)^2 accumulates the 2 x 2 block at rows 2 (t / (RT/2)), columns
+// 2 (t % (RT/2)) with two 8-byte shared loads per row of F.
+template <int RT>
+__device__ __forceinline__ void smem_gram(const float *Fs, int Q, float *Gout) {
+  constexpr int H = RT / 2;
+  const int t = threadIdx.x;
+  if (t >= H * H) return;
+  const int r0 = 2 * (t / H), c0 = 2 * (t % H);
+  float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+#pragma unroll 4
+  for (int q = 0; q < Q; ++q) {
+    const float2 x = *reinterpret_cast<const float2 *>(Fs + q * RT + r0);
+    const float2 y = *reinterpret_cast<const float2 *>(Fs + q * RT + c0);
+    a00 = fmaf(x.x, y.x, a00);
+    a01 = fmaf(x.x, y.y, a01);
+    a10 = fmaf(x.y, y.x, a10);
+    a11 = fmaf(x.y, y.y, a11);
+  }
+  Gout[r0 * RT + c0] = a00;
+  Gout[r0 * RT + c0 + 1] = a01;
+  Gout[(r0 + 1) * RT + c0] = a10;
+  Gout[(r0 + 1) * RT + c0 + 1] = a11;
+}
+
+// Reciprocal of a pivot.  ok is cleared unless d is positive, normal and finite.
+// For d in [2^-100, 2^100] (every pivot of a Gram of bounded columns): the
+// fp32 value of d is assembled from its bits (mantissa truncated to 23 bits,
+// relative error < 2^-23), its reciprocal taken with rcp.approx (relative
+// error < 2^-23), the result widened to fp64 from its bits, and one Newton
+// step y <- y + y (1 - d y) squares the relative error (< 2^-43).  No fp64
+// conversion instructions sit on the chain; outside that range the fp64
+// division is used.
+__device__ __forceinline__ double pivot_rcp(double d, bool &ok) {
+  const int hi = __double2hiint(d);
+  const unsigned lo = static_cast<unsigned>(__double2loint(d));
+  const int be = (hi >> 20) & 0x7ff;   // biased exponent of |d|
+  if (hi < 0 || be == 0 || be == 0x7ff) {
+    ok = false;   // negative, zero, subnormal, infinite or NaN
+    return 0.0;
+  }
+  if (be < 1023 - 100 || be > 1023 + 100) return 1.0 / d;
+  const float f = __int_as_float(((be - 1023 + 127) << 23) | ((hi & 0xfffff) << 3) |
+                                 static_cast<int>(lo >> 29));
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+  const int yb = __float_as_int(y);
+  const int ye = (yb >> 23) & 0xff;
+  const int ym = yb & 0x7fffff;
+  const double y0 = __hiloint2double(((ye - 127 + 1023) << 20) | (ym >> 3), ym << 29);
+  const double e = fma(-d, y0, 1.0);
+  return fma(y0, e, y0);
+}
+
+__device__ __forceinline__ void factor_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Warps 0..3: G = G1 * G2 (fp64) = L D L^T.  On return (after a barrier over
+// the four warps) Lc[k][i] = Lr[i][k] = L[i][k] for i > k (fp32, zero elsewhere)
+// and rf[k] = 1 / D[k] (fp32, zero for k >= R).  If a pivot is not positive the
+// diagonal is loaded by 1e-12 trace / R and the factorisation repeated once; if
+// that fails as well, L = I and rf = 1 (the solve returns M) and *fail = 1.
+template <int RT>
+__device__ void ldl_factor(const float *__restrict__ g1, const float *__restrict__ g2, int R,
+                           double *Craw /*[RT][RT+1]*/, double *Rs /*[RT]*/, float *Lc,
+                           float *Lr, float *rf, int *fail) {
+  constexpr int LD = RT + 1;
+  constexpr int NU = 96;                                   // update threads
+  constexpr int NS = (RT * (RT - 1) / 2 + NU - 1) / NU;    // entries per update thread
+  const unsigned full = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < RT * RT; e += 128) {
+    Lc[e] = 0.f;
+    Lr[e] = 0.f;
+  }
+  // entries of update thread u: the strict lower triangle listed by column k
+  // descending (column R-2 first), entry e = s * NU + u in slot s.  Group g >= 1
+  // of that list is column k = R-1-g with rows k+1 .. R-1.
+  const int u = tid - 32;
+  const int nent = R * (R - 1) / 2;
+  int ei[NS > 0 ? NS : 1], ek[NS > 0 ? NS : 1];
+  double a[NS > 0 ? NS : 1];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    ei[s] = 0;
+    ek[s] = -1;
+    a[s] = 0.0;
+    const int e = s * NU + u;
+    if (warp > 0 && e < nent) {
+      int g = 1;
+      while ((g + 1) * g / 2 <= e) ++g;
+      const int k = R - 1 - g;
+      ek[s] = k;
+      ei[s] = k + 1 + (e - g * (g - 1) / 2);
+    }
+  }
+  bool ok = true;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    ok = true;
+    if (warp == 0) {
+      // pivot warp: lane t holds diagonal entry t
+      double diag = lane < R ? (double)g1[lane * (RT + 1)] * (double)g2[lane * (RT + 1)] : 1.0;
+      if (attempt == 1) {
+        double tr = lane < R ? diag : 0.0;
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(full, tr, o);
+        diag += 1e-12 * tr / R;
+      }
+      double rj = pivot_rcp(__shfl_sync(full, diag, 0), ok);
+      if (lane == 0) Rs[0] = rj;
+      factor_barrier();   // column 0 and r_0 published
+      for (int j = 0; j + 1 < R; ++j) {
+        const double ct = (lane > j && lane < R) ? Craw[lane * LD + j] : 0.0;
+        diag = fma(-ct, ct * rj, diag);
+        rj = pivot_rcp(__shfl_sync(full, diag, j + 1), ok);
+        if (!ok) rj = 0.0;
+        if (lane == 0) Rs[j + 1] = rj;
+        factor_barrier();
+      }
+      if (lane == 0) *fail = ok ? 0 : 1;
+    } else {
+      // update warps: entries in registers, column j + 1 published at step j
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (ek[s] >= 0) {
+          const int i = ei[s], k = ek[s];
+          a[s] = (double)g1[i * RT + k] * (double)g2[i * RT + k];
+          if (k == 0) Craw[i * LD] = a[s];
+        }
+      }
+      factor_barrier();
+      for (int j = 0; j + 1 < R; ++j) {
+        const double rj = Rs[j];
+        const double ct = (lane > j && lane < R) ? Craw[lane * LD + j] : 0.0;
+        const double st = ct * rj;
+        const int na = (R - 2 - j) * (R - 1 - j) / 2;   // entries with column > j
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          if (s * NU + (warp - 1) * 32 < na) {   // warp-uniform
+            const double ci = __shfl_sync(full, ct, ei[s]);
+            const double sk = __shfl_sync(full, st, ek[s] < 0 ? 0 : ek[s]);
+            if (s * NU + u < na) {
+              a[s] = fma(-ci, sk, a[s]);
+              if (ek[s] == j + 1) Craw[ei[s] * LD + ek[s]] = a[s];
+            }
+          }
+        }
+        factor_barrier();
+      }
+    }
+    factor_barrier();   // *fail visible to the four warps
+    if (!*fail) break;
+  }
+  ok = !*fail;
+  if (warp == 0) {
+    if (lane < RT) rf[lane] = lane < R ? (ok ? (float)Rs[lane] : 1.f) : 0.f;
+  } else if (ok) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (ek[s] >= 0) {
+        const float l = (float)(a[s] * Rs[ek[s]]);
+        Lc[ek[s] * RT + ei[s]] = l;
+        Lr[ei[s] * RT + ek[s]] = l;
+      }
+    }
+  }
+}
+
+// F_p = M_p (G1_p * G2_p)^-1, M_p the sum of `nsplit` partial MTTKRPs (row q
+// of split s at M + s * split_stride + (p * Q + q) * row_stride).  Optionally
+// normalises the columns to unit l2.  Writes F_p, its Gram F_p^T F_p and, if Ft
+// is given, a bf16 copy transposed to [NP][Q] (rows >= R zero) for the
+// tensor-core passes.  grid P, 256 threads (Q <= 256); dynamic smem Q * RT floats.
+template <int RT>
+__global__ void __launch_bounds__(256, 1)
+    als_solve_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
+                     int64_t row_stride, const float *__restrict__ G1,
+                     const float *__restrict__ G2, float *__restrict__ F,
+                     float *__restrict__ Gout, __nv_bfloat16 *__restrict__ Ft, int NP, int Q,
+                     int R, int normalize, int *status) {
+  extern __shared__ __align__(16) float Fs[];   // [Q][RT]: rows of M, then of F
+  __shared__ double Craw[RT * (RT + 1)], Rs[RT];
+  __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT];
+  __shared__ float red[8 * RT], out[RT];
+  __shared__ int fail_s;
+  const int p = blockIdx.x, tid = threadIdx.x;
+  if (tid < 128) {
+    ldl_factor<RT>(G1 + (int64_t)p * RT * RT, G2 + (int64_t)p * RT * RT, R, Craw, Rs, Lc, Lr,
+                   rf, &fail_s);
+  } else {
+    // rows of M: sum of the partials (independent loads, 4 splits at a time)
+    for (int q = tid - 128; q < Q; q += 128) {
+      const float *base = M + ((int64_t)p * Q + q) * row_stride;
+      float m[RT];
+#pragma unroll
+      for (int r = 0; r < RT; ++r) m[r] = 0.f;
+      int sp = 0;
+      for (; sp + 4 <= nsplit; sp += 4) {
+#pragma unroll
+        for (int r4 = 0; r4 < RT / 4; ++r4) {
+          const float4 v0 = reinterpret_cast<const float4 *>(base + (sp + 0) * split_stride)[r4];
+          const float4 v1 = reinterpret_cast<const float4 *>(base + (sp + 1) * split_stride)[r4];
+          const float4 v2 = reinterpret_cast<const float4 *>(base + (sp + 2) * split_stride)[r4];
+          const float4 v3 = reinterpret_cast<const float4 *>(base + (sp + 3) * split_stride)[r4];
+          m[4 * r4] += (v0.x + v1.x) + (v2.x + v3.x);
+          m[4 * r4 + 1] += (v0.y + v1.y) + (v2.y + v3.y);
+          m[4 * r4 + 2] += (v0.z + v1.z) + (v2.z + v3.z);
+          m[4 * r4 + 3] += (v0.w + v1.w) + (v2.w + v3.w);
+        }
+      }
+      for (; sp < nsplit; ++sp) {
+#pragma unroll
+        for (int r4 = 0; r4 < RT / 4; ++r4) {
+          const float4 v = reinterpret_cast<const float4 *>(base + sp * split_stride)[r4];
+          m[4 * r4] += v.x; m[4 * r4 + 1] += v.y; m[4 * r4 + 2] += v.z; m[4 * r4 + 3] += v.w;
+        }
+      }
+      float4 *o = reinterpret_cast<float4 *>(Fs + q * RT);
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4)
+        o[r4] = make_float4(m[4 * r4], m[4 * r4 + 1], m[4 * r4 + 2], m[4 * r4 + 3]);
+    }
+  }
+  __syncthreads();
+  if (fail_s && tid == 0) atomicOr(status, kDevCholesky);
+
+  // f = M row q solved against L D L^T: forward with L, scale by 1/D, backward with L^T
+  const int q = tid;
+  float y[RT];
+#pragma unroll
+  for (int r = 0; r < RT; ++r) y[r] = 0.f;
+  if (q < Q) {
+    const float4 *mr = reinterpret_cast<const float4 *>(Fs + q * RT);
+#pragma unroll
+    for (int r4 = 0; r4 < RT / 4; ++r4) {
+      const float4 v = mr[r4];
+      y[4 * r4] = v.x; y[4 * r4 + 1] = v.y; y[4 * r4 + 2] = v.z; y[4 * r4 + 3] = v.w;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RT; ++k) {
+    const float yk = y[k];
+    const float4 *lc = reinterpret_cast<const float4 *>(Lc + k * RT);
+#pragma unroll
+    for (int i4 = (k + 1) / 4; i4 < RT / 4; ++i4) {
+      const float4 l = lc[i4];
+      if (4 * i4 + 0 > k) y[4 * i4 + 0] = fmaf(-l.x, yk, y[4 * i4 + 0]);
+      if (4 * i4 + 1 > k) y[4 * i4 + 1] = fmaf(-l.y, yk, y[4 * i4 + 1]);
+      if (4 * i4 + 2 > k) y[4 * i4 + 2] = fmaf(-l.z, yk, y[4 * i4 + 2]);
+      if (4 * i4 + 3 > k) y[4 * i4 + 3] = fmaf(-l.w, yk, y[4 * i4 + 3]);
+    }
+  }
+#pragma unroll
+  for (int r4 = 0; r4 < RT / 4; ++r4) {
+    const float4 d = reinterpret_cast<const float4 *>(rf)[r4];
+    y[4 * r4] *= d.x; y[4 * r4 + 1] *= d.y; y[4 * r4 + 2] *= d.z; y[4 * r4 + 3] *= d.w;
+  }
+#pragma unroll
+  for (int k = RT - 1; k > 0; --k) {
+    const float fk = y[k];
+    const float4 *lr = reinterpret_cast<const float4 *>(Lr + k * RT);
+#pragma unroll
+    for (int i4 = 0; i4 <= (k - 1) / 4; ++i4) {
+      const float4 l = lr[i4];
+      if (4 * i4 + 0 < k) y[4 * i4 + 0] = fmaf(-l.x, fk, y[4 * i4 + 0]);
+      if (4 * i4 + 1 < k) y[4 * i4 + 1] = fmaf(-l.y, fk, y[4 * i4 + 1]);
+      if (4 * i4 + 2 < k) y[4 * i4 + 2] = fmaf(-l.z, fk, y[4 * i4 + 2]);
+      if (4 * i4 + 3 < k) y[4 * i4 + 3] = fmaf(-l.w, fk, y[4 * i4 + 3]);
+    }
+  }
+  if (normalize) {
+    float sq[RT];
+#pragma unroll
+    for (int r = 0; r < RT; ++r) sq[r] = y[r] * y[r];
+    block_sum_rows<RT>(sq, red, out);
+    if (tid < RT) {
+      const float n = sqrtf(out[tid]);
+      red[tid] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RT; ++r) y[r] *= red[r];
+  }
+  if (q < Q) {
+    float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
+    float4 *os = reinterpret_cast<float4 *>(Fs + q * RT);
+#pragma unroll
+    for (int r4 = 0; r4 < RT / 4; ++r4) {
+      const float4 v = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
+      o[r4] = v;
+      os[r4] = v;
+    }
+  }
+  __syncthreads();
+  if (Ft && q < Q) {
+    for (int r = 0; r < NP; ++r)
+      Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(r < RT ? Fs[q * RT + r] : 0.f);
+  }
+  smem_gram<RT>(Fs, Q, Gout + (int64_t)p * RT * RT);
+}
+
+}  // namespace octen
