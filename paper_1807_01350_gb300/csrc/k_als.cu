@@ -201,26 +201,33 @@ __global__ void bf16_layouts_kernel(const float *__restrict__ Y, int Q,
 }
 
 // KR[p][r][(a,b)] = bf16(A[a][r] B[b][r]) for r < NP (zero beyond the rank).
-// One CTA per (a, replica): the A row and the B factor are staged in shared
-// memory; thread b writes the NP values of column (a, b), coalesced over b.
+// One CTA per (r, replica) with columns r of A and B staged in shared memory;
+// each thread writes 8 consecutive b of one a as a 16-byte store (Q % 8 == 0,
+// Q <= 256), so a CTA streams its Q^2 outputs contiguously.
 template <int RT>
 __global__ void __launch_bounds__(256)
-    kr_kernel(const float *__restrict__ Af, const float *__restrict__ Bf, int Q, int NP,
+    kr_kernel(const float *__restrict__ Af, const float *__restrict__ Bf, int Q,
               __nv_bfloat16 *__restrict__ KR) {
-  extern __shared__ __align__(16) float Bs[];   // [Q][RT + 1] (padded: lanes b hit distinct banks)
-  __shared__ float arow[RT];
-  const int a = blockIdx.x, p = blockIdx.y;
+  __shared__ __align__(16) float ac[256], bc[256];
+  const int r = blockIdx.x, p = blockIdx.y, NP = gridDim.x;
   const int64_t QQ = (int64_t)Q * Q;
-  for (int e = threadIdx.x; e < Q * RT; e += blockDim.x)
-    Bs[(e / RT) * (RT + 1) + e % RT] = Bf[(int64_t)p * Q * RT + e];
-  if (threadIdx.x < RT) arow[threadIdx.x] = Af[((int64_t)p * Q + a) * RT + threadIdx.x];
+  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+    ac[q] = r < RT ? Af[((int64_t)p * Q + q) * RT + r] : 0.f;
+    bc[q] = r < RT ? Bf[((int64_t)p * Q + q) * RT + r] : 0.f;
+  }
   __syncthreads();
-  __nv_bfloat16 *kr = KR + (int64_t)p * NP * QQ + (int64_t)a * Q;
-  for (int b = threadIdx.x; b < Q; b += blockDim.x) {
-#pragma unroll
-    for (int r = 0; r < RT; ++r)
-      kr[r * QQ + b] = __float2bfloat16_rn(arow[r] * Bs[b * (RT + 1) + r]);
-    for (int r = RT; r < NP; ++r) kr[r * QQ + b] = __float2bfloat16_rn(0.f);
+  uint4 *out = reinterpret_cast<uint4 *>(KR + ((int64_t)p * NP + r) * QQ);
+  const int nch = static_cast<int>(QQ / 8);
+  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+    const int e = ch * 8, a = e / Q, b = e - a * Q;
+    const float x = ac[a];
+    const float4 b0 = *reinterpret_cast<const float4 *>(bc + b);
+    const float4 b1 = *reinterpret_cast<const float4 *>(bc + b + 4);
+    __nv_bfloat162 h[4] = {__floats2bfloat162_rn(x * b0.x, x * b0.y),
+                           __floats2bfloat162_rn(x * b0.z, x * b0.w),
+                           __floats2bfloat162_rn(x * b1.x, x * b1.y),
+                           __floats2bfloat162_rn(x * b1.z, x * b1.w)};
+    out[ch] = *reinterpret_cast<const uint4 *>(h);
   }
 }
 
@@ -339,13 +346,12 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   const bool fuse_m1 = Q % 32 == 0;
   if (fuse_m1) { tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; }
   const int ks = tc_gemm_splits(m3.K, b.ksplit);
-  const dim3 gKR(Q, P);
-  const size_t smem_kr = (size_t)Q * (RT + 1) * sizeof(float);
+  const dim3 gKR(NP, P);
   const dim3 gM((Q * RT + 255) / 256, P);
   bool ok = true;
   auto c_update = [&]() {
     mk(kStAlsAux, 1);
-    kr_kernel<RT><<<gKR, 256, smem_kr, st>>>(b.Af, b.Bf, Q, NP, b.KR);
+    kr_kernel<RT><<<gKR, 256, 0, st>>>(b.Af, b.Bf, Q, b.KR);
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsGemm, 1);

@@ -157,11 +157,105 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Streaming form for Q % 4 == 0.  A CTA keeps W_p (rows padded to a multiple
+// of 4 with zeros) in shared memory and walks blocks of rows (a, b) of one
+// replica; per block it stages T2 transposed to [row][k] and every thread owns
+// 4 consecutive c (one float4) of kRG rows: the kRG loads of Y are issued
+// together, the t-term sums taken from shared memory, then the rows stored.
+constexpr int kRG = 8;
+
+__global__ void __launch_bounds__(256)
+    mode3_stream_kernel(const float *__restrict__ T2, const float *__restrict__ W,
+                        float *__restrict__ Y, int t, int Q, int S, int Qd) {
+  extern __shared__ __align__(16) float sm3[];
+  const int tp = (t + 3) & ~3;                 // padded k extent
+  const int ncg = Q / 4;                       // float4 column groups
+  const int lanes = blockDim.x / ncg;          // rows in flight per pass
+  const int rows_blk = lanes * kRG;
+  float *Ws = sm3;                             // [tp][Q]
+  float *Ts = sm3 + (size_t)tp * Q;            // [rows_blk][tp]
+  const int p = blockIdx.y;
+  const int64_t QQ = (int64_t)Q * Q;
+  for (int e = threadIdx.x; e < tp * Q; e += blockDim.x) {
+    const int k = e / Q, c = e - (e / Q) * Q;
+    const int col = c < S ? c : S + p * (Q - S) + (c - S);
+    Ws[e] = k < t ? W[(int64_t)k * Qd + col] : 0.f;
+  }
+  const int cg = threadIdx.x % ncg, rl = threadIdx.x / ncg;
+  const bool active = rl < lanes;
+  const int64_t nblk = (QQ + rows_blk - 1) / rows_blk;
+  float *Yp = Y + (int64_t)p * QQ * Q;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t row0 = blk * rows_blk;
+    __syncthreads();   // Ws ready / previous block's Ts consumed
+    for (int e = threadIdx.x; e < rows_blk * tp; e += blockDim.x) {
+      const int k = e / rows_blk, r = e - (e / rows_blk) * rows_blk;
+      Ts[r * tp + k] =
+          (k < t && row0 + r < QQ) ? T2[((int64_t)p * t + k) * QQ + row0 + r] : 0.f;
+    }
+    __syncthreads();
+    if (!active) continue;
+    float4 y[kRG], acc[kRG];
+#pragma unroll
+    for (int i = 0; i < kRG; ++i) {
+      const int64_t row = row0 + rl + (int64_t)lanes * i;
+      y[i] = row < QQ ? reinterpret_cast<const float4 *>(Yp + row * Q)[cg]
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+      acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int k = 0; k < tp; k += 4) {
+      const float4 w0 = reinterpret_cast<const float4 *>(Ws + (k + 0) * Q)[cg];
+      const float4 w1 = reinterpret_cast<const float4 *>(Ws + (k + 1) * Q)[cg];
+      const float4 w2 = reinterpret_cast<const float4 *>(Ws + (k + 2) * Q)[cg];
+      const float4 w3 = reinterpret_cast<const float4 *>(Ws + (k + 3) * Q)[cg];
+#pragma unroll
+      for (int i = 0; i < kRG; ++i) {
+        const float4 x = *reinterpret_cast<const float4 *>(Ts + (rl + lanes * i) * tp + k);
+        acc[i].x = fmaf(x.x, w0.x, fmaf(x.y, w1.x, fmaf(x.z, w2.x, fmaf(x.w, w3.x, acc[i].x))));
+        acc[i].y = fmaf(x.x, w0.y, fmaf(x.y, w1.y, fmaf(x.z, w2.y, fmaf(x.w, w3.y, acc[i].y))));
+        acc[i].z = fmaf(x.x, w0.z, fmaf(x.y, w1.z, fmaf(x.z, w2.z, fmaf(x.w, w3.z, acc[i].z))));
+        acc[i].w = fmaf(x.x, w0.w, fmaf(x.y, w1.w, fmaf(x.z, w2.w, fmaf(x.w, w3.w, acc[i].w))));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kRG; ++i) {
+      const int64_t row = row0 + rl + (int64_t)lanes * i;
+      if (row < QQ)
+        reinterpret_cast<float4 *>(Yp + row * Q)[cg] =
+            make_float4(y[i].x + acc[i].x, y[i].y + acc[i].y, y[i].z + acc[i].z,
+                        y[i].w + acc[i].w);
+    }
+  }
+}
+
 void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
                       int S, int Qd, cudaStream_t st) {
+  const int64_t QQ = (int64_t)Q * Q;
+  if (Q % 4 == 0 && Q <= 1024) {
+    const int tp = (int)((t + 3) & ~int64_t(3));
+    const int ncg = Q / 4;
+    const int lanes = 256 / ncg;
+    const int rows_blk = lanes * kRG;
+    const size_t smem = ((size_t)tp * Q + (size_t)rows_blk * tp) * sizeof(float);
+    if (smem <= 200 * 1024) {
+      cudaFuncSetAttribute(mode3_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mode3_stream_kernel, 256, smem);
+      if (per_sm < 1) per_sm = 1;
+      const int64_t nblk = (QQ + rows_blk - 1) / rows_blk;
+      int64_t gx = ((int64_t)sms * per_sm + P - 1) / P;   // one wave over all replicas
+      if (gx > nblk) gx = nblk;
+      if (gx < 1) gx = 1;
+      mode3_stream_kernel<<<dim3((unsigned)gx, P), 256, smem, st>>>(T2, W, Y, (int)t, Q, S, Qd);
+      count_launch();
+      return;
+    }
+  }
   const size_t smem = ((size_t)t * Q + (size_t)t * kRows) * sizeof(float);
   cudaFuncSetAttribute(mode3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  const int64_t QQ = (int64_t)Q * Q;
   dim3 grid((unsigned)((QQ + kRows - 1) / kRows), P);
   mode3_kernel<<<grid, 256, smem, st>>>(T2, W, Y, (int)t, Q, S, Qd);
   count_launch();

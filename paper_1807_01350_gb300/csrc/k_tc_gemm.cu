@@ -161,6 +161,7 @@ struct TcShape {
 // Plain fp32 store: D[split * s_split + z * s_z + m * s_m + n] (split-K partials).
 struct TcStoreEpi {
   static constexpr bool kRowMajor = true;   // rows are contiguous in n
+  static constexpr bool kSeg = false;
   float *D;
   int64_t s_split, s_z, s_m;
   // optional fused reduction (replica ALS): with rows m = a * Q + b, every warp
@@ -177,10 +178,43 @@ struct TcStoreEpi {
 // Mode-2 epilogue: row m = k * I + i, column c of V_all -> every replica owning c.
 struct Mode2TcEpi {
   static constexpr bool kRowMajor = false;
+  static constexpr bool kSeg = true;   // 16-byte segments along i when I % 8 == 0
   __nv_bfloat16 *T;
   const float *scale;
   int64_t I;
   int P, Q, S;
+  bool seg;
+  __device__ __forceinline__ float row_scale(int64_t m) const {
+    return scale ? scale[m / I] : 1.f;
+  }
+  // A warp's 32 rows (m_w .. m_w + 31) x 32 columns (c_base ..) staged as bf16
+  // in stg[column][row]: lane l writes rows m_w + 8 (l % 4) .. + 7 of columns
+  // c_base + 8 q + l / 4, q < 4, as one 16-byte store per replica that owns the
+  // column.  With I % 8 == 0 those 8 rows lie in one slice and start 16-byte
+  // aligned in T.
+  __device__ __forceinline__ void store_chunk(const __nv_bfloat16 *stg, int64_t m_w, int c_base,
+                                              int64_t M, int N, int lane) const {
+    const int sg = lane & 3;
+    const int64_t mseg = m_w + 8 * sg;
+    if (mseg >= M) return;
+    const int64_t k = mseg / I, i = mseg - k * I;
+    __nv_bfloat16 *Tk = T + (k * P * Q) * I + i;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 8 * q + (lane >> 2);
+      const int c = c_base + j;
+      if (c >= N) continue;
+      const uint4 v = *reinterpret_cast<const uint4 *>(stg + j * 32 + 8 * sg);
+      if (c < S) {
+        for (int p = 0; p < P; ++p)
+          *reinterpret_cast<uint4 *>(Tk + ((int64_t)p * Q + c) * I) = v;
+      } else {
+        const int p = (c - S) / (Q - S);
+        const int b = S + (c - S) - p * (Q - S);
+        *reinterpret_cast<uint4 *>(Tk + ((int64_t)p * Q + b) * I) = v;
+      }
+    }
+  }
   __device__ __forceinline__ void operator()(int, int, int m, int c, float v) const {
     const int64_t k = m / I, i = m - k * I;
     if (scale) v *= scale[k];
@@ -198,6 +232,7 @@ struct Mode2TcEpi {
 // Mode-1 epilogue: batch z = k * P + p, row a, column b -> T2[p][k][a][b].
 struct Mode1TcEpi {
   static constexpr bool kRowMajor = true;
+  static constexpr bool kSeg = false;
   float *T2;
   int64_t t;
   int P, Q;
@@ -210,53 +245,17 @@ struct Mode1TcEpi {
   }
 };
 
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-
-// TMA load multicast to the CTAs of `mask` (same shared-memory offset and
-// mbarrier offset in each of them).
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                               int x, int y, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-// Arrives (once MMAs issued so far complete) on the mbarrier at this offset in
-// every CTA of `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // Persistent GEMM: one CTA per SM walks the tiles (N fastest, then M, then the
 // batch index); tensor memory holds two accumulators so the epilogue of one
-// tile overlaps the main loop of the next.  With CL > 1 the CTAs form clusters
-// of CL along M that work on CL vertically adjacent tiles of the same N range:
-// each CTA loads its own A tile and 1/CL of the shared B tile, multicast to the
-// whole cluster, so B crosses the L2 once per cluster instead of once per CTA;
-// a stage is refilled only after the MMAs of every CTA in the cluster released it.
+// tile overlaps the main loop of the next.
 //   warp 0 lane 0 : TMA producer        full[s]  <- TMA bytes,  waits empty[s]
 //   warp 1 lane 0 : MMA issuer          empty[s] <- commit,     acc_full[b] <- commit
 //   warps 2..5    : epilogue (lane quadrant = warp % 4), acc_empty[b] <- 4 arrivals
-template <int KIND, int CL, class Epi>
+template <int KIND, class Epi>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcShape sh, const Epi epi, int batch, int *status) {
@@ -284,18 +283,15 @@ __global__ void __launch_bounds__(192, 1)
   const int nk_all = (sh.K + kElemsPerRow - 1) / kElemsPerRow;
   const int tiles_n = sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN;
   const int tiles_m = (sh.M + kBM - 1) / kBM;
-  const int groups_m = (tiles_m + CL - 1) / CL;        // CL vertically adjacent tiles
-  const int total = tiles_n * groups_m * batch;        // work items (tile groups)
+  const int total = tiles_n * tiles_m * batch;         // work items (tiles)
   const int per_split = sh.ksplit > 1 ? (nk_all + sh.ksplit - 1) / sh.ksplit : nk_all;
-  const int crank = CL > 1 ? (int)cluster_ctarank() : 0;
-  const int item0 = CL > 1 ? (int)blockIdx.x / CL : (int)blockIdx.x;
-  const int nitems = CL > 1 ? (int)gridDim.x / CL : (int)gridDim.x;
-  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
+  const int item0 = (int)blockIdx.x;
+  const int nitems = (int)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL);   // released by the MMAs of every CTA of the cluster
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -308,7 +304,6 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 1) tmem_alloc(tmem_holder, sh.tmem_cols);
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync_all();   // peers' barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
@@ -316,8 +311,8 @@ __global__ void __launch_bounds__(192, 1)
   auto decode = [&](int tile, int &z, int &m0, int &n0, int &split, int &kb0, int &nk) {
     const int nt = tile % tiles_n;
     const int rest = tile / tiles_n;
-    m0 = ((rest % groups_m) * CL + crank) * kBM;
-    z = rest / groups_m;
+    m0 = (rest % tiles_m) * kBM;
+    z = rest / tiles_m;
     if (sh.ksplit > 1) {
       split = nt; n0 = 0; kb0 = nt * per_split; nk = min(per_split, nk_all - kb0);
     } else {
@@ -334,7 +329,6 @@ __global__ void __launch_bounds__(192, 1)
       decode(tile, z, m0, n0, split, kb0, nk);
       const int a_row = (z / sh.zdiv) * sh.a_hi + (z % sh.zdiv) * sh.a_lo + m0;
       const int b_row = (z / sh.zdiv) * sh.b_hi + (z % sh.zdiv) * sh.b_lo + n0;
-      const int b_part = sh.BN / CL;   // rows of B this CTA loads for the cluster
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = it % stages;
         const uint32_t ph = (it / stages) & 1u;
@@ -346,12 +340,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         mbar_expect_tx(&full[s], a_bytes + b_bytes);
         tma_load_2d(sA + s * a_bytes, &tmA, &full[s], (kb0 + kb) * kElemsPerRow, a_row);
-        if constexpr (CL > 1) {
-          tma_load_2d_mc(sB + s * b_bytes + crank * b_part * kRowBytes, &tmB, &full[s],
-                         (kb0 + kb) * kElemsPerRow, b_row + crank * b_part, kMask);
-        } else {
-          tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb0 + kb) * kElemsPerRow, b_row);
-        }
+        tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb0 + kb) * kElemsPerRow, b_row);
       }
     }
     if (aborted) {
@@ -396,8 +385,7 @@ __global__ void __launch_bounds__(192, 1)
           mma_issue<KIND>(d, make_desc_sw128(a0 + kk * 32), make_desc_sw128(b0 + kk * 32), idesc,
                           (kb > 0 || kk > 0) ? 1u : 0u);
         }
-        if constexpr (CL > 1) mma_commit_mc(&empty[s], kMask);
-        else mma_commit(&empty[s]);
+        mma_commit(&empty[s]);
       }
       mma_commit(&acc_full[buf]);
     }
@@ -451,7 +439,23 @@ __global__ void __launch_bounds__(192, 1)
           }
           __syncwarp();
         } else {
-          if (m < sh.M) {
+          bool done = false;
+          if constexpr (Epi::kSeg) {
+            if (epi.seg) {
+              // bf16 block [32 columns][32 rows] per warp, then 16-byte segments
+              __nv_bfloat16 *stg =
+                  reinterpret_cast<__nv_bfloat16 *>(stage_all) + (warp - 2) * 32 * 32;
+              const float sc = m < sh.M ? epi.row_scale(m) : 1.f;
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                stg[j * 32 + lane] = __float2bfloat16_rn(__uint_as_float(r[j]) * sc);
+              __syncwarp();
+              epi.store_chunk(stg, m0 + quad * 32, n0 + c0, sh.M, sh.N, lane);
+              __syncwarp();
+              done = true;
+            }
+          }
+          if (!done && m < sh.M) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int n = n0 + c0 + j;
@@ -467,7 +471,6 @@ __global__ void __launch_bounds__(192, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync_all();   // no peer still writes into this CTA's memory
   if (warp == 1) tmem_dealloc(tmem, sh.tmem_cols);
 }
 
@@ -518,52 +521,33 @@ int sm_count() {
   return n;
 }
 
-template <int KIND, int CL, class Epi>
+template <int KIND, class Epi>
 bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
                const Epi &epi, int *status, cudaStream_t st) {
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
   const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes;
-  const size_t stage_bytes = Epi::kRowMajor ? 4 * 32 * 33 * sizeof(float) + 16 : 0;
-  sh.stages = static_cast<int>((200 * 1024 - stage_bytes) / per_stage);
+  const size_t stage_bytes = Epi::kRowMajor ? 4 * 32 * 33 * sizeof(float) + 16
+                             : Epi::kSeg   ? 4 * 32 * 32 * sizeof(__nv_bfloat16) + 16
+                                           : 0;
+  sh.stages = static_cast<int>((220 * 1024 - stage_bytes) / per_stage);
   if (sh.stages > 8) sh.stages = 8;
   if (sh.stages < 2) return false;
   const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 5) * 8 + 16 + stage_bytes;
-  auto kern = tc_gemm_kernel<KIND, CL, Epi>;
+  auto kern = tc_gemm_kernel<KIND, Epi>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return false;
   const int tiles_n = sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN;
-  const int64_t items =
-      (int64_t)tiles_n * ((((sh.M + kBM - 1) / kBM) + CL - 1) / CL) * batch;
+  const int64_t items = (int64_t)tiles_n * ((sh.M + kBM - 1) / kBM) * batch;
   if (items <= 0 || items > (int64_t)1 << 30) return false;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
   cfg.blockDim = dim3(192);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  int slots = sm_count();
-  if (CL > 1) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) !=
-        cudaSuccess)
-      cudaGetLastError();
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(CL * 1024);
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess ||
-        nclusters < 1) {
-      cudaGetLastError();
-      return false;
-    }
-    slots = nclusters;   // co-resident clusters
-  }
+  const int slots = sm_count();
   const int grid_items = (int)(items < slots ? items : slots);
-  cfg.gridDim = dim3(grid_items * CL);
+  cfg.gridDim = dim3(grid_items);
   if (cudaLaunchKernelEx(&cfg, kern, ma, mb, sh, epi, batch, status) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -589,24 +573,18 @@ bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st) {
   const bool fp8 = a.tx == Elem::E4M3;
   const int64_t M = a.t * a.I;
   if (M > (1 << 30) || a.J > (1 << 30)) return false;
-  CUtensorMap ma, mb, mb4;
+  CUtensorMap ma, mb;
   const int BN = 256;
-  if (!make_map(&ma, a.X, fp8, a.J, M, kBM) || !make_map(&mb, a.Vt, fp8, a.J, a.Qd, BN) ||
-      !make_map(&mb4, a.Vt, fp8, a.J, a.Qd, BN / 4))
+  if (!make_map(&ma, a.X, fp8, a.J, M, kBM) || !make_map(&mb, a.Vt, fp8, a.J, a.Qd, BN))
     return false;
   TcShape sh{};
   sh.ksplit = 1;
   sh.M = static_cast<int>(M); sh.N = a.Qd; sh.K = static_cast<int>(a.J); sh.BN = BN;
   sh.zdiv = 1; sh.a_hi = 0; sh.a_lo = 0; sh.b_hi = 0; sh.b_lo = 0;
-  Mode2TcEpi epi{static_cast<__nv_bfloat16 *>(a.T), a.slice_scale, a.I, a.P, a.Q, a.S};
-  // clusters of 4 along M share the 256-row V tile (multicast); plain
-  // persistent launch if the cluster launch is refused
-  if (fp8) {
-    if (launch_tc<1, 4>(ma, mb4, sh, 1, epi, status, st)) return true;
-    return launch_tc<1, 1>(ma, mb, sh, 1, epi, status, st);
-  }
-  if (launch_tc<0, 4>(ma, mb4, sh, 1, epi, status, st)) return true;
-  return launch_tc<0, 1>(ma, mb, sh, 1, epi, status, st);
+  Mode2TcEpi epi{static_cast<__nv_bfloat16 *>(a.T), a.slice_scale, a.I, a.P, a.Q, a.S,
+                 a.I % 8 == 0};
+  return fp8 ? launch_tc<1>(ma, mb, sh, 1, epi, status, st)
+             : launch_tc<0>(ma, mb, sh, 1, epi, status, st);
 }
 
 bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
@@ -626,7 +604,7 @@ bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
   sh.a_hi = 0; sh.a_lo = a.Q;      // A rows: p * Q
   sh.b_hi = a.P * a.Q; sh.b_lo = a.Q;   // B rows: (k * P + p) * Q
   Mode1TcEpi epi{a.T2, a.t, a.P, a.Q};
-  return launch_tc<0, 1>(ma, mb, sh, static_cast<int>(a.t * a.P), epi, status, st);
+  return launch_tc<0>(ma, mb, sh, static_cast<int>(a.t * a.P), epi, status, st);
 }
 
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
@@ -646,7 +624,7 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT};
   if (g.m1_part && (g.BN != 32 || g.Q % 32 || ks > 1)) return false;
   if (ks > 1 && (g.N > g.BN)) return false;
-  return launch_tc<0, 1>(ma, mb, sh, g.batch, epi, status, st);
+  return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st);
 }
 
 int tc_gemm_splits(int K, int ksplit) {
