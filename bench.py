@@ -207,7 +207,8 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
     import paper_1807_01350_gb300 as pkg
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    nb = warmup + steps + (steps if time_e2e else 0)
+    nbd = min(steps, 3)   # extra appends with per-stage events (the stage breakdown)
+    nb = warmup + steps + nbd + (max(steps, 2) if time_e2e else 0)
     d = stream_inputs(wl, prec, rank_seed(args.seed, rank), nb, dev)
     stream = torch.cuda.current_stream()
     g = pkg.Octen(wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.als_iters, prec, stream=stream)
@@ -220,8 +221,6 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    g.reset_stage_times()
-    g.set_timing(True)
     launches0 = pkg.launch_count()
     tc0 = pkg.tc_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -233,19 +232,27 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
             k += t
         ev1.record(stream)
         torch.cuda.synchronize()
-    g.set_timing(False)
     launches = pkg.launch_count() - launches0
     tc_launches = pkg.tc_launch_count() - tc0
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     if world > 1:
         torch.distributed.barrier()
+    # stage breakdown: further appends with CUDA events around every stage
+    # (launched one by one, since the events sit between the kernels)
+    g.reset_stage_times()
+    g.set_timing(True)
+    for s in range(nbd):
+        g.append(d["X"][k:k + t], d["W"][1 + warmup + steps + s])
+        k += t
+    torch.cuda.synchronize()
+    g.set_timing(False)
     stages = g.stage_times()
     fit = g.fit(d["X"][:k])
     # the two tensor-core contractions run once per append when the path is taken
     tc_stages = ("mode2", "mode1") if tc_launches >= 2 * steps else ()
     if tc_launches >= (2 + 2 * wl.als_iters + 1) * steps:
         tc_stages = tc_stages + ("als_gemm",)
-    out = dict(ms=ms, steps=steps, slices=steps * t, stages=stages, fit=fit,
+    out = dict(ms=ms, steps=steps, slices=steps * t, stages=stages, stage_steps=nbd, fit=fit,
                launches=launches, tc_launches=tc_launches, tc_stages=tc_stages,
                clocks=clk.summary())
     if time_e2e:
@@ -404,7 +411,7 @@ def main():
         beside[prec] = {"value": round(whole_job_rate(r["slices"], r["ms"] / 1e3, world), 3),
                         "ms_per_step": round(r["ms"] / r["steps"], 3), "fit": round(r["fit"], 6),
                         "steps": r["steps"],
-                        "stage_ms_per_step": {k: round(v[0] / r["steps"], 3)
+                        "stage_ms_per_step": {k: round(v[0] / r["stage_steps"], 3)
                                               for k, v in r["stages"].items() if v[1]}}
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -440,7 +447,9 @@ def main():
         "gpu_launches": main_run["launches"],
         "tcgen05_launches": main_run["tc_launches"],
         "roofline": roof,
-        "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in timed.items()},
+        "stage_ms_per_step": {k: round(v[0] / main_run["stage_steps"], 3)
+                              for k, v in timed.items()},
+        "stage_note": "per-stage CUDA events on separate appends launched one by one",
         "stage_roofline": comp,
         "beside": beside,
     }

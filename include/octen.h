@@ -90,7 +90,11 @@ octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
 /* One pass of Algorithm 1's loop for a batch of t >= 1 new slices X_new
  * (t x I x J, element type as in octen_init) with time projections W_new
  * (t x Qd): Y_p += Z_p, CP-ALS of every replica warm-started from U_p^T A,
- * V_p^T B, anchor matching, lift of A and B, t new rows of C.  Limit t <= 64. */
+ * V_p^T B, anchor matching, lift of A and B, t new rows of C.  Limit t <= 64.
+ * The CP-ALS of the replicas is recorded once as a CUDA graph (on a private
+ * stream, at the first append made with the stage timers off) and replayed on
+ * the context's stream at every later such append; environment variable
+ * OCTEN_GRAPH=0 issues its launches one by one instead. */
 octen_status octen_append(octen_ctx *ctx, const void *X_new, int64_t t, const float *W_new);
 
 /* One append on each of n independent decompositions (many streams with

@@ -174,10 +174,129 @@ static void gemm_dispatch_tile(const Operand &A, const Operand &B, const GemmArg
     launch_gemm<EA, EB, 64, 64>(A, B, g.M, g.N, g.K, g.batch, 1, epi, st);
 }
 
+// Skinny fp32 GEMM (N <= 32, one batch item): D = alpha A B + beta D, or the
+// split-K partials part[split][m][n] of A B.  A CTA covers 128 rows over one K
+// range in steps of 32: the A step is staged as As[k][m] (loads coalesced along
+// m or along k, whichever is contiguous), the B step as Bs[k][n] (zero beyond
+// N); thread t owns rows t % 32 + 32 j (j < 4) and columns 8 (t / 32) .. + 7.
+constexpr int kSkBM = 128, kSkBK = 32;
+
+__global__ void __launch_bounds__(128)
+    gemm_skinny_kernel(const float *__restrict__ A, int64_t sAm, int64_t sAk,
+                       const float *__restrict__ B, int64_t sBn, int64_t sBk, int M, int N, int K,
+                       int kc, float *D, int64_t sDm, int64_t sDn, float alpha, float beta,
+                       float *__restrict__ part) {
+  __shared__ float As[kSkBK][kSkBM + 1];
+  __shared__ __align__(16) float Bs[kSkBK][32];
+  const int tid = threadIdx.x, rg = tid & 31, cg = tid >> 5;
+  const int m0 = blockIdx.x * kSkBM;
+  const int k_begin = blockIdx.y * kc;
+  const int k_end = min(K, k_begin + kc);
+  float acc[4][8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[j][c] = 0.f;
+  for (int k0 = k_begin; k0 < k_end; k0 += kSkBK) {
+    __syncthreads();   // the previous step's tiles are consumed
+    if (sAm == 1) {
+      const int m = m0 + tid;
+#pragma unroll 8
+      for (int kk = 0; kk < kSkBK; ++kk) {
+        const int k = k0 + kk;
+        As[kk][tid] = (m < M && k < k_end) ? __ldg(A + m + (int64_t)k * sAk) : 0.f;
+      }
+    } else {
+      const int kk = tid & 31, k = k0 + kk;
+#pragma unroll 8
+      for (int j = 0; j < kSkBM / 4; ++j) {
+        const int mm = (tid >> 5) + 4 * j, m = m0 + mm;
+        As[kk][mm] = (m < M && k < k_end) ? __ldg(A + (int64_t)m * sAm + (int64_t)k * sAk) : 0.f;
+      }
+    }
+    {
+      const int n = tid & 31;
+#pragma unroll
+      for (int j = 0; j < kSkBK / 4; ++j) {
+        const int kk = (tid >> 5) + 4 * j, k = k0 + kk;
+        Bs[kk][n] = (n < N && k < k_end) ? __ldg(B + (int64_t)k * sBk + (int64_t)n * sBn) : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kSkBK; ++kk) {
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][8 * cg]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][8 * cg + 4]);
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float a = As[kk][rg + 32 * j];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[j][c] = fmaf(a, bv[c], acc[j][c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int m = m0 + rg + 32 * j;
+    if (m >= M) continue;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int n = 8 * cg + c;
+      if (n >= N) continue;
+      if (part) {
+        part[((int64_t)blockIdx.y * M + m) * N + n] = acc[j][c];
+      } else {
+        float *d = D + (int64_t)m * sDm + (int64_t)n * sDn;
+        *d = beta == 0.f ? alpha * acc[j][c] : fmaf(beta, *d, alpha * acc[j][c]);
+      }
+    }
+  }
+}
+
+static void gemm_skinny(const GemmArgs &g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0) return;
+  const int tiles_m = (g.M + kSkBM - 1) / kSkBM;
+  int splits = 1;
+  if (g.split_scratch) {
+    splits = 608 / tiles_m;   // about four CTAs per SM in flight
+    if (splits > g.K / 128) splits = g.K / 128;
+    const int64_t MN = (int64_t)g.M * g.N;
+    if ((int64_t)splits * MN > (int64_t)g.split_scratch_floats)
+      splits = (int)(g.split_scratch_floats / MN);
+    if (splits < 1) splits = 1;
+  }
+  int kc = ((g.K + splits - 1) / splits + kSkBK - 1) / kSkBK * kSkBK;
+  if (kc < kSkBK) kc = kSkBK;
+  splits = (g.K + kc - 1) / kc;
+  if (splits < 1) splits = 1;
+  const float *A = static_cast<const float *>(g.A);
+  const float *B = static_cast<const float *>(g.B);
+  const dim3 grid((unsigned)tiles_m, (unsigned)splits);
+  if (splits >= 2) {
+    gemm_skinny_kernel<<<grid, 128, 0, st>>>(A, g.sAm, g.sAk, B, g.sBn, g.sBk, g.M, g.N, g.K, kc,
+                                             nullptr, 0, 0, 1.f, 0.f, g.split_scratch);
+    count_launch();
+    const int64_t MN = (int64_t)g.M * g.N;
+    splitk_reduce_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(
+        g.split_scratch, splits, g.M, g.N, g.D, g.sDm, g.sDn, g.alpha, g.beta);
+    count_launch();
+  } else {
+    gemm_skinny_kernel<<<grid, 128, 0, st>>>(A, g.sAm, g.sAk, B, g.sBn, g.sBk, g.M, g.N, g.K,
+                                             g.K < 1 ? 1 : g.K, g.D, g.sDm, g.sDn, g.alpha,
+                                             g.beta, nullptr);
+    count_launch();
+  }
+}
+
 void gemm_strided(const GemmArgs &g, cudaStream_t st) {
   // zdiv = 1: the whole batch index goes through the s_hi strides
   Operand A{g.A, g.sAz, 0, g.sAm, g.sAk};
   Operand B{g.B, g.sBz, 0, g.sBn, g.sBk};
+  if (g.batch == 1 && g.N <= 32 && g.ta == Elem::F32 && g.tb == Elem::F32) {
+    gemm_skinny(g, st);
+    return;
+  }
   // few output tiles and a long K: split K over CTAs into the caller's scratch
   const int64_t tiles64 = (int64_t)((g.M + 63) / 64) * ((g.N + 63) / 64);
   if (g.batch == 1 && g.split_scratch && tiles64 < 76 && g.K >= 1024 &&

@@ -18,6 +18,11 @@ static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_tc_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_tc_launch() { g_tc_launches.fetch_add(1, std::memory_order_relaxed); }
+// launches recorded into a graph are counted when the graph runs, not when captured
+static void add_launches(int64_t n, int64_t ntc) {
+  g_launches.fetch_add(static_cast<uint64_t>(n), std::memory_order_relaxed);
+  g_tc_launches.fetch_add(static_cast<uint64_t>(ntc), std::memory_order_relaxed);
+}
 }  // namespace octen
 
 namespace {
@@ -78,6 +83,16 @@ struct octen_ctx {
   int *dstatus = nullptr;
   double *dfit = nullptr;
 
+  // The replica CP-ALS of an append (about 200 launches on fixed buffers) runs
+  // as one CUDA graph: captured on a private stream at the first append with
+  // the stage timers off, replayed on the context's stream afterwards.
+  // OCTEN_GRAPH=0 keeps the launches eager.
+  bool use_graph = true;
+  bool als_graph_tried = false;
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t als_exec = nullptr;
+  int64_t als_graph_launches = 0, als_graph_tc = 0;
+
   // per-batch scratch, grown on demand
   DevBuf Tbuf, T2buf, Wbuf, X8buf, xscale, stage[4], fitpart;
 
@@ -126,6 +141,8 @@ struct octen_ctx {
 
   ~octen_ctx() {
     cudaStreamSynchronize(st);
+    if (als_exec) cudaGraphExecDestroy(als_exec);
+    if (cap_st) cudaStreamDestroy(cap_st);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
     for (auto &b : owned) cudaFree(b.p);
     DevBuf *extra[] = {&Tbuf, &T2buf, &Wbuf, &X8buf, &xscale, &stage[0], &stage[1], &stage[2],
@@ -228,6 +245,8 @@ bool tc_wanted() {
 
 void set_types(octen_ctx *x) {
   x->use_tc = x->cfg.prec != OCTEN_FP32 && tc_wanted();
+  const char *g = getenv("OCTEN_GRAPH");
+  x->use_graph = !(g && strcmp(g, "0") == 0);
   switch (x->cfg.prec) {
     case OCTEN_FP32:
       x->xin = Elem::F32; x->tu = Elem::F32; x->tv = Elem::F32; x->tmid = Elem::F32; break;
@@ -518,6 +537,37 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
 
 namespace {
 
+// Records the replica CP-ALS of an append into x->als_exec (left null if a
+// launch is refused or the capture fails; the eager path is used then).
+void capture_als(octen_ctx *x, AlsBuffers ab) {
+  const octen_config &c = x->cfg;
+  x->als_graph_tried = true;
+  if (!x->cap_st && cudaStreamCreateWithFlags(&x->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    x->cap_st = nullptr;
+    return;
+  }
+  const uint64_t l0 = octen_launch_count(), t0 = octen_tc_launch_count();
+  if (cudaStreamBeginCapture(x->cap_st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const bool ok = als_run(x->Y, c.P, c.Q, c.R, x->RT, c.als_iters, ab, x->cap_st, Marker{});
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(x->cap_st, &g);
+  const int64_t dl = (int64_t)(octen_launch_count() - l0);
+  const int64_t dt = (int64_t)(octen_tc_launch_count() - t0);
+  add_launches(-dl, -dt);   // recorded, not run
+  if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&x->als_exec, g, 0) == cudaSuccess) {
+    x->als_graph_launches = dl;
+    x->als_graph_tc = dt;
+  } else {
+    x->als_exec = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+}
+
 // Enqueues one append on the context's stream (no final synchronisation; K is
 // advanced by the caller once the stream has finished without error).
 octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
@@ -549,7 +599,19 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   ab.Mparts = x->Mparts; ab.ksplit = x->als_ks;
   Marker mk;
   if (x->timing) { mk.fn = &octen_ctx::mark_cb; mk.arg = x; }
-  if (!als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st, mk)) {
+  bool replayed = false;
+  if (!x->timing && x->use_graph) {
+    if (!x->als_exec && !x->als_graph_tried) capture_als(x, ab);
+    if (x->als_exec) {
+      if (cudaGraphLaunch(x->als_exec, x->st) == cudaSuccess) {
+        add_launches(x->als_graph_launches, x->als_graph_tc);
+        replayed = true;
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
+  if (!replayed && !als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st, mk)) {
     // a tensor-core launch was refused: redo the CP from the warm start on SIMT
     cudaGetLastError();
     x->als_tc = false;

@@ -75,3 +75,28 @@ def test_tc_update_parity_bf16(pkg):
     g.close()
     assert pkg.tc_launch_count() > n0
     check_update(case, d, gpu, ref)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_als_graph_replay_equals_eager_launches(pkg, prec, monkeypatch):
+    """The replica CP-ALS recorded as a CUDA graph at the first append and
+    replayed afterwards gives the factors of the same kernels launched one by
+    one (OCTEN_GRAPH=0) bit for bit, and its launches are still counted."""
+    from tests.test_gpu_parity import run_gpu
+
+    case = Case(160, 144, 6, 4, 32, 8, 40, (16, 8, 16), 12, prec=prec, seed=23)
+    d = case.make()
+    n0 = pkg.launch_count()
+    g, graph = run_gpu(pkg, case, d)
+    g.close()
+    n_graph = pkg.launch_count() - n0
+    monkeypatch.setenv("OCTEN_GRAPH", "0")
+    n1 = pkg.launch_count()
+    h, eager = run_gpu(pkg, case, d)
+    h.close()
+    assert pkg.launch_count() - n1 == n_graph
+    for a, b in zip(graph, eager):
+        for key in ("Y", "A", "B", "C"):
+            assert np.array_equal(a[key], b[key]), key
+        for u, v in zip(a["raw"], b["raw"]):
+            assert np.array_equal(u, v)
