@@ -264,17 +264,53 @@ __global__ void tc_m2_kernel(const float *__restrict__ Tc, const float *__restri
 
 static int block_for(int Q) { return ((Q + 31) / 32) * 32; }
 
-// M row q of replica p is sum_{s < nsplit} M[s * split_stride + (p * Q + q) * row_stride]
-// (row_stride 0 means RT).
+int als_factor_floats(int RT) {
+  return RT == 8 ? factor_floats<8>() : (RT == 16 ? factor_floats<16>() : factor_floats<32>());
+}
+
+// Forks the factor of an update onto b.side: the Gram of Fnew (the factor
+// updated last) into Gnew, then L D L^T of Gnew * Gother into b.L.
 template <int RT>
-static void solve(const float *M, int nsplit, int64_t split_stride, const float *G1,
-                  const float *G2, float *F, float *Gout, __nv_bfloat16 *Ft, int NP, int P,
-                  int Q, int R, int normalize, int *status, cudaStream_t st,
-                  int64_t row_stride = 0) {
-  const size_t smem = (size_t)Q * RT * sizeof(float);
-  als_solve_kernel<RT><<<P, 256, smem, st>>>(M, nsplit, split_stride,
-                                             row_stride ? row_stride : RT, G1, G2, F, Gout, Ft,
-                                             NP, Q, R, normalize, status);
+static void factor_async(const float *Fnew, float *Gnew, const float *Gother, int P, int Q, int R,
+                         AlsBuffers &b, cudaStream_t st) {
+  cudaEventRecord(b.ev_fork, st);
+  cudaStreamWaitEvent(b.side, b.ev_fork, 0);
+  als_factor_kernel<RT><<<P, 256, (size_t)Q * RT * sizeof(float), b.side>>>(Fnew, Gnew, Gother, Q,
+                                                                            R, b.L, b.status);
+  count_launch();
+  cudaEventRecord(b.ev_join, b.side);
+}
+
+// Joins the factor and solves: F = M (L D L^T)^-1 with M row q of replica p
+// the sum over s < nsplit of M[s * split_stride + (p * Q + q) * row_stride].
+// Clusters of up to 8 CTAs share a replica (32 rows each at Q = 256); one CTA
+// per replica if the cluster launch is refused.
+template <int RT>
+static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_stride, float *F,
+                  __nv_bfloat16 *Ft, int NP, int P, int Q, int normalize, AlsBuffers &b,
+                  cudaStream_t st) {
+  cudaStreamWaitEvent(st, b.ev_join, 0);
+  int cl = (Q + 31) / 32;
+  if (cl > 8) cl = 8;
+  const int rows = (Q + cl - 1) / cl;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3(P * cl);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = (size_t)rows * RT * sizeof(float);
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, als_apply_kernel<RT>, M, nsplit, split_stride, row_stride,
+                         (const float *)b.L, F, Ft, NP, Q, rows, normalize) != cudaSuccess) {
+    cudaGetLastError();
+    als_apply_kernel<RT><<<P, 256, (size_t)Q * RT * sizeof(float), st>>>(
+        M, nsplit, split_stride, row_stride, b.L, F, Ft, NP, Q, Q, normalize);
+  }
   count_launch();
 }
 
@@ -288,6 +324,7 @@ static void als_run_simt(const float *Y, int P, int Q, int R, int iters, AlsBuff
   const dim3 gQP(Q, P);
   const dim3 gM3((Q * RT + 255) / 256, P);
   auto c_update = [&]() {
+    factor_async<RT>(b.Bf, b.GB, b.GA, P, Q, R, b, st);
     mk(kStAlsGemm, 1);
     als_h_kernel<RT><<<gQP, bq, smem_h, st>>>(Y, b.Bf, b.H, Q);
     count_launch();
@@ -297,24 +334,26 @@ static void als_run_simt(const float *Y, int P, int Q, int R, int iters, AlsBuff
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);
-    solve<RT>(b.M, 1, 0, b.GA, b.GB, b.Cf, b.GC, nullptr, 0, P, Q, R, 0, b.status, st);
+    apply<RT>(b.M, 1, 0, RT, b.Cf, nullptr, 0, P, Q, 0, b, st);
     mk(kStAlsSolve, 0);
   };
   for (int it = 0; it < iters; ++it) {
     c_update();
+    factor_async<RT>(b.Cf, b.GC, b.GB, P, Q, R, b, st);
     mk(kStAlsAux, 1);
     als_m1_kernel<RT><<<gQP, 256, 0, st>>>(b.H, b.Cf, b.M, Q);
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);
-    solve<RT>(b.M, 1, 0, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status, st);
+    apply<RT>(b.M, 1, 0, RT, b.Af, nullptr, 0, P, Q, 1, b, st);
     mk(kStAlsSolve, 0);
+    factor_async<RT>(b.Af, b.GA, b.GC, P, Q, R, b, st);
     mk(kStAlsGemm, 1);
     als_m2_kernel<RT><<<gQP, bq, smem_m2, st>>>(Y, b.Af, b.Cf, b.M, Q);
     count_launch();
     mk(kStAlsGemm, 0);
     mk(kStAlsSolve, 1);
-    solve<RT>(b.M, 1, 0, b.GA, b.GC, b.Bf, b.GB, nullptr, 0, P, Q, R, 1, b.status, st);
+    apply<RT>(b.M, 1, 0, RT, b.Bf, nullptr, 0, P, Q, 1, b, st);
     mk(kStAlsSolve, 0);
   }
   c_update();
@@ -345,11 +384,14 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   // M1 fused into the Tc GEMM: per-warp partials over 32 consecutive b
   const bool fuse_m1 = Q % 32 == 0;
   if (fuse_m1) { tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; }
+  // the factor kernel of each update runs beside these GEMMs: leave it room
+  m3.smem_reserve = tc.smem_reserve = 56 * 1024;
   const int ks = tc_gemm_splits(m3.K, b.ksplit);
   const dim3 gKR(NP, P);
   const dim3 gM((Q * RT + 255) / 256, P);
   bool ok = true;
   auto c_update = [&]() {
+    factor_async<RT>(b.Bf, b.GB, b.GA, P, Q, R, b, st);
     mk(kStAlsAux, 1);
     kr_kernel<RT><<<gKR, 256, 0, st>>>(b.Af, b.Bf, Q, b.KR);
     count_launch();
@@ -358,19 +400,18 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     ok = ok && tc_gemm_store(m3, b.status, st);
     mk(kStAlsGemm, 0);
     mk(kStAlsSolve, 1);
-    solve<RT>(b.Mparts, ks, (int64_t)P * Q * RT, b.GA, b.GB, b.Cf, b.GC, b.Ct, NP, P, Q, R, 0,
-              b.status, st);
+    apply<RT>(b.Mparts, ks, (int64_t)P * Q * RT, RT, b.Cf, b.Ct, NP, P, Q, 0, b, st);
     mk(kStAlsSolve, 0);
   };
   for (int it = 0; it < iters && ok; ++it) {
     c_update();
+    factor_async<RT>(b.Cf, b.GC, b.GB, P, Q, R, b, st);
     mk(kStAlsGemm, 1);
     ok = ok && tc_gemm_store(tc, b.status, st);
     mk(kStAlsGemm, 0);
     if (fuse_m1) {
       mk(kStAlsSolve, 1);
-      solve<RT>(b.Mparts, Q / 32, RT, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status,
-                st, (int64_t)(Q / 32) * RT);
+      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Af, nullptr, 0, P, Q, 1, b, st);
       mk(kStAlsSolve, 0);
     } else {
       mk(kStAlsAux, 1);
@@ -378,15 +419,16 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
       count_launch();
       mk(kStAlsAux, 0);
       mk(kStAlsSolve, 1);
-      solve<RT>(b.M, 1, 0, b.GB, b.GC, b.Af, b.GA, nullptr, 0, P, Q, R, 1, b.status, st);
+      apply<RT>(b.M, 1, 0, RT, b.Af, nullptr, 0, P, Q, 1, b, st);
       mk(kStAlsSolve, 0);
     }
+    factor_async<RT>(b.Af, b.GA, b.GC, P, Q, R, b, st);
     mk(kStAlsAux, 1);
     tc_m2_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Af, Q, b.M);
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);
-    solve<RT>(b.M, 1, 0, b.GA, b.GC, b.Bf, b.GB, nullptr, 0, P, Q, R, 1, b.status, st);
+    apply<RT>(b.M, 1, 0, RT, b.Bf, nullptr, 0, P, Q, 1, b, st);
     mk(kStAlsSolve, 0);
   }
   if (ok) c_update();
@@ -403,9 +445,16 @@ int als_tc_splits(int P, int Q, int desired) {
 bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
              cudaStream_t st, const Marker &mk) {
   const int smem = (int)((size_t)Q * RT * sizeof(float));
-  if (RT == 8) cudaFuncSetAttribute(als_solve_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (RT == 16) cudaFuncSetAttribute(als_solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (RT == 32) cudaFuncSetAttribute(als_solve_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (RT == 8) {
+    cudaFuncSetAttribute(als_factor_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(als_apply_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  } else if (RT == 16) {
+    cudaFuncSetAttribute(als_factor_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(als_apply_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  } else {
+    cudaFuncSetAttribute(als_factor_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(als_apply_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
   if (b.use_tc) {
     if (RT == 8) return als_run_tc<8>(Y, P, Q, R, iters, b, st, mk);
     if (RT == 16) return als_run_tc<16>(Y, P, Q, R, iters, b, st, mk);

@@ -8,86 +8,127 @@
 namespace octen {
 
 // ---------------------------------------------------------------------------
-// Anchor match, one CTA per replica.  ref_a = PA rows [0, S) (= u^T A_prev).
+// Anchor match.  ref_a = PA rows [0, S) (= u^T A_prev).
 //   sim[r][s] = |cos(At[:S, r], ref_a[:, s])| + |cos(Bt[:S, r], ref_b[:, s])|
 // greedy: largest similarity among unmatched pairs, ties to lowest s then r;
 // d_a[s] = <At[:S, pi(s)], ref_a[:, s]> / ||ref_a[:, s]||^2 (0 -> 1), same for b.
+// Dot products, norms, similarities and scales are fp64.  An fp64 warp
+// instruction costs ~64 cycles on this GPU, so the S-term dot products are
+// spread over P * RT CTAs (one per replica and column r) before one CTA per
+// replica matches; the greedy scan compares the similarities through their
+// bit patterns (ordered like the values for non-negative doubles) with integer
+// instructions.
 // ---------------------------------------------------------------------------
+
+// Scratch layout per replica p (doubles): dA[RT][RT], dB[RT][RT], then
+// nta[RT], ntb[RT], nra[RT], nrb[RT].
 template <int RT>
-__global__ void __launch_bounds__(256)
-    align_kernel(const float *__restrict__ At, const float *__restrict__ Bt,
-                 const float *__restrict__ Ct, const float *__restrict__ PA,
-                 const float *__restrict__ PB, int Q, int S, int R, float *__restrict__ Ah,
-                 float *__restrict__ Bh, float *__restrict__ Ch, int *__restrict__ perm_out,
-                 double *__restrict__ scales_out) {
-  __shared__ double dA[RT * RT], dB[RT * RT], sim[RT * RT];
-  __shared__ double nra[RT], nrb[RT], nta[RT], ntb[RT];
-  __shared__ double da[RT], db[RT];
-  __shared__ int perm[RT];
-  const int p = blockIdx.x;
+__host__ __device__ constexpr int align_scratch_per_replica() { return 2 * RT * RT + 4 * RT; }
+
+// grid (RT, P), 96 threads: warp 0 row r of dA, warp 1 row r of dB, warp 2 the
+// four squared norms of column r.
+template <int RT>
+__global__ void __launch_bounds__(96)
+    align_dots_kernel(const float *__restrict__ At, const float *__restrict__ Bt,
+                      const float *__restrict__ PA, const float *__restrict__ PB, int Q, int S,
+                      int R, double *__restrict__ scratch) {
+  const int r = blockIdx.x, p = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double *sc = scratch + (int64_t)p * align_scratch_per_replica<RT>();
   const float *at = At + (int64_t)p * Q * RT, *bt = Bt + (int64_t)p * Q * RT;
-  const float *ct = Ct + (int64_t)p * Q * RT;
-  // dot products of anchor columns (fp64)
-  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
-    const int r = e / RT, s = e % RT;
-    double sa = 0.0, sb = 0.0;
-    if (r < R && s < R) {
-      for (int q = 0; q < S; ++q) {
-        sa += (double)at[q * RT + r] * (double)PA[(int64_t)q * R + s];
-        sb += (double)bt[q * RT + r] * (double)PB[(int64_t)q * R + s];
-      }
-    }
-    dA[e] = sa;
-    dB[e] = sb;
-  }
-  if (threadIdx.x < RT) {
-    const int r = threadIdx.x;
+  if (warp < 2) {
+    const float *t = warp == 0 ? at : bt;
+    const float *ref = warp == 0 ? PA : PB;
+    double acc = 0.0;
+    if (r < R && lane < R)
+      for (int q = 0; q < S; ++q)
+        acc = fma((double)t[q * RT + r], (double)ref[(int64_t)q * R + lane], acc);
+    if (lane < RT) sc[warp * RT * RT + r * RT + lane] = acc;
+  } else {
     double a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
     if (r < R) {
-      for (int q = 0; q < S; ++q) {
-        const double ra = PA[(int64_t)q * R + r], rb = PB[(int64_t)q * R + r];
+      for (int q = lane; q < S; q += 32) {
         const double ta = at[q * RT + r], tb = bt[q * RT + r];
-        a1 += ra * ra; a2 += rb * rb; a3 += ta * ta; a4 += tb * tb;
+        const double ra = PA[(int64_t)q * R + r], rb = PB[(int64_t)q * R + r];
+        a1 = fma(ta, ta, a1); a2 = fma(tb, tb, a2); a3 = fma(ra, ra, a3); a4 = fma(rb, rb, a4);
       }
     }
-    nra[r] = a1; nrb[r] = a2; nta[r] = a3; ntb[r] = a4;
+    for (int o = 16; o > 0; o >>= 1) {
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+      a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+      a4 += __shfl_xor_sync(0xffffffffu, a4, o);
+    }
+    if (lane == 0) {
+      double *n = sc + 2 * RT * RT;
+      n[r] = a1; n[RT + r] = a2; n[2 * RT + r] = a3; n[3 * RT + r] = a4;
+    }
+  }
+}
+
+// grid P, 256 threads: similarities, greedy matching (warp 0), scales, and the
+// aligned replica factors Ah = At[:, pi] / d_a, Bh = Bt[:, pi] / d_b,
+// Ch = Ct[:, pi] d_a d_b (the scales applied as fp32 factors).
+template <int RT>
+__global__ void __launch_bounds__(256)
+    align_match_kernel(const float *__restrict__ At, const float *__restrict__ Bt,
+                       const float *__restrict__ Ct, const double *__restrict__ scratch, int Q,
+                       int R, float *__restrict__ Ah, float *__restrict__ Bh,
+                       float *__restrict__ Ch, int *__restrict__ perm_out,
+                       double *__restrict__ scales_out) {
+  __shared__ double dA[RT * RT], dB[RT * RT], nrm[4 * RT], sq[4 * RT];
+  __shared__ unsigned long long key[RT * RT];
+  __shared__ float fa[RT], fb[RT], fc[RT];
+  __shared__ int perm[RT];
+  const int p = blockIdx.x;
+  const double *sc = scratch + (int64_t)p * align_scratch_per_replica<RT>();
+  for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
+    dA[e] = sc[e];
+    dB[e] = sc[RT * RT + e];
+  }
+  if (threadIdx.x < 4 * RT) {
+    const double v = sc[2 * RT * RT + threadIdx.x];
+    nrm[threadIdx.x] = v;
+    sq[threadIdx.x] = sqrt(v);   // nta, ntb, nra, nrb -> their square roots
   }
   __syncthreads();
+  const double *nta = sq, *ntb = sq + RT, *nra = sq + 2 * RT, *nrb = sq + 3 * RT;
   for (int e = threadIdx.x; e < RT * RT; e += blockDim.x) {
     const int r = e / RT, s = e % RT;
     double v = 0.0;
     if (r < R && s < R) {
-      const double den_a = sqrt(nta[r]) * sqrt(nra[s]);
-      const double den_b = sqrt(ntb[r]) * sqrt(nrb[s]);
+      const double den_a = nta[r] * nra[s];
+      const double den_b = ntb[r] * nrb[s];
       if (den_a > 0.0) v += fabs(dA[e]) / den_a;
       if (den_b > 0.0) v += fabs(dB[e]) / den_b;
       if (!isfinite(v)) v = 0.0;   // a diverged replica still gets a valid matching
     }
-    sim[e] = v;
+    key[e] = static_cast<unsigned long long>(__double_as_longlong(v));   // v >= 0
   }
   __syncthreads();
-  // greedy matching by warp 0: lane s scans its column for the best free r
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     unsigned used_r = 0u, used_s = 0u;
     for (int round = 0; round < R; ++round) {
-      double best = -1.0;
+      unsigned long long best = 0ull;
       int br = -1;
       if (lane < R && !((used_s >> lane) & 1u)) {
         for (int r = 0; r < R; ++r) {
           if ((used_r >> r) & 1u) continue;
-          const double v = sim[r * RT + lane];
-          if (v > best || br < 0) { best = v; br = r; }
+          const unsigned long long v = key[r * RT + lane];
+          if (br < 0 || v > best) { best = v; br = r; }
         }
       }
-      // warp argmax over lanes: larger value wins, ties to the lower lane (s)
+      // warp argmax over lanes: larger value wins, ties to the lower lane (s);
+      // lanes with nothing left carry br = -1 and never win
       int bs = lane;
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int obr = __shfl_xor_sync(0xffffffffu, br, o);
         const int obs = __shfl_xor_sync(0xffffffffu, bs, o);
-        if (ov > best || (ov == best && obs < bs)) { best = ov; br = obr; bs = obs; }
+        const bool take = obr >= 0 && (br < 0 || ov > best || (ov == best && obs < bs));
+        if (take) { best = ov; br = obr; bs = obs; }
       }
+      if (br < 0) break;   // every lane holds the same winner after the butterfly
       if (lane == 0) perm[bs] = br;
       used_r |= 1u << br;
       used_s |= 1u << bs;
@@ -95,26 +136,30 @@ __global__ void __launch_bounds__(256)
     __syncwarp();
     if (lane < R) {
       const int s = lane, r = perm[s];
-      double a = nra[s] > 0.0 ? dA[r * RT + s] / nra[s] : 0.0;
-      double b = nrb[s] > 0.0 ? dB[r * RT + s] / nrb[s] : 0.0;
+      const double n2a = nrm[2 * RT + s], n2b = nrm[3 * RT + s];
+      double a = n2a > 0.0 ? dA[r * RT + s] / n2a : 0.0;
+      double b = n2b > 0.0 ? dB[r * RT + s] / n2b : 0.0;
       if (a == 0.0) a = 1.0;
       if (b == 0.0) b = 1.0;
-      da[s] = a;
-      db[s] = b;
+      fa[s] = (float)(1.0 / a);
+      fb[s] = (float)(1.0 / b);
+      fc[s] = (float)(a * b);
       perm_out[p * R + s] = r;
       scales_out[(int64_t)p * 2 * R + s] = a;
       scales_out[(int64_t)p * 2 * R + R + s] = b;
     }
   }
   __syncthreads();
+  const float *at = At + (int64_t)p * Q * RT, *bt = Bt + (int64_t)p * Q * RT;
+  const float *ct = Ct + (int64_t)p * Q * RT;
   for (int e = threadIdx.x; e < Q * RT; e += blockDim.x) {
     const int q = e / RT, s = e % RT;
     float va = 0.f, vb = 0.f, vc = 0.f;
     if (s < R) {
       const int r = perm[s];
-      va = (float)((double)at[q * RT + r] / da[s]);
-      vb = (float)((double)bt[q * RT + r] / db[s]);
-      vc = (float)((double)ct[q * RT + r] * (da[s] * db[s]));
+      va = at[q * RT + r] * fa[s];
+      vb = bt[q * RT + r] * fb[s];
+      vc = ct[q * RT + r] * fc[s];
     }
     const int64_t o = (int64_t)p * Q * RT + e;
     Ah[o] = va;
@@ -123,16 +168,32 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <int RT>
+static void align_launch(const float *At, const float *Bt, const float *Ct, const float *PA,
+                         const float *PB, int P, int Q, int S, int R, float *Ah, float *Bh,
+                         float *Ch, int *perm, double *scales, double *scratch, cudaStream_t st) {
+  align_dots_kernel<RT><<<dim3(RT, P), 96, 0, st>>>(At, Bt, PA, PB, Q, S, R, scratch);
+  count_launch();
+  align_match_kernel<RT><<<P, 256, 0, st>>>(At, Bt, Ct, scratch, Q, R, Ah, Bh, Ch, perm, scales);
+  count_launch();
+}
+
+size_t align_scratch_doubles(int P, int RT) {
+  return (size_t)P * (RT == 8    ? align_scratch_per_replica<8>()
+                      : RT == 16 ? align_scratch_per_replica<16>()
+                                 : align_scratch_per_replica<32>());
+}
+
 void align_replicas(const float *At, const float *Bt, const float *Ct, const float *PA,
                     const float *PB, int P, int Q, int S, int R, int RT, float *Ah,
-                    float *Bh, float *Ch, int *perm, double *scales, cudaStream_t st) {
+                    float *Bh, float *Ch, int *perm, double *scales, double *scratch,
+                    cudaStream_t st) {
   if (RT == 8)
-    align_kernel<8><<<P, 256, 0, st>>>(At, Bt, Ct, PA, PB, Q, S, R, Ah, Bh, Ch, perm, scales);
+    align_launch<8>(At, Bt, Ct, PA, PB, P, Q, S, R, Ah, Bh, Ch, perm, scales, scratch, st);
   else if (RT == 16)
-    align_kernel<16><<<P, 256, 0, st>>>(At, Bt, Ct, PA, PB, Q, S, R, Ah, Bh, Ch, perm, scales);
+    align_launch<16>(At, Bt, Ct, PA, PB, P, Q, S, R, Ah, Bh, Ch, perm, scales, scratch, st);
   else
-    align_kernel<32><<<P, 256, 0, st>>>(At, Bt, Ct, PA, PB, Q, S, R, Ah, Bh, Ch, perm, scales);
-  count_launch();
+    align_launch<32>(At, Bt, Ct, PA, PB, P, Q, S, R, Ah, Bh, Ch, perm, scales, scratch, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -18,8 +18,13 @@
 //     fixed set of entries each, kept in registers.  At step j every owner of an
 //     entry (i, k), k > j, subtracts c_ij c_kj r_j from it; the owners of
 //     column j + 1 publish its final (unscaled) values c_{i,j+1} to shared memory.
-// One named barrier over the four warps closes each step.  Warps 4..7 sum the
-// MTTKRP's partial products into shared memory meanwhile.
+// One named barrier over the four warps closes each step.
+//
+// The factor of an update depends only on factors that are already final, so
+// it is a kernel of its own (als_factor_kernel, which also forms the Gram of
+// the factor updated last) that runs beside the MTTKRP of the update; the
+// solve proper (als_apply_kernel) sums the MTTKRP's partials and substitutes,
+// with a cluster of CTAs per replica.
 #pragma once
 
 #include "octen_internal.cuh"
@@ -217,137 +222,199 @@ __device__ void ldl_factor(const float *__restrict__ g1, const float *__restrict
   }
 }
 
-// F_p = M_p (G1_p * G2_p)^-1, M_p the sum of `nsplit` partial MTTKRPs (row q
-// of split s at M + s * split_stride + (p * Q + q) * row_stride).  Optionally
-// normalises the columns to unit l2.  Writes F_p, its Gram F_p^T F_p and, if Ft
-// is given, a bf16 copy transposed to [NP][Q] (rows >= R zero) for the
-// tensor-core passes.  grid P, 256 threads (Q <= 256); dynamic smem Q * RT floats.
+// Per replica: the packed factor written by als_factor_kernel and read by
+// als_apply_kernel, [Lc (RT x RT) | Lr (RT x RT) | rf (RT)] floats.
+template <int RT>
+__host__ __device__ constexpr int factor_floats() { return 2 * RT * RT + RT; }
+
+// Gram of the factor updated last (F_p, Q x RT, global) -> Gnew_p, then the
+// L D L^T factor of Gnew_p * Gother_p -> Lout_p.  It depends only on factors
+// that are already final, so it runs beside the MTTKRP of the same update.
+// grid P, 256 threads; dynamic smem Q * RT floats.
 template <int RT>
 __global__ void __launch_bounds__(256, 1)
-    als_solve_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
-                     int64_t row_stride, const float *__restrict__ G1,
-                     const float *__restrict__ G2, float *__restrict__ F,
-                     float *__restrict__ Gout, __nv_bfloat16 *__restrict__ Ft, int NP, int Q,
-                     int R, int normalize, int *status) {
-  extern __shared__ __align__(16) float Fs[];   // [Q][RT]: rows of M, then of F
+    als_factor_kernel(const float *__restrict__ Fnew, float *__restrict__ Gnew,
+                      const float *__restrict__ Gother, int Q, int R, float *__restrict__ Lout,
+                      int *status) {
+  extern __shared__ __align__(16) float Fs[];   // [Q][RT]
+  __shared__ __align__(16) float Gs[RT * RT];
   __shared__ double Craw[RT * (RT + 1)], Rs[RT];
   __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT];
-  __shared__ float red[8 * RT], out[RT];
   __shared__ int fail_s;
   const int p = blockIdx.x, tid = threadIdx.x;
-  if (tid < 128) {
-    ldl_factor<RT>(G1 + (int64_t)p * RT * RT, G2 + (int64_t)p * RT * RT, R, Craw, Rs, Lc, Lr,
-                   rf, &fail_s);
-  } else {
-    // rows of M: sum of the partials (independent loads, 4 splits at a time)
-    for (int q = tid - 128; q < Q; q += 128) {
-      const float *base = M + ((int64_t)p * Q + q) * row_stride;
-      float m[RT];
-#pragma unroll
-      for (int r = 0; r < RT; ++r) m[r] = 0.f;
-      int sp = 0;
-      for (; sp + 4 <= nsplit; sp += 4) {
-#pragma unroll
-        for (int r4 = 0; r4 < RT / 4; ++r4) {
-          const float4 v0 = reinterpret_cast<const float4 *>(base + (sp + 0) * split_stride)[r4];
-          const float4 v1 = reinterpret_cast<const float4 *>(base + (sp + 1) * split_stride)[r4];
-          const float4 v2 = reinterpret_cast<const float4 *>(base + (sp + 2) * split_stride)[r4];
-          const float4 v3 = reinterpret_cast<const float4 *>(base + (sp + 3) * split_stride)[r4];
-          m[4 * r4] += (v0.x + v1.x) + (v2.x + v3.x);
-          m[4 * r4 + 1] += (v0.y + v1.y) + (v2.y + v3.y);
-          m[4 * r4 + 2] += (v0.z + v1.z) + (v2.z + v3.z);
-          m[4 * r4 + 3] += (v0.w + v1.w) + (v2.w + v3.w);
-        }
-      }
-      for (; sp < nsplit; ++sp) {
-#pragma unroll
-        for (int r4 = 0; r4 < RT / 4; ++r4) {
-          const float4 v = reinterpret_cast<const float4 *>(base + sp * split_stride)[r4];
-          m[4 * r4] += v.x; m[4 * r4 + 1] += v.y; m[4 * r4 + 2] += v.z; m[4 * r4 + 3] += v.w;
-        }
-      }
-      float4 *o = reinterpret_cast<float4 *>(Fs + q * RT);
-#pragma unroll
-      for (int r4 = 0; r4 < RT / 4; ++r4)
-        o[r4] = make_float4(m[4 * r4], m[4 * r4 + 1], m[4 * r4 + 2], m[4 * r4 + 3]);
-    }
-  }
+  const float4 *src = reinterpret_cast<const float4 *>(Fnew + (int64_t)p * Q * RT);
+  float4 *dst = reinterpret_cast<float4 *>(Fs);
+  for (int e = tid; e < Q * RT / 4; e += blockDim.x) dst[e] = src[e];
+  __syncthreads();
+  smem_gram<RT>(Fs, Q, Gs);
+  __syncthreads();
+  for (int e = tid; e < RT * RT; e += blockDim.x) Gnew[(int64_t)p * RT * RT + e] = Gs[e];
+  if (tid < 128)
+    ldl_factor<RT>(Gs, Gother + (int64_t)p * RT * RT, R, Craw, Rs, Lc, Lr, rf, &fail_s);
   __syncthreads();
   if (fail_s && tid == 0) atomicOr(status, kDevCholesky);
+  float *lo = Lout + (int64_t)p * factor_floats<RT>();
+  for (int e = tid; e < RT * RT; e += blockDim.x) {
+    lo[e] = Lc[e];
+    lo[RT * RT + e] = Lr[e];
+  }
+  if (tid < RT) lo[2 * RT * RT + tid] = rf[tid];
+}
 
-  // f = M row q solved against L D L^T: forward with L, scale by 1/D, backward with L^T
-  const int q = tid;
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// fp32 at the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ float ld_cluster(const float *p, uint32_t rank) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  uint32_t ra;
+  float v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// F_p = M_p (L D L^T)^-1 for rows [rank * rows_per_cta, ...) of replica p,
+// M_p the sum of `nsplit` partial MTTKRPs (row q of split s at M + s *
+// split_stride + (p * Q + q) * row_stride).  A cluster of CTAs shares a
+// replica (grid P * cluster size); with `normalize` the column norms are summed
+// over the cluster through distributed shared memory and the columns scaled to
+// unit l2.  Writes F_p and, if Ft is given, a bf16 copy transposed to [NP][Q]
+// (rows >= R zero) for the tensor-core passes.  256 threads; dynamic smem
+// rows_per_cta * RT floats.
+template <int RT>
+__global__ void __launch_bounds__(256)
+    als_apply_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
+                     int64_t row_stride, const float *__restrict__ Lin, float *__restrict__ F,
+                     __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int rows_per_cta,
+                     int normalize) {
+  extern __shared__ __align__(16) float Ms[];   // [rows_per_cta][RT]
+  __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT];
+  __shared__ float red[8 * RT], part[RT], scale[RT];
+  const int tid = threadIdx.x;
+  const uint32_t ncta = cluster_size(), crank = cluster_rank();
+  const int p = blockIdx.x / ncta;
+  const int row0 = crank * rows_per_cta;
+  const int nrows = Q - row0 < rows_per_cta ? (Q - row0 > 0 ? Q - row0 : 0) : rows_per_cta;
+  {
+    const float4 *li = reinterpret_cast<const float4 *>(Lin + (int64_t)p * factor_floats<RT>());
+    float4 *lc = reinterpret_cast<float4 *>(Lc), *lr = reinterpret_cast<float4 *>(Lr);
+    for (int e = tid; e < RT * RT / 4; e += blockDim.x) {
+      lc[e] = li[e];
+      lr[e] = li[RT * RT / 4 + e];
+    }
+    if (tid < RT) rf[tid] = Lin[(int64_t)p * factor_floats<RT>() + 2 * RT * RT + tid];
+  }
+  // rows of M: RT / 4 threads per row, each a float4 of columns summed over the splits
+  constexpr int TPR = RT / 4;
+  for (int e = tid; e < nrows * TPR; e += blockDim.x) {
+    const int rr = e / TPR, c4 = e - (e / TPR) * TPR;
+    const float *base = M + ((int64_t)p * Q + row0 + rr) * row_stride + 4 * c4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int sp = 0;
+    for (; sp + 4 <= nsplit; sp += 4) {
+      const float4 v0 = *reinterpret_cast<const float4 *>(base + (sp + 0) * split_stride);
+      const float4 v1 = *reinterpret_cast<const float4 *>(base + (sp + 1) * split_stride);
+      const float4 v2 = *reinterpret_cast<const float4 *>(base + (sp + 2) * split_stride);
+      const float4 v3 = *reinterpret_cast<const float4 *>(base + (sp + 3) * split_stride);
+      acc.x += (v0.x + v1.x) + (v2.x + v3.x);
+      acc.y += (v0.y + v1.y) + (v2.y + v3.y);
+      acc.z += (v0.z + v1.z) + (v2.z + v3.z);
+      acc.w += (v0.w + v1.w) + (v2.w + v3.w);
+    }
+    for (; sp < nsplit; ++sp) {
+      const float4 v = *reinterpret_cast<const float4 *>(base + sp * split_stride);
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    *reinterpret_cast<float4 *>(Ms + rr * RT + 4 * c4) = acc;
+  }
+  __syncthreads();
+
+  // f = M row solved against L D L^T: forward with L, scale by 1/D, backward with L^T
+  const bool own = tid < nrows;
   float y[RT];
 #pragma unroll
   for (int r = 0; r < RT; ++r) y[r] = 0.f;
-  if (q < Q) {
-    const float4 *mr = reinterpret_cast<const float4 *>(Fs + q * RT);
+  if (own) {
+    const float4 *mr = reinterpret_cast<const float4 *>(Ms + tid * RT);
 #pragma unroll
     for (int r4 = 0; r4 < RT / 4; ++r4) {
       const float4 v = mr[r4];
       y[4 * r4] = v.x; y[4 * r4 + 1] = v.y; y[4 * r4 + 2] = v.z; y[4 * r4 + 3] = v.w;
     }
-  }
 #pragma unroll
-  for (int k = 0; k < RT; ++k) {
-    const float yk = y[k];
-    const float4 *lc = reinterpret_cast<const float4 *>(Lc + k * RT);
+    for (int k = 0; k < RT; ++k) {
+      const float yk = y[k];
+      const float4 *lc = reinterpret_cast<const float4 *>(Lc + k * RT);
 #pragma unroll
-    for (int i4 = (k + 1) / 4; i4 < RT / 4; ++i4) {
-      const float4 l = lc[i4];
-      if (4 * i4 + 0 > k) y[4 * i4 + 0] = fmaf(-l.x, yk, y[4 * i4 + 0]);
-      if (4 * i4 + 1 > k) y[4 * i4 + 1] = fmaf(-l.y, yk, y[4 * i4 + 1]);
-      if (4 * i4 + 2 > k) y[4 * i4 + 2] = fmaf(-l.z, yk, y[4 * i4 + 2]);
-      if (4 * i4 + 3 > k) y[4 * i4 + 3] = fmaf(-l.w, yk, y[4 * i4 + 3]);
+      for (int i4 = (k + 1) / 4; i4 < RT / 4; ++i4) {
+        const float4 l = lc[i4];
+        if (4 * i4 + 0 > k) y[4 * i4 + 0] = fmaf(-l.x, yk, y[4 * i4 + 0]);
+        if (4 * i4 + 1 > k) y[4 * i4 + 1] = fmaf(-l.y, yk, y[4 * i4 + 1]);
+        if (4 * i4 + 2 > k) y[4 * i4 + 2] = fmaf(-l.z, yk, y[4 * i4 + 2]);
+        if (4 * i4 + 3 > k) y[4 * i4 + 3] = fmaf(-l.w, yk, y[4 * i4 + 3]);
+      }
     }
-  }
 #pragma unroll
-  for (int r4 = 0; r4 < RT / 4; ++r4) {
-    const float4 d = reinterpret_cast<const float4 *>(rf)[r4];
-    y[4 * r4] *= d.x; y[4 * r4 + 1] *= d.y; y[4 * r4 + 2] *= d.z; y[4 * r4 + 3] *= d.w;
-  }
+    for (int r4 = 0; r4 < RT / 4; ++r4) {
+      const float4 d = reinterpret_cast<const float4 *>(rf)[r4];
+      y[4 * r4] *= d.x; y[4 * r4 + 1] *= d.y; y[4 * r4 + 2] *= d.z; y[4 * r4 + 3] *= d.w;
+    }
 #pragma unroll
-  for (int k = RT - 1; k > 0; --k) {
-    const float fk = y[k];
-    const float4 *lr = reinterpret_cast<const float4 *>(Lr + k * RT);
+    for (int k = RT - 1; k > 0; --k) {
+      const float fk = y[k];
+      const float4 *lr = reinterpret_cast<const float4 *>(Lr + k * RT);
 #pragma unroll
-    for (int i4 = 0; i4 <= (k - 1) / 4; ++i4) {
-      const float4 l = lr[i4];
-      if (4 * i4 + 0 < k) y[4 * i4 + 0] = fmaf(-l.x, fk, y[4 * i4 + 0]);
-      if (4 * i4 + 1 < k) y[4 * i4 + 1] = fmaf(-l.y, fk, y[4 * i4 + 1]);
-      if (4 * i4 + 2 < k) y[4 * i4 + 2] = fmaf(-l.z, fk, y[4 * i4 + 2]);
-      if (4 * i4 + 3 < k) y[4 * i4 + 3] = fmaf(-l.w, fk, y[4 * i4 + 3]);
+      for (int i4 = 0; i4 <= (k - 1) / 4; ++i4) {
+        const float4 l = lr[i4];
+        if (4 * i4 + 0 < k) y[4 * i4 + 0] = fmaf(-l.x, fk, y[4 * i4 + 0]);
+        if (4 * i4 + 1 < k) y[4 * i4 + 1] = fmaf(-l.y, fk, y[4 * i4 + 1]);
+        if (4 * i4 + 2 < k) y[4 * i4 + 2] = fmaf(-l.z, fk, y[4 * i4 + 2]);
+        if (4 * i4 + 3 < k) y[4 * i4 + 3] = fmaf(-l.w, fk, y[4 * i4 + 3]);
+      }
     }
   }
   if (normalize) {
+    // column sums of squares over this CTA's rows, then over the cluster
     float sq[RT];
 #pragma unroll
     for (int r = 0; r < RT; ++r) sq[r] = y[r] * y[r];
-    block_sum_rows<RT>(sq, red, out);
+    block_sum_rows<RT>(sq, red, part);
+    cluster_barrier();   // every CTA's partial sums are in place
     if (tid < RT) {
-      const float n = sqrtf(out[tid]);
-      red[tid] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
+      float tot = 0.f;
+      for (uint32_t c = 0; c < ncta; ++c) tot += ld_cluster(part + tid, c);
+      const float n = sqrtf(tot);
+      scale[tid] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
     }
-    __syncthreads();
+    cluster_barrier();   // peers are done reading `part`; `scale` visible CTA-wide
 #pragma unroll
-    for (int r = 0; r < RT; ++r) y[r] *= red[r];
+    for (int r = 0; r < RT; ++r) y[r] *= scale[r];
   }
-  if (q < Q) {
+  if (own) {
+    const int q = row0 + tid;
     float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
-    float4 *os = reinterpret_cast<float4 *>(Fs + q * RT);
 #pragma unroll
-    for (int r4 = 0; r4 < RT / 4; ++r4) {
-      const float4 v = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
-      o[r4] = v;
-      os[r4] = v;
+    for (int r4 = 0; r4 < RT / 4; ++r4)
+      o[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
+    if (Ft) {
+#pragma unroll
+      for (int r = 0; r < RT; ++r)
+        Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(y[r]);
+      for (int r = RT; r < NP; ++r) Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(0.f);
     }
   }
-  __syncthreads();
-  if (Ft && q < Q) {
-    for (int r = 0; r < NP; ++r)
-      Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(r < RT ? Fs[q * RT + r] : 0.f);
-  }
-  smem_gram<RT>(Fs, Q, Gout + (int64_t)p * RT * RT);
 }
 
 }  // namespace octen

@@ -523,14 +523,15 @@ int sm_count() {
 
 template <int KIND, class Epi>
 bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
-               const Epi &epi, int *status, cudaStream_t st) {
+               const Epi &epi, int *status, cudaStream_t st, int smem_reserve = 0) {
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
   const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes;
   const size_t stage_bytes = Epi::kRowMajor ? 4 * 32 * 33 * sizeof(float) + 16
                              : Epi::kSeg   ? 4 * 32 * 32 * sizeof(__nv_bfloat16) + 16
                                            : 0;
-  sh.stages = static_cast<int>((220 * 1024 - stage_bytes) / per_stage);
+  const int64_t room = 220 * 1024 - (int64_t)stage_bytes - smem_reserve;
+  sh.stages = room > 0 ? static_cast<int>(room / (int64_t)per_stage) : 0;
   if (sh.stages > 8) sh.stages = 8;
   if (sh.stages < 2) return false;
   const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 5) * 8 + 16 + stage_bytes;
@@ -624,7 +625,7 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT};
   if (g.m1_part && (g.BN != 32 || g.Q % 32 || ks > 1)) return false;
   if (ks > 1 && (g.N > g.BN)) return false;
-  return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st);
+  return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve);
 }
 
 int tc_gemm_splits(int K, int ksplit) {

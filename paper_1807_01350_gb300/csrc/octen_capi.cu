@@ -78,8 +78,12 @@ struct octen_ctx {
   int als_ks = 1;
   __nv_bfloat16 *Xa = nullptr, *Xc = nullptr, *KR = nullptr, *Ctb = nullptr;
   float *Mparts = nullptr;
+  // replica CP-ALS: the factor of each update runs on als_side beside its MTTKRP
+  cudaStream_t als_side = nullptr;
+  cudaEvent_t als_fork = nullptr, als_join = nullptr;
+  float *Lfac = nullptr;
   int *perm = nullptr;
-  double *scales = nullptr;
+  double *scales = nullptr, *align_scratch = nullptr;
   int *dstatus = nullptr;
   double *dfit = nullptr;
 
@@ -143,6 +147,12 @@ struct octen_ctx {
     cudaStreamSynchronize(st);
     if (als_exec) cudaGraphExecDestroy(als_exec);
     if (cap_st) cudaStreamDestroy(cap_st);
+    if (als_side) {
+      cudaStreamSynchronize(als_side);
+      cudaStreamDestroy(als_side);
+    }
+    if (als_fork) cudaEventDestroy(als_fork);
+    if (als_join) cudaEventDestroy(als_join);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
     for (auto &b : owned) cudaFree(b.p);
     DevBuf *extra[] = {&Tbuf, &T2buf, &Wbuf, &X8buf, &xscale, &stage[0], &stage[1], &stage[2],
@@ -441,8 +451,10 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
             x->alloc(x->Bh, P * Q * RT) && x->alloc(x->Ch, P * Q * RT) &&
             x->alloc(x->M, P * Q * RT) && x->alloc(x->H, P * Q * Q * RT) &&
             x->alloc(x->perm, P * c.R) && x->alloc(x->scales, P * 2 * c.R) &&
+            x->alloc(x->align_scratch, align_scratch_doubles(c.P, x->RT)) &&
             x->alloc(x->dstatus, 1) && x->alloc(x->dfit, 2) && x->alloc(x->GA, P * RT * RT) &&
             x->alloc(x->GB, P * RT * RT) && x->alloc(x->GC, P * RT * RT) &&
+            x->alloc(x->Lfac, P * (size_t)als_factor_floats(x->RT)) &&
             x->alloc(x->splitk, octen_ctx::kSplitkFloats);
   if (ok && x->use_tc && als_tc_eligible(c.Q)) {
     const int mt = (c.Q + 127) / 128;
@@ -462,6 +474,11 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     if (vt) x->owned.push_back({vt, 0});
     x->Ut_rep = ut;
     x->Vt = vt;
+  }
+  if (ok) {
+    ok = cudaStreamCreateWithFlags(&x->als_side, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x->als_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x->als_join, cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -597,6 +614,7 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   ab.M = x->M; ab.H = x->H; ab.status = x->dstatus;
   ab.use_tc = x->als_tc; ab.Xa = x->Xa; ab.Xc = x->Xc; ab.KR = x->KR; ab.Ct = x->Ctb;
   ab.Mparts = x->Mparts; ab.ksplit = x->als_ks;
+  ab.side = x->als_side; ab.ev_fork = x->als_fork; ab.ev_join = x->als_join; ab.L = x->Lfac;
   Marker mk;
   if (x->timing) { mk.fn = &octen_ctx::mark_cb; mk.arg = x; }
   bool replayed = false;
@@ -623,7 +641,7 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   // 3. anchor match against u^T A_prev, v^T B_prev
   x->mark(kStAlign, 1);
   align_replicas(x->At, x->Bt, x->Ct, x->PA, x->PB, c.P, c.Q, c.S, c.R, RT, x->Ah, x->Bh,
-                 x->Ch, x->perm, x->scales, x->st);
+                 x->Ch, x->perm, x->scales, x->align_scratch, x->st);
   x->mark(kStAlign, 0);
   // 4. lift A and B, solve the new rows of C, update G_p
   x->mark(kStLift, 1);

@@ -106,6 +106,9 @@ struct TcStoreArgs {
   const float *m1_B = nullptr;
   float *m1_part = nullptr;
   int Q = 0, RT = 0;
+  // shared memory (bytes) to leave free on every SM for a kernel that runs
+  // beside this GEMM (fewer pipeline stages)
+  int smem_reserve = 0;
 };
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st);
 int tc_gemm_splits(int K, int ksplit);   // the split count tc_gemm_store will use
@@ -145,7 +148,13 @@ struct AlsBuffers {
   __nv_bfloat16 *Ct = nullptr;                  // P x kAlsNP x Q
   float *Mparts = nullptr;                      // ksplit x P x Q x RT
   int ksplit = 1;
+  // the factor of every update runs on `side` beside the update's MTTKRP:
+  // fork after the previous update, join before the solve
+  cudaStream_t side = nullptr;                  // non-blocking
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  float *L = nullptr;                           // P x als_factor_floats(RT)
 };
+int als_factor_floats(int RT);
 // Returns false if a tensor-core launch was refused (the caller then reruns
 // the SIMT path).
 bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
@@ -161,7 +170,10 @@ void warm_start(const float *PF, int P, int Q, int S, int R, int RT, float *F, f
 // Anchor match (FP64).  ref rows = PA/PB rows [0, S).
 void align_replicas(const float *At, const float *Bt, const float *Ct, const float *PA,
                     const float *PB, int P, int Q, int S, int R, int RT, float *Ah,
-                    float *Bh, float *Ch, int *perm, double *scales, cudaStream_t st);
+                    float *Bh, float *Ch, int *perm, double *scales, double *scratch,
+                    cudaStream_t st);
+// doubles of scratch align_replicas needs
+size_t align_scratch_doubles(int P, int RT);
 
 // e (Qd x R) for the lift: shared rows summed (sum_mode=1) or averaged.
 void lift_rhs(const float *Fh, const float *PF, int P, int Q, int S, int R, int RT, int Qd,
