@@ -125,14 +125,17 @@ def stream_inputs(wl, prec, seed, nbatch, device):
                 C0=f32(C0))
 
 
-def stage_work(wl, prec):
-    """Algorithmic work per launch of each timed stage: (flops, bytes)."""
+def stage_work(wl, prec, layouts=False):
+    """Algorithmic work per launch of each timed stage: (flops, bytes).  With
+    `layouts` the mode-3 pass also writes the two bf16 copies of X_p that the
+    tensor-core CP-ALS reads."""
     t, I, J, P, Q, R, Qd = wl.batch, wl.I, wl.J, wl.P, wl.Q, wl.R, wl.Qd
     xb = 4 if prec == "fp32" else (1 if prec == "fp8" else 2)
     return {
         "mode2": (2.0 * t * I * J * Qd, t * I * J * xb + Qd * J * xb + t * I * P * Q * (4 if prec == "fp32" else 2)),
         "mode1": (2.0 * t * P * Q * Q * I, t * P * Q * I * (4 if prec == "fp32" else 2) + P * Q * I * (4 if prec == "fp32" else 2)),
-        "mode3": (2.0 * t * P * Q ** 3, 2.0 * 4 * P * Q ** 3 + 4.0 * t * P * Q * Q),
+        "mode3": (2.0 * t * P * Q ** 3, 2.0 * 4 * P * Q ** 3 + 4.0 * t * P * Q * Q
+                  + (2.0 * 2 * P * Q ** 3 if layouts else 0.0)),
         "als_gemm": (2.0 * P * Q ** 3 * R, 4.0 * P * Q ** 3),
     }
 
@@ -140,17 +143,17 @@ def stage_work(wl, prec):
 def als_gemm_tc_bytes(wl):
     """Algorithmic bytes per tensor-core ALS GEMM launch, averaged over an
     append: the M3 GEMM reads the bf16 copy Xc and the Khatri-Rao operand, the
-    Tc GEMM reads the bf16 copy Xa and writes Tc (fp32, rank padded to RT)."""
+    Tc GEMM reads the bf16 copy Xa and writes Tc (bf16, rank padded to RT)."""
     P, Q, R, it = wl.P, wl.Q, wl.R, wl.als_iters
     RT = 8 if R <= 8 else (16 if R <= 16 else 32)
     NP = 32
     m3 = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q * Q
-    tc = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q + 4.0 * P * Q * Q * RT
+    tc = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q + 2.0 * P * Q * Q * RT
     return ((it + 1) * m3 + it * tc) / (2 * it + 1)
 
 
 def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic, tc_stages=()):
-    flops, nbytes = stage_work(wl, prec)[stage]
+    flops, nbytes = stage_work(wl, prec, layouts="als_gemm" in tc_stages)[stage]
     sec = ms_per_launch / 1e3
     if stage == "mode3":
         bound, peak, unit, achieved = "hbm", pk["hbm"], "GB/s", nbytes / sec / 1e9

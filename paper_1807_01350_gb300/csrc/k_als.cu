@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256)
     const float x = ac[a];
     const float4 b0 = *reinterpret_cast<const float4 *>(bc + b);
     const float4 b1 = *reinterpret_cast<const float4 *>(bc + b + 4);
-    __nv_bfloat162 h[4] = {__floats2bfloat162_rn(x * b0.x, x * b0.y),
+    __align__(16) __nv_bfloat162 h[4] = {__floats2bfloat162_rn(x * b0.x, x * b0.y),
                            __floats2bfloat162_rn(x * b0.z, x * b0.w),
                            __floats2bfloat162_rn(x * b1.x, x * b1.y),
                            __floats2bfloat162_rn(x * b1.z, x * b1.w)};
@@ -231,35 +231,47 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// M1[p][a][r] = sum_b Tc[p][(a,b)][r] B[p][b][r]     thread (a, r)
-template <int RT>
-__global__ void tc_m1_kernel(const float *__restrict__ Tc, const float *__restrict__ Bf, int Q,
-                             float *__restrict__ M) {
+// M1[p][a][r] = sum_b Tc[p][(a,b)][r] B[p][b][r] and M2[p][b][r] = sum_a
+// Tc[p][(a,b)][r] A[p][a][r], Tc in bf16.  A CTA of 256 threads owns 32 output
+// column pairs (32 / (RT / 2) rows of RT / 2 pairs); thread (pair j < 32,
+// slice s < 8) sums every 8th term of the reduction starting at s, and the 8
+// slice sums are added in shared memory in a fixed order.
+//   kind 1 (M1): output row a, reduction over b: term b at Tc[(a, b)]
+//   kind 2 (M2): output row b, reduction over a: term a at Tc[(a, b)]
+template <int RT, int KIND>
+__global__ void __launch_bounds__(256)
+    tc_mred_kernel(const __nv_bfloat16 *__restrict__ Tc, const float *__restrict__ Fac, int Q,
+                   float *__restrict__ M) {
+  constexpr int PAIRS = RT / 2;          // column pairs per output row
+  constexpr int ROWS = 32 / PAIRS;       // output rows per CTA (32 pairs per CTA)
+  __shared__ float2 part[8][32];
   const int p = blockIdx.y;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Q * RT) return;
-  const int a = e / RT, r = e % RT;
-  const float *t = Tc + ((int64_t)p * Q + a) * Q * RT + r;
-  const float *bf = Bf + (int64_t)p * Q * RT + r;
-  float acc = 0.f;
-  for (int b = 0; b < Q; ++b) acc = fmaf(__ldg(t + (int64_t)b * RT), __ldg(bf + b * RT), acc);
-  M[(int64_t)p * Q * RT + e] = acc;
-}
-
-// M2[p][b][r] = sum_a Tc[p][(a,b)][r] A[p][a][r]     thread (b, r)
-template <int RT>
-__global__ void tc_m2_kernel(const float *__restrict__ Tc, const float *__restrict__ Af, int Q,
-                             float *__restrict__ M) {
-  const int p = blockIdx.y;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Q * RT) return;
-  const int r = e % RT;
-  const float *t = Tc + (int64_t)p * Q * Q * RT + e;
-  const float *af = Af + (int64_t)p * Q * RT + r;
-  float acc = 0.f;
-  for (int a = 0; a < Q; ++a)
-    acc = fmaf(__ldg(t + (int64_t)a * Q * RT), __ldg(af + a * RT), acc);
-  M[(int64_t)p * Q * RT + e] = acc;
+  const int j = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int row = blockIdx.x * ROWS + j / PAIRS, r = 2 * (j % PAIRS);
+  float ax = 0.f, ay = 0.f;
+  if (row < Q) {
+    const __nv_bfloat16 *t = Tc + (int64_t)p * Q * Q * RT + r;
+    const float *f = Fac + (int64_t)p * Q * RT + r;
+#pragma unroll 4
+    for (int k = sl; k < Q; k += 8) {
+      const int64_t ab = KIND == 1 ? (int64_t)row * Q + k : (int64_t)k * Q + row;
+      const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(t + ab * RT));
+      const float2 w = *reinterpret_cast<const float2 *>(f + k * RT);
+      ax = fmaf(v.x, w.x, ax);
+      ay = fmaf(v.y, w.y, ay);
+    }
+  }
+  part[sl][j] = make_float2(ax, ay);
+  __syncthreads();
+  if (sl == 0 && row < Q) {
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sx += part[q][j].x;
+      sy += part[q][j].y;
+    }
+    *reinterpret_cast<float2 *>(M + ((int64_t)p * Q + row) * RT + r) = make_float2(sx, sy);
+  }
 }
 
 static int block_for(int Q) { return ((Q + 31) / 32) * 32; }
@@ -365,11 +377,13 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
                        cudaStream_t st, const Marker &mk) {
   const int NP = kAlsNP;
   const int64_t QQ = (int64_t)Q * Q;
-  mk(kStAlsAux, 1);
-  bf16_layouts_kernel<<<dim3((Q + 31) / 32, (unsigned)((QQ + 31) / 32), P), dim3(32, 8), 0, st>>>(
-      Y, Q, b.Xa, b.Xc);
-  count_launch();
-  mk(kStAlsAux, 0);
+  if (!b.layouts_ready) {
+    mk(kStAlsAux, 1);
+    bf16_layouts_kernel<<<dim3((Q + 31) / 32, (unsigned)((QQ + 31) / 32), P), dim3(32, 8), 0,
+                          st>>>(Y, Q, b.Xa, b.Xc);
+    count_launch();
+    mk(kStAlsAux, 0);
+  }
   // M3 = Xc . KR^T (split over K = (a, b)), Tc = Xa . C
   TcStoreArgs m3{};
   m3.A = b.Xc; m3.a_inner = QQ; m3.a_rows = (int64_t)P * Q; m3.a_rows_per_z = Q;
@@ -380,7 +394,9 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   tc.A = b.Xa; tc.a_inner = Q; tc.a_rows = (int64_t)P * QQ; tc.a_rows_per_z = (int)QQ;
   tc.B = b.Ct; tc.b_inner = Q; tc.b_rows = (int64_t)P * NP; tc.b_rows_per_z = NP;
   tc.M = (int)QQ; tc.N = RT; tc.K = Q; tc.BN = NP; tc.batch = P; tc.ksplit = 1;
-  tc.D = b.H; tc.s_split = 0; tc.s_z = QQ * RT; tc.s_m = RT;
+  // Tc is kept in bf16 (half the bytes; it fits the L2 for the M2 pass)
+  __nv_bfloat16 *Th = reinterpret_cast<__nv_bfloat16 *>(b.H);
+  tc.D = nullptr; tc.Dh = Th; tc.s_split = 0; tc.s_z = QQ * RT; tc.s_m = RT;
   // M1 fused into the Tc GEMM: per-warp partials over 32 consecutive b
   const bool fuse_m1 = Q % 32 == 0;
   if (fuse_m1) { tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; }
@@ -388,7 +404,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   m3.smem_reserve = tc.smem_reserve = 56 * 1024;
   const int ks = tc_gemm_splits(m3.K, b.ksplit);
   const dim3 gKR(NP, P);
-  const dim3 gM((Q * RT + 255) / 256, P);
+  const dim3 gM((Q + 32 / (RT / 2) - 1) / (32 / (RT / 2)), P);   // 32 output pairs per CTA
   bool ok = true;
   auto c_update = [&]() {
     factor_async<RT>(b.Bf, b.GB, b.GA, P, Q, R, b, st);
@@ -415,7 +431,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
       mk(kStAlsSolve, 0);
     } else {
       mk(kStAlsAux, 1);
-      tc_m1_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Bf, Q, b.M);
+      tc_mred_kernel<RT, 1><<<gM, 256, 0, st>>>(Th, b.Bf, Q, b.M);
       count_launch();
       mk(kStAlsAux, 0);
       mk(kStAlsSolve, 1);
@@ -424,7 +440,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     }
     factor_async<RT>(b.Af, b.GA, b.GC, P, Q, R, b, st);
     mk(kStAlsAux, 1);
-    tc_m2_kernel<RT><<<gM, 256, 0, st>>>(b.H, b.Af, Q, b.M);
+    tc_mred_kernel<RT, 2><<<gM, 256, 0, st>>>(Th, b.Af, Q, b.M);
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);

@@ -162,18 +162,24 @@ __global__ void __launch_bounds__(256)
 // replica; per block it stages T2 transposed to [row][k] and every thread owns
 // 4 consecutive c (one float4) of kRG rows: the kRG loads of Y are issued
 // together, the t-term sums taken from shared memory, then the rows stored.
+// With Xa / Xc given it also writes the bf16 copies of the updated X_p that
+// the tensor-core CP-ALS reads, Xa[p][(a,b)][c] and Xc[p][c][(a,b)] (the
+// latter through a [c][row] block in shared memory, 16-byte stores).
 constexpr int kRG = 8;
 
 __global__ void __launch_bounds__(256)
     mode3_stream_kernel(const float *__restrict__ T2, const float *__restrict__ W,
-                        float *__restrict__ Y, int t, int Q, int S, int Qd) {
+                        float *__restrict__ Y, int t, int Q, int S, int Qd,
+                        __nv_bfloat16 *__restrict__ Xa, __nv_bfloat16 *__restrict__ Xc) {
   extern __shared__ __align__(16) float sm3[];
   const int tp = (t + 3) & ~3;                 // padded k extent
   const int ncg = Q / 4;                       // float4 column groups
   const int lanes = blockDim.x / ncg;          // rows in flight per pass
   const int rows_blk = lanes * kRG;
+  const int xp = rows_blk + 1;                 // pitch of the [c][row] bf16 block
   float *Ws = sm3;                             // [tp][Q]
   float *Ts = sm3 + (size_t)tp * Q;            // [rows_blk][tp]
+  __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(Ts + (size_t)rows_blk * tp);   // [Q][xp]
   const int p = blockIdx.y;
   const int64_t QQ = (int64_t)Q * Q;
   for (int e = threadIdx.x; e < tp * Q; e += blockDim.x) {
@@ -194,49 +200,81 @@ __global__ void __launch_bounds__(256)
           (k < t && row0 + r < QQ) ? T2[((int64_t)p * t + k) * QQ + row0 + r] : 0.f;
     }
     __syncthreads();
-    if (!active) continue;
-    float4 y[kRG], acc[kRG];
-#pragma unroll
-    for (int i = 0; i < kRG; ++i) {
-      const int64_t row = row0 + rl + (int64_t)lanes * i;
-      y[i] = row < QQ ? reinterpret_cast<const float4 *>(Yp + row * Q)[cg]
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
-      acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int k = 0; k < tp; k += 4) {
-      const float4 w0 = reinterpret_cast<const float4 *>(Ws + (k + 0) * Q)[cg];
-      const float4 w1 = reinterpret_cast<const float4 *>(Ws + (k + 1) * Q)[cg];
-      const float4 w2 = reinterpret_cast<const float4 *>(Ws + (k + 2) * Q)[cg];
-      const float4 w3 = reinterpret_cast<const float4 *>(Ws + (k + 3) * Q)[cg];
+    if (active) {
+      float4 y[kRG], acc[kRG];
 #pragma unroll
       for (int i = 0; i < kRG; ++i) {
-        const float4 x = *reinterpret_cast<const float4 *>(Ts + (rl + lanes * i) * tp + k);
-        acc[i].x = fmaf(x.x, w0.x, fmaf(x.y, w1.x, fmaf(x.z, w2.x, fmaf(x.w, w3.x, acc[i].x))));
-        acc[i].y = fmaf(x.x, w0.y, fmaf(x.y, w1.y, fmaf(x.z, w2.y, fmaf(x.w, w3.y, acc[i].y))));
-        acc[i].z = fmaf(x.x, w0.z, fmaf(x.y, w1.z, fmaf(x.z, w2.z, fmaf(x.w, w3.z, acc[i].z))));
-        acc[i].w = fmaf(x.x, w0.w, fmaf(x.y, w1.w, fmaf(x.z, w2.w, fmaf(x.w, w3.w, acc[i].w))));
+        const int64_t row = row0 + rl + (int64_t)lanes * i;
+        y[i] = row < QQ ? reinterpret_cast<const float4 *>(Yp + row * Q)[cg]
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      for (int k = 0; k < tp; k += 4) {
+        const float4 w0 = reinterpret_cast<const float4 *>(Ws + (k + 0) * Q)[cg];
+        const float4 w1 = reinterpret_cast<const float4 *>(Ws + (k + 1) * Q)[cg];
+        const float4 w2 = reinterpret_cast<const float4 *>(Ws + (k + 2) * Q)[cg];
+        const float4 w3 = reinterpret_cast<const float4 *>(Ws + (k + 3) * Q)[cg];
+#pragma unroll
+        for (int i = 0; i < kRG; ++i) {
+          const float4 x = *reinterpret_cast<const float4 *>(Ts + (rl + lanes * i) * tp + k);
+          acc[i].x = fmaf(x.x, w0.x, fmaf(x.y, w1.x, fmaf(x.z, w2.x, fmaf(x.w, w3.x, acc[i].x))));
+          acc[i].y = fmaf(x.x, w0.y, fmaf(x.y, w1.y, fmaf(x.z, w2.y, fmaf(x.w, w3.y, acc[i].y))));
+          acc[i].z = fmaf(x.x, w0.z, fmaf(x.y, w1.z, fmaf(x.z, w2.z, fmaf(x.w, w3.z, acc[i].z))));
+          acc[i].w = fmaf(x.x, w0.w, fmaf(x.y, w1.w, fmaf(x.z, w2.w, fmaf(x.w, w3.w, acc[i].w))));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kRG; ++i) {
+        const int64_t row = row0 + rl + (int64_t)lanes * i;
+        const float4 v = make_float4(y[i].x + acc[i].x, y[i].y + acc[i].y, y[i].z + acc[i].z,
+                                     y[i].w + acc[i].w);
+        if (row < QQ) reinterpret_cast<float4 *>(Yp + row * Q)[cg] = v;
+        if (Xa) {
+          __align__(8) const __nv_bfloat16 h[4] = {
+              __float2bfloat16_rn(v.x), __float2bfloat16_rn(v.y), __float2bfloat16_rn(v.z),
+              __float2bfloat16_rn(v.w)};
+          if (row < QQ)
+            *reinterpret_cast<uint2 *>(Xa + ((int64_t)p * QQ + row) * Q + 4 * cg) =
+                *reinterpret_cast<const uint2 *>(h);
+          const int rr = rl + lanes * i;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) Xs[(4 * cg + j) * xp + rr] = h[j];
+        }
       }
     }
+    if (Xc) {
+      // the block's rows of every c: 8 rows (16 bytes) per store
+      __syncthreads();
+      const int nseg = rows_blk / 8;
+      for (int e = threadIdx.x; e < Q * nseg; e += blockDim.x) {
+        const int c = e / nseg, sg = e - (e / nseg) * nseg;
+        const int64_t r0 = row0 + 8 * sg;
+        __nv_bfloat16 *dst = Xc + ((int64_t)p * Q + c) * QQ + r0;
+        const __nv_bfloat16 *src = Xs + c * xp + 8 * sg;
+        if (r0 + 8 <= QQ) {
+          __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
-    for (int i = 0; i < kRG; ++i) {
-      const int64_t row = row0 + rl + (int64_t)lanes * i;
-      if (row < QQ)
-        reinterpret_cast<float4 *>(Yp + row * Q)[cg] =
-            make_float4(y[i].x + acc[i].x, y[i].y + acc[i].y, y[i].z + acc[i].z,
-                        y[i].w + acc[i].w);
+          for (int j = 0; j < 8; ++j) h[j] = src[j];
+          *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
+        } else {
+          for (int j = 0; j < 8 && r0 + j < QQ; ++j) dst[j] = src[j];
+        }
+      }
     }
   }
 }
 
-void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
-                      int S, int Qd, cudaStream_t st) {
+bool mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
+                      int S, int Qd, cudaStream_t st, __nv_bfloat16 *Xa, __nv_bfloat16 *Xc) {
   const int64_t QQ = (int64_t)Q * Q;
   if (Q % 4 == 0 && Q <= 1024) {
     const int tp = (int)((t + 3) & ~int64_t(3));
     const int ncg = Q / 4;
     const int lanes = 256 / ncg;
     const int rows_blk = lanes * kRG;
-    const size_t smem = ((size_t)tp * Q + (size_t)rows_blk * tp) * sizeof(float);
+    const bool layouts = Xa != nullptr && Xc != nullptr;
+    const size_t smem = ((size_t)tp * Q + (size_t)rows_blk * tp) * sizeof(float) +
+                        (layouts ? (size_t)Q * (rows_blk + 1) * sizeof(__nv_bfloat16) : 0);
     if (smem <= 200 * 1024) {
       cudaFuncSetAttribute(mode3_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            200 * 1024);
@@ -249,9 +287,10 @@ void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int 
       int64_t gx = ((int64_t)sms * per_sm + P - 1) / P;   // one wave over all replicas
       if (gx > nblk) gx = nblk;
       if (gx < 1) gx = 1;
-      mode3_stream_kernel<<<dim3((unsigned)gx, P), 256, smem, st>>>(T2, W, Y, (int)t, Q, S, Qd);
+      mode3_stream_kernel<<<dim3((unsigned)gx, P), 256, smem, st>>>(
+          T2, W, Y, (int)t, Q, S, Qd, layouts ? Xa : nullptr, layouts ? Xc : nullptr);
       count_launch();
-      return;
+      return layouts;
     }
   }
   const size_t smem = ((size_t)t * Q + (size_t)t * kRows) * sizeof(float);
@@ -259,6 +298,7 @@ void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int 
   dim3 grid((unsigned)((QQ + kRows - 1) / kRows), P);
   mode3_kernel<<<grid, 256, smem, st>>>(T2, W, Y, (int)t, Q, S, Qd);
   count_launch();
+  return false;
 }
 
 }  // namespace octen

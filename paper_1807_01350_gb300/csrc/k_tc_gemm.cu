@@ -158,7 +158,8 @@ struct TcShape {
   int ksplit;           // > 1: blockIdx.x is the K split (a single N tile)
 };
 
-// Plain fp32 store: D[split * s_split + z * s_z + m * s_m + n] (split-K partials).
+// Plain store: D[split * s_split + z * s_z + m * s_m + n] (split-K partials), in
+// fp32, or rounded to bf16 at the same offsets of Dh when Dh is given.
 struct TcStoreEpi {
   static constexpr bool kRowMajor = true;   // rows are contiguous in n
   static constexpr bool kSeg = false;
@@ -170,8 +171,11 @@ struct TcStoreEpi {
   const float *Bfac;
   float *part;
   int Q, RT;
-  __device__ __forceinline__ float *row(int z, int split, int m) const {
-    return D + (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m;
+  __nv_bfloat16 *Dh;
+  __device__ __forceinline__ void store(int z, int split, int m, int n, float v) const {
+    const int64_t o = (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n;
+    if (Dh) Dh[o] = __float2bfloat16_rn(v);
+    else D[o] = v;
   }
 };
 
@@ -239,9 +243,9 @@ struct Mode1TcEpi {
   const float *Bfac = nullptr;   // no fused reduction
   float *part = nullptr;
   int RT = 0;
-  __device__ __forceinline__ float *row(int z, int, int a) const {
+  __device__ __forceinline__ void store(int z, int, int a, int b, float v) const {
     const int k = z / P, p = z - k * P;
-    return T2 + (((int64_t)p * t + k) * Q + a) * Q;
+    T2[(((int64_t)p * t + k) * Q + a) * Q + b] = v;
   }
 };
 
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(192, 1)
           const int n = n0 + c0 + lane;
           for (int i = 0; i < 32; ++i) {
             const int mi = m0 + quad * 32 + i;
-            if (mi < sh.M && n < sh.N) epi.row(z, split, mi)[n] = stg[i * 33 + lane];
+            if (mi < sh.M && n < sh.N) epi.store(z, split, mi, n, stg[i * 33 + lane]);
           }
           if (epi.part != nullptr) {
             const int mb = m0 + quad * 32;   // 32 rows of one a when 32 divides Q
@@ -622,7 +626,7 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   const int per = (nk + ks - 1) / ks;
   ks = (nk + per - 1) / per;            // every split gets at least one K block
   sh.ksplit = ks;
-  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT};
+  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT, g.Dh};
   if (g.m1_part && (g.BN != 32 || g.Q % 32 || ks > 1)) return false;
   if (ks > 1 && (g.N > g.BN)) return false;
   return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve);

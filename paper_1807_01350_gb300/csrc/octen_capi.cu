@@ -82,6 +82,7 @@ struct octen_ctx {
   cudaStream_t als_side = nullptr;
   cudaEvent_t als_fork = nullptr, als_join = nullptr;
   float *Lfac = nullptr;
+  bool layouts_ready = false;   // Xa / Xc hold bf16(Y) from the last mode-3 pass
   int *perm = nullptr;
   double *scales = nullptr, *align_scratch = nullptr;
   int *dstatus = nullptr;
@@ -96,6 +97,7 @@ struct octen_ctx {
   cudaStream_t cap_st = nullptr;
   cudaGraphExec_t als_exec = nullptr;
   int64_t als_graph_launches = 0, als_graph_tc = 0;
+  bool als_graph_layouts = false;   // the graph was recorded with Xa / Xc given
 
   // per-batch scratch, grown on demand
   DevBuf Tbuf, T2buf, Wbuf, X8buf, xscale, stage[4], fitpart;
@@ -269,9 +271,11 @@ void set_types(octen_ctx *x) {
 
 constexpr int64_t kChunk = 64;  // slices per compression pass
 
-// Z_p (+)= compression of t slices (t <= kChunk) into Yacc.
+// Z_p (+)= compression of t slices (t <= kChunk) into Yacc.  With `layouts`
+// the mode-3 pass may also leave the bf16 copies of Yacc for the tensor-core
+// CP-ALS in x->Xa / x->Xc (x->layouts_ready says whether it did).
 octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float *Wd,
-                            float *Yacc) {
+                            float *Yacc, bool layouts = false) {
   const octen_config &c = x->cfg;
   const size_t tb = (size_t)t * c.P * c.Q * c.I * elem_size(x->tmid);
   if (!x->grow(x->Tbuf, tb)) return x->fail(OCTEN_ENOMEM, "scratch T (%zu bytes)", tb);
@@ -308,7 +312,10 @@ octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float
   }
   x->mark(kStMode1, 0);
   x->mark(kStMode3, 1);
-  mode3_accumulate(static_cast<float *>(x->T2buf.p), Wd, Yacc, t, c.P, c.Q, c.S, x->Qd, x->st);
+  const bool want = layouts && x->als_tc;
+  x->layouts_ready =
+      mode3_accumulate(static_cast<float *>(x->T2buf.p), Wd, Yacc, t, c.P, c.Q, c.S, x->Qd, x->st,
+                       want ? x->Xa : nullptr, want ? x->Xc : nullptr);
   x->mark(kStMode3, 0);
   return OCTEN_OK;
 }
@@ -578,6 +585,7 @@ void capture_als(octen_ctx *x, AlsBuffers ab) {
   if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&x->als_exec, g, 0) == cudaSuccess) {
     x->als_graph_launches = dl;
     x->als_graph_tc = dt;
+    x->als_graph_layouts = ab.layouts_ready;
   } else {
     x->als_exec = nullptr;
   }
@@ -600,7 +608,7 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   const float *Wd = static_cast<const float *>(x->stage_in(W_new, (size_t)t * Qd * 4, 1));
   if (!Xd || !Wd) return x->fail(OCTEN_ENOMEM, "staging the batch");
   // 1. compress the batch and update the summaries
-  octen_status s = compress_chunk(x, Xd, t, Wd, x->Y);
+  octen_status s = compress_chunk(x, Xd, t, Wd, x->Y, true);
   if (s != OCTEN_OK) return s;
   // 2. CP of every summary, warm-started from the projected previous factors
   x->mark(kStWarm, 1);
@@ -615,12 +623,13 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   ab.use_tc = x->als_tc; ab.Xa = x->Xa; ab.Xc = x->Xc; ab.KR = x->KR; ab.Ct = x->Ctb;
   ab.Mparts = x->Mparts; ab.ksplit = x->als_ks;
   ab.side = x->als_side; ab.ev_fork = x->als_fork; ab.ev_join = x->als_join; ab.L = x->Lfac;
+  ab.layouts_ready = x->layouts_ready;
   Marker mk;
   if (x->timing) { mk.fn = &octen_ctx::mark_cb; mk.arg = x; }
   bool replayed = false;
   if (!x->timing && x->use_graph) {
     if (!x->als_exec && !x->als_graph_tried) capture_als(x, ab);
-    if (x->als_exec) {
+    if (x->als_exec && x->als_graph_layouts == ab.layouts_ready) {
       if (cudaGraphLaunch(x->als_exec, x->st) == cudaSuccess) {
         add_launches(x->als_graph_launches, x->als_graph_tc);
         replayed = true;

@@ -101,6 +101,7 @@ struct TcStoreArgs {
   const void *B; int64_t b_inner, b_rows; int b_rows_per_z;
   int M, N, K, BN, batch, ksplit;
   float *D; int64_t s_split, s_z, s_m;
+  __nv_bfloat16 *Dh = nullptr;   // if set: the output rounded to bf16 here instead of D
   // optional fused reduction for rows m = a * Q + b (needs BN == 32, Q % 32 == 0):
   // m1_part[z][m / 32][n] = sum over the 32 rows of D(m, n) * m1_B[z][b][n]
   const float *m1_B = nullptr;
@@ -115,8 +116,11 @@ int tc_gemm_splits(int K, int ksplit);   // the split count tc_gemm_store will u
 
 // Mode-3 contraction and summary update: Y[p][a][b][c] +=
 //   sum_k T2[p][k][a][b] * W_all[k][col_p(c)].
-void mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
-                      int S, int Qd, cudaStream_t st);
+// With Xa and Xc given it may also write the bf16 layouts of the updated Y
+// that the tensor-core CP-ALS reads (returns true if it did).
+bool mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
+                      int S, int Qd, cudaStream_t st, __nv_bfloat16 *Xa = nullptr,
+                      __nv_bfloat16 *Xc = nullptr);
 
 // Layout / precision conversions of the projections.
 void make_replica_transpose(const float *M_all, int64_t rows, int P, int Q, int S, int Qd,
@@ -139,7 +143,8 @@ struct AlsBuffers {
   float *Af, *Bf, *Cf;   // current factors, P x Q x RT
   float *GA, *GB, *GC;   // their Grams, P x RT x RT
   float *M;              // MTTKRP result, P x Q x RT
-  float *H;              // P x Q x Q x RT: SIMT pass-1 product or the Tc GEMM output
+  float *H;              // P x Q x Q x RT: SIMT pass-1 product (fp32), or the Tc GEMM
+                         // output (bf16, first half of the buffer)
   int *status;
   // tensor-core path (bf16 / e4m3 modes, Q % 8 == 0)
   bool use_tc = false;
@@ -148,6 +153,7 @@ struct AlsBuffers {
   __nv_bfloat16 *Ct = nullptr;                  // P x kAlsNP x Q
   float *Mparts = nullptr;                      // ksplit x P x Q x RT
   int ksplit = 1;
+  bool layouts_ready = false;                   // Xa, Xc already hold bf16(X_p)
   // the factor of every update runs on `side` beside the update's MTTKRP:
   // fork after the previous update, join before the solve
   cudaStream_t side = nullptr;                  // non-blocking
