@@ -402,6 +402,9 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   if (fuse_m1) { tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; }
   // the factor kernel of each update runs beside these GEMMs: leave it room
   m3.smem_reserve = tc.smem_reserve = 56 * 1024;
+  // the bf16 copies of X_p stream through once per pass (evict-first), so Tc
+  // stays in the L2 for the M2 pass
+  m3.a_stream = tc.a_stream = true;
   const int ks = tc_gemm_splits(m3.K, b.ksplit);
   const dim3 gKR(NP, P);
   const dim3 gM((Q + 32 / (RT / 2) - 1) / (32 / (RT / 2)), P);   // 32 output pairs per CTA

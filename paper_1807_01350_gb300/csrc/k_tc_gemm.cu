@@ -70,6 +70,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+// Same load with an L2 cache policy (from createpolicy) attached.
+__device__ __forceinline__ void tma_load_2d_policy(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                                   int x, int y, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// L2 policy that evicts the lines it brings in first (operands read once).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *holder, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                    smem_u32(holder)),
@@ -156,6 +173,7 @@ struct TcShape {
   int zdiv;             // batch index z -> rows (z / zdiv) * hi + (z % zdiv) * lo
   int a_hi, a_lo, b_hi, b_lo;
   int ksplit;           // > 1: blockIdx.x is the K split (a single N tile)
+  int a_stream;         // A is read once: load it with an L2 evict-first policy
 };
 
 // Plain store: D[split * s_split + z * s_z + m * s_m + n] (split-K partials), in
@@ -326,6 +344,7 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0 && lane == 0) {
     // TMA producer
+    const uint64_t a_policy = sh.a_stream ? policy_evict_first() : 0;
     uint32_t it = 0;
     bool aborted = false;
     for (int tile = item0; tile < total && !aborted; tile += nitems) {
@@ -343,7 +362,11 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         mbar_expect_tx(&full[s], a_bytes + b_bytes);
-        tma_load_2d(sA + s * a_bytes, &tmA, &full[s], (kb0 + kb) * kElemsPerRow, a_row);
+        if (sh.a_stream)
+          tma_load_2d_policy(sA + s * a_bytes, &tmA, &full[s], (kb0 + kb) * kElemsPerRow, a_row,
+                             a_policy);
+        else
+          tma_load_2d(sA + s * a_bytes, &tmA, &full[s], (kb0 + kb) * kElemsPerRow, a_row);
         tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb0 + kb) * kElemsPerRow, b_row);
       }
     }
@@ -586,6 +609,7 @@ bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st) {
   sh.ksplit = 1;
   sh.M = static_cast<int>(M); sh.N = a.Qd; sh.K = static_cast<int>(a.J); sh.BN = BN;
   sh.zdiv = 1; sh.a_hi = 0; sh.a_lo = 0; sh.b_hi = 0; sh.b_lo = 0;
+  sh.a_stream = 1;   // the slices are read once
   Mode2TcEpi epi{static_cast<__nv_bfloat16 *>(a.T), a.slice_scale, a.I, a.P, a.Q, a.S,
                  a.I % 8 == 0};
   return fp8 ? launch_tc<1>(ma, mb, sh, 1, epi, status, st)
@@ -621,6 +645,7 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   TcShape sh{};
   sh.M = g.M; sh.N = g.N; sh.K = g.K; sh.BN = g.BN;
   sh.zdiv = 1; sh.a_hi = g.a_rows_per_z; sh.a_lo = 0; sh.b_hi = g.b_rows_per_z; sh.b_lo = 0;
+  sh.a_stream = g.a_stream ? 1 : 0;
   const int nk = (g.K + 63) / 64;
   int ks = g.ksplit < 1 ? 1 : (g.ksplit > nk ? nk : g.ksplit);
   const int per = (nk + ks - 1) / ks;

@@ -110,6 +110,9 @@ struct TcStoreArgs {
   // shared memory (bytes) to leave free on every SM for a kernel that runs
   // beside this GEMM (fewer pipeline stages)
   int smem_reserve = 0;
+  // A is read once: its TMA loads carry an L2 evict-first policy so that it
+  // does not push the reused operands and the fresh outputs out of the L2
+  bool a_stream = false;
 };
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st);
 int tc_gemm_splits(int K, int ksplit);   // the split count tc_gemm_store will use
