@@ -373,6 +373,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one append of --slices slices on the workload's shapes with 4 existing "
+                         "slices, kernels launched one by one (small case for profiler captures)")
     ap.add_argument("--compress-only", action="store_true",
                     help="time octen_compress alone on --slices slices (profiling case)")
     ap.add_argument("--slices", type=int, default=4)
@@ -389,6 +392,8 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, wl, world, rank)
+    if args.profile_case:
+        return main_profile_case(args, wl)
     if args.compress_only:
         return main_compress_only(args, wl)
 
@@ -467,6 +472,43 @@ def main():
                                 "cores": cpu_cores(), "kind": "oracle",
                                 "sample": smp.describe(1, t_rep, t_lift)}
     print(json.dumps(line), flush=True)
+
+
+def main_profile_case(args, wl):
+    """Init from 4 existing slices and one append of --slices new slices on the
+    workload's shapes (every kernel of an append at full size, a few GB on the
+    device), with the CP-ALS launched kernel by kernel rather than as a graph."""
+    os.environ["OCTEN_GRAPH"] = "0"
+    import torch
+
+    from paper_1807_01350_gb300 import build as B
+    B.build()
+    import paper_1807_01350_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t_old, t = 4, args.slices
+    A, B_, C = factors(wl.I, wl.J, t_old + t, wl.R, args.seed, cond=wl.cond,
+                       big_frac=wl.big_frac)
+    U, V = projections(wl.I, wl.J, wl.P, wl.Q, wl.S, args.seed, args.prec)
+    W0 = time_projection(t_old, wl.P, wl.Q, wl.S, args.seed, -1)
+    W1 = time_projection(t, wl.P, wl.Q, wl.S, args.seed, 0)
+    A0, B0, C0 = init_factors(A, B_, C[:t_old], 0.01, args.seed)
+    dt = torch.float32 if args.prec == "fp32" else torch.bfloat16
+    X = slice_batch_torch(A, B_, C, 0, t_old + t, wl.noise, args.seed, dev, dt)
+    f32 = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=dev)
+    g = pkg.Octen(wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.als_iters, args.prec)
+    g.init(X[:t_old], f32(U), f32(V), f32(W0), f32(A0), f32(B0), f32(C0))
+    n0 = pkg.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g.append(X[t_old:], f32(W1))
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "profile_case", "workload": wl.name, "prec": args.prec,
+                      "slices": t, "append_ms": round(e0.elapsed_time(e1), 3),
+                      "launches": pkg.launch_count() - n0}), flush=True)
+    g.close()
 
 
 def main_compress_only(args, wl):

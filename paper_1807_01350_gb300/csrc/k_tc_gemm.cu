@@ -181,6 +181,7 @@ struct TcShape {
 struct TcStoreEpi {
   static constexpr bool kRowMajor = true;   // rows are contiguous in n
   static constexpr bool kSeg = false;
+  static constexpr bool kBf16Rows = true;   // may store bf16 rows (Dh)
   float *D;
   int64_t s_split, s_z, s_m;
   // optional fused reduction (replica ALS): with rows m = a * Q + b, every warp
@@ -194,6 +195,11 @@ struct TcStoreEpi {
     const int64_t o = (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n;
     if (Dh) Dh[o] = __float2bfloat16_rn(v);
     else D[o] = v;
+  }
+  // 8 bf16 values of row m from column n (n % 8 == 0; strides multiples of 8)
+  __device__ __forceinline__ void store_bf16x8(int z, int split, int m, int n, uint4 v) const {
+    const int64_t o = (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n;
+    *reinterpret_cast<uint4 *>(Dh + o) = v;
   }
 };
 
@@ -255,6 +261,7 @@ struct Mode2TcEpi {
 struct Mode1TcEpi {
   static constexpr bool kRowMajor = true;
   static constexpr bool kSeg = false;
+  static constexpr bool kBf16Rows = false;
   float *T2;
   int64_t t;
   int P, Q;
@@ -450,9 +457,32 @@ __global__ void __launch_bounds__(192, 1)
           for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(r[j]);
           __syncwarp();
           const int n = n0 + c0 + lane;
-          for (int i = 0; i < 32; ++i) {
-            const int mi = m0 + quad * 32 + i;
-            if (mi < sh.M && n < sh.N) epi.store(z, split, mi, n, stg[i * 33 + lane]);
+          bool stored = false;
+          if constexpr (Epi::kBf16Rows) {
+            if (epi.Dh && sh.N % 8 == 0) {
+              // bf16 rows: lane l packs columns 8 (l % 4) .. + 7 of rows l / 4 + 8 q
+              const int c8 = 8 * (lane & 3);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int i = (lane >> 2) + 8 * q;
+                const int mi = m0 + quad * 32 + i;
+                const int nb = n0 + c0 + c8;
+                if (mi < sh.M && nb < sh.N) {
+                  const float *src = stg + i * 33 + c8;
+                  __align__(16) __nv_bfloat162 h[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(src[2 * e], src[2 * e + 1]);
+                  epi.store_bf16x8(z, split, mi, nb, *reinterpret_cast<const uint4 *>(h));
+                }
+              }
+              stored = true;
+            }
+          }
+          if (!stored) {
+            for (int i = 0; i < 32; ++i) {
+              const int mi = m0 + quad * 32 + i;
+              if (mi < sh.M && n < sh.N) epi.store(z, split, mi, n, stg[i * 33 + lane]);
+            }
           }
           if (epi.part != nullptr) {
             const int mb = m0 + quad * 32;   // 32 rows of one a when 32 divides Q
