@@ -405,7 +405,8 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   // the bf16 copies of X_p stream through once per pass (evict-first), so Tc
   // stays in the L2 for the M2 pass
   m3.a_stream = tc.a_stream = true;
-  const int ks = tc_gemm_splits(m3.K, b.ksplit);
+  m3.katoms = tc.katoms = kAlsKAtoms;
+  const int ks = tc_gemm_splits(m3.K, b.ksplit, kAlsKAtoms);
   const dim3 gKR(NP, P);
   const dim3 gM((Q + 32 / (RT / 2) - 1) / (32 / (RT / 2)), P);   // 32 output pairs per CTA
   bool ok = true;
@@ -458,7 +459,7 @@ bool als_tc_eligible(int Q) { return Q % 8 == 0 && tc_supported(); }
 
 int als_tc_splits(int P, int Q, int desired) {
   (void)P;
-  return tc_gemm_splits(Q * Q, desired);
+  return tc_gemm_splits(Q * Q, desired, kAlsKAtoms);
 }
 
 bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,

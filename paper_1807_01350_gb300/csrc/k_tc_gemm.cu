@@ -174,6 +174,7 @@ struct TcShape {
   int a_hi, a_lo, b_hi, b_lo;
   int ksplit;           // > 1: blockIdx.x is the K split (a single N tile)
   int a_stream;         // A is read once: load it with an L2 evict-first policy
+  int katoms;           // 128-byte K atoms per pipeline stage (1 or 2)
 };
 
 // Plain store: D[split * s_split + z * s_z + m * s_m + n] (split-K partials), in
@@ -292,8 +293,11 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int stages = sh.stages;
-  const uint32_t a_bytes = kBM * kRowBytes;
-  const uint32_t b_bytes = sh.BN * kRowBytes;
+  // a stage holds `katoms` 128-byte K atoms of each operand, atom after atom
+  const int katoms = sh.katoms;
+  const uint32_t a_atom = kBM * kRowBytes, b_atom = sh.BN * kRowBytes;
+  const uint32_t a_bytes = a_atom * katoms;
+  const uint32_t b_bytes = b_atom * katoms;
   uint8_t *sA = smem;
   uint8_t *sB = smem + stages * a_bytes;
   uint64_t *full = reinterpret_cast<uint64_t *>(sB + stages * b_bytes);
@@ -309,7 +313,8 @@ __global__ void __launch_bounds__(192, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kElemsPerRow = KIND == 0 ? 64 : 128;   // 128 bytes of K
-  const int nk_all = (sh.K + kElemsPerRow - 1) / kElemsPerRow;
+  const int kStageElems = kElemsPerRow * katoms;
+  const int nk_all = (sh.K + kStageElems - 1) / kStageElems;   // stages of K
   const int tiles_n = sh.ksplit > 1 ? sh.ksplit : (sh.N + sh.BN - 1) / sh.BN;
   const int tiles_m = (sh.M + kBM - 1) / kBM;
   const int total = tiles_n * tiles_m * batch;         // work items (tiles)
@@ -369,12 +374,16 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         mbar_expect_tx(&full[s], a_bytes + b_bytes);
-        if (sh.a_stream)
-          tma_load_2d_policy(sA + s * a_bytes, &tmA, &full[s], (kb0 + kb) * kElemsPerRow, a_row,
-                             a_policy);
-        else
-          tma_load_2d(sA + s * a_bytes, &tmA, &full[s], (kb0 + kb) * kElemsPerRow, a_row);
-        tma_load_2d(sB + s * b_bytes, &tmB, &full[s], (kb0 + kb) * kElemsPerRow, b_row);
+        for (int at = 0; at < katoms; ++at) {
+          // K atoms past the end are filled with zeros by the TMA unit
+          const int kx = ((kb0 + kb) * katoms + at) * kElemsPerRow;
+          if (sh.a_stream)
+            tma_load_2d_policy(sA + s * a_bytes + at * a_atom, &tmA, &full[s], kx, a_row,
+                               a_policy);
+          else
+            tma_load_2d(sA + s * a_bytes + at * a_atom, &tmA, &full[s], kx, a_row);
+          tma_load_2d(sB + s * b_bytes + at * b_atom, &tmB, &full[s], kx, b_row);
+        }
       }
     }
     if (aborted) {
@@ -414,10 +423,13 @@ __global__ void __launch_bounds__(192, 1)
         }
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
+        for (int at = 0; at < katoms; ++at) {
 #pragma unroll
-        for (int kk = 0; kk < kRowBytes / 32; ++kk) {
-          mma_issue<KIND>(d, make_desc_sw128(a0 + kk * 32), make_desc_sw128(b0 + kk * 32), idesc,
-                          (kb > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+            mma_issue<KIND>(d, make_desc_sw128(a0 + at * a_atom + kk * 32),
+                            make_desc_sw128(b0 + at * b_atom + kk * 32), idesc,
+                            (kb > 0 || at > 0 || kk > 0) ? 1u : 0u);
+          }
         }
         mma_commit(&empty[s]);
       }
@@ -583,7 +595,8 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
                const Epi &epi, int *status, cudaStream_t st, int smem_reserve = 0) {
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
-  const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes;
+  if (sh.katoms < 1) sh.katoms = 1;
+  const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes * sh.katoms;
   const size_t stage_bytes = Epi::kRowMajor ? 4 * 32 * 33 * sizeof(float) + 16
                              : Epi::kSeg   ? 4 * 32 * 32 * sizeof(__nv_bfloat16) + 16
                                            : 0;
@@ -640,6 +653,7 @@ bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st) {
   sh.M = static_cast<int>(M); sh.N = a.Qd; sh.K = static_cast<int>(a.J); sh.BN = BN;
   sh.zdiv = 1; sh.a_hi = 0; sh.a_lo = 0; sh.b_hi = 0; sh.b_lo = 0;
   sh.a_stream = 1;   // the slices are read once
+  sh.katoms = 1;
   Mode2TcEpi epi{static_cast<__nv_bfloat16 *>(a.T), a.slice_scale, a.I, a.P, a.Q, a.S,
                  a.I % 8 == 0};
   return fp8 ? launch_tc<1>(ma, mb, sh, 1, epi, status, st)
@@ -676,10 +690,8 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   sh.M = g.M; sh.N = g.N; sh.K = g.K; sh.BN = g.BN;
   sh.zdiv = 1; sh.a_hi = g.a_rows_per_z; sh.a_lo = 0; sh.b_hi = g.b_rows_per_z; sh.b_lo = 0;
   sh.a_stream = g.a_stream ? 1 : 0;
-  const int nk = (g.K + 63) / 64;
-  int ks = g.ksplit < 1 ? 1 : (g.ksplit > nk ? nk : g.ksplit);
-  const int per = (nk + ks - 1) / ks;
-  ks = (nk + per - 1) / per;            // every split gets at least one K block
+  sh.katoms = g.katoms < 1 ? 1 : g.katoms;
+  const int ks = tc_gemm_splits(g.K, g.ksplit, sh.katoms);
   sh.ksplit = ks;
   TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT, g.Dh};
   if (g.m1_part && (g.BN != 32 || g.Q % 32 || ks > 1)) return false;
@@ -687,11 +699,11 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve);
 }
 
-int tc_gemm_splits(int K, int ksplit) {
-  const int nk = (K + 63) / 64;
+int tc_gemm_splits(int K, int ksplit, int katoms) {
+  const int nk = (K + 64 * katoms - 1) / (64 * katoms);   // pipeline stages of K
   int ks = ksplit < 1 ? 1 : (ksplit > nk ? nk : ksplit);
   const int per = (nk + ks - 1) / ks;
-  return (nk + per - 1) / per;
+  return (nk + per - 1) / per;   // every split gets at least one stage
 }
 
 }  // namespace octen

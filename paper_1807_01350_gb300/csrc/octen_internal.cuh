@@ -113,9 +113,14 @@ struct TcStoreArgs {
   // A is read once: its TMA loads carry an L2 evict-first policy so that it
   // does not push the reused operands and the fresh outputs out of the L2
   bool a_stream = false;
+  // 128-byte K atoms per pipeline stage: 2 halves the barrier round trips and
+  // commits per byte for the narrow (N = 32) GEMMs
+  int katoms = 1;
 };
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st);
-int tc_gemm_splits(int K, int ksplit);   // the split count tc_gemm_store will use
+// the split count tc_gemm_store will use
+int tc_gemm_splits(int K, int ksplit, int katoms = 1);
+constexpr int kAlsKAtoms = 2;   // K atoms per stage of the replica-ALS GEMMs
 
 // Mode-3 contraction and summary update: Y[p][a][b][c] +=
 //   sum_k T2[p][k][a][b] * W_all[k][col_p(c)].
