@@ -285,7 +285,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 //   warp 0 lane 0 : TMA producer        full[s]  <- TMA bytes,  waits empty[s]
 //   warp 1 lane 0 : MMA issuer          empty[s] <- commit,     acc_full[b] <- commit
 //   warps 2..5    : epilogue (lane quadrant = warp % 4), acc_empty[b] <- 4 arrivals
-template <int KIND, class Epi>
+template <int KIND, class Epi, int KATOMS>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcShape sh, const Epi epi, int batch, int *status) {
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(192, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int stages = sh.stages;
   // a stage holds `katoms` 128-byte K atoms of each operand, atom after atom
-  const int katoms = sh.katoms;
+  constexpr int katoms = KATOMS;
   const uint32_t a_atom = kBM * kRowBytes, b_atom = sh.BN * kRowBytes;
   const uint32_t a_bytes = a_atom * katoms;
   const uint32_t b_bytes = b_atom * katoms;
@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         mbar_expect_tx(&full[s], a_bytes + b_bytes);
+#pragma unroll
         for (int at = 0; at < katoms; ++at) {
           // K atoms past the end are filled with zeros by the TMA unit
           const int kx = ((kb0 + kb) * katoms + at) * kElemsPerRow;
@@ -423,6 +424,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
+#pragma unroll
         for (int at = 0; at < katoms; ++at) {
 #pragma unroll
           for (int kk = 0; kk < kRowBytes / 32; ++kk) {
@@ -595,7 +597,7 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
                const Epi &epi, int *status, cudaStream_t st, int smem_reserve = 0) {
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
-  if (sh.katoms < 1) sh.katoms = 1;
+  if (sh.katoms != 2) sh.katoms = 1;   // kernels exist for 1 and 2 atoms per stage
   const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes * sh.katoms;
   const size_t stage_bytes = Epi::kRowMajor ? 4 * 32 * 33 * sizeof(float) + 16
                              : Epi::kSeg   ? 4 * 32 * 32 * sizeof(__nv_bfloat16) + 16
@@ -605,7 +607,7 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
   if (sh.stages > 8) sh.stages = 8;
   if (sh.stages < 2) return false;
   const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 5) * 8 + 16 + stage_bytes;
-  auto kern = tc_gemm_kernel<KIND, Epi>;
+  auto kern = sh.katoms == 2 ? tc_gemm_kernel<KIND, Epi, 2> : tc_gemm_kernel<KIND, Epi, 1>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return false;
@@ -690,7 +692,7 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   sh.M = g.M; sh.N = g.N; sh.K = g.K; sh.BN = g.BN;
   sh.zdiv = 1; sh.a_hi = g.a_rows_per_z; sh.a_lo = 0; sh.b_hi = g.b_rows_per_z; sh.b_lo = 0;
   sh.a_stream = g.a_stream ? 1 : 0;
-  sh.katoms = g.katoms < 1 ? 1 : g.katoms;
+  sh.katoms = g.katoms == 2 ? 2 : 1;
   const int ks = tc_gemm_splits(g.K, g.ksplit, sh.katoms);
   sh.ksplit = ks;
   TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT, g.Dh};
