@@ -26,10 +26,12 @@ class Case:
     rel: float = 0.01
     seed: int = 0
     big_frac: float = 0.0
+    cond: float | None = None
 
     def make(self):
         K = self.t_old + sum(self.batches)
-        A, B, C = factors(self.I, self.J, K, self.R, self.seed, big_frac=self.big_frac)
+        A, B, C = factors(self.I, self.J, K, self.R, self.seed, cond=self.cond,
+                          big_frac=self.big_frac)
         X = slice_batch(A, B, C, 0, K, self.noise, self.seed)
         if self.prec != "fp32":
             X = round_to(X, "bf16")       # the slices the update receives are bf16

@@ -1,0 +1,59 @@
+"""Whole updates at the benchmark workloads' full slice and replica sizes,
+through the same C ABI calls and kernels that bench.py times (tensor-core
+contractions, tensor-core CP-ALS replayed as a CUDA graph, fp64 factor
+kernels), against the FP64 oracle on the same seeded inputs.
+
+To keep the oracle within about a minute per case, the existing tensor is a
+single slice (the oracle's cost is in compressing and decomposing the new
+batch); everything else is the workload: slice size, replica count and size,
+anchors, rank, sweeps, batch size, noise and factor structure. Tolerances as in
+the other update tests: bf16 summaries within 5e-3, factors within 5e-2, fit
+within 1e-3, FMS >= 0.99; fp8 6e-2 / 2e-1 / 3e-3 / 0.99; fp32 1e-5 / 1e-3 /
+1e-4 / 0.999."""
+import pytest
+
+from tests._cases import Case
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CASES = {
+    # 4000 x 4000 slices, P = 16 replicas of 256^3, S = 32, R = 32, 30 sweeps,
+    # a batch of 16 slices, 20 % of the time steps 10x larger (bf16 headline)
+    "c4_bf16": Case(4000, 4000, 32, 16, 256, 32, 1, (16,), 30, prec="bf16", noise=0.01,
+                    seed=51, big_frac=0.2),
+    # the same workload with e4m3 slices (per-slice absmax scaling) and e4m3 V
+    "c4_fp8": Case(4000, 4000, 32, 16, 256, 32, 1, (16,), 30, prec="fp8", noise=0.01,
+                   seed=54, big_frac=0.2),
+    # 2000 x 2000, P = 16 of 200^3 (Q % 32 != 0: the unfused M1 reduction),
+    # R = 20, factor columns of condition number 10, 0.5 % noise, batch of 50
+    "c3_bf16": Case(2000, 2000, 20, 16, 200, 20, 1, (50,), 30, prec="bf16", noise=0.005,
+                    seed=52, cond=10.0),
+    # 1000 x 1000 fp32 (SIMT contractions and CP-ALS), P = 8 of 100^3, R = 10,
+    # batches of 10 slices
+    "c2_fp32": Case(1000, 1000, 10, 8, 100, 10, 10, (10,), 30, prec="fp32", seed=53),
+}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1807_01350_gb300 as p
+
+    assert torch.cuda.is_available()
+    p.lib()
+    return p
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_full_size_update_matches_oracle(pkg, name):
+    from tests.test_gpu_parity import check_update, run_gpu
+
+    case = CASES[name]
+    d = case.make()
+    n0 = pkg.tc_launch_count()
+    g, gpu = run_gpu(pkg, case, d)
+    g.close()
+    if case.prec != "fp32":
+        assert pkg.tc_launch_count() > n0, "the tensor-core path should run"
+    _, ref = case.oracle_run(d)
+    check_update(case, d, gpu, ref)
