@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from synth import WORKLOADS, factors, init_factors, projections, slice_batch  # noqa: E402
-from synth import slice_batch_torch, time_projection  # noqa: E402
+from synth import round_to, slice_batch_torch, time_projection  # noqa: E402
 
 METRIC = "new slices/sec (compress+CP update) at fit >= oracle-1e-3; BF16/FP8 vs FP32"
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max clock
@@ -146,6 +146,8 @@ def stage_work(wl, prec, layouts=False):
         "mode3": (2.0 * t * P * Q ** 3, 2.0 * 4 * P * Q ** 3 + 4.0 * t * P * Q * Q
                   + (2.0 * 2 * P * Q ** 3 if layouts else 0.0)),
         "als_gemm": (2.0 * P * Q ** 3 * R, 4.0 * P * Q ** 3),
+        # e4m3 quantisation: an absmax pass and a scale-and-convert pass over the bf16 slices
+        "quantize": (0.0, t * I * J * (2.0 + 2.0 + 1.0)),
     }
 
 
@@ -164,7 +166,7 @@ def als_gemm_tc_bytes(wl):
 def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic, tc_stages=()):
     flops, nbytes = stage_work(wl, prec, layouts="als_gemm" in tc_stages)[stage]
     sec = ms_per_launch / 1e3
-    if stage == "mode3":
+    if stage in ("mode3", "quantize"):
         bound, peak, unit, achieved = "hbm", pk["hbm"], "GB/s", nbytes / sec / 1e9
     elif stage == "als_gemm" and stage in tc_stages:
         bound, peak, unit = "hbm", pk["hbm"], "GB/s"
@@ -317,18 +319,23 @@ class OracleSampler:
     anchor match; `lift()` = the lift of A and B and the solve of the new rows
     of C.  One append costs P replica pieces plus one lift."""
 
-    def __init__(self, wl, seed=0):
+    def __init__(self, wl, seed=0, prec=None):
         import oracle
 
         self.o_mod = oracle
         self.wl = wl
+        self.prec = prec or wl.prec
         I, J, R, P, Q, S, t = wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.batch
         A, B, C = factors(I, J, 1 + t, R, seed, cond=wl.cond, big_frac=wl.big_frac)
-        self.X = slice_batch(A, B, C, 0, 1 + t, wl.noise, seed)
-        U, V = projections(I, J, P, Q, S, seed, wl.prec)
+        # the slices as the library receives them (bf16 unless fp32)
+        self.X = round_to(slice_batch(A, B, C, 0, 1 + t, wl.noise, seed),
+                          "fp32" if self.prec == "fp32" else "bf16")
+        U, V = projections(I, J, P, Q, S, seed, self.prec)
         Wo = time_projection(1, P, Q, S, seed, -1)
         Wn = time_projection(t, P, Q, S, seed, 0)
         A0, B0, C0 = init_factors(A, B, C[:1], 0.01, seed)
+        self.inputs = dict(U=U, V=V, Wo=Wo, Wn=Wn, A0=A0, B0=B0, C0=C0)
+        self.Wn = Wn
         self.o = oracle.OctenOracle(I, J, R, P, Q, S, wl.als_iters)
         self.o.init(self.X[:1], U, V, Wo, A0, B0, C0)
         self.Wp = [oracle.replica_block(Wn, p, Q, S) for p in range(P)]
@@ -355,11 +362,58 @@ class OracleSampler:
         O.lift_C(self.Wp, [h[2] for h in hats], o.G)
         return time.perf_counter() - t0
 
+    def full_append(self):
+        """The oracle's whole append of the batch (every replica, the lift);
+        returns its wall time.  Changes the oracle's state."""
+        t0 = time.perf_counter()
+        self.o.append(self.X[1:], self.Wn)
+        return time.perf_counter() - t0
+
+    def gpu_parity(self, pkg, prec):
+        """The library on the same inputs (init from the same slice, the same
+        append): worst replica summary error, the fits and the factor-match
+        score against the oracle's state after full_append()."""
+        import torch
+
+        wl, d, o, O = self.wl, self.inputs, self.o, self.o_mod
+        dev = torch.device("cuda", torch.cuda.current_device())
+        f32 = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=dev)
+        xs = f32(self.X).to(torch.float32 if prec == "fp32" else torch.bfloat16)
+        g = pkg.Octen(wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.als_iters, prec)
+        g.init(xs[:1], f32(d["U"]), f32(d["V"]), f32(d["Wo"]), f32(d["A0"]), f32(d["B0"]),
+               f32(d["C0"]))
+        g.append(xs[1:], f32(d["Wn"]))
+        Y = g.replicas()
+        A, B, C = g.factors()
+        fit_gpu = g.fit(xs)
+        g.close()
+        err = max(float(np.linalg.norm(Y[p] - o.Y[p]) / np.linalg.norm(o.Y[p]))
+                  for p in range(wl.P))
+        return {"replica_rel_err_max": round(err, 7),
+                "fit": round(fit_gpu, 6), "fit_oracle": round(O.fit(self.X, o.A, o.B, o.C), 6),
+                "fms": round(_fms((A, B, C), (o.A, o.B, o.C)), 6),
+                "case": f"{wl.name} shapes, {prec}: init from 1 slice, one append of {wl.batch}"}
+
     def describe(self, n_rep, t_rep, t_lift):
         wl = self.wl
         return (f"one append of {wl.batch} slices at {wl.name}: compression + CP-ALS + anchor "
                 f"match timed on {n_rep} of {wl.P} replicas ({t_rep:.2f} s each) and scaled to "
                 f"{wl.P}, plus the full lift of A, B and the new C rows ({t_lift:.2f} s)")
+
+
+def _fms(model, ref):
+    """Factor-match score: mean over matched columns of the product over modes
+    of |cos|, columns matched by the assignment that maximises the sum."""
+    from scipy.optimize import linear_sum_assignment
+
+    sim = np.ones((ref[0].shape[1],) * 2)
+    for F, G in zip(model, ref):
+        F = np.asarray(F, np.float64)
+        G = np.asarray(G, np.float64)
+        nf, ng = np.linalg.norm(F, axis=0), np.linalg.norm(G, axis=0)
+        sim = sim * np.abs(F.T @ G) / np.outer(np.where(nf > 0, nf, 1), np.where(ng > 0, ng, 1))
+    rows, cols = linear_sum_assignment(-sim)
+    return float(sim[rows, cols].mean())
 
 
 def cpu_cores():
@@ -445,7 +499,15 @@ def main():
                         traffic_from_profiles(dominant, args.prec), tcs)
     comp = {s: roofline_for(s, st[s][0] / st[s][1], wl, args.prec, pk,
                             traffic_from_profiles(s, args.prec), tcs)
-            for s in ("mode2", "mode1", "mode3", "als_gemm") if st[s][1]}
+            for s in ("quantize", "mode2", "mode1", "mode3", "als_gemm") if st[s][1]}
+    # the compression as a whole (quantise, mode 2, mode 1, mode 3): time at
+    # each kernel's roofline over the measured time
+    cstages = [s for s in ("quantize", "mode2", "mode1", "mode3") if s in comp]
+    t_meas = sum(comp[s]["ms_per_launch"] for s in cstages)
+    t_roof = sum(comp[s]["ms_per_launch"] * comp[s]["frac"] for s in cstages)
+    compression_roofline = {"stages": cstages, "measured_ms": round(t_meas, 4),
+                            "at_roofline_ms": round(t_roof, 4),
+                            "frac": round(t_roof / t_meas, 4) if t_meas > 0 else None}
     value = whole_job_rate(main_run["slices"], main_run["ms"] / 1e3, world)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "slices/s", "n_gpus": world,
@@ -468,18 +530,22 @@ def main():
                               for k, v in timed.items()},
         "stage_note": "per-stage CUDA events on separate appends launched one by one",
         "stage_roofline": comp,
+        "compression_roofline": compression_roofline,
         "beside": beside,
     }
     if "e2e" in main_run:
         line["e2e"] = main_run["e2e"]
     if world == 1 and not args.no_cpu_baseline:
-        smp = OracleSampler(wl, args.seed)
-        t_rep = smp.replica(0)
-        t_lift = smp.lift()
-        sec = wl.P * t_rep + t_lift
-        line["cpu_baseline"] = {"value": round(wl.batch / sec, 5), "unit": "slices/s",
-                                "cores": cpu_cores(), "kind": "oracle",
-                                "sample": smp.describe(1, t_rep, t_lift)}
+        smp = OracleSampler(wl, args.seed, args.prec)
+        sec = smp.full_append()
+        line["cpu_baseline"] = {
+            "value": round(wl.batch / sec, 5), "unit": "slices/s", "cores": cpu_cores(),
+            "kind": "oracle",
+            "sample": f"one whole append of {wl.batch} slices at {wl.name} ({args.prec} inputs) "
+                      f"after an init from 1 slice: compression and CP-ALS of all {wl.P} "
+                      f"replicas, anchor match, lift ({sec:.1f} s)"}
+        import paper_1807_01350_gb300 as pkg
+        line["parity"] = smp.gpu_parity(pkg, args.prec)
     print(json.dumps(line), flush=True)
 
 
@@ -560,7 +626,7 @@ def main_reference(args, wl, world, rank):
     the batch's slices over P replica pieces plus one lift."""
     if rank != 0:
         return
-    smp = OracleSampler(wl, args.seed)
+    smp = OracleSampler(wl, args.seed, args.prec)
     t_lift = None
     reps = []
     for s in range(args.warmup + args.steps):
