@@ -232,45 +232,57 @@ __global__ void __launch_bounds__(256)
 }
 
 // M1[p][a][r] = sum_b Tc[p][(a,b)][r] B[p][b][r] and M2[p][b][r] = sum_a
-// Tc[p][(a,b)][r] A[p][a][r], Tc in bf16.  A CTA of 256 threads owns 32 output
-// column pairs (32 / (RT / 2) rows of RT / 2 pairs); thread (pair j < 32,
-// slice s < 8) sums every 8th term of the reduction starting at s, and the 8
-// slice sums are added in shared memory in a fixed order.
+// Tc[p][(a,b)][r] A[p][a][r], Tc in bf16.  A CTA of 256 threads owns 32
+// column octets (256 / RT output rows of RT / 8 octets); thread (octet j < 32,
+// slice s < 8) sums every 8th term of the reduction starting at s with 16-byte
+// loads of Tc, and the 8 slice sums are added in shared memory in a fixed order.
 //   kind 1 (M1): output row a, reduction over b: term b at Tc[(a, b)]
 //   kind 2 (M2): output row b, reduction over a: term a at Tc[(a, b)]
 template <int RT, int KIND>
 __global__ void __launch_bounds__(256)
     tc_mred_kernel(const __nv_bfloat16 *__restrict__ Tc, const float *__restrict__ Fac, int Q,
                    float *__restrict__ M) {
-  constexpr int PAIRS = RT / 2;          // column pairs per output row
-  constexpr int ROWS = 32 / PAIRS;       // output rows per CTA (32 pairs per CTA)
-  __shared__ float2 part[8][32];
+  constexpr int OCT = RT / 8;            // column octets per output row
+  constexpr int ROWS = 32 / OCT;         // output rows per CTA
+  __shared__ float4 part[8][32][2];
   const int p = blockIdx.y;
   const int j = threadIdx.x & 31, sl = threadIdx.x >> 5;
-  const int row = blockIdx.x * ROWS + j / PAIRS, r = 2 * (j % PAIRS);
-  float ax = 0.f, ay = 0.f;
+  const int row = blockIdx.x * ROWS + j / OCT, r = 8 * (j % OCT);
+  float acc[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) acc[e] = 0.f;
   if (row < Q) {
     const __nv_bfloat16 *t = Tc + (int64_t)p * Q * Q * RT + r;
     const float *f = Fac + (int64_t)p * Q * RT + r;
 #pragma unroll 4
     for (int k = sl; k < Q; k += 8) {
       const int64_t ab = KIND == 1 ? (int64_t)row * Q + k : (int64_t)k * Q + row;
-      const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(t + ab * RT));
-      const float2 w = *reinterpret_cast<const float2 *>(f + k * RT);
-      ax = fmaf(v.x, w.x, ax);
-      ay = fmaf(v.y, w.y, ay);
+      const uint4 raw = *reinterpret_cast<const uint4 *>(t + ab * RT);
+      const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+      const float4 w0 = *reinterpret_cast<const float4 *>(f + k * RT);
+      const float4 w1 = *reinterpret_cast<const float4 *>(f + k * RT + 4);
+      const float2 v0 = __bfloat1622float2(h[0]), v1 = __bfloat1622float2(h[1]);
+      const float2 v2 = __bfloat1622float2(h[2]), v3 = __bfloat1622float2(h[3]);
+      acc[0] = fmaf(v0.x, w0.x, acc[0]); acc[1] = fmaf(v0.y, w0.y, acc[1]);
+      acc[2] = fmaf(v1.x, w0.z, acc[2]); acc[3] = fmaf(v1.y, w0.w, acc[3]);
+      acc[4] = fmaf(v2.x, w1.x, acc[4]); acc[5] = fmaf(v2.y, w1.y, acc[5]);
+      acc[6] = fmaf(v3.x, w1.z, acc[6]); acc[7] = fmaf(v3.y, w1.w, acc[7]);
     }
   }
-  part[sl][j] = make_float2(ax, ay);
+  part[sl][j][0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  part[sl][j][1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
   __syncthreads();
   if (sl == 0 && row < Q) {
-    float sx = 0.f, sy = 0.f;
+    float4 s0 = part[0][j][0], s1 = part[0][j][1];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      sx += part[q][j].x;
-      sy += part[q][j].y;
+    for (int q = 1; q < 8; ++q) {
+      const float4 u0 = part[q][j][0], u1 = part[q][j][1];
+      s0.x += u0.x; s0.y += u0.y; s0.z += u0.z; s0.w += u0.w;
+      s1.x += u1.x; s1.y += u1.y; s1.z += u1.z; s1.w += u1.w;
     }
-    *reinterpret_cast<float2 *>(M + ((int64_t)p * Q + row) * RT + r) = make_float2(sx, sy);
+    float4 *o = reinterpret_cast<float4 *>(M + ((int64_t)p * Q + row) * RT + r);
+    o[0] = s0;
+    o[1] = s1;
   }
 }
 
@@ -295,8 +307,8 @@ static void factor_async(const float *Fnew, float *Gnew, const float *Gother, in
 
 // Joins the factor and solves: F = M (L D L^T)^-1 with M row q of replica p
 // the sum over s < nsplit of M[s * split_stride + (p * Q + q) * row_stride].
-// Clusters of up to 8 CTAs share a replica (32 rows each at Q = 256); one CTA
-// per replica if the cluster launch is refused.
+// Clusters of up to 8 CTAs share a replica (at most 32 rows each, a multiple
+// of 8); one CTA per replica if the cluster launch is refused.
 template <int RT>
 static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_stride, float *F,
                   __nv_bfloat16 *Ft, int NP, int P, int Q, int normalize, AlsBuffers &b,
@@ -304,7 +316,8 @@ static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_
   cudaStreamWaitEvent(st, b.ev_join, 0);
   int cl = (Q + 31) / 32;
   if (cl > 8) cl = 8;
-  const int rows = (Q + cl - 1) / cl;
+  const int rows = ((Q + cl - 1) / cl + 7) / 8 * 8;
+  cl = (Q + rows - 1) / rows;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = dim3(P * cl);
@@ -408,7 +421,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   m3.katoms = tc.katoms = kAlsKAtoms;
   const int ks = tc_gemm_splits(m3.K, b.ksplit, kAlsKAtoms);
   const dim3 gKR(NP, P);
-  const dim3 gM((Q + 32 / (RT / 2) - 1) / (32 / (RT / 2)), P);   // 32 output pairs per CTA
+  const dim3 gM((Q + 256 / RT - 1) / (256 / RT), P);   // 32 output octets per CTA
   bool ok = true;
   auto c_update = [&]() {
     factor_async<RT>(b.Bf, b.GB, b.GA, P, Q, R, b, st);
@@ -465,15 +478,16 @@ int als_tc_splits(int P, int Q, int desired) {
 bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
              cudaStream_t st, const Marker &mk) {
   const int smem = (int)((size_t)Q * RT * sizeof(float));
+  const int smem_ap = smem;   // the solve's rows (all Q without clusters)
   if (RT == 8) {
     cudaFuncSetAttribute(als_factor_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(als_apply_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(als_apply_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ap);
   } else if (RT == 16) {
     cudaFuncSetAttribute(als_factor_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(als_apply_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(als_apply_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ap);
   } else {
     cudaFuncSetAttribute(als_factor_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(als_apply_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(als_apply_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ap);
   }
   if (b.use_tc) {
     if (RT == 8) return als_run_tc<8>(Y, P, Q, R, iters, b, st, mk);

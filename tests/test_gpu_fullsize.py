@@ -8,8 +8,15 @@ single slice (the oracle's cost is in compressing and decomposing the new
 batch); everything else is the workload: slice size, replica count and size,
 anchors, rank, sweeps, batch size, noise and factor structure. Tolerances as in
 the other update tests: bf16 summaries within 5e-3, factors within 5e-2, fit
-within 1e-3, FMS >= 0.99; fp8 6e-2 / 2e-1 / 3e-3 / 0.99; fp32 1e-5 / 1e-3 /
-1e-4 / 0.999."""
+within 1e-3, FMS >= 0.99; fp32 1e-5 / 1e-3 / 1e-4 / 0.999.
+
+The e4m3 case is checked against the oracle run on the e4m3-quantised slices
+(per-slice absmax / 448 scale, round to nearest even, saturating; the scale
+folded back), which is what the fp8 path computes, at the bf16 tolerances; its
+fit is taken on the bf16 slices on both sides.  (At this shape, with one
+existing slice and a fifth of the slices ten times larger, the quantisation
+itself costs about 1.2e-2 of fit against the unquantised oracle: 0.9862 ->
+0.9744 in an fp64 oracle run on the quantised slices, 0.9743 on the GPU.)"""
 import pytest
 
 from tests._cases import Case
@@ -44,9 +51,22 @@ def pkg():
     return p
 
 
+def quantised_e4m3(X):
+    """Per-slice absmax / 448 scaling, RNE to e4m3 (saturating), scale folded back."""
+    import numpy as np
+
+    from synth import round_to
+
+    out = np.empty_like(X)
+    for k in range(X.shape[0]):
+        s = np.abs(X[k]).max() / 448.0
+        out[k] = round_to(X[k] / s, "e4m3") * s if s > 0 else X[k]
+    return out
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_full_size_update_matches_oracle(pkg, name):
-    from tests.test_gpu_parity import check_update, run_gpu
+    from tests.test_gpu_parity import TOL, check_update, run_gpu
 
     case = CASES[name]
     d = case.make()
@@ -55,5 +75,10 @@ def test_full_size_update_matches_oracle(pkg, name):
     g.close()
     if case.prec != "fp32":
         assert pkg.tc_launch_count() > n0, "the tensor-core path should run"
-    _, ref = case.oracle_run(d)
-    check_update(case, d, gpu, ref)
+    if case.prec == "fp8":
+        dq = dict(d, X=quantised_e4m3(d["X"]))
+        _, ref = case.oracle_run(dq)
+        check_update(case, dq, gpu, ref, tol=TOL["bf16"], X_fit=d["X"])
+    else:
+        _, ref = case.oracle_run(d)
+        check_update(case, d, gpu, ref)
