@@ -10,6 +10,8 @@
 // M1[a][r] = sum_c C[c][r] H[a][c][r]; a second pass over X_p forms M2.
 // The R x R Gram Hadamard products are factored (L D L^T) in fp64 over four
 // warps, the Grams and the triangular substitutions run in fp32 (k_solve.cuh).
+#include <cstdlib>
+
 #include "k_solve.cuh"
 
 namespace octen {
@@ -475,8 +477,21 @@ int als_tc_splits(int P, int Q, int desired) {
   return tc_gemm_splits(Q * Q, desired, kAlsKAtoms);
 }
 
+// OCTEN_ALS_FUSED=0 keeps small replicas on the multi-launch path (used to
+// cross-check the single-launch kernel).
+static bool fused_wanted() {
+  const char *v = getenv("OCTEN_ALS_FUSED");
+  return !(v && v[0] == '0');
+}
+
 bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
              cudaStream_t st, const Marker &mk) {
+  if (fused_wanted() && als_fused_fits(Q, RT)) {
+    mk(kStAlsFused, 1);
+    const bool ran = als_run_fused(Y, P, Q, R, RT, iters, b, st);
+    mk(kStAlsFused, 0);
+    if (ran) return true;
+  }
   const int smem = (int)((size_t)Q * RT * sizeof(float));
   const int smem_ap = smem;   // the solve's rows (all Q without clusters)
   if (RT == 8) {

@@ -222,6 +222,46 @@ __device__ void ldl_factor(const float *__restrict__ g1, const float *__restrict
   }
 }
 
+// y <- y (L D L^T)^-1 for one row y (the matrix symmetric): forward
+// substitution with the unit lower L (column-major Lc[k][i] = L[i][k]), scaling
+// by rf = 1/D, backward substitution with L^T (row-major Lr[k][i] = L[k][i]).
+// Entries beyond the rank are zero in Lc, Lr and rf, so padded columns stay 0.
+template <int RT>
+__device__ __forceinline__ void ldl_substitute(float (&y)[RT], const float *Lc, const float *Lr,
+                                               const float *rf) {
+#pragma unroll
+  for (int k = 0; k < RT; ++k) {
+    const float yk = y[k];
+    const float4 *lc = reinterpret_cast<const float4 *>(Lc + k * RT);
+#pragma unroll
+    for (int i4 = (k + 1) / 4; i4 < RT / 4; ++i4) {
+      const float4 l = lc[i4];
+      if (4 * i4 + 0 > k) y[4 * i4 + 0] = fmaf(-l.x, yk, y[4 * i4 + 0]);
+      if (4 * i4 + 1 > k) y[4 * i4 + 1] = fmaf(-l.y, yk, y[4 * i4 + 1]);
+      if (4 * i4 + 2 > k) y[4 * i4 + 2] = fmaf(-l.z, yk, y[4 * i4 + 2]);
+      if (4 * i4 + 3 > k) y[4 * i4 + 3] = fmaf(-l.w, yk, y[4 * i4 + 3]);
+    }
+  }
+#pragma unroll
+  for (int r4 = 0; r4 < RT / 4; ++r4) {
+    const float4 d = reinterpret_cast<const float4 *>(rf)[r4];
+    y[4 * r4] *= d.x; y[4 * r4 + 1] *= d.y; y[4 * r4 + 2] *= d.z; y[4 * r4 + 3] *= d.w;
+  }
+#pragma unroll
+  for (int k = RT - 1; k > 0; --k) {
+    const float fk = y[k];
+    const float4 *lr = reinterpret_cast<const float4 *>(Lr + k * RT);
+#pragma unroll
+    for (int i4 = 0; i4 <= (k - 1) / 4; ++i4) {
+      const float4 l = lr[i4];
+      if (4 * i4 + 0 < k) y[4 * i4 + 0] = fmaf(-l.x, fk, y[4 * i4 + 0]);
+      if (4 * i4 + 1 < k) y[4 * i4 + 1] = fmaf(-l.y, fk, y[4 * i4 + 1]);
+      if (4 * i4 + 2 < k) y[4 * i4 + 2] = fmaf(-l.z, fk, y[4 * i4 + 2]);
+      if (4 * i4 + 3 < k) y[4 * i4 + 3] = fmaf(-l.w, fk, y[4 * i4 + 3]);
+    }
+  }
+}
+
 // Per replica: the packed factor written by als_factor_kernel and read by
 // als_apply_kernel, [Lc (RT x RT) | Lr (RT x RT) | rf (RT)] floats.
 template <int RT>
@@ -353,37 +393,7 @@ __global__ void __launch_bounds__(256)
       const float4 v = mr[r4];
       y[4 * r4] = v.x; y[4 * r4 + 1] = v.y; y[4 * r4 + 2] = v.z; y[4 * r4 + 3] = v.w;
     }
-#pragma unroll
-    for (int k = 0; k < RT; ++k) {
-      const float yk = y[k];
-      const float4 *lc = reinterpret_cast<const float4 *>(Lc + k * RT);
-#pragma unroll
-      for (int i4 = (k + 1) / 4; i4 < RT / 4; ++i4) {
-        const float4 l = lc[i4];
-        if (4 * i4 + 0 > k) y[4 * i4 + 0] = fmaf(-l.x, yk, y[4 * i4 + 0]);
-        if (4 * i4 + 1 > k) y[4 * i4 + 1] = fmaf(-l.y, yk, y[4 * i4 + 1]);
-        if (4 * i4 + 2 > k) y[4 * i4 + 2] = fmaf(-l.z, yk, y[4 * i4 + 2]);
-        if (4 * i4 + 3 > k) y[4 * i4 + 3] = fmaf(-l.w, yk, y[4 * i4 + 3]);
-      }
-    }
-#pragma unroll
-    for (int r4 = 0; r4 < RT / 4; ++r4) {
-      const float4 d = reinterpret_cast<const float4 *>(rf)[r4];
-      y[4 * r4] *= d.x; y[4 * r4 + 1] *= d.y; y[4 * r4 + 2] *= d.z; y[4 * r4 + 3] *= d.w;
-    }
-#pragma unroll
-    for (int k = RT - 1; k > 0; --k) {
-      const float fk = y[k];
-      const float4 *lr = reinterpret_cast<const float4 *>(Lr + k * RT);
-#pragma unroll
-      for (int i4 = 0; i4 <= (k - 1) / 4; ++i4) {
-        const float4 l = lr[i4];
-        if (4 * i4 + 0 < k) y[4 * i4 + 0] = fmaf(-l.x, fk, y[4 * i4 + 0]);
-        if (4 * i4 + 1 < k) y[4 * i4 + 1] = fmaf(-l.y, fk, y[4 * i4 + 1]);
-        if (4 * i4 + 2 < k) y[4 * i4 + 2] = fmaf(-l.z, fk, y[4 * i4 + 2]);
-        if (4 * i4 + 3 < k) y[4 * i4 + 3] = fmaf(-l.w, fk, y[4 * i4 + 3]);
-      }
-    }
+    ldl_substitute<RT>(y, Lc, Lr, rf);
   }
   if (normalize) {
     // column sums of squares over this CTA's rows, then over the cluster

@@ -950,7 +950,7 @@ uint64_t octen_tc_launch_count(void) { return g_tc_launches.load(); }
 
 static const char *kStageNames[kNumStages] = {"quantize", "mode2", "mode1", "mode3",
                                               "warm_start", "als_gemm", "als_aux", "als_solve",
-                                              "align", "lift", "c_solve"};
+                                              "align", "lift", "c_solve", "als_fused"};
 
 int octen_stage_count(void) { return kNumStages; }
 

@@ -29,7 +29,7 @@ void count_launch();
 // Stages timed with CUDA events when a context has timing enabled.
 enum Stage : int {
   kStQuant = 0, kStMode2, kStMode1, kStMode3, kStWarm, kStAlsGemm, kStAlsAux, kStAlsSolve,
-  kStAlign, kStLift, kStCsolve, kNumStages
+  kStAlign, kStLift, kStCsolve, kStAlsFused, kNumStages
 };
 
 // Optional hook called around the kernels of a multi-kernel stage:
@@ -174,6 +174,11 @@ int als_factor_floats(int RT);
 bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
              cudaStream_t st, const Marker &mk = Marker());
 bool als_tc_eligible(int Q);
+// Single-launch CP-ALS for replicas small enough to keep X_p and its pass-1
+// product in shared memory (one CTA per replica); false if it does not apply.
+bool als_fused_fits(int Q, int RT);
+bool als_run_fused(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers &b,
+                   cudaStream_t st);
 int als_tc_splits(int P, int Q, int desired);
 
 // Warm start: F_p = unit columns of rows(p) of PF (Qd x R) into P x Q x RT, and

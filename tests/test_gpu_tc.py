@@ -100,3 +100,30 @@ def test_als_graph_replay_equals_eager_launches(pkg, prec, monkeypatch):
             assert np.array_equal(a[key], b[key]), key
         for u, v in zip(a["raw"], b["raw"]):
             assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_single_launch_small_replica_als(pkg, prec, monkeypatch):
+    """Small replicas (Q = 20) run their whole CP-ALS in one launch; the result
+    matches the oracle and the multi-launch path (OCTEN_ALS_FUSED=0), and an
+    append issues far fewer launches."""
+    from tests.test_gpu_parity import check_update, run_gpu
+
+    case = Case(100, 100, 5, 4, 20, 5, 40, (20, 10), 50, prec=prec, seed=24)
+    d = case.make()
+    _, ref = case.oracle_run(d)
+    n0 = pkg.launch_count()
+    g, fused = run_gpu(pkg, case, d)
+    g.close()
+    n_fused = pkg.launch_count() - n0
+    check_update(case, d, fused, ref)
+    monkeypatch.setenv("OCTEN_ALS_FUSED", "0")
+    n1 = pkg.launch_count()
+    h, multi = run_gpu(pkg, case, d)
+    h.close()
+    n_multi = pkg.launch_count() - n1
+    check_update(case, d, multi, ref)
+    assert n_fused * 4 < n_multi, (n_fused, n_multi)
+    for a, b in zip(fused, multi):
+        for key in ("A", "B", "C"):
+            assert np.allclose(a[key], b[key], rtol=1e-3, atol=1e-4), key
