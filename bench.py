@@ -436,6 +436,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--replay", type=int, default=0,
+                    help="replay a stream of this many slices through appends of the workload's "
+                         "batch size (the scalability runs; e.g. --workload q3_100 --replay 1000000)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one append of --slices slices on the workload's shapes with 4 existing "
                          "slices, kernels launched one by one (small case for profiler captures)")
@@ -455,6 +458,8 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, wl, world, rank)
+    if args.replay:
+        return main_replay(args, wl)
     if args.profile_case:
         return main_profile_case(args, wl)
     if args.compress_only:
@@ -547,6 +552,65 @@ def main():
         import paper_1807_01350_gb300 as pkg
         line["parity"] = smp.gpu_parity(pkg, args.prec)
     print(json.dumps(line), flush=True)
+
+
+def main_replay(args, wl):
+    """Algorithm 1 over a long stream (the scalability replay of Sec. "[Q3]
+    Scalability Evaluation"): init from the workload's existing slices, then
+    appends of its batch size until --replay slices in all.  Slices are drawn on
+    the GPU a window at a time (outside the timed appends); each window's
+    appends are timed with CUDA events, so the time per append along the stream
+    shows how the cost grows with K."""
+    import torch
+
+    from paper_1807_01350_gb300 import build as B
+    B.build()
+    import paper_1807_01350_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    K, t, t_old = args.replay, wl.batch, wl.t_old
+    A, B_, C = factors(wl.I, wl.J, K, wl.R, args.seed, cond=wl.cond, big_frac=wl.big_frac)
+    U, V = projections(wl.I, wl.J, wl.P, wl.Q, wl.S, args.seed, args.prec)
+    W0 = time_projection(t_old, wl.P, wl.Q, wl.S, args.seed, -1)
+    A0, B0, C0 = init_factors(A, B_, C[:t_old], 0.01, args.seed)
+    dt = torch.float32 if args.prec == "fp32" else torch.bfloat16
+    f32 = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=dev)
+    g = pkg.Octen(wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.als_iters, args.prec)
+    g.init(slice_batch_torch(A, B_, C, 0, t_old, wl.noise, args.seed, dev, dt), f32(U), f32(V),
+           f32(W0), f32(A0), f32(B0), f32(C0))
+    window = 1000   # appends per timed window
+    k, b, total_ms, windows = t_old, 0, 0.0, []
+    with ClockSampler(0) as clk:
+        while k + t <= K:
+            n = min(window, (K - k) // t)
+            X = slice_batch_torch(A, B_, C, k, k + n * t, wl.noise, args.seed, dev, dt)
+            Ws = [f32(time_projection(t, wl.P, wl.Q, wl.S, args.seed, b + i)) for i in range(n)]
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for i in range(n):
+                g.append(X[i * t:(i + 1) * t], Ws[i])
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            total_ms += ms
+            k += n * t
+            b += n
+            windows.append([k, round(ms / n, 4)])
+            del X, Ws
+    g.close()
+    slices = k - t_old
+    print(json.dumps({
+        "metric": METRIC, "value": round(slices / (total_ms / 1e3), 3), "unit": "slices/s",
+        "n_gpus": 1, "steps": b, "ms_per_step": round(total_ms / b, 4),
+        "higher_is_better": True, "dtype": args.prec, "data": "synthetic planted-CP slices (seeded)",
+        "config": {"workload": wl.name, "I": wl.I, "J": wl.J, "R": wl.R, "P": wl.P, "Q": wl.Q,
+                   "S": wl.S, "batch_slices": t, "existing_slices": t_old, "K": k,
+                   "als_iters": wl.als_iters},
+        "clocks": clk.summary(),
+        "replay": {"note": "time per append (ms) after each window of appends, by slices so far",
+                   "ms_per_append_by_K": windows}}), flush=True)
 
 
 def main_profile_case(args, wl):

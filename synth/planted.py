@@ -75,6 +75,18 @@ WORKLOADS = {
     # 4000 x 4000 slices, rank 32, 20 % of slices 10x larger, 32 x 16 slices
     "c4": Workload("c4_fp8_4000x4000_P16_Q256_R32", 4000, 4000, 64, 16, 32,
                    16, 256, 32, 32, 30, "fp8", 0.01, big_frac=0.2),
+    # scalability replay (Sec. "[Q3] Scalability Evaluation"): small slices,
+    # a long time mode, 10 % of it as the existing tensor, batches of 10.  The
+    # paper does not give P, Q, S, R for these runs; the 100 x 100 one takes the
+    # small dense workload's, the smaller ones scale them down.  `updates` is
+    # the default replay length (a stream of 10^4 slices); bench.py --replay
+    # extends it up to 10^6.
+    "q3_20": Workload("q3_fp32_20x20_P4_Q8_R3", 20, 20, 1000, 10, 900,
+                      4, 8, 3, 3, 50, "fp32", 0.01),
+    "q3_50": Workload("q3_fp32_50x50_P4_Q12_R4", 50, 50, 1000, 10, 900,
+                      4, 12, 4, 4, 50, "fp32", 0.01),
+    "q3_100": Workload("q3_fp32_100x100_P4_Q20_R5", 100, 100, 1000, 10, 900,
+                       4, 20, 5, 5, 50, "fp32", 0.01),
 }
 
 

@@ -82,3 +82,17 @@ def test_full_size_update_matches_oracle(pkg, name):
     else:
         _, ref = case.oracle_run(d)
         check_update(case, d, gpu, ref)
+
+
+def test_long_stream_of_small_slices(pkg):
+    """The scalability setting (Sec. "[Q3] Scalability Evaluation"): 20 x 20
+    slices, 10 % of the stream as the existing tensor, then 50 appends of 10
+    slices (the single-launch CP-ALS path); every append against the oracle."""
+    from tests.test_gpu_parity import check_update, run_gpu
+
+    case = Case(20, 20, 3, 4, 8, 3, 100, (10,) * 50, 50, prec="fp32", seed=55)
+    d = case.make()
+    g, gpu = run_gpu(pkg, case, d)
+    g.close()
+    _, ref = case.oracle_run(d)
+    check_update(case, d, gpu, ref)
