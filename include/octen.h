@@ -81,8 +81,13 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
  * otherwise) into the P summaries Y_p with U_all, V_all and W_old (t_old x Qd),
  * stores U_all, V_all (rounded per precision), takes A0 (I x R), B0 (J x R),
  * C0 (t_old x R) as the existing factors, forms G_p = W_old,p^T C0 and
- * precomputes the lift operators of Eq. 7.  All array arguments are required.
- * May be called once per context (ESTATE otherwise). */
+ * precomputes the lift operators of Eq. 7.  With C0 == NULL the existing
+ * decomposition is computed instead: CP-ALS of X_old (the model
+ * X_old[k][i][j] = sum_r A[i][r] B[j][r] C[k][r]) from the starting guesses A0,
+ * B0, with the same sweeps as the replica CP (als_iters sweeps: C, A, B, A and
+ * B normalised to unit l2, a final C update); it needs a workspace of about
+ * 4 t_old (I + J) R bytes.  The other arrays are required.  May be called once
+ * per context (ESTATE otherwise). */
 octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
                         const float *U_all, const float *V_all, const float *W_old,
                         const float *A0, const float *B0, const float *C0);

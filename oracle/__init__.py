@@ -9,6 +9,7 @@ from .octen import (  # noqa: F401
     align,
     compress,
     cp_als,
+    decompose_existing,
     eq4_identifiable,
     eq8_min_replicas,
     fit,

@@ -149,6 +149,14 @@ def cp_als(X: np.ndarray, A0: np.ndarray, B0: np.ndarray, iters: int,
     return A, B, C
 
 
+def decompose_existing(X_old: np.ndarray, A0: np.ndarray, B0: np.ndarray, iters: int):
+    """The existing decomposition when none is supplied (the paper assumes one
+    exists, Sec. "Problem Formulation"): cp_als of the existing tensor, whose
+    slices X_old[k] are I x J, in the mode order (i, j, k) of the model
+    X_old[k][i][j] = sum_r A[i][r] B[j][r] C[k][r], from the guesses A0, B0."""
+    return cp_als(np.transpose(np.asarray(X_old, dtype=np.float64), (1, 2, 0)), A0, B0, iters)
+
+
 # ----------------------------------------------------------------------------
 # Sec. "Factor match for identifiability" (Eq. 5, Algorithm 1 match loop)
 # ----------------------------------------------------------------------------
@@ -317,11 +325,15 @@ class OctenOracle:
         return [replica_block(M_all, p, self.Q, self.S) for p in range(self.P)]
 
     def init(self, X_old, U_all, V_all, W_old, A0, B0, C0):
-        """Summaries of the existing tensor plus its existing decomposition."""
+        """Summaries of the existing tensor plus its existing decomposition
+        (computed by decompose_existing from A0, B0 when C0 is None)."""
         self.U = self._split(np.asarray(U_all, dtype=np.float64))
         self.V = self._split(np.asarray(V_all, dtype=np.float64))
         W = self._split(np.asarray(W_old, dtype=np.float64))
         self.Y = [compress(X_old, self.U[p], self.V[p], W[p]) for p in range(self.P)]
+        if C0 is None:
+            # A0, B0 are starting guesses for a CP-ALS of the existing tensor
+            A0, B0, C0 = decompose_existing(X_old, A0, B0, self.als_iters)
         self.A = np.asarray(A0, dtype=np.float64).copy()
         self.B = np.asarray(B0, dtype=np.float64).copy()
         self.C = np.asarray(C0, dtype=np.float64).copy()

@@ -168,7 +168,9 @@ class Octen:
         if st != 0:
             raise OctenError(st, self._lib.octen_last_error(self._h).decode())
 
-    def init(self, X_old, U_all, V_all, W_old, A0, B0, C0):
+    def init(self, X_old, U_all, V_all, W_old, A0, B0, C0=None):
+        """octen_init; with C0 None the existing decomposition is computed on
+        the GPU by CP-ALS of X_old from the starting guesses A0, B0."""
         keep: list = []
         t_old = int(X_old.shape[0])
         self._check(self._lib.octen_init(

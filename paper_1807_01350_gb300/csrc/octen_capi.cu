@@ -508,8 +508,10 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
                         const float *B0, const float *C0) {
   if (!x) return OCTEN_EINVAL;
   if (x->initialized) return x->fail(OCTEN_ESTATE, "octen_init called twice");
-  if (!X_old || !U_all || !V_all || !W_old || !A0 || !B0 || !C0 || t_old < 1)
-    return x->fail(OCTEN_EINVAL, "octen_init: every array is required and t_old >= 1");
+  if (!X_old || !U_all || !V_all || !W_old || !A0 || !B0 || t_old < 1)
+    return x->fail(OCTEN_EINVAL,
+                   "octen_init: X_old, U_all, V_all, W_old, A0, B0 are required and t_old >= 1");
+  const bool decompose = C0 == nullptr;   // A0, B0 are starting guesses
   const octen_config &c = x->cfg;
   const int Qd = x->Qd;
   // projections: round once to the operand formats, build the operand layouts
@@ -540,11 +542,34 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
       cudaStreamSynchronize(x->st);
     }
   }
-  // existing factors and G_p = W_old,p^T C_old
+  // existing factors (given, or a CP-ALS of X_old from A0, B0) and G_p = W_old,p^T C_old
   if (!ensure_c_capacity(x, t_old)) return x->fail(OCTEN_ENOMEM, "C");
-  cudaMemcpyAsync(x->A, A0, (size_t)c.I * c.R * 4, cudaMemcpyDefault, x->st);
-  cudaMemcpyAsync(x->B, B0, (size_t)c.J * c.R * 4, cudaMemcpyDefault, x->st);
-  cudaMemcpyAsync(x->C, C0, (size_t)t_old * c.R * 4, cudaMemcpyDefault, x->st);
+  if (decompose) {
+    const void *Xd = x->stage_in(X_old, t_old * slice, 2);
+    const float *A0d = static_cast<const float *>(x->stage_in(A0, (size_t)c.I * c.R * 4, 0));
+    const float *B0d = static_cast<const float *>(x->stage_in(B0, (size_t)c.J * c.R * 4, 1));
+    if (!Xd || !A0d || !B0d) return x->fail(OCTEN_ENOMEM, "staging X_old, A0, B0");
+    float *work = nullptr;
+    const size_t wf = dense_cp_work_floats(t_old, c.I, c.J, x->RT);
+    if (cudaMalloc(&work, wf * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return x->fail(OCTEN_ENOMEM, "dense CP-ALS workspace (%zu bytes)", wf * sizeof(float));
+    }
+    DenseCpArgs a{};
+    a.X = Xd; a.xt = x->xin; a.K = t_old; a.I = c.I; a.J = c.J; a.R = c.R;
+    a.iters = c.als_iters; a.A0 = A0d; a.B0 = B0d;
+    a.A_out = x->A; a.B_out = x->B; a.C_out = x->C; a.work = work;
+    a.splitk = x->splitk; a.splitk_floats = octen_ctx::kSplitkFloats;
+    a.status = x->dstatus; a.st = x->st;
+    dense_cp(a, x->RT);
+    s = x->sync_check("init decomposition");
+    cudaFree(work);
+    if (s != OCTEN_OK) return s;
+  } else {
+    cudaMemcpyAsync(x->A, A0, (size_t)c.I * c.R * 4, cudaMemcpyDefault, x->st);
+    cudaMemcpyAsync(x->B, B0, (size_t)c.J * c.R * 4, cudaMemcpyDefault, x->st);
+    cudaMemcpyAsync(x->C, C0, (size_t)t_old * c.R * 4, cudaMemcpyDefault, x->st);
+  }
   update_g(Wd, x->C, t_old, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
   s = x->sync_check("init summaries");
   if (s != OCTEN_OK) return s;

@@ -191,6 +191,24 @@ void align_replicas(const float *At, const float *Bt, const float *Ct, const flo
                     const float *PB, int P, int Q, int S, int R, int RT, float *Ah,
                     float *Bh, float *Ch, int *perm, double *scales, double *scratch,
                     cudaStream_t st);
+// Dense CP-ALS of the existing tensor X (K x I x J, [k][i][j], element type
+// xt) from the initial guesses A0 (I x R), B0 (J x R): `iters` sweeps as in the
+// replica CP-ALS, results into A_out (I x R), B_out (J x R), C_out (K x R).
+// `work` holds dense_cp_work_floats(K, I, J, RT) floats.
+struct DenseCpArgs {
+  const void *X; Elem xt;
+  int64_t K, I, J;
+  int R, iters;
+  const float *A0, *B0;
+  float *A_out, *B_out, *C_out;
+  float *work;
+  float *splitk; size_t splitk_floats;
+  int *status;
+  cudaStream_t st;
+};
+size_t dense_cp_work_floats(int64_t K, int64_t I, int64_t J, int RT);
+void dense_cp(const DenseCpArgs &a, int RT);
+
 // doubles of scratch align_replicas needs
 size_t align_scratch_doubles(int P, int RT);
 

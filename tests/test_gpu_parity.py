@@ -250,3 +250,35 @@ def test_append_many_uneven_streams(pkg):
         assert fms((A, B, C), (ref[0]["A"], ref[0]["B"], ref[0]["C"])) > TOL["bf16"]["fms"]
         single.close()
         g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_init_decomposition_matches_oracle(pkg, prec):
+    """octen_init without C0: the existing decomposition is a CP-ALS of X_old
+    on the GPU from the guesses A0, B0; it and the update that follows match
+    the oracle doing the same (oracle.decompose_existing)."""
+    case = Case(60, 50, 4, 3, 12, 3, 30, (10,), 30, prec=prec, seed=62)
+    d = case.make()
+    g = pkg.Octen(case.I, case.J, case.R, case.P, case.Q, case.S, case.iters, case.prec)
+    g.init(slices(d["X"][:case.t_old], case.prec), dev(d["U"]), dev(d["V"]), dev(d["W"][0]),
+           dev(d["A0"]), dev(d["B0"]), None)
+    A, B, C = g.factors()
+    Ar, Br, Cr = oracle.decompose_existing(d["X"][:case.t_old], d["A0"], d["B0"], case.iters)
+    tol = TOL[prec]
+    for name, x, y in (("A", A, Ar), ("B", B, Br), ("C", C, Cr)):
+        assert rel(x, y) < tol["F"], (name, rel(x, y))
+    f_gpu = g.fit(slices(d["X"][:case.t_old], case.prec))
+    f_ref = oracle.fit(d["X"][:case.t_old], Ar, Br, Cr)
+    assert abs(f_gpu - f_ref) < tol["fit"], (f_gpu, f_ref)
+    assert f_ref > 0.98
+    # the update from there
+    o = oracle.OctenOracle(case.I, case.J, case.R, case.P, case.Q, case.S, case.iters)
+    o.init(d["X"][:case.t_old], d["U"], d["V"], d["W"][0], d["A0"], d["B0"], None)
+    k = case.t_old
+    g.append(slices(d["X"][k:k + 10], case.prec), dev(d["W"][1]))
+    o.append(d["X"][k:k + 10], d["W"][1])
+    A, B, C = g.factors()
+    assert fms((A, B, C), (o.A, o.B, o.C)) > tol["fms"]
+    assert abs(g.fit(slices(d["X"][:k + 10], case.prec))
+               - oracle.fit(d["X"][:k + 10], o.A, o.B, o.C)) < tol["fit"]
+    g.close()

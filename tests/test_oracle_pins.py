@@ -394,3 +394,22 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     monkeypatch.setattr(oracle, "align", no_sign)
     with pytest.raises(AssertionError):
         test_align_recovers_known_permutation_and_scales()
+
+
+def test_existing_decomposition_recovers_planted_factors():
+    """decompose_existing (the init without a supplied decomposition) on an exact
+    rank-R tensor X_old[k][i][j] = sum_r A[i][r] B[j][r] C[k][r], from perturbed
+    guesses, reproduces the tensor (fit 1) and its factors up to permutation and
+    scale (FMS 1)."""
+    rng = np.random.default_rng(61)
+    I, J, K, R = 12, 10, 9, 3
+    A, B, C = rng.standard_normal((I, R)), rng.standard_normal((J, R)), rng.standard_normal((K, R))
+    X = np.stack([(A * C[k]) @ B.T for k in range(K)])   # [k][i][j]
+    A0 = A + 0.05 * rng.standard_normal(A.shape)
+    B0 = B + 0.05 * rng.standard_normal(B.shape)
+    Ah, Bh, Ch = oracle.decompose_existing(X, A0, B0, 60)
+    assert oracle.fit(X, Ah, Bh, Ch) > 1 - 1e-9
+    assert fms((Ah, Bh, Ch), (A, B, C)) > 1 - 1e-9
+    # the mode order matters: the same guesses on the (k, i, j) order fail to
+    # fit, the shapes do not even agree
+    assert Ah.shape == (I, R) and Bh.shape == (J, R) and Ch.shape == (K, R)
