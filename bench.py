@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from synth import WORKLOADS, factors, init_factors, projections, slice_batch  # noqa: E402
-from synth import round_to, slice_batch_torch, time_projection  # noqa: E402
+from synth import round_to, slice_batch_torch, time_projection, uneven_streams  # noqa: E402
 
 METRIC = "new slices/sec (compress+CP update) at fit >= oracle-1e-3; BF16/FP8 vs FP32"
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max clock
@@ -436,6 +436,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--uneven-streams", type=int, default=0,
+                    help="the batched uneven-streams workload with this many streams (64 in the "
+                         "configuration): one append per stream per step through octen_append_many")
     ap.add_argument("--replay", type=int, default=0,
                     help="replay a stream of this many slices through appends of the workload's "
                          "batch size (the scalability runs; e.g. --workload q3_100 --replay 1000000)")
@@ -458,6 +461,8 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, wl, world, rank)
+    if args.uneven_streams:
+        return main_uneven(args)
     if args.replay:
         return main_replay(args, wl)
     if args.profile_case:
@@ -552,6 +557,92 @@ def main():
         import paper_1807_01350_gb300 as pkg
         line["parity"] = smp.gpu_parity(pkg, args.prec)
     print(json.dumps(line), flush=True)
+
+
+def main_uneven(args):
+    """The batched uneven-streams workload: n independent decompositions of
+    different shapes, ranks and batch sizes, each on its own CUDA stream; a step
+    is one append on every stream through octen_append_many (all enqueued
+    before any is waited for).  Compared with the same n updates in FP32, one
+    after another (octen_append per stream)."""
+    import torch
+
+    from paper_1807_01350_gb300 import build as B
+    B.build()
+    import paper_1807_01350_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfgs = uneven_streams(args.uneven_streams, args.seed)
+    f32 = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=dev)
+    streams = []   # one CUDA stream per decomposition, alive as long as its context
+
+    def make(prec):
+        dt = torch.float32 if prec == "fp32" else torch.bfloat16
+        ctxs, batches, ws = [], [], []
+        streams.clear()
+        for wl, sd in cfgs:
+            A, B_, C = factors(wl.I, wl.J, wl.t_old + 2 * wl.batch, wl.R, sd)
+            U, V = projections(wl.I, wl.J, wl.P, wl.Q, wl.S, sd, prec)
+            A0, B0, C0 = init_factors(A, B_, C[:wl.t_old], 0.01, sd)
+            streams.append(torch.cuda.Stream())
+            g = pkg.Octen(wl.I, wl.J, wl.R, wl.P, wl.Q, wl.S, wl.als_iters, prec,
+                          stream=streams[-1])
+            X0 = slice_batch_torch(A, B_, C, 0, wl.t_old, wl.noise, sd, dev, dt)
+            g.init(X0, f32(U), f32(V), f32(time_projection(wl.t_old, wl.P, wl.Q, wl.S, sd, -1)),
+                   f32(A0), f32(B0), f32(C0))
+            del X0
+            ctxs.append(g)
+            batches.append([slice_batch_torch(A, B_, C, wl.t_old + b * wl.batch,
+                                              wl.t_old + (b + 1) * wl.batch, wl.noise, sd, dev, dt)
+                            for b in range(2)])
+            ws.append([f32(time_projection(wl.batch, wl.P, wl.Q, wl.S, sd, b)) for b in range(2)])
+        torch.cuda.synchronize()
+        return ctxs, batches, ws
+
+    slices = sum(wl.batch for wl, _ in cfgs)
+    ctxs, batches, ws = make("bf16")
+    warm, steps = max(args.warmup, 3), args.steps
+    for s in range(warm):
+        pkg.append_many(ctxs, [b[s % 2] for b in batches], [w[s % 2] for w in ws])
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        for s in range(steps):
+            pkg.append_many(ctxs, [b[s % 2] for b in batches], [w[s % 2] for w in ws])
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+    for g in ctxs:
+        g.close()
+    del ctxs, batches, ws
+    torch.cuda.empty_cache()
+    # the FP32 comparison: the same streams, one update after another
+    ctxs, batches, ws = make("fp32")
+    for g, b, w in zip(ctxs, batches, ws):
+        g.append(b[0], w[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, b, w in zip(ctxs, batches, ws):
+        g.append(b[1], w[1])
+    torch.cuda.synchronize()
+    sec32 = time.perf_counter() - t0
+    for g in ctxs:
+        g.close()
+    value = slices * steps / sec
+    print(json.dumps({
+        "metric": METRIC, "value": round(value, 3), "unit": "slices/s", "n_gpus": 1,
+        "steps": steps, "warmup": warm, "ms_per_step": round(1e3 * sec / steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic planted-CP slices (seeded), resident in HBM",
+        "config": {"workload": f"c5_uneven_streams_x{len(cfgs)}", "streams": len(cfgs),
+                   "slices_per_step": slices,
+                   "shapes": [[wl.I, wl.J, wl.R, wl.batch, wl.Q] for wl, _ in cfgs[:8]],
+                   "parallelism": "one CUDA stream per decomposition, octen_append_many"},
+        "clocks": clk.summary(),
+        "fp32_sequential": {"value": round(slices / sec32, 3), "unit": "slices/s",
+                            "ms_per_step": round(1e3 * sec32, 3),
+                            "note": "the same updates in fp32, octen_append one stream after another"},
+        "speedup_vs_fp32_sequential": round(value / (slices / sec32), 3)}), flush=True)
 
 
 def main_replay(args, wl):

@@ -16,4 +16,5 @@ from .planted import (  # noqa: F401
     slice_batch,
     slice_batch_torch,
     time_projection,
+    uneven_streams,
 )

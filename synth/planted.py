@@ -90,6 +90,28 @@ WORKLOADS = {
 }
 
 
+def uneven_streams(n: int = 64, seed: int = 0) -> list:
+    """The batched uneven-streams workload: n independent planted-CP streams with
+    I, J uniform in [200, 3000] (rounded up to a multiple of 8, the 16-byte row
+    pitch the TMA loads of bf16 slices need), rank R uniform in [5, 32], batch
+    size t uniform in [5, 50], compressed size Q uniform in [20, 150], P = 8,
+    S = min(R, Q // 2), 30 sweeps, bf16 slices with 1 % noise; 5 t existing
+    slices per stream.  Each entry is a Workload plus its own seed."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 5]))
+    out = []
+    for s in range(n):
+        I = int(-(-int(rng.integers(200, 3001)) // 8) * 8)
+        J = int(-(-int(rng.integers(200, 3001)) // 8) * 8)
+        R = int(rng.integers(5, 33))
+        t = int(rng.integers(5, 51))
+        Q = int(rng.integers(20, 151))
+        S = min(R, Q // 2)
+        wl = Workload(f"c5_stream{s}_{I}x{J}_P8_Q{Q}_R{R}_t{t}", I, J, 5 * t, t, 1,
+                      8, Q, S, R, 30, "bf16", 0.01)
+        out.append((wl, seed * 1000 + s))
+    return out
+
+
 def _conditioned(rows: int, R: int, cond: float, rng: np.random.Generator) -> np.ndarray:
     q, _ = np.linalg.qr(rng.standard_normal((rows, R)))
     h, _ = np.linalg.qr(rng.standard_normal((R, R)))
