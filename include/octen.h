@@ -97,9 +97,12 @@ octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
  * (t x Qd): Y_p += Z_p, CP-ALS of every replica warm-started from U_p^T A,
  * V_p^T B, anchor matching, lift of A and B, t new rows of C.  Limit t <= 64.
  * The CP-ALS of the replicas is recorded once as a CUDA graph (on a private
- * stream, at the first append made with the stage timers off) and replayed on
+ * stream, at the second append made with the stage timers off) and replayed on
  * the context's stream at every later such append; environment variable
- * OCTEN_GRAPH=0 issues its launches one by one instead. */
+ * OCTEN_GRAPH=0 issues its launches one by one instead.  The first call for
+ * each tensor-core GEMM shape times its candidate tile configurations (only
+ * ones that give bit-identical results) and keeps the fastest for the process;
+ * OCTEN_AUTOTUNE=0 keeps the defaults. */
 octen_status octen_append(octen_ctx *ctx, const void *X_new, int64_t t, const float *W_new);
 
 /* One append on each of n independent decompositions (many streams with

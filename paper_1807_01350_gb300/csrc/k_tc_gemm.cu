@@ -14,6 +14,12 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <array>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+
 #include "octen_internal.cuh"
 
 namespace octen {
@@ -630,6 +636,81 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner.  For every GEMM shape the first call (outside stream capture)
+// times the candidate launch configurations with CUDA events on the caller's
+// stream and keeps the fastest for the rest of the process.  Only choices that
+// leave every output bit unchanged are tuned: the K atoms per pipeline stage
+// (the MMAs run in the same order either way) and, for mode 2, the N tile (each
+// output's K sum is the same sequence whatever tile it falls in).  The split-K
+// count, which changes the summation, is fixed by the caller.  The timing
+// launches write the same outputs as the final one and are not counted as
+// launches.  OCTEN_AUTOTUNE=0 keeps the defaults.
+struct TuneChoice {
+  int katoms, BN;
+};
+
+std::mutex g_tune_mu;
+std::map<std::array<int64_t, 8>, TuneChoice> g_tune;
+
+bool autotune_enabled() {
+  const char *v = getenv("OCTEN_AUTOTUNE");
+  return !(v && strcmp(v, "0") == 0);
+}
+
+bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;   // be safe: no synchronising work
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// launch(choice) issues one GEMM with that choice and returns false if refused.
+template <class Launch>
+TuneChoice tuned(const std::array<int64_t, 8> &key, const TuneChoice *cand, int ncand,
+                 cudaStream_t st, Launch launch) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  if (ncand < 2 || !autotune_enabled() || stream_capturing(st)) return cand[0];
+  const uint64_t l0 = octen_launch_count(), t0 = octen_tc_launch_count();
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  TuneChoice best = cand[0];
+  float best_ms = 3.4e38f;
+  for (int c = 0; c < ncand; ++c) {
+    if (!launch(cand[c])) {   // warm-up (and the check that it runs)
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, st);
+    const bool ok = launch(cand[c]) && launch(cand[c]);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  adjust_launch_counts(-(int64_t)(octen_launch_count() - l0),
+                       -(int64_t)(octen_tc_launch_count() - t0));
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+
 }  // namespace
 
 bool tc_supported() {
@@ -646,20 +727,26 @@ bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st) {
   const bool fp8 = a.tx == Elem::E4M3;
   const int64_t M = a.t * a.I;
   if (M > (1 << 30) || a.J > (1 << 30)) return false;
-  CUtensorMap ma, mb;
-  const int BN = 256;
-  if (!make_map(&ma, a.X, fp8, a.J, M, kBM) || !make_map(&mb, a.Vt, fp8, a.J, a.Qd, BN))
+  CUtensorMap ma, mb256, mb128;
+  if (!make_map(&ma, a.X, fp8, a.J, M, kBM) || !make_map(&mb256, a.Vt, fp8, a.J, a.Qd, 256) ||
+      !make_map(&mb128, a.Vt, fp8, a.J, a.Qd, 128))
     return false;
-  TcShape sh{};
-  sh.ksplit = 1;
-  sh.M = static_cast<int>(M); sh.N = a.Qd; sh.K = static_cast<int>(a.J); sh.BN = BN;
-  sh.zdiv = 1; sh.a_hi = 0; sh.a_lo = 0; sh.b_hi = 0; sh.b_lo = 0;
-  sh.a_stream = 1;   // the slices are read once
-  sh.katoms = 1;
   Mode2TcEpi epi{static_cast<__nv_bfloat16 *>(a.T), a.slice_scale, a.I, a.P, a.Q, a.S,
                  a.I % 8 == 0};
-  return fp8 ? launch_tc<1>(ma, mb, sh, 1, epi, status, st)
-             : launch_tc<0>(ma, mb, sh, 1, epi, status, st);
+  auto launch = [&](const TuneChoice &c) {
+    TcShape sh{};
+    sh.ksplit = 1;
+    sh.M = static_cast<int>(M); sh.N = a.Qd; sh.K = static_cast<int>(a.J); sh.BN = c.BN;
+    sh.zdiv = 1; sh.a_hi = 0; sh.a_lo = 0; sh.b_hi = 0; sh.b_lo = 0;
+    sh.a_stream = 1;   // the slices are read once
+    sh.katoms = c.katoms;
+    const CUtensorMap &mb = c.BN == 256 ? mb256 : mb128;
+    return fp8 ? launch_tc<1>(ma, mb, sh, 1, epi, status, st)
+               : launch_tc<0>(ma, mb, sh, 1, epi, status, st);
+  };
+  static const TuneChoice cand[] = {{1, 256}, {2, 128}, {1, 128}};
+  const std::array<int64_t, 8> key{2, fp8 ? 1 : 0, M, a.Qd, a.J, a.I, a.P, a.Q};
+  return launch(tuned(key, cand, 3, st, launch));
 }
 
 bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
@@ -688,17 +775,33 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   if (!make_map(&ma, g.A, false, g.a_inner, g.a_rows, kBM) ||
       !make_map(&mb, g.B, false, g.b_inner, g.b_rows, g.BN))
     return false;
-  TcShape sh{};
-  sh.M = g.M; sh.N = g.N; sh.K = g.K; sh.BN = g.BN;
-  sh.zdiv = 1; sh.a_hi = g.a_rows_per_z; sh.a_lo = 0; sh.b_hi = g.b_rows_per_z; sh.b_lo = 0;
-  sh.a_stream = g.a_stream ? 1 : 0;
-  sh.katoms = g.katoms == 2 ? 2 : 1;
-  const int ks = tc_gemm_splits(g.K, g.ksplit, sh.katoms);
-  sh.ksplit = ks;
-  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT, g.Dh};
+  // the split count is fixed by the caller's K atoms (it sets the summation)
+  const int katoms0 = g.katoms == 2 ? 2 : 1;
+  const int ks = tc_gemm_splits(g.K, g.ksplit, katoms0);
   if (g.m1_part && (g.BN != 32 || g.Q % 32 || ks > 1)) return false;
   if (ks > 1 && (g.N > g.BN)) return false;
-  return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve);
+  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT, g.Dh};
+  auto launch = [&](const TuneChoice &c) {
+    TcShape sh{};
+    sh.M = g.M; sh.N = g.N; sh.K = g.K; sh.BN = g.BN;
+    sh.zdiv = 1; sh.a_hi = g.a_rows_per_z; sh.a_lo = 0; sh.b_hi = g.b_rows_per_z; sh.b_lo = 0;
+    sh.a_stream = g.a_stream ? 1 : 0;
+    sh.katoms = c.katoms;
+    sh.ksplit = ks;
+    return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve);
+  };
+  // with split-K the other atom count is a candidate only if it cuts K at the
+  // same places (the splits set the summation)
+  const int katoms1 = katoms0 == 2 ? 1 : 2;
+  auto split_elems = [&](int k) {
+    const int nk = (g.K + 64 * k - 1) / (64 * k);
+    return ((nk + ks - 1) / ks) * 64 * k;
+  };
+  const TuneChoice cand[] = {{katoms0, g.BN}, {katoms1, g.BN}};
+  const int ncand = ks > 1 && split_elems(katoms0) != split_elems(katoms1) ? 1 : 2;
+  const std::array<int64_t, 8> key{1, g.M, g.N, g.K, g.batch, ks, g.Dh != nullptr,
+                                   g.m1_part != nullptr};
+  return launch(tuned(key, cand, ncand, st, launch));
 }
 
 int tc_gemm_splits(int K, int ksplit, int katoms) {

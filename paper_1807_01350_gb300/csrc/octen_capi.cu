@@ -18,8 +18,9 @@ static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_tc_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_tc_launch() { g_tc_launches.fetch_add(1, std::memory_order_relaxed); }
-// launches recorded into a graph are counted when the graph runs, not when captured
-static void add_launches(int64_t n, int64_t ntc) {
+// launches recorded into a graph are counted when the graph runs, not when
+// captured; the autotuner's timing launches are not counted
+void adjust_launch_counts(int64_t n, int64_t ntc) {
   g_launches.fetch_add(static_cast<uint64_t>(n), std::memory_order_relaxed);
   g_tc_launches.fetch_add(static_cast<uint64_t>(ntc), std::memory_order_relaxed);
 }
@@ -89,8 +90,9 @@ struct octen_ctx {
   double *dfit = nullptr;
 
   // The replica CP-ALS of an append (about 200 launches on fixed buffers) runs
-  // as one CUDA graph: captured on a private stream at the first append with
-  // the stage timers off, replayed on the context's stream afterwards.
+  // as one CUDA graph: captured on a private stream at the second append with
+  // the stage timers off (the first one runs eagerly, so that the GEMM
+  // autotuner has timed its shapes), replayed on the context's stream afterwards.
   // OCTEN_GRAPH=0 keeps the launches eager.
   bool use_graph = true;
   bool als_graph_tried = false;
@@ -98,6 +100,7 @@ struct octen_ctx {
   cudaGraphExec_t als_exec = nullptr;
   int64_t als_graph_launches = 0, als_graph_tc = 0;
   bool als_graph_layouts = false;   // the graph was recorded with Xa / Xc given
+  int64_t appends = 0;              // appends enqueued so far
 
   // per-batch scratch, grown on demand
   DevBuf Tbuf, T2buf, Wbuf, X8buf, xscale, stage[4], fitpart;
@@ -606,7 +609,7 @@ void capture_als(octen_ctx *x, AlsBuffers ab) {
   const cudaError_t e = cudaStreamEndCapture(x->cap_st, &g);
   const int64_t dl = (int64_t)(octen_launch_count() - l0);
   const int64_t dt = (int64_t)(octen_tc_launch_count() - t0);
-  add_launches(-dl, -dt);   // recorded, not run
+  adjust_launch_counts(-dl, -dt);   // recorded, not run
   if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&x->als_exec, g, 0) == cudaSuccess) {
     x->als_graph_launches = dl;
     x->als_graph_tc = dt;
@@ -653,10 +656,10 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   if (x->timing) { mk.fn = &octen_ctx::mark_cb; mk.arg = x; }
   bool replayed = false;
   if (!x->timing && x->use_graph) {
-    if (!x->als_exec && !x->als_graph_tried) capture_als(x, ab);
+    if (!x->als_exec && !x->als_graph_tried && x->appends > 0) capture_als(x, ab);
     if (x->als_exec && x->als_graph_layouts == ab.layouts_ready) {
       if (cudaGraphLaunch(x->als_exec, x->st) == cudaSuccess) {
-        add_launches(x->als_graph_launches, x->als_graph_tc);
+        adjust_launch_counts(x->als_graph_launches, x->als_graph_tc);
         replayed = true;
       } else {
         cudaGetLastError();
@@ -690,6 +693,7 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
               x->splitk, octen_ctx::kSplitkFloats, C_new, x->dstatus, x->st);
   update_g(Wd, C_new, t, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
   x->mark(kStCsolve, 0);
+  ++x->appends;
   return OCTEN_OK;
 }
 

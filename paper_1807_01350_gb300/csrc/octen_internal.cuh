@@ -25,6 +25,8 @@ inline size_t elem_size(Elem e) { return e == Elem::F32 ? 4 : (e == Elem::BF16 ?
 
 // Counts every kernel launch issued through the launch helpers below.
 void count_launch();
+// Adds to the launch counters (negative: launches that did not do the work).
+void adjust_launch_counts(int64_t n, int64_t ntc);
 
 // Stages timed with CUDA events when a context has timing enabled.
 enum Stage : int {

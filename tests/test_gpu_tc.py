@@ -127,3 +127,23 @@ def test_single_launch_small_replica_als(pkg, prec, monkeypatch):
     for a, b in zip(fused, multi):
         for key in ("A", "B", "C"):
             assert np.allclose(a[key], b[key], rtol=1e-3, atol=1e-4), key
+
+
+def test_autotuned_gemms_give_bit_identical_results(pkg, monkeypatch):
+    """The GEMM autotuner only picks among configurations with identical
+    results: an update with the defaults (OCTEN_AUTOTUNE=0, run first so the
+    process-wide choices for these shapes are not yet made) equals the same
+    update with the tuned choices bit for bit."""
+    from tests.test_gpu_parity import run_gpu
+
+    case = Case(176, 152, 6, 3, 40, 8, 24, (16, 8, 16), 10, prec="bf16", seed=25)
+    d = case.make()
+    monkeypatch.setenv("OCTEN_AUTOTUNE", "0")
+    g, plain = run_gpu(pkg, case, d)
+    g.close()
+    monkeypatch.delenv("OCTEN_AUTOTUNE")
+    h, tuned = run_gpu(pkg, case, d)
+    h.close()
+    for a, b in zip(plain, tuned):
+        for key in ("Y", "A", "B", "C"):
+            assert np.array_equal(a[key], b[key]), key
