@@ -19,3 +19,12 @@ from .octen import (  # noqa: F401
     mttkrp,
     replica_block,
 )
+from .octen_n import (  # noqa: F401
+    OctenOracleN,
+    align_n,
+    compress_n,
+    cp_als_n,
+    fit_n,
+    khatri_rao_list,
+    mttkrp_n,
+)
