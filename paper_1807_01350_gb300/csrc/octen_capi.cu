@@ -338,62 +338,23 @@ octen_status compress_all(octen_ctx *x, const void *Xd, int64_t t, const float *
 // Qd > rows the stack has full column rank: L = (U Omega U^T)^-1 U, shape
 // rows x Qd (Omega weights the anchor columns by P).  Otherwise the distinct
 // rows have full row rank: L = U (U^T U)^-1, stored transposed (Qd x rows).
+LiftEnv lift_env(octen_ctx *x) {
+  const octen_config &c = x->cfg;
+  return LiftEnv{x->Qd, c.P, c.Q, c.S, c.R, x->RT, x->st, x->dstatus, x->e, x->splitk,
+                 octen_ctx::kSplitkFloats};
+}
+
 octen_status build_lift(octen_ctx *x, const float *Ur, int64_t rows, float *L, int &over) {
-  const int Qd = x->Qd;
-  over = Qd > rows ? 1 : 0;
-  const int n = over ? (int)rows : Qd;
-  float *Gm = nullptr;
-  if (cudaMalloc(&Gm, (size_t)n * n * sizeof(float)) != cudaSuccess) {
-    cudaGetLastError();
-    return x->fail(OCTEN_ENOMEM, "lift Gram (%d x %d)", n, n);
-  }
-  float *Uw = nullptr;
-  GemmArgs g{};
-  g.ta = Elem::F32; g.tb = Elem::F32; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
-  g.D = Gm; g.sDm = n; g.sDn = 1; g.M = n; g.N = n;
-  if (over) {
-    if (cudaMalloc(&Uw, (size_t)rows * Qd * sizeof(float)) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(Gm);
-      return x->fail(OCTEN_ENOMEM, "lift weights");
-    }
-    scale_columns(Ur, rows, Qd, x->cfg.S, (float)x->cfg.P, Uw, x->st);
-    g.A = Ur; g.sAm = Qd; g.sAk = 1;
-    g.B = Uw; g.sBn = Qd; g.sBk = 1;
-    g.K = Qd;
-    gemm_strided(g, x->st);
-    cholesky_f32(Gm, n, x->dstatus, x->st);
-    cudaMemcpyAsync(L, Ur, (size_t)rows * Qd * sizeof(float), cudaMemcpyDeviceToDevice, x->st);
-    chol_solve_f32(Gm, n, L, Qd, x->st);
-  } else {
-    g.A = Ur; g.sAm = 1; g.sAk = Qd;
-    g.B = Ur; g.sBn = 1; g.sBk = Qd;
-    g.K = (int)rows;
-    gemm_strided(g, x->st);
-    cholesky_f32(Gm, n, x->dstatus, x->st);
-    transpose_f32(Ur, rows, Qd, L, x->st);   // L <- U^T (Qd x rows)
-    chol_solve_f32(Gm, n, L, (int)rows, x->st);
-  }
-  octen_status s = x->sync_check("lift operator");
-  cudaFree(Gm);
-  if (Uw) cudaFree(Uw);
-  return s;
+  if (!lift_build(lift_env(x), Ur, rows, L, over))
+    return x->fail(OCTEN_ENOMEM, "lift operator (%lld rows)", (long long)rows);
+  return x->sync_check("lift operator");
 }
 
 // Delta of one global factor: F += Lift * e (Qd x R rhs built from the
 // aligned replica blocks and the projected previous factor PF).
 void lift_mode(octen_ctx *x, const float *Fh, const float *PF, const float *L, int over,
                int64_t rows, float *F) {
-  const octen_config &c = x->cfg;
-  lift_rhs(Fh, PF, c.P, c.Q, c.S, c.R, x->RT, x->Qd, over, x->e, x->st);
-  GemmArgs g{};
-  g.A = L; g.ta = Elem::F32;
-  if (over) { g.sAm = x->Qd; g.sAk = 1; } else { g.sAm = 1; g.sAk = rows; }
-  g.B = x->e; g.tb = Elem::F32; g.sBn = 1; g.sBk = c.R;
-  g.D = F; g.sDm = c.R; g.sDn = 1;
-  g.M = (int)rows; g.N = c.R; g.K = x->Qd; g.batch = 1; g.alpha = 1.f; g.beta = 1.f;
-  g.split_scratch = x->splitk; g.split_scratch_floats = octen_ctx::kSplitkFloats;
-  gemm_strided(g, x->st);
+  lift_apply(lift_env(x), Fh, PF, L, over, rows, F);
 }
 
 // PF = U_all^T F (Qd x R)

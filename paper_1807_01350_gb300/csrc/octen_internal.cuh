@@ -227,6 +227,22 @@ void update_g(const float *W, const float *C_new, int64_t t, int P, int Q, int S
               int R, float *G, cudaStream_t st);
 
 // Dense fp32 SPD factor / solve (init-time lift operators).
+// Lift of Eq. 7 for one non-temporal mode (k_lift.cu).
+struct LiftEnv {
+  int Qd, P, Q, S, R, RT;
+  cudaStream_t st;
+  int *status;
+  float *e;                      // Qd x R right-hand side scratch
+  float *splitk;
+  size_t splitk_floats;
+};
+// L (rows x Qd or Qd x rows) for the rounded projection Ur (rows x Qd); false on
+// allocation or CUDA failure (the stream is synchronised).
+bool lift_build(const LiftEnv &v, const float *Ur, int64_t rows, float *L, int &over);
+// F (rows x R) += L e, e from the aligned replica blocks Fh and the projected
+// previous factor PF.
+void lift_apply(const LiftEnv &v, const float *Fh, const float *PF, const float *L, int over,
+                int64_t rows, float *F);
 void cholesky_f32(float *Gm, int n, int *status, cudaStream_t st);
 void chol_solve_f32(const float *L, int n, float *Bm, int m, cudaStream_t st);
 void scale_columns(const float *in, int64_t rows, int cols, int S, float w_shared,
