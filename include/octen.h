@@ -214,6 +214,81 @@ octen_status octen_set_timing(octen_ctx *ctx, int on);
 octen_status octen_stage_times(const octen_ctx *ctx, double *ms, uint64_t *launches);
 octen_status octen_reset_stage_times(octen_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * N-mode extension (Sec. "Extending to Higher-Order Tensors"): a tensor with
+ * N - 1 non-temporal modes I_1 x ... x I_{N-1} growing in its N-th (time)
+ * mode.  Every replica p compresses every non-temporal mode n with its own
+ * projection block of U_n,all (I_n x Qd, the same column convention as U_all
+ * above: anchors [0, S) shared, replica p's private block after them) and the
+ * time mode with W (t x Qd), keeps the N-way summary Y_p (Q^N), decomposes it
+ * by CP-ALS (per sweep: the time factor, then each non-temporal factor
+ * normalised to unit l2; a final time-factor update), matches the replicas on
+ * the anchor rows of every non-temporal mode (similarity: the sum over those
+ * modes of |cos|; scales per mode, the time factor scaled by their product)
+ * and lifts each non-temporal factor as in Eq. 7 with its own stacked
+ * projection; the new rows of the time factor are solved as in the 3-mode
+ * update.  With N = 3 this is the 3-mode update in fp32.
+ *
+ * fp32 throughout.  Slices are laid out [k][i_1]...[i_{N-1}], summaries
+ * [p][q_1]...[q_{N-1}][c].  Pointers may be device or host memory (host
+ * inputs are staged on the context's stream).  Same status codes and
+ * threading rules as the 3-mode calls.
+ * ------------------------------------------------------------------------ */
+typedef struct octen_nctx octen_nctx;
+
+#define OCTEN_MAX_MODES 6
+
+/* Limits: 3 <= N <= OCTEN_MAX_MODES, 1 <= R <= 32, 1 <= S < Q <= 256, P >= 1,
+ * als_iters >= 1, 1 <= dims[n] <= 2^24 for n < N - 1 (later entries ignored),
+ * Q^N <= 2^24 and P Q^N <= 2^28, and the replica CP state of one summary must
+ * fit one thread block's shared memory (N Q R-ish floats; X_p itself is read
+ * from global memory when it does not fit). */
+typedef struct {
+  int32_t N;
+  int32_t R, P, Q, S;
+  int32_t als_iters;
+  int64_t dims[OCTEN_MAX_MODES - 1];
+} octen_nconfig;
+
+/* Creates a context (summaries, projections, factors, scratch on the device).
+ * EINVAL on the limits above, ENOMEM on allocation failure. */
+octen_status octen_n_create(const octen_nconfig *cfg, void *cuda_stream, octen_nctx **out);
+
+/* Existing summaries and decomposition: compresses X_old (t_old slices) with
+ * U_all[n] (n < N - 1, each I_n x Qd) and W_old (t_old x Qd), takes A0[n]
+ * (I_n x R) and C0 (t_old x R) as the existing factors (all required), forms
+ * G_p = W_old,p^T C0 and the lift operators of every non-temporal mode.  Once
+ * per context (ESTATE otherwise). */
+octen_status octen_n_init(octen_nctx *ctx, const float *X_old, int64_t t_old,
+                          const float *const *U_all, const float *W_old,
+                          const float *const *A0, const float *C0);
+
+/* One update with t new slices (1 <= t <= 64) and their time projections
+ * W_new (t x Qd). */
+octen_status octen_n_append(octen_nctx *ctx, const float *X_new, int64_t t,
+                            const float *W_new);
+
+/* Copies A[n] (I_n x R, n < N - 1) and C (K x R); A, any A[n] and C may be
+ * NULL.  *K_out (if non-NULL) gets K. */
+octen_status octen_n_get_factors(const octen_nctx *ctx, float *const *A, float *C,
+                                 int64_t *K_out);
+
+/* Copies the summaries Y (P x Q^N, [p][q_1]...[q_{N-1}][c]) out. */
+octen_status octen_n_get_replicas(const octen_nctx *ctx, float *Y);
+
+/* The last update's replica factors, F[n] (P x Q x R) for n < N - 1 and the
+ * time factor F[N - 1]: which = 0 the raw CP-ALS output, 1 the matched ones.
+ * perm (P x R int32) and scales (P x (N - 1) x R fp64, the per-mode anchor
+ * scales) may be NULL, as may F and any F[n]. */
+octen_status octen_n_get_replica_factors(const octen_nctx *ctx, int which, float *const *F,
+                                         int32_t *perm, double *scales);
+
+/* Rows of the time factor so far. */
+int64_t octen_n_rows(const octen_nctx *ctx);
+
+void octen_n_destroy(octen_nctx *ctx);
+const char *octen_n_last_error(const octen_nctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,8 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Octen", "OctenError", "append_many", "compress", "lib", "library_path", "PREC",
-           "launch_count"]
+__all__ = ["Octen", "OctenN", "OctenError", "append_many", "compress", "lib", "library_path",
+           "PREC", "launch_count"]
 
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 _STATUS = {0: "OCTEN_OK", 1: "OCTEN_EINVAL", 2: "OCTEN_ENOMEM", 3: "OCTEN_ECUDA",
@@ -27,6 +27,15 @@ class OctenError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+MAX_MODES = 6
+
+
+class _NConfig(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("R", ctypes.c_int32), ("P", ctypes.c_int32),
+                ("Q", ctypes.c_int32), ("S", ctypes.c_int32), ("als_iters", ctypes.c_int32),
+                ("dims", ctypes.c_int64 * (MAX_MODES - 1))]
 
 
 class _Config(ctypes.Structure):
@@ -84,6 +93,21 @@ def lib() -> ctypes.CDLL:
         L.octen_set_timing.argtypes = [vp, ctypes.c_int]
         L.octen_stage_times.argtypes = [vp, vp, vp]
         L.octen_reset_stage_times.argtypes = [vp]
+        L.octen_n_create.argtypes = [ctypes.POINTER(_NConfig), vp, ctypes.POINTER(vp)]
+        L.octen_n_init.argtypes = [vp, vp, i64, vp, f32p, vp, f32p]
+        L.octen_n_append.argtypes = [vp, vp, i64, f32p]
+        L.octen_n_get_factors.argtypes = [vp, vp, f32p, ctypes.POINTER(i64)]
+        L.octen_n_get_replicas.argtypes = [vp, f32p]
+        L.octen_n_get_replica_factors.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.octen_n_rows.argtypes = [vp]
+        L.octen_n_rows.restype = i64
+        L.octen_n_destroy.argtypes = [vp]
+        L.octen_n_destroy.restype = None
+        L.octen_n_last_error.argtypes = [vp]
+        L.octen_n_last_error.restype = ctypes.c_char_p
+        for name in ("octen_n_create", "octen_n_init", "octen_n_append", "octen_n_get_factors",
+                     "octen_n_get_replicas", "octen_n_get_replica_factors"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("octen_create", "octen_init", "octen_append", "octen_append_many",
                      "octen_get_factors",
                      "octen_fit", "octen_get_replicas", "octen_get_replica_factors",
@@ -274,6 +298,92 @@ class Octen:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.octen_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class OctenN:
+    """One online CP decomposition of an N-mode tensor growing in its last
+    (time) mode, fp32 (octen_n_* in include/octen.h).  dims are the N - 1
+    non-temporal sizes; slices are [k][i_1]...[i_{N-1}]."""
+
+    def __init__(self, dims, R, P, Q, S, als_iters, stream=None):
+        self._lib = lib()
+        self.dims = [int(d) for d in dims]
+        self.N = len(self.dims) + 1
+        if not 3 <= self.N <= MAX_MODES:
+            raise OctenError(1, f"N = {self.N} modes: 3 <= N <= {MAX_MODES}")
+        dd = (ctypes.c_int64 * (MAX_MODES - 1))(*(self.dims + [0] * (MAX_MODES - self.N)))
+        self.cfg = _NConfig(self.N, int(R), int(P), int(Q), int(S), int(als_iters), dd)
+        self.R, self.P, self.Q, self.S = R, P, Q, S
+        self.Qd = S + P * (Q - S)
+        h = ctypes.c_void_p()
+        st = self._lib.octen_n_create(ctypes.byref(self.cfg), _stream_handle(stream),
+                                      ctypes.byref(h))
+        if st != 0:
+            raise OctenError(st, "octen_n_create failed")
+        self._h = h
+
+    def _check(self, st: int):
+        if st != 0:
+            raise OctenError(st, self._lib.octen_n_last_error(self._h).decode())
+
+    def _ptrs(self, arrays, keep):
+        return (ctypes.c_void_p * len(arrays))(*[_f32(a, keep) for a in arrays])
+
+    def init(self, X_old, Us, W_old, A0s, C0):
+        keep: list = []
+        us = self._ptrs(Us, keep)
+        a0 = self._ptrs(A0s, keep)
+        keep += [us, a0]
+        self._check(self._lib.octen_n_init(self._h, _f32(X_old, keep), int(X_old.shape[0]), us,
+                                           _f32(W_old, keep), a0, _f32(C0, keep)))
+
+    def append(self, X_new, W_new):
+        keep: list = []
+        self._check(self._lib.octen_n_append(self._h, _f32(X_new, keep), int(X_new.shape[0]),
+                                             _f32(W_new, keep)))
+
+    def append_ptr(self, x_ptr: int, t: int, w_ptr: int):
+        """Append from raw fp32 pointers (device or host)."""
+        self._check(self._lib.octen_n_append(self._h, x_ptr, int(t), w_ptr))
+
+    @property
+    def rows(self) -> int:
+        return int(self._lib.octen_n_rows(self._h))
+
+    def factors(self):
+        """([A_1, ..., A_{N-1}], C) as numpy arrays."""
+        As = [np.empty((d, self.R), np.float32) for d in self.dims]
+        C = np.empty((self.rows, self.R), np.float32)
+        ap = (ctypes.c_void_p * len(As))(*[a.ctypes.data for a in As])
+        k = ctypes.c_int64()
+        self._check(self._lib.octen_n_get_factors(self._h, ap, C.ctypes.data, ctypes.byref(k)))
+        return As, C
+
+    def replicas(self):
+        Y = np.empty((self.P,) + (self.Q,) * self.N, np.float32)
+        self._check(self._lib.octen_n_get_replicas(self._h, Y.ctypes.data))
+        return Y
+
+    def replica_factors(self, which: int = 0):
+        """([F_1, ..., F_{N-1}, C_rep] each P x Q x R, perm P x R, scales P x (N-1) x R)."""
+        Fs = [np.empty((self.P, self.Q, self.R), np.float32) for _ in range(self.N)]
+        fp = (ctypes.c_void_p * self.N)(*[f.ctypes.data for f in Fs])
+        perm = np.empty((self.P, self.R), np.int32)
+        scales = np.empty((self.P, self.N - 1, self.R), np.float64)
+        self._check(self._lib.octen_n_get_replica_factors(self._h, int(which), fp,
+                                                          perm.ctypes.data, scales.ctypes.data))
+        return Fs, perm, scales
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.octen_n_destroy(self._h)
             self._h = None
 
     def __del__(self):

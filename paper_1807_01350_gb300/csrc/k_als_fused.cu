@@ -30,36 +30,6 @@ __device__ __forceinline__ void mttkrp_barrier() {
   asm volatile("bar.sync 2, 128;" ::: "memory");
 }
 
-// Rows q < Q of M solved against the factor in (Lc, Lr, rf) into F; with
-// `normalize` the columns are scaled to unit l2 (norms over the CTA).
-template <int RT>
-__device__ void fused_solve(const float *M, float *F, int Q, bool normalize, const float *Lc,
-                            const float *Lr, const float *rf, float *red, float *scl) {
-  const int tid = threadIdx.x;
-  const bool own = tid < Q;
-  float y[RT];
-#pragma unroll
-  for (int r = 0; r < RT; ++r) y[r] = own ? M[tid * RT + r] : 0.f;
-  if (own) ldl_substitute<RT>(y, Lc, Lr, rf);
-  if (normalize) {
-    float sq[RT];
-#pragma unroll
-    for (int r = 0; r < RT; ++r) sq[r] = y[r] * y[r];
-    block_sum_rows<RT>(sq, red, scl);
-    if (tid < RT) {
-      const float n = sqrtf(scl[tid]);
-      red[tid] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < RT; ++r) y[r] *= red[r];
-  }
-  if (own) {
-#pragma unroll
-    for (int r = 0; r < RT; ++r) F[tid * RT + r] = y[r];
-  }
-}
-
 // grid P, 256 threads (Q <= 256); dynamic smem fused_floats(Q, RT) floats.
 // In: X_p (Y), the warm-started A, B (unit columns, rank padded to RT with
 // zeros) and their Grams.  Out: the replica factors A, B, C.
@@ -118,7 +88,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     }
     __syncthreads();
     if (fail_s && tid == 0) atomicOr(status, kDevCholesky);
-    fused_solve<RT>(M, C, Q, false, Lc, Lr, rf, red, scl);
+    solve_rows_smem<RT>(M, C, Q, false, Lc, Lr, rf, red, scl);
     __syncthreads();
     smem_gram<RT>(C, Q, GC);
     __syncthreads();
@@ -140,7 +110,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     }
     __syncthreads();
     if (fail_s && tid == 0) atomicOr(status, kDevCholesky);
-    fused_solve<RT>(M, A, Q, true, Lc, Lr, rf, red, scl);
+    solve_rows_smem<RT>(M, A, Q, true, Lc, Lr, rf, red, scl);
     __syncthreads();
     smem_gram<RT>(A, Q, GA);
     __syncthreads();
@@ -162,7 +132,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     }
     __syncthreads();
     if (fail_s && tid == 0) atomicOr(status, kDevCholesky);
-    fused_solve<RT>(M, B, Q, true, Lc, Lr, rf, red, scl);
+    solve_rows_smem<RT>(M, B, Q, true, Lc, Lr, rf, red, scl);
     __syncthreads();
     smem_gram<RT>(B, Q, GB);
     __syncthreads();

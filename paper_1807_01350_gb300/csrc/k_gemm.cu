@@ -174,8 +174,8 @@ static void gemm_dispatch_tile(const Operand &A, const Operand &B, const GemmArg
     launch_gemm<EA, EB, 64, 64>(A, B, g.M, g.N, g.K, g.batch, 1, epi, st);
 }
 
-// Skinny fp32 GEMM (N <= 32, one batch item): D = alpha A B + beta D, or the
-// split-K partials part[split][m][n] of A B.  A CTA covers 128 rows over one K
+// Skinny fp32 GEMM (N <= 32): D = alpha A B + beta D, or (one batch item only)
+// the split-K partials part[split][m][n] of A B; batch items along grid z.  A CTA covers 128 rows over one K
 // range in steps of 32: the A step is staged as As[k][m] (loads coalesced along
 // m or along k, whichever is contiguous), the B step as Bs[k][n] (zero beyond
 // N); thread t owns rows t % 32 + 32 j (j < 4) and columns 8 (t / 32) .. + 7.
@@ -185,8 +185,12 @@ __global__ void __launch_bounds__(128)
     gemm_skinny_kernel(const float *__restrict__ A, int64_t sAm, int64_t sAk,
                        const float *__restrict__ B, int64_t sBn, int64_t sBk, int M, int N, int K,
                        int kc, float *D, int64_t sDm, int64_t sDn, float alpha, float beta,
-                       float *__restrict__ part) {
+                       float *__restrict__ part, int64_t sAz, int64_t sBz, int64_t sDz) {
   __shared__ float As[kSkBK][kSkBM + 1];
+  // batch item blockIdx.z (never split: part is null then)
+  A += blockIdx.z * sAz;
+  B += blockIdx.z * sBz;
+  D += blockIdx.z * sDz;
   __shared__ __align__(16) float Bs[kSkBK][32];
   const int tid = threadIdx.x, rg = tid & 31, cg = tid >> 5;
   const int m0 = blockIdx.x * kSkBM;
@@ -258,7 +262,7 @@ static void gemm_skinny(const GemmArgs &g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return;
   const int tiles_m = (g.M + kSkBM - 1) / kSkBM;
   int splits = 1;
-  if (g.split_scratch) {
+  if (g.split_scratch && g.batch == 1) {
     splits = 608 / tiles_m;   // about four CTAs per SM in flight
     if (splits > g.K / 128) splits = g.K / 128;
     const int64_t MN = (int64_t)g.M * g.N;
@@ -272,10 +276,10 @@ static void gemm_skinny(const GemmArgs &g, cudaStream_t st) {
   if (splits < 1) splits = 1;
   const float *A = static_cast<const float *>(g.A);
   const float *B = static_cast<const float *>(g.B);
-  const dim3 grid((unsigned)tiles_m, (unsigned)splits);
+  const dim3 grid((unsigned)tiles_m, (unsigned)splits, (unsigned)g.batch);
   if (splits >= 2) {
     gemm_skinny_kernel<<<grid, 128, 0, st>>>(A, g.sAm, g.sAk, B, g.sBn, g.sBk, g.M, g.N, g.K, kc,
-                                             nullptr, 0, 0, 1.f, 0.f, g.split_scratch);
+                                             nullptr, 0, 0, 1.f, 0.f, g.split_scratch, 0, 0, 0);
     count_launch();
     const int64_t MN = (int64_t)g.M * g.N;
     splitk_reduce_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(
@@ -284,7 +288,7 @@ static void gemm_skinny(const GemmArgs &g, cudaStream_t st) {
   } else {
     gemm_skinny_kernel<<<grid, 128, 0, st>>>(A, g.sAm, g.sAk, B, g.sBn, g.sBk, g.M, g.N, g.K,
                                              g.K < 1 ? 1 : g.K, g.D, g.sDm, g.sDn, g.alpha,
-                                             g.beta, nullptr);
+                                             g.beta, nullptr, g.sAz, g.sBz, g.sDz);
     count_launch();
   }
 }
@@ -293,7 +297,7 @@ void gemm_strided(const GemmArgs &g, cudaStream_t st) {
   // zdiv = 1: the whole batch index goes through the s_hi strides
   Operand A{g.A, g.sAz, 0, g.sAm, g.sAk};
   Operand B{g.B, g.sBz, 0, g.sBn, g.sBk};
-  if (g.batch == 1 && g.N <= 32 && g.ta == Elem::F32 && g.tb == Elem::F32) {
+  if ((g.batch == 1 || g.skinny_batch) && g.N <= 32 && g.ta == Elem::F32 && g.tb == Elem::F32) {
     gemm_skinny(g, st);
     return;
   }

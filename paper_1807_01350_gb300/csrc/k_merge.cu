@@ -3,7 +3,7 @@
 // projections (Sec. "Update results", Eq. 6-7), the least-squares solve of the
 // new rows of C, and the dense fp32 Cholesky / triangular solves that build the
 // lift operators once per stream.
-#include "octen_internal.cuh"
+#include "k_match.cuh"
 
 namespace octen {
 
@@ -107,33 +107,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    unsigned used_r = 0u, used_s = 0u;
-    for (int round = 0; round < R; ++round) {
-      unsigned long long best = 0ull;
-      int br = -1;
-      if (lane < R && !((used_s >> lane) & 1u)) {
-        for (int r = 0; r < R; ++r) {
-          if ((used_r >> r) & 1u) continue;
-          const unsigned long long v = key[r * RT + lane];
-          if (br < 0 || v > best) { best = v; br = r; }
-        }
-      }
-      // warp argmax over lanes: larger value wins, ties to the lower lane (s);
-      // lanes with nothing left carry br = -1 and never win
-      int bs = lane;
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int obr = __shfl_xor_sync(0xffffffffu, br, o);
-        const int obs = __shfl_xor_sync(0xffffffffu, bs, o);
-        const bool take = obr >= 0 && (br < 0 || ov > best || (ov == best && obs < bs));
-        if (take) { best = ov; br = obr; bs = obs; }
-      }
-      if (br < 0) break;   // every lane holds the same winner after the butterfly
-      if (lane == 0) perm[bs] = br;
-      used_r |= 1u << br;
-      used_s |= 1u << bs;
-    }
-    __syncwarp();
+    greedy_match_warp<RT>(key, R, perm);
     if (lane < R) {
       const int s = lane, r = perm[s];
       const double n2a = nrm[2 * RT + s], n2b = nrm[3 * RT + s];

@@ -1,0 +1,428 @@
+// Kernels of the N-mode extension (Sec. "Extending to Higher-Order Tensors"):
+// a tensor with N - 1 non-temporal modes I_1 x ... x I_{N-1} growing in its
+// N-th (time) mode.  Every replica p compresses every mode with its own
+// projection (first S columns shared, Eq. 1), keeps the N-way summary
+// Y_p[q_1]...[q_{N-1}][c] (X_p = Y_p + Z_p), decomposes it by CP-ALS, and the
+// replica factors are matched on their anchor rows in every non-temporal mode
+// before each factor is lifted as in Eq. 7.
+//
+// Compression of a chunk of t slices X[k][i_1]...[i_{N-1}] (fp32) as a chain
+// of skinny GEMMs that each contract the innermost index and write their
+// result transposed, so that the next index to contract becomes innermost:
+//   X [(k, i_1..i_{N-2})][i_{N-1}]         x U_{N-1} of all replicas (N = P Q)
+//     -> T [p][q_{N-1}][(k, i_1..i_{N-2})]
+//   T [p][(q_{m+1}.., k, i_1..i_{m-1})][i_m] x U_m,p      (batched over p)
+//     -> T [p][q_m][(q_{m+1}.., k, i_1..i_{m-1})]
+//   ... down to m = 1, leaving T [p][(q_1..q_{N-1})][k];
+//   Y_p[(q_1..q_{N-1})][c] += sum_k T[p][(q..)][k] W_p[k][c].
+// The first product reads every slice once for all replicas (the anchor
+// columns are computed once per replica, as in the 3-mode mode-2 pass); the
+// later ones work on tensors already shrunk by Q / I_m per step.
+#include "k_match.cuh"
+#include "k_solve.cuh"
+
+namespace octen {
+
+namespace {
+
+constexpr int kNThreads = 256;
+
+__host__ __device__ inline int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// Shared floats of the replica ALS: X Q^NN (if it is kept in shared memory,
+// rounded up to a multiple of 4) | F NN Q RT | M Q RT | Mp max(Q RT, 128) |
+// G NN RT^2 | Hp, Lc, Lr RT^2 each | rf RT | red 8 RT | scl RT.  Every array
+// after X has a length that is a multiple of 4 (RT is a multiple of 8).
+size_t nals_floats(int NN, int Q, int RT, bool x_in_smem) {
+  const size_t q = (size_t)Q, rt = (size_t)RT;
+  const size_t x = x_in_smem ? (((size_t)ipow(Q, NN) + 3) & ~size_t(3)) : 0;
+  const size_t mp = q * rt > 128 ? q * rt : 128;
+  return x + (size_t)NN * q * rt + q * rt + mp + (size_t)NN * rt * rt + 3 * rt * rt +
+         10 * rt;
+}
+
+__device__ __forceinline__ void nals_mttkrp_barrier() {
+  asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+
+// MTTKRP of mode n by the 128 threads u = 0..127 (warps 4..7):
+//   M[q][r] = sum over the other indices of X[..q..] prod_{m != n} F_m[idx_m][r].
+// The other modes are split into an inner mode ml (the last one other than n)
+// and the outer ones; the outer index range is split into `ns` parts when Q RT
+// is below 128, so that every thread has work, and the parts are summed in
+// order afterwards.
+template <int RT, int NN>
+__device__ void nals_mttkrp(const float *X, const float *F, int Q, int R, int n, float *M,
+                            float *Mp, int u) {
+  int64_t pw[NN];
+  pw[NN - 1] = 1;
+#pragma unroll
+  for (int m = NN - 2; m >= 0; --m) pw[m] = pw[m + 1] * Q;
+  const int ml = n == NN - 1 ? NN - 2 : NN - 1;
+  const int64_t sl = pw[ml];
+  const int pairs = Q * RT;
+  const int ns = pairs >= 128 ? 1 : 128 / pairs;
+  const int64_t nouter = ipow(Q, NN - 2);
+  const int64_t chunk = (nouter + ns - 1) / ns;
+  for (int w = u; w < pairs * ns; w += 128) {
+    const int part = w / pairs, e = w - part * pairs;
+    const int q = e / RT, r = e - q * RT;
+    float acc = 0.f;
+    if (r < R) {
+      const int64_t o0 = part * chunk;
+      const int64_t o1 = o0 + chunk < nouter ? o0 + chunk : nouter;
+      const float *fl = F + (size_t)ml * Q * RT + r;
+      for (int64_t o = o0; o < o1; ++o) {
+        int64_t rem = o, off = q * pw[n];
+        float pr = 1.f;
+#pragma unroll
+        for (int m = NN - 1; m >= 0; --m) {
+          if (m == n || m == ml) continue;
+          const int d = (int)(rem % Q);
+          rem /= Q;
+          off += d * pw[m];
+          pr *= F[((size_t)m * Q + d) * RT + r];
+        }
+        const float *xp = X + off;
+        for (int d = 0; d < Q; ++d) acc = fmaf(xp[d * sl], pr * fl[d * RT], acc);
+      }
+    }
+    if (ns == 1) M[e] = acc;
+    else Mp[w] = acc;
+  }
+  if (ns > 1) {
+    nals_mttkrp_barrier();
+    for (int e = u; e < pairs; e += 128) {
+      float s = 0.f;
+      for (int part = 0; part < ns; ++part) s += Mp[part * pairs + e];
+      M[e] = s;
+    }
+  }
+}
+
+}  // namespace
+
+// grid P, 256 threads.  Per replica: the CP of the N-way summary X_p by
+// alternating least squares in the order of the oracle's CP sweep: the time
+// factor, then every non-temporal factor normalised to unit l2, `iters` times,
+// and a final time-factor update.  Warps 0..3 factor the normal equations
+// (fp64 L D L^T of the Hadamard product of the other factors' Grams) while
+// warps 4..7 form the MTTKRP; the whole CTA then substitutes.
+struct NAlsArgs {
+  const float *Y;                  // P x Q^NN summaries
+  float *F[kMaxNModes];            // in: warm starts of modes 0..NN-2; out: all NN factors
+  const float *G0[kMaxNModes];     // Grams of the warm starts (P x RT x RT)
+  int Q, R, iters, x_in_smem;
+  int *status;
+};
+
+template <int RT, int NN>
+__global__ void __launch_bounds__(kNThreads, 1) nals_kernel(NAlsArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ double Craw[RT * (RT + 1)], Rs[RT];
+  __shared__ int fail_s;
+  const int p = blockIdx.x, tid = threadIdx.x, Q = a.Q, R = a.R;
+  const int64_t nx = ipow(Q, NN);
+  const float *X = a.Y + (size_t)p * nx;
+  float *base = sm;
+  if (a.x_in_smem) {
+    for (int64_t e = tid; e < nx; e += blockDim.x) base[e] = X[e];
+    X = base;
+    base += (nx + 3) & ~int64_t(3);
+  }
+  float *F = base;                                   // [NN][Q][RT]
+  float *M = F + (size_t)NN * Q * RT;                // [Q][RT]
+  float *Mp = M + Q * RT;                            // MTTKRP partials
+  float *G = Mp + (Q * RT > 128 ? Q * RT : 128);     // [NN][RT][RT]
+  float *Hp = G + NN * RT * RT;
+  float *Lc = Hp + RT * RT, *Lr = Lc + RT * RT, *rf = Lr + RT * RT;
+  float *red = rf + RT, *scl = red + 8 * RT;
+#pragma unroll
+  for (int m = 0; m < NN - 1; ++m) {
+    for (int e = tid; e < Q * RT; e += blockDim.x)
+      F[(size_t)m * Q * RT + e] = a.F[m][(size_t)p * Q * RT + e];
+    for (int e = tid; e < RT * RT; e += blockDim.x)
+      G[m * RT * RT + e] = a.G0[m][(size_t)p * RT * RT + e];
+  }
+  __syncthreads();
+
+  auto update = [&](int n, bool normalize) {
+    const int ml = n == NN - 1 ? NN - 2 : NN - 1;
+    if (tid < 128) {
+      for (int e = tid; e < RT * RT; e += 128) {
+        float h = 1.f;
+#pragma unroll
+        for (int m = 0; m < NN; ++m)
+          if (m != n && m != ml) h *= G[m * RT * RT + e];
+        Hp[e] = h;
+      }
+      factor_barrier();
+      ldl_factor<RT>(Hp, G + ml * RT * RT, R, Craw, Rs, Lc, Lr, rf, &fail_s);
+    } else {
+      nals_mttkrp<RT, NN>(X, F, Q, R, n, M, Mp, tid - 128);
+    }
+    __syncthreads();
+    if (fail_s && tid == 0) atomicOr(a.status, kDevCholesky);
+    solve_rows_smem<RT>(M, F + (size_t)n * Q * RT, Q, normalize, Lc, Lr, rf, red, scl);
+    __syncthreads();
+    smem_gram<RT>(F + (size_t)n * Q * RT, Q, G + n * RT * RT);
+    __syncthreads();
+  };
+
+  for (int it = 0; it < a.iters; ++it) {
+    update(NN - 1, false);
+    for (int n = 0; n < NN - 1; ++n) update(n, true);
+  }
+  update(NN - 1, false);
+#pragma unroll
+  for (int m = 0; m < NN; ++m)
+    for (int e = tid; e < Q * RT; e += blockDim.x)
+      a.F[m][(size_t)p * Q * RT + e] = F[(size_t)m * Q * RT + e];
+}
+
+namespace {
+
+template <int RT, int NN>
+bool nals_launch(const NAlsArgs &a, int P, size_t smem, cudaStream_t st) {
+  if (cudaFuncSetAttribute(nals_kernel<RT, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return false;
+  nals_kernel<RT, NN><<<P, kNThreads, smem, st>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return false;
+  count_launch();
+  return true;
+}
+
+template <int RT>
+bool nals_dispatch(int NN, const NAlsArgs &a, int P, size_t smem, cudaStream_t st) {
+  switch (NN) {
+    case 3: return nals_launch<RT, 3>(a, P, smem, st);
+    case 4: return nals_launch<RT, 4>(a, P, smem, st);
+    case 5: return nals_launch<RT, 5>(a, P, smem, st);
+    case 6: return nals_launch<RT, 6>(a, P, smem, st);
+    default: return false;
+  }
+}
+
+constexpr size_t kNalsSmemLimit = 200 * 1024;
+
+}  // namespace
+
+bool nals_fits(int NN, int Q, int RT) {
+  return Q <= kNThreads && nals_floats(NN, Q, RT, false) * sizeof(float) <= kNalsSmemLimit;
+}
+
+bool nals_run(const NAlsInput &in, cudaStream_t st) {
+  const int NN = in.NN, RT = in.RT;
+  if (NN < 3 || NN > kMaxNModes || !nals_fits(NN, in.Q, RT)) return false;
+  NAlsArgs a{};
+  a.Y = in.Y;
+  for (int m = 0; m < NN; ++m) a.F[m] = in.F[m];
+  for (int m = 0; m < NN - 1; ++m) a.G0[m] = in.G0[m];
+  a.Q = in.Q; a.R = in.R; a.iters = in.iters; a.status = in.status;
+  const bool xs = nals_floats(NN, in.Q, RT, true) * sizeof(float) <= kNalsSmemLimit;
+  a.x_in_smem = xs ? 1 : 0;
+  const size_t smem = nals_floats(NN, in.Q, RT, xs) * sizeof(float);
+  if (RT == 8) return nals_dispatch<8>(NN, a, in.P, smem, st);
+  if (RT == 16) return nals_dispatch<16>(NN, a, in.P, smem, st);
+  return nals_dispatch<32>(NN, a, in.P, smem, st);
+}
+
+// ---------------------------------------------------------------------------
+// Anchor match of the N-mode replicas (fp64), the 3-mode rule mode by mode:
+//   sim[r][s] = sum over the non-temporal modes of |cos(F_n[:S, r], ref_n[:, s])|
+// (ref_n = rows [0, S) of U_n^T A_n, a cosine with a zero norm counts 0), the
+// greedy one-to-one matching, per-mode anchor scales
+//   d_n[s] = <F_n[:S, pi(s)], ref_n[:, s]> / ||ref_n[:, s]||^2   (0 -> 1),
+// and the aligned factors F_n[:, pi] / d_n, C[:, pi] prod_n d_n.
+// grid P, 256 threads.
+// ---------------------------------------------------------------------------
+struct NAlignArgs {
+  const float *F[kMaxNModes];    // raw replica factors, non-temporal modes then time
+  const float *PF[kMaxNModes];   // U_n^T A_n, Qd x R (non-temporal modes)
+  float *Fh[kMaxNModes];         // aligned factors, same layout as F
+  int nm, Q, S, R;
+  int *perm;                     // P x R
+  double *scales;                // P x nm x R
+};
+
+template <int RT>
+__global__ void __launch_bounds__(kNThreads) n_align_kernel(NAlignArgs a) {
+  __shared__ double sim[RT * RT], nt[RT], nr[RT], prod[RT];
+  __shared__ unsigned long long key[RT * RT];
+  __shared__ int perm[RT];
+  __shared__ float fs[RT];
+  const int p = blockIdx.x, tid = threadIdx.x, Q = a.Q, S = a.S, R = a.R;
+  for (int e = tid; e < RT * RT; e += blockDim.x) sim[e] = 0.0;
+  for (int n = 0; n < a.nm; ++n) {
+    const float *F = a.F[n] + (size_t)p * Q * RT;
+    const float *ref = a.PF[n];
+    __syncthreads();   // the previous mode's norms are consumed
+    if (tid < RT) {
+      double v = 0.0;
+      if (tid < R)
+        for (int q = 0; q < S; ++q) {
+          const double x = F[q * RT + tid];
+          v = fma(x, x, v);
+        }
+      nt[tid] = sqrt(v);
+    } else if (tid < 2 * RT) {
+      const int s = tid - RT;
+      double v = 0.0;
+      if (s < R)
+        for (int q = 0; q < S; ++q) {
+          const double x = ref[(size_t)q * R + s];
+          v = fma(x, x, v);
+        }
+      nr[s] = sqrt(v);
+    }
+    __syncthreads();
+    for (int e = tid; e < RT * RT; e += blockDim.x) {
+      const int r = e / RT, s = e % RT;
+      if (r >= R || s >= R) continue;
+      double dot = 0.0;
+      for (int q = 0; q < S; ++q)
+        dot = fma((double)F[q * RT + r], (double)ref[(size_t)q * R + s], dot);
+      const double den = nt[r] * nr[s];
+      if (den > 0.0) sim[e] += fabs(dot) / den;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < RT * RT; e += blockDim.x) {
+    const int r = e / RT, s = e % RT;
+    double v = (r < R && s < R) ? sim[e] : 0.0;
+    if (!isfinite(v)) v = 0.0;   // a diverged replica still gets a valid matching
+    key[e] = static_cast<unsigned long long>(__double_as_longlong(v));
+  }
+  if (tid < RT) prod[tid] = 1.0;
+  __syncthreads();
+  if (tid < 32) greedy_match_warp<RT>(key, R, perm);
+  __syncthreads();
+  for (int n = 0; n < a.nm; ++n) {
+    const float *F = a.F[n] + (size_t)p * Q * RT;
+    const float *ref = a.PF[n];
+    if (tid < R) {
+      const int s = tid, r = perm[s];
+      double dot = 0.0, n2 = 0.0;
+      for (int q = 0; q < S; ++q) {
+        const double x = ref[(size_t)q * R + s];
+        dot = fma((double)F[q * RT + r], x, dot);
+        n2 = fma(x, x, n2);
+      }
+      double d = n2 > 0.0 ? dot / n2 : 0.0;
+      if (d == 0.0) d = 1.0;
+      prod[s] *= d;
+      fs[s] = (float)(1.0 / d);
+      a.scales[((size_t)p * a.nm + n) * R + s] = d;
+    }
+    __syncthreads();
+    float *Fh = a.Fh[n] + (size_t)p * Q * RT;
+    for (int e = tid; e < Q * RT; e += blockDim.x) {
+      const int q = e / RT, s = e % RT;
+      Fh[e] = s < R ? F[q * RT + perm[s]] * fs[s] : 0.f;
+    }
+    __syncthreads();   // fs is rewritten by the next mode
+  }
+  {
+    const float *C = a.F[a.nm] + (size_t)p * Q * RT;
+    float *Ch = a.Fh[a.nm] + (size_t)p * Q * RT;
+    for (int e = tid; e < Q * RT; e += blockDim.x) {
+      const int q = e / RT, s = e % RT;
+      Ch[e] = s < R ? C[q * RT + perm[s]] * (float)prod[s] : 0.f;
+    }
+    if (tid < R) a.perm[p * R + tid] = perm[tid];
+  }
+}
+
+void n_align(const NAlignInput &in, cudaStream_t st) {
+  NAlignArgs a{};
+  for (int n = 0; n <= in.nm; ++n) {
+    a.F[n] = in.F[n];
+    a.Fh[n] = in.Fh[n];
+  }
+  for (int n = 0; n < in.nm; ++n) a.PF[n] = in.PF[n];
+  a.nm = in.nm; a.Q = in.Q; a.S = in.S; a.R = in.R; a.perm = in.perm; a.scales = in.scales;
+  if (in.RT == 8) n_align_kernel<8><<<in.P, kNThreads, 0, st>>>(a);
+  else if (in.RT == 16) n_align_kernel<16><<<in.P, kNThreads, 0, st>>>(a);
+  else n_align_kernel<32><<<in.P, kNThreads, 0, st>>>(a);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Compression chain (see the top of the file).
+// ---------------------------------------------------------------------------
+int64_t ncompress_rows_max(int nm, const int64_t *dims, int Q, int64_t t) {
+  int64_t rows = t;
+  for (int n = 0; n + 1 < nm; ++n) rows *= dims[n];   // first product: (k, i_1..i_{N-2})
+  int64_t best = rows;
+  // per-replica elements after the first product: Q rows; contracting mode m
+  // leaves rows_out = elements_in / I_m * Q ... tracked as elements
+  int64_t elems = rows * Q;
+  for (int m = nm - 2; m >= 0; --m) {
+    const int64_t rin = elems / dims[m];
+    if (rin > best) best = rin;
+    elems = rin * Q;
+    if (elems > best) best = elems;
+  }
+  return best;
+}
+
+int64_t ncompress_buf_floats(int nm, const int64_t *dims, int P, int Q, int64_t t) {
+  int64_t rows = t;
+  for (int n = 0; n + 1 < nm; ++n) rows *= dims[n];
+  int64_t best = rows * Q;
+  int64_t elems = rows * Q;
+  for (int m = nm - 2; m >= 0; --m) {
+    elems = elems / dims[m] * Q;
+    if (elems > best) best = elems;
+  }
+  return best * P;
+}
+
+void ncompress_chunk(const NCompressInput &c, const float *X, int64_t t, const float *Wt,
+                     float *Y, cudaStream_t st) {
+  const int nm = c.nm, P = c.P, Q = c.Q;
+  // 1. innermost mode, all replicas at once
+  int64_t rows = t;
+  for (int n = 0; n + 1 < nm; ++n) rows *= c.dims[n];
+  const int64_t Il = c.dims[nm - 1];
+  {
+    GemmArgs g{};
+    g.A = X; g.ta = Elem::F32; g.sAm = Il; g.sAk = 1;
+    g.B = c.Ut[nm - 1]; g.tb = Elem::F32; g.sBn = Il; g.sBk = 1;
+    g.D = c.bufA; g.sDm = 1; g.sDn = rows;
+    g.M = (int)rows; g.N = P * Q; g.K = (int)Il; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
+    gemm_strided(g, st);
+  }
+  float *in = c.bufA, *out = c.bufB;
+  int64_t elems = rows * Q;   // per replica
+  // 2. the other non-temporal modes, innermost first, per replica
+  for (int m = nm - 2; m >= 0; --m) {
+    const int64_t Im = c.dims[m];
+    const int64_t rin = elems / Im;
+    GemmArgs g{};
+    g.A = in; g.ta = Elem::F32; g.sAz = elems; g.sAm = Im; g.sAk = 1;
+    g.B = c.Ut[m]; g.tb = Elem::F32; g.sBz = (int64_t)Q * Im; g.sBn = Im; g.sBk = 1;
+    g.D = out; g.sDz = rin * Q; g.sDm = 1; g.sDn = rin;
+    g.M = (int)rin; g.N = Q; g.K = (int)Im; g.batch = P; g.alpha = 1.f; g.beta = 0.f;
+    g.skinny_batch = true;
+    gemm_strided(g, st);
+    elems = rin * Q;
+    float *tmp = in; in = out; out = tmp;
+  }
+  // 3. time mode into the summaries
+  const int64_t nq = elems / t;   // Q^(N-1)
+  GemmArgs g{};
+  g.A = in; g.ta = Elem::F32; g.sAz = elems; g.sAm = t; g.sAk = 1;
+  g.B = Wt; g.tb = Elem::F32; g.sBz = (int64_t)Q * t; g.sBn = t; g.sBk = 1;
+  g.D = Y; g.sDz = nq * Q; g.sDm = Q; g.sDn = 1;
+  g.M = (int)nq; g.N = Q; g.K = (int)t; g.batch = P; g.alpha = 1.f; g.beta = 1.f;
+  g.skinny_batch = true;
+  gemm_strided(g, st);
+}
+
+}  // namespace octen

@@ -267,6 +267,38 @@ __device__ __forceinline__ void ldl_substitute(float (&y)[RT], const float *Lc, 
 template <int RT>
 __host__ __device__ constexpr int factor_floats() { return 2 * RT * RT + RT; }
 
+// Whole CTA (Q <= blockDim.x, a multiple of 32): rows q < Q of M (Q x RT,
+// shared) solved against the factor in (Lc, Lr, rf) into F; with `normalize`
+// the columns are scaled to unit l2 (norms over the CTA).
+template <int RT>
+__device__ void solve_rows_smem(const float *M, float *F, int Q, bool normalize,
+                                const float *Lc, const float *Lr, const float *rf, float *red,
+                                float *scl) {
+  const int tid = threadIdx.x;
+  const bool own = tid < Q;
+  float y[RT];
+#pragma unroll
+  for (int r = 0; r < RT; ++r) y[r] = own ? M[tid * RT + r] : 0.f;
+  if (own) ldl_substitute<RT>(y, Lc, Lr, rf);
+  if (normalize) {
+    float sq[RT];
+#pragma unroll
+    for (int r = 0; r < RT; ++r) sq[r] = y[r] * y[r];
+    block_sum_rows<RT>(sq, red, scl);
+    if (tid < RT) {
+      const float n = sqrtf(scl[tid]);
+      red[tid] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RT; ++r) y[r] *= red[r];
+  }
+  if (own) {
+#pragma unroll
+    for (int r = 0; r < RT; ++r) F[tid * RT + r] = y[r];
+  }
+}
+
 // Gram of the factor updated last (F_p, Q x RT, global) -> Gnew_p, then the
 // L D L^T factor of Gnew_p * Gother_p -> Lout_p.  It depends only on factors
 // that are already final, so it runs beside the MTTKRP of the same update.

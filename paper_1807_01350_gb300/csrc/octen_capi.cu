@@ -18,6 +18,15 @@ static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_tc_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_tc_launch() { g_tc_launches.fetch_add(1, std::memory_order_relaxed); }
+bool is_device_pointer(const void *p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
 // launches recorded into a graph are counted when the graph runs, not when
 // captured; the autotuner's timing launches are not counted
 void adjust_launch_counts(int64_t n, int64_t ntc) {
@@ -34,15 +43,7 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
-bool is_device_ptr(const void *p) {
-  if (p == nullptr) return false;
-  cudaPointerAttributes a{};
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool is_device_ptr(const void *p) { return is_device_pointer(p); }
 
 int round_rt(int R) { return R <= 8 ? 8 : (R <= 16 ? 16 : 32); }
 

@@ -59,6 +59,8 @@ struct GemmArgs {
   // over CTAs (partials reduced by a second kernel)
   float *split_scratch = nullptr;
   size_t split_scratch_floats = 0;
+  // N <= 32 with several batch items: the skinny kernel per item (grid z)
+  bool skinny_batch = false;
 };
 void gemm_strided(const GemmArgs &g, cudaStream_t st);
 
@@ -248,6 +250,53 @@ void chol_solve_f32(const float *L, int n, float *Bm, int m, cudaStream_t st);
 void scale_columns(const float *in, int64_t rows, int cols, int S, float w_shared,
                    float *out, cudaStream_t st);
 void transpose_f32(const float *in, int64_t rows, int64_t cols, float *out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// N-mode extension (k_nmode.cu): N - 1 <= 5 non-temporal modes plus time.
+// ---------------------------------------------------------------------------
+constexpr int kMaxNModes = 6;
+
+// Compression of fp32 slices X[k][i_1]...[i_{nm}] into the summaries
+// Y[p][q_1]...[q_{nm}][c] (accumulated).  Ut[n] = [p][q][i] replica
+// transposes of the projections; Wt = [p][c][k] of the chunk's time rows;
+// bufA, bufB hold ncompress_buf_floats(...) floats each.
+struct NCompressInput {
+  int nm, P, Q;
+  const int64_t *dims;
+  const float *const *Ut;
+  float *bufA, *bufB;
+};
+void ncompress_chunk(const NCompressInput &c, const float *X, int64_t t, const float *Wt,
+                     float *Y, cudaStream_t st);
+int64_t ncompress_rows_max(int nm, const int64_t *dims, int Q, int64_t t);
+int64_t ncompress_buf_floats(int nm, const int64_t *dims, int P, int Q, int64_t t);
+
+// CP-ALS of the P N-way summaries (one CTA per replica).  F[0..NN-2] hold the
+// warm starts (P x Q x RT, unit columns) and G0 their Grams; on return F[0..NN-1]
+// hold the replica factors (F[NN-1] the time factor).
+struct NAlsInput {
+  const float *Y;
+  float *F[kMaxNModes];
+  const float *G0[kMaxNModes];
+  int NN, P, Q, R, RT, iters;
+  int *status;
+};
+bool nals_fits(int NN, int Q, int RT);
+bool nals_run(const NAlsInput &in, cudaStream_t st);
+
+// Anchor match of the N-mode replica factors (fp64).
+struct NAlignInput {
+  const float *F[kMaxNModes];    // nm non-temporal factors, then time
+  const float *PF[kMaxNModes];
+  float *Fh[kMaxNModes];
+  int nm, P, Q, S, R, RT;
+  int *perm;
+  double *scales;
+};
+void n_align(const NAlignInput &in, cudaStream_t st);
+
+// true for device (or managed) memory
+bool is_device_pointer(const void *p);
 
 // Fit: sums of ||X_k||^2 and ||X_k - A diag(C[k]) B^T||^2 over all slices,
 // written to out[0], out[1] (fp64).  partial: ceil(J/256)*ceil(I/32)*K*2 doubles.

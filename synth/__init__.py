@@ -18,3 +18,4 @@ from .planted import (  # noqa: F401
     time_projection,
     uneven_streams,
 )
+from .nmode import NWORKLOADS, NWorkload, nfactors, ninit_factors, nprojections, nslice_batch  # noqa: F401
