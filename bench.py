@@ -447,6 +447,9 @@ def main():
                          "slices, kernels launched one by one (small case for profiler captures)")
     ap.add_argument("--compress-only", action="store_true",
                     help="time octen_compress alone on --slices slices (profiling case)")
+    ap.add_argument("--nmode", default="",
+                    help="the N-mode extension's workload of this name (n4_100, n5_30): appends "
+                         "through the octen_n_* path, with the FP64 N-mode oracle beside it")
     ap.add_argument("--slices", type=int, default=4)
     ap.add_argument("--existing", type=int, default=0,
                     help="override the number of existing slices (small profiling cases)")
@@ -461,6 +464,8 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, wl, world, rank)
+    if args.nmode:
+        return main_nmode(args)
     if args.uneven_streams:
         return main_uneven(args)
     if args.replay:
@@ -643,6 +648,138 @@ def main_uneven(args):
                             "ms_per_step": round(1e3 * sec32, 3),
                             "note": "the same updates in fp32, octen_append one stream after another"},
         "speedup_vs_fp32_sequential": round(value / (slices / sec32), 3)}), flush=True)
+
+
+def ncompress_flops(wl, t):
+    """Multiply-adds x 2 of the N-mode compression chain for t slices: the first
+    product over every slice for all P Q columns, the per-replica products of
+    the other non-temporal modes, the time contraction."""
+    dims, P, Q = list(wl.dims), wl.P, wl.Q
+    rows = t * int(np.prod(dims[:-1]))
+    fl = 2.0 * rows * dims[-1] * P * Q
+    elems = rows * Q
+    for m in range(len(dims) - 2, -1, -1):
+        rin = elems // dims[m]
+        fl += 2.0 * P * rin * Q * dims[m]
+        elems = rin * Q
+    fl += 2.0 * P * (elems // t) * Q * t
+    return fl
+
+
+def nals_flops(wl):
+    """Algorithmic flops of the replica CP-ALS of one append: per update an
+    N-way MTTKRP (2 Q^N R) and the R x R solve applied to Q rows (2 Q R^2)."""
+    N, Q, R = len(wl.dims) + 1, wl.Q, wl.R
+    per_update = 2.0 * Q ** N * R + 2.0 * Q * R * R
+    return wl.P * (wl.als_iters * N + 1) * per_update
+
+
+def main_nmode(args):
+    """The N-mode extension (Sec. "Extending to Higher-Order Tensors"): a
+    stream of appends of the workload's batch size through octen_n_append with
+    the slices resident in HBM; the FP64 N-mode oracle runs the first append
+    beside it (parity and the CPU baseline)."""
+    import torch
+
+    from paper_1807_01350_gb300 import build as B
+    B.build()
+    import paper_1807_01350_gb300 as pkg
+    from oracle import octen_n
+    from synth import NWORKLOADS, nfactors, ninit_factors, nprojections, nslice_batch
+
+    wl = NWORKLOADS[args.nmode]
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nb, t, t_old = 4, wl.batch, wl.t_old
+    K = t_old + nb * t
+    As, C = nfactors(wl.dims, K, wl.R, args.seed)
+    X = round_to(nslice_batch(As, C, 0, K, wl.noise, args.seed), "fp32")
+    Us = nprojections(wl.dims, wl.P, wl.Q, wl.S, args.seed)
+    A0s, C0 = ninit_factors(As, C[:t_old], 0.01, args.seed)
+    Ws = [time_projection(t_old, wl.P, wl.Q, wl.S, args.seed, -1)] + \
+        [time_projection(t, wl.P, wl.Q, wl.S, args.seed, b) for b in range(nb)]
+    f32 = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=dev)
+    Xd = f32(X)
+    Wd = [f32(w) for w in Ws]
+    batches = [Xd[t_old + b * t:t_old + (b + 1) * t] for b in range(nb)]
+
+    def fresh():
+        g = pkg.OctenN(wl.dims, wl.R, wl.P, wl.Q, wl.S, wl.als_iters)
+        g.init(Xd[:t_old], [f32(u) for u in Us], Wd[0], [f32(a) for a in A0s], f32(C0))
+        return g
+
+    # parity of the first append against the oracle
+    g = fresh()
+    g.append(batches[0], Wd[1])
+    A_gpu, C_gpu = g.factors()
+    g.close()
+    o = octen_n.OctenOracleN(list(wl.dims), wl.R, wl.P, wl.Q, wl.S, wl.als_iters)
+    o.init(X[:t_old], Us, Ws[0], A0s, C0)
+    t0 = time.perf_counter()
+    o.append(X[t_old:t_old + t], Ws[1])
+    cpu_sec = time.perf_counter() - t0
+    relf = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))
+    f_gpu = octen_n.fit_n(X[:t_old + t], A_gpu, C_gpu)
+    f_ref = octen_n.fit_n(X[:t_old + t], o.A, o.C)
+    parity = {"A_rel_err_max": max(relf(a, b) for a, b in zip(A_gpu, o.A)),
+              "C_rel_err": relf(C_gpu, o.C), "fit_gpu": round(f_gpu, 6),
+              "fit_oracle": round(f_ref, 6), "tol": {"F": 1e-3, "fit": 1e-4},
+              "ok": bool(max(relf(a, b) for a, b in zip(A_gpu, o.A)) < 1e-3 and
+                         relf(C_gpu, o.C) < 1e-3 and abs(f_gpu - f_ref) < 1e-4)}
+
+    # timed stream
+    g = fresh()
+    warm, steps = max(args.warmup, 3), args.steps
+    for s in range(warm):
+        g.append(batches[s % nb], Wd[1 + s % nb])
+    torch.cuda.synchronize()
+    l0 = pkg.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        for s in range(steps):
+            g.append(batches[s % nb], Wd[1 + s % nb])
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = pkg.launch_count() - l0
+    # stage breakdown on further appends with the stage timers on
+    g.set_timing(True)
+    for s in range(nb):
+        g.append(batches[s % nb], Wd[1 + s % nb])
+    st = g.stage_times()
+    g.close()
+    pk = peaks()
+    stage_ms = {k: v[0] / v[1] for k, v in st.items() if v[1]}
+    work = {"compress": ncompress_flops(wl, t), "als": nals_flops(wl)}
+    stage_roof = {}
+    for k, fl in work.items():
+        a = fl / (stage_ms[k] / 1e3) / 1e12
+        stage_roof[k] = {"bound": "alu", "achieved": round(a, 3), "peak": round(FP32_ALU_TFLOPS, 1),
+                         "unit": "TFLOP/s", "frac": round(a / FP32_ALU_TFLOPS, 4),
+                         "flops_per_launch": fl, "ms_per_launch": round(stage_ms[k], 4),
+                         "traffic": None}
+    dominant = max(work, key=lambda k: stage_ms[k])
+    value = steps * t / (ms / 1e3)
+    print(json.dumps({
+        "metric": "new slices/sec, N-mode online CP update (fp32)", "value": round(value, 3),
+        "unit": "slices/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+        "ms_per_step": round(ms / steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic planted N-mode CP slices (seeded), resident in HBM",
+        "config": {"workload": wl.name, "N": len(wl.dims) + 1, "dims": list(wl.dims),
+                   "R": wl.R, "P": wl.P, "Q": wl.Q, "S": wl.S, "batch_slices": t,
+                   "existing_slices": t_old, "als_iters": wl.als_iters,
+                   "l2": f"{nb} batches of {t * wl.slice_elems * 4 / 2**20:.0f} MiB cycled"},
+        "clocks": clk.summary(), "gpu_launches": launches,
+        "roofline": dict(stage_roof[dominant], kernel=dominant),
+        "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_roofline": stage_roof,
+        "cpu_baseline": {"value": round(t / cpu_sec, 5), "unit": "slices/s", "cores": cpu_cores(),
+                         "kind": "oracle",
+                         "sample": f"one whole append of {t} slices at {wl.name} after an init "
+                                   f"from {t_old} slices ({cpu_sec:.1f} s)"},
+        "parity": parity}), flush=True)
 
 
 def main_replay(args, wl):

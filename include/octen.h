@@ -286,6 +286,14 @@ octen_status octen_n_get_replica_factors(const octen_nctx *ctx, int which, float
 /* Rows of the time factor so far. */
 int64_t octen_n_rows(const octen_nctx *ctx);
 
+/* Stage timers of the N-mode update (measurement aid): with timing on, every
+ * append records CUDA events around compress, warm_start, als, align, lift
+ * and c_solve; same conventions as octen_stage_times. */
+int octen_n_stage_count(void);
+const char *octen_n_stage_name(int i);
+octen_status octen_n_set_timing(octen_nctx *ctx, int on);
+octen_status octen_n_stage_times(const octen_nctx *ctx, double *ms, uint64_t *launches);
+
 void octen_n_destroy(octen_nctx *ctx);
 const char *octen_n_last_error(const octen_nctx *ctx);
 

@@ -105,8 +105,15 @@ def lib() -> ctypes.CDLL:
         L.octen_n_destroy.restype = None
         L.octen_n_last_error.argtypes = [vp]
         L.octen_n_last_error.restype = ctypes.c_char_p
+        L.octen_n_stage_count.argtypes = []
+        L.octen_n_stage_count.restype = ctypes.c_int
+        L.octen_n_stage_name.argtypes = [ctypes.c_int]
+        L.octen_n_stage_name.restype = ctypes.c_char_p
+        L.octen_n_set_timing.argtypes = [vp, ctypes.c_int]
+        L.octen_n_stage_times.argtypes = [vp, vp, vp]
         for name in ("octen_n_create", "octen_n_init", "octen_n_append", "octen_n_get_factors",
-                     "octen_n_get_replicas", "octen_n_get_replica_factors"):
+                     "octen_n_get_replicas", "octen_n_get_replica_factors",
+                     "octen_n_set_timing", "octen_n_stage_times"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("octen_create", "octen_init", "octen_append", "octen_append_many",
                      "octen_get_factors",
@@ -380,6 +387,18 @@ class OctenN:
         self._check(self._lib.octen_n_get_replica_factors(self._h, int(which), fp,
                                                           perm.ctypes.data, scales.ctypes.data))
         return Fs, perm, scales
+
+    def set_timing(self, on: bool = True):
+        self._check(self._lib.octen_n_set_timing(self._h, int(bool(on))))
+
+    def stage_times(self) -> dict:
+        """{stage: (milliseconds, timed intervals)} accumulated while timing is on."""
+        n = self._lib.octen_n_stage_count()
+        ms = np.zeros(n, np.float64)
+        cnt = np.zeros(n, np.uint64)
+        self._check(self._lib.octen_n_stage_times(self._h, ms.ctypes.data, cnt.ctypes.data))
+        return {self._lib.octen_n_stage_name(i).decode(): (float(ms[i]), int(cnt[i]))
+                for i in range(n)}
 
     def close(self):
         if getattr(self, "_h", None):

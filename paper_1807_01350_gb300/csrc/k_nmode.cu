@@ -33,16 +33,31 @@ __host__ __device__ inline int64_t ipow(int64_t b, int e) {
   return r;
 }
 
+// The Khatri-Rao form of the MTTKRP keeps the product of the outer factors'
+// rows for every outer index combination (Q^(NN-2) x RT floats) and their X
+// offsets; it applies for Q <= 32 while that table stays small.
+constexpr int kKrMaxFloats = 8192;
+__host__ __device__ inline bool nals_use_kr(int NN, int Q, int RT) {
+  return Q <= 32 && ipow(Q, NN - 2) * RT <= kKrMaxFloats;
+}
+
 // Shared floats of the replica ALS: X Q^NN (if it is kept in shared memory,
-// rounded up to a multiple of 4) | F NN Q RT | M Q RT | Mp max(Q RT, 128) |
-// G NN RT^2 | Hp, Lc, Lr RT^2 each | rf RT | red 8 RT | scl RT.  Every array
-// after X has a length that is a multiple of 4 (RT is a multiple of 8).
+// rounded up to a multiple of 4) | F NN Q RT | M Q RT | Mp max(Q, 128) RT |
+// G NN RT^2 | Hp, Lc, Lr RT^2 each | rf RT | red 8 RT | scl RT | with the
+// Khatri-Rao form: KRo Q^(NN-2) RT | Oo Q^(NN-2) ints (rounded up to 4).
+// Every array after X has a length that is a multiple of 4 (RT is a multiple
+// of 8).
 size_t nals_floats(int NN, int Q, int RT, bool x_in_smem) {
   const size_t q = (size_t)Q, rt = (size_t)RT;
   const size_t x = x_in_smem ? (((size_t)ipow(Q, NN) + 3) & ~size_t(3)) : 0;
-  const size_t mp = q * rt > 128 ? q * rt : 128;
+  const size_t mp = (q > 128 ? q : 128) * rt;
+  size_t kr = 0;
+  if (nals_use_kr(NN, Q, RT)) {
+    const size_t no = (size_t)ipow(Q, NN - 2);
+    kr = no * rt + ((no + 3) & ~size_t(3));
+  }
   return x + (size_t)NN * q * rt + q * rt + mp + (size_t)NN * rt * rt + 3 * rt * rt +
-         10 * rt;
+         10 * rt + kr;
 }
 
 __device__ __forceinline__ void nals_mttkrp_barrier() {
@@ -52,54 +67,222 @@ __device__ __forceinline__ void nals_mttkrp_barrier() {
 // MTTKRP of mode n by the 128 threads u = 0..127 (warps 4..7):
 //   M[q][r] = sum over the other indices of X[..q..] prod_{m != n} F_m[idx_m][r].
 // The other modes are split into an inner mode ml (the last one other than n)
-// and the outer ones; the outer index range is split into `ns` parts when Q RT
-// is below 128, so that every thread has work, and the parts are summed in
-// order afterwards.
+// and the outer ones.  A work item is one (q, r < R) and a contiguous range of
+// the outer index combinations (the range split into `ns` parts when Q R is
+// below 128, so that every thread has work; the parts are summed in order
+// afterwards).  Per outer combination: the product of the outer factors' rows
+// (once) and the inner sum over ml; the outer digits advance like an odometer
+// (no divisions in the loop).  Entries r >= R of M are left untouched (zero).
 template <int RT, int NN>
 __device__ void nals_mttkrp(const float *X, const float *F, int Q, int R, int n, float *M,
                             float *Mp, int u) {
-  int64_t pw[NN];
+  int pw[NN];
   pw[NN - 1] = 1;
 #pragma unroll
   for (int m = NN - 2; m >= 0; --m) pw[m] = pw[m + 1] * Q;
   const int ml = n == NN - 1 ? NN - 2 : NN - 1;
-  const int64_t sl = pw[ml];
-  const int pairs = Q * RT;
-  const int ns = pairs >= 128 ? 1 : 128 / pairs;
-  const int64_t nouter = ipow(Q, NN - 2);
-  const int64_t chunk = (nouter + ns - 1) / ns;
-  for (int w = u; w < pairs * ns; w += 128) {
-    const int part = w / pairs, e = w - part * pairs;
-    const int q = e / RT, r = e - q * RT;
+  int sl = 0, pwn = 0;   // strides of modes ml and n (selected without indexing pw at run time)
+#pragma unroll
+  for (int m = 0; m < NN; ++m) {
+    if (m == ml) sl = pw[m];
+    if (m == n) pwn = pw[m];
+  }
+  const int items = Q * R;
+  const int ns = items >= 128 ? 1 : 128 / items;
+  const int nouter = (int)ipow(Q, NN - 2);
+  const int chunk = (nouter + ns - 1) / ns;
+  for (int w = u; w < items * ns; w += 128) {
+    const int part = w / items, e = w - part * items;
+    const int q = e / R, r = e - q * R;
+    const int o0 = part * chunk;
+    const int o1 = o0 + chunk < nouter ? o0 + chunk : nouter;
     float acc = 0.f;
-    if (r < R) {
-      const int64_t o0 = part * chunk;
-      const int64_t o1 = o0 + chunk < nouter ? o0 + chunk : nouter;
+    if (o0 < o1) {
+      int dig[NN];
+      int rem = o0;
+#pragma unroll
+      for (int m = NN - 1; m >= 0; --m) {
+        dig[m] = 0;
+        if (m == n || m == ml) continue;
+        dig[m] = rem % Q;
+        rem /= Q;
+      }
       const float *fl = F + (size_t)ml * Q * RT + r;
-      for (int64_t o = o0; o < o1; ++o) {
-        int64_t rem = o, off = q * pw[n];
+      const float *xq = X + q * pwn;
+      for (int o = o0; o < o1; ++o) {
+        int off = 0;
         float pr = 1.f;
+#pragma unroll
+        for (int m = 0; m < NN; ++m) {
+          if (m == n || m == ml) continue;
+          off += dig[m] * pw[m];
+          pr *= F[(m * Q + dig[m]) * RT + r];
+        }
+        const float *xp = xq + off;
+        float s = 0.f;
+        for (int d = 0; d < Q; ++d) s = fmaf(xp[d * sl], fl[d * RT], s);
+        acc = fmaf(pr, s, acc);
 #pragma unroll
         for (int m = NN - 1; m >= 0; --m) {
           if (m == n || m == ml) continue;
-          const int d = (int)(rem % Q);
-          rem /= Q;
-          off += d * pw[m];
-          pr *= F[((size_t)m * Q + d) * RT + r];
+          if (++dig[m] < Q) break;
+          dig[m] = 0;
         }
-        const float *xp = X + off;
-        for (int d = 0; d < Q; ++d) acc = fmaf(xp[d * sl], pr * fl[d * RT], acc);
       }
     }
-    if (ns == 1) M[e] = acc;
+    if (ns == 1) M[q * RT + r] = acc;
     else Mp[w] = acc;
   }
   if (ns > 1) {
     nals_mttkrp_barrier();
-    for (int e = u; e < pairs; e += 128) {
+    for (int e = u; e < items; e += 128) {
       float s = 0.f;
-      for (int part = 0; part < ns; ++part) s += Mp[part * pairs + e];
-      M[e] = s;
+      for (int part = 0; part < ns; ++part) s += Mp[part * items + e];
+      M[(e / R) * RT + e % R] = s;
+    }
+  }
+}
+
+// MTTKRP of mode n in Khatri-Rao form by warps 4..7 (u = 0..127), Q <= 32.
+// First the outer modes' (all but n and the inner mode ml) row products
+// KRo[o][r] and the X offsets Oo[o] of every outer combination o; then
+//  - non-temporal n (ml = the time mode, stride 1): a warp per q at a time,
+//    lanes over (phase s, inner index d): acc[r] = sum over the phase's o of
+//    X[q, o, d] KRo[o][r], times F_ml[d][r], summed over the warp;
+//  - time mode n (ml = the last non-temporal mode): lanes over (s, c), 4 nsw
+//    groups over o: t[r] = sum_d X[o, d, c] F_ml[d][r], acc[r] += KRo[o][r] t[r];
+//    the groups' partials are summed in order.
+// Lanes read consecutive X addresses (the stride-1 index runs across them).
+template <int RT, int NN>
+__device__ void nals_mttkrp_kr(const float *X, const float *F, int Q, int n, float *M,
+                               float *Mp, float *KRo, int *Oo, int u) {
+  int pw[NN];
+  pw[NN - 1] = 1;
+#pragma unroll
+  for (int m = NN - 2; m >= 0; --m) pw[m] = pw[m + 1] * Q;
+  const int ml = n == NN - 1 ? NN - 2 : NN - 1;
+  int sl = 0, pwn = 0;
+#pragma unroll
+  for (int m = 0; m < NN; ++m) {
+    if (m == ml) sl = pw[m];
+    if (m == n) pwn = pw[m];
+  }
+  const int nouter = (int)ipow(Q, NN - 2);
+  for (int o = u; o < nouter; o += 128) {
+    int rem = o, off = 0;
+    float4 pr[RT / 4];
+#pragma unroll
+    for (int r4 = 0; r4 < RT / 4; ++r4) pr[r4] = make_float4(1.f, 1.f, 1.f, 1.f);
+#pragma unroll
+    for (int m = NN - 1; m >= 0; --m) {
+      if (m == n || m == ml) continue;
+      const int dg = rem % Q;
+      rem /= Q;
+      off += dg * pw[m];
+      const float4 *f = reinterpret_cast<const float4 *>(F + (m * Q + dg) * RT);
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4) {
+        const float4 v = f[r4];
+        pr[r4].x *= v.x; pr[r4].y *= v.y; pr[r4].z *= v.z; pr[r4].w *= v.w;
+      }
+    }
+    float4 *k = reinterpret_cast<float4 *>(KRo + o * RT);
+#pragma unroll
+    for (int r4 = 0; r4 < RT / 4; ++r4) k[r4] = pr[r4];
+    Oo[o] = off;
+  }
+  nals_mttkrp_barrier();
+  const int w = u >> 5, lane = u & 31;
+  const int nsw = 32 / Q;
+  const int s = lane / Q, i = lane - s * Q;
+  const bool active = s < nsw;
+  const float *Fl = F + (size_t)ml * Q * RT;
+  float acc[RT];
+  if (n != NN - 1) {
+    for (int q = w; q < Q; q += 4) {
+#pragma unroll
+      for (int r = 0; r < RT; ++r) acc[r] = 0.f;
+      if (active) {
+        const float *xq = X + q * pwn + i;
+#pragma unroll 4
+        for (int o = s; o < nouter; o += nsw) {
+          const float x = xq[Oo[o]];
+          const float4 *kr = reinterpret_cast<const float4 *>(KRo + o * RT);
+#pragma unroll
+          for (int r4 = 0; r4 < RT / 4; ++r4) {
+            const float4 k = kr[r4];
+            acc[4 * r4] = fmaf(x, k.x, acc[4 * r4]);
+            acc[4 * r4 + 1] = fmaf(x, k.y, acc[4 * r4 + 1]);
+            acc[4 * r4 + 2] = fmaf(x, k.z, acc[4 * r4 + 2]);
+            acc[4 * r4 + 3] = fmaf(x, k.w, acc[4 * r4 + 3]);
+          }
+        }
+        const float4 *f = reinterpret_cast<const float4 *>(Fl + i * RT);
+#pragma unroll
+        for (int r4 = 0; r4 < RT / 4; ++r4) {
+          const float4 v = f[r4];
+          acc[4 * r4] *= v.x;
+          acc[4 * r4 + 1] *= v.y;
+          acc[4 * r4 + 2] *= v.z;
+          acc[4 * r4 + 3] *= v.w;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RT; ++r)
+        for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+      if (lane < RT) {
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+          if (r == lane) v = acc[r];
+        M[q * RT + lane] = v;
+      }
+    }
+  } else {
+    const int ng = 4 * nsw;
+#pragma unroll
+    for (int r = 0; r < RT; ++r) acc[r] = 0.f;
+    if (active) {
+      const int g = w * nsw + s;
+#pragma unroll 2
+      for (int o = g; o < nouter; o += ng) {
+        const float *xo = X + Oo[o] + i;
+        float t[RT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) t[r] = 0.f;
+#pragma unroll 4
+        for (int d = 0; d < Q; ++d) {
+          const float x = xo[d * sl];
+          const float4 *f = reinterpret_cast<const float4 *>(Fl + d * RT);
+#pragma unroll
+          for (int r4 = 0; r4 < RT / 4; ++r4) {
+            const float4 v = f[r4];
+            t[4 * r4] = fmaf(x, v.x, t[4 * r4]);
+            t[4 * r4 + 1] = fmaf(x, v.y, t[4 * r4 + 1]);
+            t[4 * r4 + 2] = fmaf(x, v.z, t[4 * r4 + 2]);
+            t[4 * r4 + 3] = fmaf(x, v.w, t[4 * r4 + 3]);
+          }
+        }
+        const float4 *kr = reinterpret_cast<const float4 *>(KRo + o * RT);
+#pragma unroll
+        for (int r4 = 0; r4 < RT / 4; ++r4) {
+          const float4 k = kr[r4];
+          acc[4 * r4] = fmaf(k.x, t[4 * r4], acc[4 * r4]);
+          acc[4 * r4 + 1] = fmaf(k.y, t[4 * r4 + 1], acc[4 * r4 + 1]);
+          acc[4 * r4 + 2] = fmaf(k.z, t[4 * r4 + 2], acc[4 * r4 + 2]);
+          acc[4 * r4 + 3] = fmaf(k.w, t[4 * r4 + 3], acc[4 * r4 + 3]);
+        }
+      }
+      float4 *mp = reinterpret_cast<float4 *>(Mp + ((size_t)g * Q + i) * RT);
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4)
+        mp[r4] = make_float4(acc[4 * r4], acc[4 * r4 + 1], acc[4 * r4 + 2], acc[4 * r4 + 3]);
+    }
+    nals_mttkrp_barrier();
+    for (int e = u; e < Q * RT; e += 128) {
+      float sum = 0.f;
+      for (int g = 0; g < ng; ++g) sum += Mp[(size_t)g * Q * RT + e];
+      M[e] = sum;
     }
   }
 }
@@ -137,10 +320,14 @@ __global__ void __launch_bounds__(kNThreads, 1) nals_kernel(NAlsArgs a) {
   float *F = base;                                   // [NN][Q][RT]
   float *M = F + (size_t)NN * Q * RT;                // [Q][RT]
   float *Mp = M + Q * RT;                            // MTTKRP partials
-  float *G = Mp + (Q * RT > 128 ? Q * RT : 128);     // [NN][RT][RT]
+  float *G = Mp + (Q > 128 ? Q : 128) * RT;          // [NN][RT][RT]
   float *Hp = G + NN * RT * RT;
   float *Lc = Hp + RT * RT, *Lr = Lc + RT * RT, *rf = Lr + RT * RT;
   float *red = rf + RT, *scl = red + 8 * RT;
+  const bool use_kr = nals_use_kr(NN, Q, RT);
+  float *KRo = scl + RT;                                        // [Q^(NN-2)][RT]
+  int *Oo = reinterpret_cast<int *>(KRo + ipow(Q, NN - 2) * RT);
+  for (int e = tid; e < Q * RT; e += blockDim.x) M[e] = 0.f;   // columns r >= R stay zero
 #pragma unroll
   for (int m = 0; m < NN - 1; ++m) {
     for (int e = tid; e < Q * RT; e += blockDim.x)
@@ -163,7 +350,8 @@ __global__ void __launch_bounds__(kNThreads, 1) nals_kernel(NAlsArgs a) {
       factor_barrier();
       ldl_factor<RT>(Hp, G + ml * RT * RT, R, Craw, Rs, Lc, Lr, rf, &fail_s);
     } else {
-      nals_mttkrp<RT, NN>(X, F, Q, R, n, M, Mp, tid - 128);
+      if (use_kr) nals_mttkrp_kr<RT, NN>(X, F, Q, n, M, Mp, KRo, Oo, tid - 128);
+      else nals_mttkrp<RT, NN>(X, F, Q, R, n, M, Mp, tid - 128);
     }
     __syncthreads();
     if (fail_s && tid == 0) atomicOr(a.status, kDevCholesky);

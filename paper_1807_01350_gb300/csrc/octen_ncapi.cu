@@ -25,6 +25,11 @@ constexpr int64_t kNRowsMax = 4000000;
 constexpr int64_t kNBufFloatsMax = int64_t(1) << 28;
 constexpr int64_t kNBatchMax = 64;
 
+// stages timed with CUDA events when timing is on
+enum NStage : int { kNCompress = 0, kNWarm, kNAls, kNAlign, kNLift, kNCsolve, kNStages };
+const char *const kNStageNames[kNStages] = {"compress", "warm_start", "als", "align", "lift",
+                                            "c_solve"};
+
 }  // namespace
 
 struct octen_nctx {
@@ -52,8 +57,45 @@ struct octen_nctx {
   void *stg[2] = {nullptr, nullptr};
   size_t stg_bytes[2] = {0, 0};
 
+  // stage timers
+  bool timing = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  cudaEvent_t open_ev = nullptr;
+  struct Pending { int stage; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  double stage_ms[kNStages] = {};
+  uint64_t stage_n[kNStages] = {};
+
+  void mark(int stage, int begin) {
+    if (!timing) return;
+    if (evused == evpool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      evpool.push_back(e);
+    }
+    cudaEvent_t e = evpool[evused++];
+    cudaEventRecord(e, st);
+    if (begin) open_ev = e;
+    else if (open_ev) pending.push_back({stage, open_ev, e});
+  }
+  void flush_timers() {
+    for (const Pending &q : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+        stage_ms[q.stage] += ms;
+        stage_n[q.stage] += 1;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    pending.clear();
+    evused = 0;
+  }
+
   ~octen_nctx() {
     cudaStreamSynchronize(st);
+    for (cudaEvent_t e : evpool) cudaEventDestroy(e);
     for (void *p : owned) cudaFree(p);
     if (C) cudaFree(C);
     for (void *p : stg) cudaFree(p);
@@ -105,6 +147,7 @@ struct octen_nctx {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(OCTEN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    if (!pending.empty()) flush_timers();
     int flags = 0;
     cudaMemcpy(&flags, dstatus, sizeof(int), cudaMemcpyDeviceToHost);
     if (flags) {
@@ -328,19 +371,25 @@ octen_status octen_n_append(octen_nctx *x, const float *X_new, int64_t t, const 
   const float *Wd = x->stage_in(W_new, (size_t)t * Qd * 4, 1);
   if (!Xd || !Wd) return x->fail(OCTEN_ENOMEM, "staging the batch");
   // 1. compress the batch into the summaries
+  x->mark(kNCompress, 1);
   x->compress(Xd, t, Wd);
+  x->mark(kNCompress, 0);
   // 2. CP of every summary, warm-started from U_n,p^T A_n
+  x->mark(kNWarm, 1);
   for (int n = 0; n < nm; ++n) {
     x->project(n);
     warm_start(x->PF[n], c.P, c.Q, c.S, c.R, RT, x->Ft[n], x->Gw[n], x->st);
   }
+  x->mark(kNWarm, 0);
   NAlsInput ai{};
   ai.Y = x->Y;
   for (int n = 0; n <= nm; ++n) ai.F[n] = x->Ft[n];
   for (int n = 0; n < nm; ++n) ai.G0[n] = x->Gw[n];
   ai.NN = x->NN; ai.P = c.P; ai.Q = c.Q; ai.R = c.R; ai.RT = RT; ai.iters = c.als_iters;
   ai.status = x->dstatus;
+  x->mark(kNAls, 1);
   if (!nals_run(ai, x->st)) return x->fail(OCTEN_ECUDA, "replica CP-ALS launch failed");
+  x->mark(kNAls, 0);
   // 3. anchor match in every non-temporal mode
   NAlignInput mi{};
   for (int n = 0; n <= nm; ++n) {
@@ -350,14 +399,20 @@ octen_status octen_n_append(octen_nctx *x, const float *X_new, int64_t t, const 
   for (int n = 0; n < nm; ++n) mi.PF[n] = x->PF[n];
   mi.nm = nm; mi.P = c.P; mi.Q = c.Q; mi.S = c.S; mi.R = c.R; mi.RT = RT;
   mi.perm = x->perm; mi.scales = x->scales;
+  x->mark(kNAlign, 1);
   n_align(mi, x->st);
+  x->mark(kNAlign, 0);
   // 4. lift every non-temporal factor, solve the new rows of the time factor
+  x->mark(kNLift, 1);
   for (int n = 0; n < nm; ++n)
     lift_apply(x->lift_env(), x->Fh[n], x->PF[n], x->L[n], x->over[n], x->dims[n], x->A[n]);
+  x->mark(kNLift, 0);
   float *C_new = x->C + x->K * c.R;
+  x->mark(kNCsolve, 1);
   solve_c_new(Wd, x->Fh[nm], x->G, t, c.P, c.Q, c.S, Qd, c.R, RT, x->csolve, x->splitk,
               octen_nctx::kSplitkFloats, C_new, x->dstatus, x->st);
   update_g(Wd, C_new, t, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
+  x->mark(kNCsolve, 0);
   const octen_status s = x->sync_check("append");
   if (s != OCTEN_OK) return s;
   x->K += t;
@@ -406,6 +461,26 @@ octen_status octen_n_get_replica_factors(const octen_nctx *cx, int which, float 
 }
 
 int64_t octen_n_rows(const octen_nctx *x) { return x ? x->K : 0; }
+
+int octen_n_stage_count(void) { return kNStages; }
+
+const char *octen_n_stage_name(int i) { return i >= 0 && i < kNStages ? kNStageNames[i] : ""; }
+
+octen_status octen_n_set_timing(octen_nctx *x, int on) {
+  if (!x) return OCTEN_EINVAL;
+  x->timing = on != 0;
+  return OCTEN_OK;
+}
+
+octen_status octen_n_stage_times(const octen_nctx *cx, double *ms, uint64_t *launches) {
+  octen_nctx *x = const_cast<octen_nctx *>(cx);
+  if (!x) return OCTEN_EINVAL;
+  for (int i = 0; i < kNStages; ++i) {
+    if (ms) ms[i] = x->stage_ms[i];
+    if (launches) launches[i] = x->stage_n[i];
+  }
+  return OCTEN_OK;
+}
 
 void octen_n_destroy(octen_nctx *x) { delete x; }
 
