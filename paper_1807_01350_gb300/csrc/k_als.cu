@@ -288,6 +288,19 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Ft[p][r][q] = bf16(F[p][q][r]) for r < NP (zero beyond RT): the transposed
+// bf16 operand of a factor.  grid (ceil(Q / 256), P), 256 threads.
+template <int RT>
+__global__ void __launch_bounds__(256)
+    factor_bf16_t_kernel(const float *__restrict__ F, int Q, int NP,
+                         __nv_bfloat16 *__restrict__ Ft) {
+  const int p = blockIdx.y, q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const float *f = F + ((int64_t)p * Q + q) * RT;
+  for (int r = 0; r < NP; ++r)
+    Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(r < RT ? f[r] : 0.f);
+}
+
 static int block_for(int Q) { return ((Q + 31) / 32) * 32; }
 
 int als_factor_floats(int RT) {
@@ -424,9 +437,40 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   const int ks = tc_gemm_splits(m3.K, b.ksplit, kAlsKAtoms);
   const dim3 gKR(NP, P);
   const dim3 gM((Q + 256 / RT - 1) / (256 / RT), P);   // 32 output octets per CTA
+  // With 32 | Q the M3 pass needs no Khatri-Rao operand: the GEMM contracts b,
+  //   Tb[(c, a)][r] = sum_b Xc[(c, a)][b] B[b][r]   (B^T in bf16 as the B operand),
+  // and its epilogue reduces every 32 consecutive a with weights A[a][r] in
+  // fp32 (the fused reduction of the Tc pass), so M3[c][r] = sum of Q / 32
+  // partials; Tb itself is never stored.
+  const bool m3_fused = fuse_m1 && b.Bt != nullptr;
+  TcStoreArgs m3f{};
+  if (m3_fused) {
+    m3f.A = b.Xc; m3f.a_inner = Q; m3f.a_rows = (int64_t)P * QQ; m3f.a_rows_per_z = (int)QQ;
+    m3f.B = b.Bt; m3f.b_inner = Q; m3f.b_rows = (int64_t)P * NP; m3f.b_rows_per_z = NP;
+    m3f.M = (int)QQ; m3f.N = RT; m3f.K = Q; m3f.BN = NP; m3f.batch = P; m3f.ksplit = 1;
+    m3f.D = nullptr; m3f.Dh = nullptr; m3f.s_split = 0; m3f.s_z = 0; m3f.s_m = 0;
+    m3f.m1_B = b.Af; m3f.m1_part = b.Mparts; m3f.Q = Q; m3f.RT = RT;
+    m3f.smem_reserve = 56 * 1024;
+    m3f.a_stream = true;
+    m3f.katoms = kAlsKAtoms;
+    // B^T of the warm start; every later B update writes it from its solve
+    mk(kStAlsAux, 1);
+    factor_bf16_t_kernel<RT><<<dim3((Q + 255) / 256, P), 256, 0, st>>>(b.Bf, Q, NP, b.Bt);
+    count_launch();
+    mk(kStAlsAux, 0);
+  }
   bool ok = true;
   auto c_update = [&]() {
     factor_async<RT>(b.Bf, b.GB, b.GA, P, Q, R, b, st);
+    if (m3_fused) {
+      mk(kStAlsGemm, 1);
+      ok = ok && tc_gemm_store(m3f, b.status, st);
+      mk(kStAlsGemm, 0);
+      mk(kStAlsSolve, 1);
+      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Cf, b.Ct, NP, P, Q, 0, b, st);
+      mk(kStAlsSolve, 0);
+      return;
+    }
     mk(kStAlsAux, 1);
     kr_kernel<RT><<<gKR, 256, 0, st>>>(b.Af, b.Bf, Q, b.KR);
     count_launch();
@@ -463,7 +507,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);
-    apply<RT>(b.M, 1, 0, RT, b.Bf, nullptr, 0, P, Q, 1, b, st);
+    apply<RT>(b.M, 1, 0, RT, b.Bf, m3_fused ? b.Bt : nullptr, NP, P, Q, 1, b, st);
     mk(kStAlsSolve, 0);
   }
   if (ok) c_update();

@@ -198,6 +198,7 @@ struct TcStoreEpi {
   float *part;
   int Q, RT;
   __nv_bfloat16 *Dh;
+  __device__ __forceinline__ bool stores() const { return D != nullptr || Dh != nullptr; }
   __device__ __forceinline__ void store(int z, int split, int m, int n, float v) const {
     const int64_t o = (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n;
     if (Dh) Dh[o] = __float2bfloat16_rn(v);
@@ -275,6 +276,7 @@ struct Mode1TcEpi {
   const float *Bfac = nullptr;   // no fused reduction
   float *part = nullptr;
   int RT = 0;
+  __device__ __forceinline__ bool stores() const { return true; }
   __device__ __forceinline__ void store(int z, int, int a, int b, float v) const {
     const int k = z / P, p = z - k * P;
     T2[(((int64_t)p * t + k) * Q + a) * Q + b] = v;
@@ -498,7 +500,7 @@ __global__ void __launch_bounds__(192, 1)
               stored = true;
             }
           }
-          if (!stored) {
+          if (!stored && epi.stores()) {   // else only the fused reduction below
             for (int i = 0; i < 32; ++i) {
               const int mi = m0 + quad * 32 + i;
               if (mi < sh.M && n < sh.N) epi.store(z, split, mi, n, stg[i * 33 + lane]);

@@ -78,7 +78,7 @@ struct octen_ctx {
   // tensor-core ALS (bf16 / e4m3 modes with Q % 8 == 0)
   bool als_tc = false;
   int als_ks = 1;
-  __nv_bfloat16 *Xa = nullptr, *Xc = nullptr, *KR = nullptr, *Ctb = nullptr;
+  __nv_bfloat16 *Xa = nullptr, *Xc = nullptr, *KR = nullptr, *Ctb = nullptr, *Btb = nullptr;
   float *Mparts = nullptr;
   // replica CP-ALS: the factor of each update runs on als_side beside its MTTKRP
   cudaStream_t als_side = nullptr;
@@ -435,6 +435,7 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     const size_t nparts = (size_t)(x->als_ks > (c.Q / 32) ? x->als_ks : (c.Q / 32));
     ok = x->alloc(x->Xa, P * Q * Q * Q) && x->alloc(x->Xc, P * Q * Q * Q) &&
          x->alloc(x->KR, P * kAlsNP * Q * Q) && x->alloc(x->Ctb, P * kAlsNP * Q) &&
+         x->alloc(x->Btb, P * kAlsNP * Q) &&
          x->alloc(x->Mparts, nparts * P * Q * RT);
     x->als_tc = ok;
   }
@@ -611,6 +612,7 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   ab.Af = x->At; ab.Bf = x->Bt; ab.Cf = x->Ct; ab.GA = x->GA; ab.GB = x->GB; ab.GC = x->GC;
   ab.M = x->M; ab.H = x->H; ab.status = x->dstatus;
   ab.use_tc = x->als_tc; ab.Xa = x->Xa; ab.Xc = x->Xc; ab.KR = x->KR; ab.Ct = x->Ctb;
+  ab.Bt = x->Btb;
   ab.Mparts = x->Mparts; ab.ksplit = x->als_ks;
   ab.side = x->als_side; ab.ev_fork = x->als_fork; ab.ev_join = x->als_join; ab.L = x->Lfac;
   ab.layouts_ready = x->layouts_ready;

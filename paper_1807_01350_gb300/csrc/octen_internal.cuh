@@ -108,6 +108,7 @@ struct TcStoreArgs {
   __nv_bfloat16 *Dh = nullptr;   // if set: the output rounded to bf16 here instead of D
   // optional fused reduction for rows m = a * Q + b (needs BN == 32, Q % 32 == 0):
   // m1_part[z][m / 32][n] = sum over the 32 rows of D(m, n) * m1_B[z][b][n]
+  // (with D and Dh both null only this reduction is written)
   const float *m1_B = nullptr;
   float *m1_part = nullptr;
   int Q = 0, RT = 0;
@@ -163,6 +164,7 @@ struct AlsBuffers {
   __nv_bfloat16 *Xa = nullptr, *Xc = nullptr;   // P x Q^3 each
   __nv_bfloat16 *KR = nullptr;                  // P x kAlsNP x Q^2
   __nv_bfloat16 *Ct = nullptr;                  // P x kAlsNP x Q
+  __nv_bfloat16 *Bt = nullptr;                  // P x kAlsNP x Q (B^T, the M3 operand)
   float *Mparts = nullptr;                      // ksplit x P x Q x RT
   int ksplit = 1;
   bool layouts_ready = false;                   // Xa, Xc already hold bf16(X_p)
