@@ -106,6 +106,12 @@ struct octen_ctx {
   // per-batch scratch, grown on demand
   DevBuf Tbuf, T2buf, Wbuf, X8buf, xscale, stage[4], fitpart;
 
+  // host slices of an append are copied in chunks on copy_st, so that the
+  // mode-2 contraction of one chunk runs while the next is in flight
+  static constexpr int kCopyChunks = 8;
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_ev[kCopyChunks] = {}, copy_ready = nullptr;
+
   // stage timers (CUDA events on the context's stream)
   bool timing = false;
   std::vector<cudaEvent_t> evpool;
@@ -160,6 +166,13 @@ struct octen_ctx {
     if (als_fork) cudaEventDestroy(als_fork);
     if (als_join) cudaEventDestroy(als_join);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    if (copy_st) {
+      cudaStreamSynchronize(copy_st);
+      cudaStreamDestroy(copy_st);
+    }
+    for (cudaEvent_t e : copy_ev)
+      if (e) cudaEventDestroy(e);
+    if (copy_ready) cudaEventDestroy(copy_ready);
     for (auto &b : owned) cudaFree(b.p);
     DevBuf *extra[] = {&Tbuf, &T2buf, &Wbuf, &X8buf, &xscale, &stage[0], &stage[1], &stage[2],
                        &stage[3], &fitpart};
@@ -275,30 +288,40 @@ void set_types(octen_ctx *x) {
 
 constexpr int64_t kChunk = 64;  // slices per compression pass
 
-// Z_p (+)= compression of t slices (t <= kChunk) into Yacc.  With `layouts`
-// the mode-3 pass may also leave the bf16 copies of Yacc for the tensor-core
-// CP-ALS in x->Xa / x->Xc (x->layouts_ready says whether it did).
-octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float *Wd,
-                            float *Yacc, bool layouts = false) {
+// Scratch of one compression pass of t slices.
+octen_status compress_scratch(octen_ctx *x, int64_t t) {
   const octen_config &c = x->cfg;
   const size_t tb = (size_t)t * c.P * c.Q * c.I * elem_size(x->tmid);
   if (!x->grow(x->Tbuf, tb)) return x->fail(OCTEN_ENOMEM, "scratch T (%zu bytes)", tb);
   const size_t t2b = (size_t)t * c.P * c.Q * c.Q * sizeof(float);
   if (!x->grow(x->T2buf, t2b)) return x->fail(OCTEN_ENOMEM, "scratch T2 (%zu bytes)", t2b);
-  Mode2Args m2{};
-  m2.X = Xd; m2.tx = x->xin; m2.Vt = x->Vt; m2.tv = x->tv; m2.slice_scale = nullptr;
-  m2.T = x->Tbuf.p; m2.tt = x->tmid; m2.t = t; m2.I = c.I; m2.J = c.J;
-  m2.P = c.P; m2.Q = c.Q; m2.S = c.S; m2.Qd = x->Qd;
   if (c.prec == OCTEN_FP8E4M3) {
     const size_t xb = (size_t)t * c.I * c.J;
     if (!x->grow(x->X8buf, xb) || !x->grow(x->xscale, (size_t)t * sizeof(float)))
       return x->fail(OCTEN_ENOMEM, "scratch for e4m3 slices");
+  }
+  return OCTEN_OK;
+}
+
+// Quantisation (fp8) and mode-2 contraction of slices [k0, k0 + n) of a pass
+// whose slices start at Xd (device).
+void compress_mode2(octen_ctx *x, const void *Xd, int64_t k0, int64_t n) {
+  const octen_config &c = x->cfg;
+  const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
+  Mode2Args m2{};
+  m2.X = static_cast<const char *>(Xd) + k0 * slice; m2.tx = x->xin; m2.Vt = x->Vt;
+  m2.tv = x->tv; m2.slice_scale = nullptr;
+  m2.T = static_cast<char *>(x->Tbuf.p) + (size_t)k0 * c.P * c.Q * c.I * elem_size(x->tmid);
+  m2.tt = x->tmid; m2.t = n; m2.I = c.I; m2.J = c.J;
+  m2.P = c.P; m2.Q = c.Q; m2.S = c.S; m2.Qd = x->Qd;
+  if (c.prec == OCTEN_FP8E4M3) {
+    const int64_t IJ = c.I * c.J;
+    __nv_fp8_e4m3 *x8 = static_cast<__nv_fp8_e4m3 *>(x->X8buf.p) + k0 * IJ;
+    float *sc = static_cast<float *>(x->xscale.p) + k0;
     x->mark(kStQuant, 1);
-    quantize_e4m3(static_cast<const __nv_bfloat16 *>(Xd), t, c.I * c.J,
-                  static_cast<__nv_fp8_e4m3 *>(x->X8buf.p), static_cast<float *>(x->xscale.p),
-                  x->st);
+    quantize_e4m3(static_cast<const __nv_bfloat16 *>(m2.X), n, IJ, x8, sc, x->st);
     x->mark(kStQuant, 0);
-    m2.X = x->X8buf.p; m2.tx = Elem::E4M3; m2.slice_scale = static_cast<float *>(x->xscale.p);
+    m2.X = x8; m2.tx = Elem::E4M3; m2.slice_scale = sc;
   }
   x->mark(kStMode2, 1);
   if (!(x->use_tc && mode2_tc(m2, x->dstatus, x->st))) {
@@ -306,6 +329,14 @@ octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float
     mode2_simt(m2, x->st);
   }
   x->mark(kStMode2, 0);
+}
+
+// Mode-1 and mode-3 contractions of a pass of t slices (after its mode 2):
+// Z_p (+)= into Yacc.  With `layouts` the mode-3 pass may also leave the bf16
+// copies of Yacc for the tensor-core CP-ALS in x->Xa / x->Xc
+// (x->layouts_ready says whether it did).
+void compress_finish(octen_ctx *x, int64_t t, const float *Wd, float *Yacc, bool layouts) {
+  const octen_config &c = x->cfg;
   Mode1Args m1{};
   m1.Ut = x->Ut_rep; m1.T = x->Tbuf.p; m1.te = x->tmid; m1.T2 = static_cast<float *>(x->T2buf.p);
   m1.t = t; m1.I = c.I; m1.P = c.P; m1.Q = c.Q;
@@ -321,6 +352,52 @@ octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float
       mode3_accumulate(static_cast<float *>(x->T2buf.p), Wd, Yacc, t, c.P, c.Q, c.S, x->Qd, x->st,
                        want ? x->Xa : nullptr, want ? x->Xc : nullptr);
   x->mark(kStMode3, 0);
+}
+
+// Z_p (+)= compression of t slices (t <= kChunk, device) into Yacc.
+octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float *Wd,
+                            float *Yacc, bool layouts = false) {
+  octen_status s = compress_scratch(x, t);
+  if (s != OCTEN_OK) return s;
+  compress_mode2(x, Xd, 0, t);
+  compress_finish(x, t, Wd, Yacc, layouts);
+  return OCTEN_OK;
+}
+
+// The same for t host slices: they are copied into staging slot 2 in up to
+// kCopyChunks pieces on copy_st, and the mode-2 contraction of each piece
+// starts as soon as it has arrived.  The caller ensures 16-byte aligned piece
+// offsets (I J a multiple of 16), which the tensor-map operands need.
+octen_status compress_chunk_host(octen_ctx *x, const void *Xh, int64_t t, const float *Wd,
+                                 float *Yacc, bool layouts) {
+  const octen_config &c = x->cfg;
+  const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
+  octen_status s = compress_scratch(x, t);
+  if (s != OCTEN_OK) return s;
+  if (!x->grow(x->stage[2], t * slice)) return x->fail(OCTEN_ENOMEM, "staging the batch");
+  // the staging slot is free once the stream's earlier work is done
+  cudaEventRecord(x->copy_ready, x->st);
+  cudaStreamWaitEvent(x->copy_st, x->copy_ready, 0);
+  const int64_t per = (t + octen_ctx::kCopyChunks - 1) / octen_ctx::kCopyChunks;
+  const int64_t step = per < 2 ? 2 : per;
+  int nc = 0;
+  for (int64_t k0 = 0; k0 < t; k0 += step, ++nc) {
+    const int64_t n = t - k0 < step ? t - k0 : step;
+    if (cudaMemcpyAsync(static_cast<char *>(x->stage[2].p) + k0 * slice,
+                        static_cast<const char *>(Xh) + k0 * slice, n * slice,
+                        cudaMemcpyHostToDevice, x->copy_st) != cudaSuccess) {
+      cudaStreamSynchronize(x->copy_st);   // no copy of the caller's buffer stays in flight
+      return x->fail(OCTEN_ECUDA, "copying the batch");
+    }
+    cudaEventRecord(x->copy_ev[nc], x->copy_st);
+  }
+  nc = 0;
+  for (int64_t k0 = 0; k0 < t; k0 += step, ++nc) {
+    const int64_t n = t - k0 < step ? t - k0 : step;
+    cudaStreamWaitEvent(x->st, x->copy_ev[nc], 0);
+    compress_mode2(x, x->stage[2].p, k0, n);
+  }
+  compress_finish(x, t, Wd, Yacc, layouts);
   return OCTEN_OK;
 }
 
@@ -447,6 +524,12 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     if (vt) x->owned.push_back({vt, 0});
     x->Ut_rep = ut;
     x->Vt = vt;
+  }
+  if (ok) {
+    ok = cudaStreamCreateWithFlags(&x->copy_st, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x->copy_ready, cudaEventDisableTiming) == cudaSuccess;
+    for (cudaEvent_t &e : x->copy_ev)
+      ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
   }
   if (ok) {
     ok = cudaStreamCreateWithFlags(&x->als_side, cudaStreamNonBlocking) == cudaSuccess &&
@@ -595,11 +678,18 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   const int Qd = x->Qd, RT = x->RT;
   if (!ensure_c_capacity(x, x->K + t)) return x->fail(OCTEN_ENOMEM, "C");
   const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
-  const void *Xd = x->stage_in(X_new, t * slice, 2);
   const float *Wd = static_cast<const float *>(x->stage_in(W_new, (size_t)t * Qd * 4, 1));
-  if (!Xd || !Wd) return x->fail(OCTEN_ENOMEM, "staging the batch");
-  // 1. compress the batch and update the summaries
-  octen_status s = compress_chunk(x, Xd, t, Wd, x->Y, true);
+  if (!Wd) return x->fail(OCTEN_ENOMEM, "staging W_new");
+  // 1. compress the batch and update the summaries (host slices arrive in
+  // pieces that overlap the mode-2 contraction of the ones before)
+  octen_status s;
+  if (!is_device_ptr(X_new) && t >= 2 && (c.I * c.J) % 16 == 0 && x->copy_st) {
+    s = compress_chunk_host(x, X_new, t, Wd, x->Y, true);
+  } else {
+    const void *Xd = x->stage_in(X_new, t * slice, 2);
+    if (!Xd) return x->fail(OCTEN_ENOMEM, "staging the batch");
+    s = compress_chunk(x, Xd, t, Wd, x->Y, true);
+  }
   if (s != OCTEN_OK) return s;
   // 2. CP of every summary, warm-started from the projected previous factors
   x->mark(kStWarm, 1);
@@ -661,13 +751,25 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   return OCTEN_OK;
 }
 
+// After a failed enqueue: nothing the call issued may still read the caller's
+// buffers when it returns.
+void drain(octen_ctx *x) {
+  if (!x) return;
+  if (x->copy_st) cudaStreamSynchronize(x->copy_st);
+  cudaStreamSynchronize(x->st);
+  cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
 
 octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
   octen_status s = append_enqueue(x, X_new, t, W_new);
-  if (s != OCTEN_OK) return s;
+  if (s != OCTEN_OK) {
+    drain(x);
+    return s;
+  }
   s = x->sync_check("append");
   if (s != OCTEN_OK) return s;
   x->K += t;
@@ -682,7 +784,10 @@ octen_status octen_append_many(octen_ctx *const *ctxs, int n, const void *const 
   for (int i = 0; i < n; ++i) {
     const octen_status s = append_enqueue(ctxs[i], X_new[i], t[i], W_new[i]);
     enqueued[i] = s == OCTEN_OK;
-    if (s != OCTEN_OK && first == OCTEN_OK) first = s;
+    if (s != OCTEN_OK) {
+      drain(ctxs[i]);
+      if (first == OCTEN_OK) first = s;
+    }
   }
   for (int i = 0; i < n; ++i) {
     if (!enqueued[i]) continue;

@@ -147,3 +147,37 @@ def test_autotuned_gemms_give_bit_identical_results(pkg, monkeypatch):
     for a, b in zip(plain, tuned):
         for key in ("Y", "A", "B", "C"):
             assert np.array_equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "fp32"])
+def test_host_batches_copied_in_pieces_equal_device_batches(pkg, prec):
+    """Host slices of an append are copied in pieces whose mode-2 contraction
+    starts as each piece arrives; the result equals the same update from
+    device-resident slices bit for bit (each output keeps its summation order)."""
+    from tests.test_gpu_parity import dev, slices
+
+    case = Case(96, 80, 5, 3, 16, 4, 12, (16, 5, 2), 8, prec=prec, seed=27)
+    d = case.make()
+
+    def host(a):
+        import torch
+        t = torch.as_tensor(np.asarray(a, np.float32))
+        return t if prec == "fp32" else t.to(torch.bfloat16)
+
+    out = []
+    for conv in (lambda a: slices(a, prec), host):
+        g = pkg.Octen(case.I, case.J, case.R, case.P, case.Q, case.S, case.iters, prec)
+        g.init(slices(d["X"][:case.t_old], prec), dev(d["U"]), dev(d["V"]), dev(d["W"][0]),
+               dev(d["A0"]), dev(d["B0"]), dev(d["C0"]))
+        k = case.t_old
+        states = []
+        for b, t in enumerate(case.batches):
+            g.append(conv(d["X"][k:k + t]), np.asarray(d["W"][b + 1], np.float32))
+            k += t
+            A, B, C = g.factors()
+            states.append((g.replicas(), A, B, C))
+        g.close()
+        out.append(states)
+    for a, b in zip(*out):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
