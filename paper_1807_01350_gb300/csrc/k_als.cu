@@ -307,15 +307,18 @@ int als_factor_floats(int RT) {
   return RT == 8 ? factor_floats<8>() : (RT == 16 ? factor_floats<16>() : factor_floats<32>());
 }
 
-// Forks the factor of an update onto b.side: the Gram of Fnew (the factor
-// updated last) into Gnew, then L D L^T of Gnew * Gother into b.L.
+// Shared memory the tensor-core GEMMs leave free on every SM for the factor
+// kernel (als_ldl_kernel, at most 26 KB with the per-block reservation).
+constexpr int kLdlReserve = 28 * 1024;
+
+// Forks the factor of an update onto b.side: L D L^T of Gnew * Gother into
+// b.L (Gnew the Gram of the factor updated last, formed by its solve).
 template <int RT>
-static void factor_async(const float *Fnew, float *Gnew, const float *Gother, int P, int Q, int R,
-                         AlsBuffers &b, cudaStream_t st) {
+static void factor_async(const float *Gnew, const float *Gother, int P, int R, AlsBuffers &b,
+                         cudaStream_t st) {
   cudaEventRecord(b.ev_fork, st);
   cudaStreamWaitEvent(b.side, b.ev_fork, 0);
-  als_factor_kernel<RT><<<P, 256, (size_t)Q * RT * sizeof(float), b.side>>>(Fnew, Gnew, Gother, Q,
-                                                                            R, b.L, b.status);
+  als_ldl_kernel<RT><<<P, 128, 0, b.side>>>(Gnew, Gother, R, b.L, b.status);
   count_launch();
   cudaEventRecord(b.ev_join, b.side);
 }
@@ -326,8 +329,8 @@ static void factor_async(const float *Fnew, float *Gnew, const float *Gother, in
 // of 8); one CTA per replica if the cluster launch is refused.
 template <int RT>
 static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_stride, float *F,
-                  __nv_bfloat16 *Ft, int NP, int P, int Q, int normalize, AlsBuffers &b,
-                  cudaStream_t st) {
+                  __nv_bfloat16 *Ft, int NP, int P, int Q, int normalize, float *Gout,
+                  AlsBuffers &b, cudaStream_t st) {
   cudaStreamWaitEvent(st, b.ev_join, 0);
   int cl = (Q + 31) / 32;
   if (cl > 8) cl = 8;
@@ -346,10 +349,10 @@ static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (cudaLaunchKernelEx(&cfg, als_apply_kernel<RT>, M, nsplit, split_stride, row_stride,
-                         (const float *)b.L, F, Ft, NP, Q, rows, normalize) != cudaSuccess) {
+                         (const float *)b.L, F, Ft, NP, Q, rows, normalize, Gout) != cudaSuccess) {
     cudaGetLastError();
     als_apply_kernel<RT><<<P, 256, (size_t)Q * RT * sizeof(float), st>>>(
-        M, nsplit, split_stride, row_stride, b.L, F, Ft, NP, Q, Q, normalize);
+        M, nsplit, split_stride, row_stride, b.L, F, Ft, NP, Q, Q, normalize, Gout);
   }
   count_launch();
 }
@@ -364,7 +367,7 @@ static void als_run_simt(const float *Y, int P, int Q, int R, int iters, AlsBuff
   const dim3 gQP(Q, P);
   const dim3 gM3((Q * RT + 255) / 256, P);
   auto c_update = [&]() {
-    factor_async<RT>(b.Bf, b.GB, b.GA, P, Q, R, b, st);
+    factor_async<RT>(b.GB, b.GA, P, R, b, st);
     mk(kStAlsGemm, 1);
     als_h_kernel<RT><<<gQP, bq, smem_h, st>>>(Y, b.Bf, b.H, Q);
     count_launch();
@@ -374,26 +377,26 @@ static void als_run_simt(const float *Y, int P, int Q, int R, int iters, AlsBuff
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);
-    apply<RT>(b.M, 1, 0, RT, b.Cf, nullptr, 0, P, Q, 0, b, st);
+    apply<RT>(b.M, 1, 0, RT, b.Cf, nullptr, 0, P, Q, 0, b.GC, b, st);
     mk(kStAlsSolve, 0);
   };
   for (int it = 0; it < iters; ++it) {
     c_update();
-    factor_async<RT>(b.Cf, b.GC, b.GB, P, Q, R, b, st);
+    factor_async<RT>(b.GC, b.GB, P, R, b, st);
     mk(kStAlsAux, 1);
     als_m1_kernel<RT><<<gQP, 256, 0, st>>>(b.H, b.Cf, b.M, Q);
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);
-    apply<RT>(b.M, 1, 0, RT, b.Af, nullptr, 0, P, Q, 1, b, st);
+    apply<RT>(b.M, 1, 0, RT, b.Af, nullptr, 0, P, Q, 1, b.GA, b, st);
     mk(kStAlsSolve, 0);
-    factor_async<RT>(b.Af, b.GA, b.GC, P, Q, R, b, st);
+    factor_async<RT>(b.GA, b.GC, P, R, b, st);
     mk(kStAlsGemm, 1);
     als_m2_kernel<RT><<<gQP, bq, smem_m2, st>>>(Y, b.Af, b.Cf, b.M, Q);
     count_launch();
     mk(kStAlsGemm, 0);
     mk(kStAlsSolve, 1);
-    apply<RT>(b.M, 1, 0, RT, b.Bf, nullptr, 0, P, Q, 1, b, st);
+    apply<RT>(b.M, 1, 0, RT, b.Bf, nullptr, 0, P, Q, 1, b.GB, b, st);
     mk(kStAlsSolve, 0);
   }
   c_update();
@@ -428,8 +431,9 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   // M1 fused into the Tc GEMM: per-warp partials over 32 consecutive b
   const bool fuse_m1 = Q % 32 == 0;
   if (fuse_m1) { tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; }
-  // the factor kernel of each update runs beside these GEMMs: leave it room
-  m3.smem_reserve = tc.smem_reserve = 56 * 1024;
+  // the factor kernel of each update (about 25 KB of shared memory) runs
+  // beside these GEMMs: leave it room
+  m3.smem_reserve = tc.smem_reserve = kLdlReserve;
   // the bf16 copies of X_p stream through once per pass (evict-first), so Tc
   // stays in the L2 for the M2 pass
   m3.a_stream = tc.a_stream = true;
@@ -450,7 +454,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     m3f.M = (int)QQ; m3f.N = RT; m3f.K = Q; m3f.BN = NP; m3f.batch = P; m3f.ksplit = 1;
     m3f.D = nullptr; m3f.Dh = nullptr; m3f.s_split = 0; m3f.s_z = 0; m3f.s_m = 0;
     m3f.m1_B = b.Af; m3f.m1_part = b.Mparts; m3f.Q = Q; m3f.RT = RT;
-    m3f.smem_reserve = 56 * 1024;
+    m3f.smem_reserve = kLdlReserve;
     m3f.a_stream = true;
     m3f.katoms = kAlsKAtoms;
     // B^T of the warm start; every later B update writes it from its solve
@@ -461,13 +465,13 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   }
   bool ok = true;
   auto c_update = [&]() {
-    factor_async<RT>(b.Bf, b.GB, b.GA, P, Q, R, b, st);
+    factor_async<RT>(b.GB, b.GA, P, R, b, st);
     if (m3_fused) {
       mk(kStAlsGemm, 1);
       ok = ok && tc_gemm_store(m3f, b.status, st);
       mk(kStAlsGemm, 0);
       mk(kStAlsSolve, 1);
-      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Cf, b.Ct, NP, P, Q, 0, b, st);
+      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Cf, b.Ct, NP, P, Q, 0, b.GC, b, st);
       mk(kStAlsSolve, 0);
       return;
     }
@@ -479,18 +483,18 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     ok = ok && tc_gemm_store(m3, b.status, st);
     mk(kStAlsGemm, 0);
     mk(kStAlsSolve, 1);
-    apply<RT>(b.Mparts, ks, (int64_t)P * Q * RT, RT, b.Cf, b.Ct, NP, P, Q, 0, b, st);
+    apply<RT>(b.Mparts, ks, (int64_t)P * Q * RT, RT, b.Cf, b.Ct, NP, P, Q, 0, b.GC, b, st);
     mk(kStAlsSolve, 0);
   };
   for (int it = 0; it < iters && ok; ++it) {
     c_update();
-    factor_async<RT>(b.Cf, b.GC, b.GB, P, Q, R, b, st);
+    factor_async<RT>(b.GC, b.GB, P, R, b, st);
     mk(kStAlsGemm, 1);
     ok = ok && tc_gemm_store(tc, b.status, st);
     mk(kStAlsGemm, 0);
     if (fuse_m1) {
       mk(kStAlsSolve, 1);
-      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Af, nullptr, 0, P, Q, 1, b, st);
+      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Af, nullptr, 0, P, Q, 1, b.GA, b, st);
       mk(kStAlsSolve, 0);
     } else {
       mk(kStAlsAux, 1);
@@ -498,16 +502,16 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
       count_launch();
       mk(kStAlsAux, 0);
       mk(kStAlsSolve, 1);
-      apply<RT>(b.M, 1, 0, RT, b.Af, nullptr, 0, P, Q, 1, b, st);
+      apply<RT>(b.M, 1, 0, RT, b.Af, nullptr, 0, P, Q, 1, b.GA, b, st);
       mk(kStAlsSolve, 0);
     }
-    factor_async<RT>(b.Af, b.GA, b.GC, P, Q, R, b, st);
+    factor_async<RT>(b.GA, b.GC, P, R, b, st);
     mk(kStAlsAux, 1);
     tc_mred_kernel<RT, 2><<<gM, 256, 0, st>>>(Th, b.Af, Q, b.M);
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);
-    apply<RT>(b.M, 1, 0, RT, b.Bf, m3_fused ? b.Bt : nullptr, NP, P, Q, 1, b, st);
+    apply<RT>(b.M, 1, 0, RT, b.Bf, m3_fused ? b.Bt : nullptr, NP, P, Q, 1, b.GB, b, st);
     mk(kStAlsSolve, 0);
   }
   if (ok) c_update();
@@ -539,13 +543,10 @@ bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers 
   const int smem = (int)((size_t)Q * RT * sizeof(float));
   const int smem_ap = smem;   // the solve's rows (all Q without clusters)
   if (RT == 8) {
-    cudaFuncSetAttribute(als_factor_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(als_apply_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ap);
   } else if (RT == 16) {
-    cudaFuncSetAttribute(als_factor_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(als_apply_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ap);
   } else {
-    cudaFuncSetAttribute(als_factor_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(als_apply_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ap);
   }
   if (b.use_tc) {

@@ -4,7 +4,7 @@
 // factor of the current normal equations in shared memory and runs every sweep
 // without leaving the kernel.  For small Q the separate-launch form is bound by
 // launch latency (about ten launches per sweep); here the fp64 L D L^T of each
-// update (warps 0..3, the same device code as als_factor_kernel) runs while
+// update (warps 0..3, the same device code as als_ldl_kernel) runs while
 // warps 4..7 form the update's MTTKRP, and the whole CP costs one launch.
 #include "k_solve.cuh"
 

@@ -21,10 +21,10 @@
 // One named barrier over the four warps closes each step.
 //
 // The factor of an update depends only on factors that are already final, so
-// it is a kernel of its own (als_factor_kernel, which also forms the Gram of
-// the factor updated last) that runs beside the MTTKRP of the update; the
-// solve proper (als_apply_kernel) sums the MTTKRP's partials and substitutes,
-// with a cluster of CTAs per replica.
+// it is a kernel of its own (als_ldl_kernel) that runs beside the MTTKRP of the
+// update; the solve proper (als_apply_kernel) sums the MTTKRP's partials,
+// substitutes, and forms the Gram of the factor it writes (for the factors of
+// the next updates), with a cluster of CTAs per replica.
 #pragma once
 
 #include "octen_internal.cuh"
@@ -262,7 +262,7 @@ __device__ __forceinline__ void ldl_substitute(float (&y)[RT], const float *Lc, 
   }
 }
 
-// Per replica: the packed factor written by als_factor_kernel and read by
+// Per replica: the packed factor written by als_ldl_kernel and read by
 // als_apply_kernel, [Lc (RT x RT) | Lr (RT x RT) | rf (RT)] floats.
 template <int RT>
 __host__ __device__ constexpr int factor_floats() { return 2 * RT * RT + RT; }
@@ -299,30 +299,27 @@ __device__ void solve_rows_smem(const float *M, float *F, int Q, bool normalize,
   }
 }
 
-// Gram of the factor updated last (F_p, Q x RT, global) -> Gnew_p, then the
-// L D L^T factor of Gnew_p * Gother_p -> Lout_p.  It depends only on factors
-// that are already final, so it runs beside the MTTKRP of the same update.
-// grid P, 256 threads; dynamic smem Q * RT floats.
+// L D L^T factor of Gnew_p * Gother_p -> Lout_p (the Grams of the two factors
+// that stay fixed in the update, already formed by the solves that wrote
+// them).  It depends only on factors that are already final, so it runs beside
+// the MTTKRP of the same update.  grid P, 128 threads (the four factor warps).
 template <int RT>
-__global__ void __launch_bounds__(256, 1)
-    als_factor_kernel(const float *__restrict__ Fnew, float *__restrict__ Gnew,
-                      const float *__restrict__ Gother, int Q, int R, float *__restrict__ Lout,
-                      int *status) {
-  extern __shared__ __align__(16) float Fs[];   // [Q][RT]
-  __shared__ __align__(16) float Gs[RT * RT];
+__global__ void __launch_bounds__(128)
+    als_ldl_kernel(const float *__restrict__ Gnew, const float *__restrict__ Gother, int R,
+                   float *__restrict__ Lout, int *status) {
+  __shared__ __align__(16) float G1[RT * RT], G2[RT * RT];
   __shared__ double Craw[RT * (RT + 1)], Rs[RT];
   __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT];
   __shared__ int fail_s;
   const int p = blockIdx.x, tid = threadIdx.x;
-  const float4 *src = reinterpret_cast<const float4 *>(Fnew + (int64_t)p * Q * RT);
-  float4 *dst = reinterpret_cast<float4 *>(Fs);
-  for (int e = tid; e < Q * RT / 4; e += blockDim.x) dst[e] = src[e];
+  const float4 *g1 = reinterpret_cast<const float4 *>(Gnew + (int64_t)p * RT * RT);
+  const float4 *g2 = reinterpret_cast<const float4 *>(Gother + (int64_t)p * RT * RT);
+  for (int e = tid; e < RT * RT / 4; e += blockDim.x) {
+    reinterpret_cast<float4 *>(G1)[e] = g1[e];
+    reinterpret_cast<float4 *>(G2)[e] = g2[e];
+  }
   __syncthreads();
-  smem_gram<RT>(Fs, Q, Gs);
-  __syncthreads();
-  for (int e = tid; e < RT * RT; e += blockDim.x) Gnew[(int64_t)p * RT * RT + e] = Gs[e];
-  if (tid < 128)
-    ldl_factor<RT>(Gs, Gother + (int64_t)p * RT * RT, R, Craw, Rs, Lc, Lr, rf, &fail_s);
+  ldl_factor<RT>(G1, G2, R, Craw, Rs, Lc, Lr, rf, &fail_s);
   __syncthreads();
   if (fail_s && tid == 0) atomicOr(status, kDevCholesky);
   float *lo = Lout + (int64_t)p * factor_floats<RT>();
@@ -363,16 +360,17 @@ __device__ __forceinline__ float ld_cluster(const float *p, uint32_t rank) {
 // replica (grid P * cluster size); with `normalize` the column norms are summed
 // over the cluster through distributed shared memory and the columns scaled to
 // unit l2.  Writes F_p and, if Ft is given, a bf16 copy transposed to [NP][Q]
-// (rows >= R zero) for the tensor-core passes.  256 threads; dynamic smem
-// rows_per_cta * RT floats.
+// (rows >= R zero) for the tensor-core passes; with Gout the Gram F_p^T F_p
+// (each CTA's rows, then the partials summed over the cluster in rank order).
+// 256 threads; dynamic smem rows_per_cta * RT floats.
 template <int RT>
 __global__ void __launch_bounds__(256)
     als_apply_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
                      int64_t row_stride, const float *__restrict__ Lin, float *__restrict__ F,
                      __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int rows_per_cta,
-                     int normalize) {
+                     int normalize, float *__restrict__ Gout) {
   extern __shared__ __align__(16) float Ms[];   // [rows_per_cta][RT]
-  __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT];
+  __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT], Gp[RT * RT];
   __shared__ float red[8 * RT], part[RT], scale[RT];
   const int tid = threadIdx.x;
   const uint32_t ncta = cluster_size(), crank = cluster_rank();
@@ -456,6 +454,25 @@ __global__ void __launch_bounds__(256)
         Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(y[r]);
       for (int r = RT; r < NP; ++r) Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(0.f);
     }
+  }
+  if (Gout) {
+    __syncthreads();   // every row of Ms has been read
+    if (own) {
+      float4 *mr = reinterpret_cast<float4 *>(Ms + tid * RT);
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4)
+        mr[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
+    }
+    __syncthreads();
+    smem_gram<RT>(Ms, nrows, Gp);
+    cluster_barrier();   // every CTA's partial Gram is in place
+    const int e0 = (int)(crank * (RT * RT) / ncta), e1 = (int)((crank + 1) * (RT * RT) / ncta);
+    for (int e = e0 + tid; e < e1; e += blockDim.x) {
+      float g = 0.f;
+      for (uint32_t c = 0; c < ncta; ++c) g += ld_cluster(Gp + e, c);
+      Gout[(int64_t)p * RT * RT + e] = g;
+    }
+    cluster_barrier();   // peers are done reading Gp
   }
 }
 
