@@ -721,6 +721,15 @@ TuneChoice tuned(const std::array<int64_t, 8> &key, const TuneChoice *cand, int 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (getenv("OCTEN_AUTOTUNE_LOG")) {   // diagnostics: the timings behind each choice
+    fprintf(stderr, "octen autotune key");
+    for (int64_t v : key) fprintf(stderr, " %lld", (long long)v);
+    for (int c = 0; c < ncand && c < kMaxCand; ++c)
+      fprintf(stderr, " | katoms %d BN %d: %.4f ms%s", cand[c].katoms, cand[c].BN,
+              runs[c] ? cand_ms[c] / 2 : -1.f, cand[c].katoms == best.katoms &&
+              cand[c].BN == best.BN ? " *" : "");
+    fprintf(stderr, "\n");
+  }
   adjust_launch_counts(-(int64_t)(octen_launch_count() - l0),
                        -(int64_t)(octen_tc_launch_count() - t0));
   std::lock_guard<std::mutex> lock(g_tune_mu);
