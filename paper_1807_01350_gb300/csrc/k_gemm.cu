@@ -141,11 +141,130 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// fp32 GEMM with both operands K-contiguous and 16-byte aligned rows, 128 x 128
+// tiles: float4 global loads prefetched into registers during the previous
+// tile's arithmetic, double-buffered shared tiles (stored [k][m] / [k][n]),
+// and an 8 x 8 block per thread read as four 16-byte shared loads per k
+// (rows ty*4 .. +3 and 64 + ty*4 .., columns tx*4 .. +3 and 64 + tx*4 ..).
+// Every output is the same sequence of FMAs over k as in gemm_kernel.
+constexpr int kTnBK = 16, kTnLD = 128 + 4;
+
+__device__ __forceinline__ void tn_load(const float *p, int64_t s_row, int rows, int r0, int k0,
+                                        int K, int t, float4 (&v)[2]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int idx = t + 256 * h, row = idx >> 2, k = k0 + 4 * (idx & 3);
+    const int r = r0 + row;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < rows) {
+      const float *q = p + (int64_t)r * s_row + k;
+      if (k + 3 < K) {
+        x = __ldg(reinterpret_cast<const float4 *>(q));
+      } else {
+        if (k < K) x.x = __ldg(q);
+        if (k + 1 < K) x.y = __ldg(q + 1);
+        if (k + 2 < K) x.z = __ldg(q + 2);
+      }
+    }
+    v[h] = x;
+  }
+}
+
+__device__ __forceinline__ void tn_store(float (*S)[kTnLD], int t, const float4 (&v)[2]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int idx = t + 256 * h, row = idx >> 2, k = 4 * (idx & 3);
+    S[k][row] = v[h].x;
+    S[k + 1][row] = v[h].y;
+    S[k + 2][row] = v[h].z;
+    S[k + 3][row] = v[h].w;
+  }
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(kThreads, 2)
+    sgemm_tn_kernel(Operand A, Operand B, int M, int N, int K, int zdiv, Epi epi) {
+  __shared__ __align__(16) float As[2][kTnBK][kTnLD];
+  __shared__ __align__(16) float Bs[2][kTnBK][kTnLD];
+  const int z = blockIdx.z;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 128;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const float *pa = static_cast<const float *>(A.p) + (int64_t)(z / zdiv) * A.s_hi +
+                    (int64_t)(z % zdiv) * A.s_lo;
+  const float *pb = static_cast<const float *>(B.p) + (int64_t)(z / zdiv) * B.s_hi +
+                    (int64_t)(z % zdiv) * B.s_lo;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  float4 ra[2], rb[2];
+  tn_load(pa, A.s_row, M, m0, 0, K, t, ra);
+  tn_load(pb, B.s_row, N, n0, 0, K, t, rb);
+  tn_store(As[0], t, ra);
+  tn_store(Bs[0], t, rb);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += kTnBK) {
+    const bool more = k0 + kTnBK < K;
+    if (more) {   // the next tile's loads are in flight during this tile's arithmetic
+      tn_load(pa, A.s_row, M, m0, k0 + kTnBK, K, t, ra);
+      tn_load(pb, B.s_row, N, n0, k0 + kTnBK, K, t, rb);
+    }
+#pragma unroll
+    for (int kk = 0; kk < kTnBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      tn_store(As[buf ^ 1], t, ra);
+      tn_store(Bs[buf ^ 1], t, rb);
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (n < N) epi(z, zdiv, m, n, acc[i][j]);
+    }
+  }
+}
+
+// The K-contiguous fp32 kernel applies when both operands have unit K stride
+// and every row (and batch offset) starts 16-byte aligned.
+static bool tn_ok(const Operand &A, const Operand &B) {
+  auto al = [](const Operand &o) {
+    return o.s_k == 1 && o.s_row % 4 == 0 && o.s_hi % 4 == 0 && o.s_lo % 4 == 0 &&
+           (reinterpret_cast<uintptr_t>(o.p) & 15) == 0;
+  };
+  return al(A) && al(B);
+}
+
 template <Elem EA, Elem EB, int BM, int BN, class Epi>
 static void launch_gemm(const Operand &A, const Operand &B, int M, int N, int K, int batch,
                         int zdiv, const Epi &epi, cudaStream_t st, int kc = 0) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  if constexpr (EA == Elem::F32 && EB == Elem::F32 && BM == 128 && BN == 128) {
+    if (kc == 0 && K > 0 && tn_ok(A, B)) {
+      sgemm_tn_kernel<Epi><<<grid, kThreads, 0, st>>>(A, B, M, N, K, zdiv, epi);
+      count_launch();
+      return;
+    }
+  }
   gemm_kernel<EA, EB, BM, BN, Epi><<<grid, kThreads, 0, st>>>(A, B, M, N, K, zdiv, kc, epi);
   count_launch();
 }
