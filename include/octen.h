@@ -102,7 +102,15 @@ octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
  * OCTEN_GRAPH=0 issues its launches one by one instead.  The first call for
  * each tensor-core GEMM shape times its candidate tile configurations (only
  * ones that give bit-identical results) and keeps the fastest for the process;
- * OCTEN_AUTOTUNE=0 keeps the defaults. */
+ * OCTEN_AUTOTUNE=0 keeps the defaults.  Host slices are copied in pieces on a
+ * stream of the library's, each piece's mode-2 contraction starting as it
+ * arrives.  Failure: EINVAL, ESTATE and ENOMEM are returned before any state
+ * changes (every allocation precedes the first kernel).  After ECUDA,
+ * ETIMEOUT or ENUMERIC the update has run in part: the summaries hold the
+ * batch, the factors may be partly updated and K is not advanced; discard
+ * the context or resume from a checkpoint (octen_save / octen_load).  No
+ * work of a failed call is still reading the caller's buffers when it
+ * returns. */
 octen_status octen_append(octen_ctx *ctx, const void *X_new, int64_t t, const float *W_new);
 
 /* One append on each of n independent decompositions (many streams with

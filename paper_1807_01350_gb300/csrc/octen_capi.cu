@@ -677,6 +677,10 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   const octen_config &c = x->cfg;
   const int Qd = x->Qd, RT = x->RT;
   if (!ensure_c_capacity(x, x->K + t)) return x->fail(OCTEN_ENOMEM, "C");
+  // the append's scratch is allocated before its first kernel, so that a
+  // refused allocation leaves the context unchanged
+  const size_t cs = (size_t)Qd * c.R + t * c.R + t * Qd + t * t;
+  if (!x->grow(x->Wbuf, cs * sizeof(float))) return x->fail(OCTEN_ENOMEM, "C solve scratch");
   const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
   const float *Wd = static_cast<const float *>(x->stage_in(W_new, (size_t)t * Qd * 4, 1));
   if (!Wd) return x->fail(OCTEN_ENOMEM, "staging W_new");
@@ -739,8 +743,6 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   lift_mode(x, x->Ah, x->PA, x->La, x->a_over, c.I, x->A);
   lift_mode(x, x->Bh, x->PB, x->Lb, x->b_over, c.J, x->B);
   x->mark(kStLift, 0);
-  const size_t cs = (size_t)Qd * c.R + t * c.R + t * Qd + t * t;
-  if (!x->grow(x->Wbuf, cs * sizeof(float))) return x->fail(OCTEN_ENOMEM, "C solve scratch");
   float *C_new = x->C + x->K * c.R;
   x->mark(kStCsolve, 1);
   solve_c_new(Wd, x->Ch, x->G, t, c.P, c.Q, c.S, Qd, c.R, RT, static_cast<float *>(x->Wbuf.p),
