@@ -169,8 +169,10 @@ __global__ void __launch_bounds__(256)
 // Tensor-core path (bf16 / e4m3 modes): both passes of a sweep are GEMMs with
 // K-major bf16 operands.
 //   Xa[p][a][b][c] = bf16(X_p)          (rows (a, b), K = c)
-//   Xc[p][c][a][b] = bf16(X_p)          (rows c, K = (a, b))
-//   M3[c][r]  = sum_(a,b) Xc[c][(a,b)] KR[r][(a,b)],  KR[r][(a,b)] = A[a][r] B[b][r]
+//   Xc[p][c][a][b] = bf16(X_p)          (rows (c, a), K = b)
+//   M3[c][r] = sum_a A[a][r] sum_b Xc[(c,a)][b] B[b][r]      (32 | Q: the a sum in
+//              the GEMM's epilogue, per 32 rows; otherwise M3 = Xc . KR^T over
+//              K = (a, b) with KR[r][(a,b)] = A[a][r] B[b][r])
 //   Tc[(a,b)][r] = sum_c Xa[(a,b)][c] C[c][r]
 //   M1[a][r] = sum_b Tc[(a,b)][r] B[b][r],  M2[b][r] = sum_a Tc[(a,b)][r] A[a][r]
 // ---------------------------------------------------------------------------

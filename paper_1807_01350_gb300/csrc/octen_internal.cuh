@@ -162,10 +162,11 @@ struct AlsBuffers {
   // tensor-core path (bf16 / e4m3 modes, Q % 8 == 0)
   bool use_tc = false;
   __nv_bfloat16 *Xa = nullptr, *Xc = nullptr;   // P x Q^3 each
-  __nv_bfloat16 *KR = nullptr;                  // P x kAlsNP x Q^2
-  __nv_bfloat16 *Ct = nullptr;                  // P x kAlsNP x Q
+  __nv_bfloat16 *KR = nullptr;                  // P x kAlsNP x Q^2 (M3 operand when 32 does not divide Q)
+  __nv_bfloat16 *Ct = nullptr;                  // P x kAlsNP x Q (C^T, the Tc operand)
   __nv_bfloat16 *Bt = nullptr;                  // P x kAlsNP x Q (B^T, the M3 operand)
-  float *Mparts = nullptr;                      // ksplit x P x Q x RT
+  float *Mparts = nullptr;                      // partials: fused P x Q x Q/32 x RT, or split-K
+                                                // ksplit x P x Q x RT
   int ksplit = 1;
   bool layouts_ready = false;                   // Xa, Xc already hold bf16(X_p)
   // the factor of every update runs on `side` beside the update's MTTKRP:
