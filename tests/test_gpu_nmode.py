@@ -37,6 +37,11 @@ CASES = {
     # slices large enough that one compression pass takes fewer slices than
     # the existing tensor holds (two passes at init)
     "n4_chunked": NCase((300, 300, 4), 2, 2, 4, 2, 50, (5,), 20, seed=17),
+    # summaries too large for shared memory (read from global memory) and an
+    # outer index table too large for the Khatri-Rao form (the odometer MTTKRP):
+    # six modes with Q = 8, and three modes with Q = 40 > 32
+    "n6_global": NCase((6, 5, 4, 5, 6), 2, 2, 8, 2, 6, (2,), 10, seed=18),
+    "n3_q40": NCase((48, 44), 3, 2, 40, 4, 8, (3,), 10, seed=19),
 }
 
 
