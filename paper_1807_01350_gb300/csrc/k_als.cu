@@ -332,7 +332,7 @@ static void factor_async(const float *Gnew, const float *Gother, int P, int R, A
 template <int RT>
 static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_stride, float *F,
                   __nv_bfloat16 *Ft, int NP, int P, int Q, int normalize, float *Gout,
-                  AlsBuffers &b, cudaStream_t st) {
+                  AlsBuffers &b, cudaStream_t st, int segQ = 0) {
   cudaStreamWaitEvent(st, b.ev_join, 0);
   int cl = (Q + 31) / 32;
   if (cl > 8) cl = 8;
@@ -351,10 +351,11 @@ static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (cudaLaunchKernelEx(&cfg, als_apply_kernel<RT>, M, nsplit, split_stride, row_stride,
-                         (const float *)b.L, F, Ft, NP, Q, rows, normalize, Gout) != cudaSuccess) {
+                         (const float *)b.L, F, Ft, NP, Q, rows, normalize, Gout,
+                         segQ) != cudaSuccess) {
     cudaGetLastError();
     als_apply_kernel<RT><<<P, 256, (size_t)Q * RT * sizeof(float), st>>>(
-        M, nsplit, split_stride, row_stride, b.L, F, Ft, NP, Q, Q, normalize, Gout);
+        M, nsplit, split_stride, row_stride, b.L, F, Ft, NP, Q, Q, normalize, Gout, segQ);
   }
   count_launch();
 }
@@ -430,9 +431,15 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   // Tc is kept in bf16 (half the bytes; it fits the L2 for the M2 pass)
   __nv_bfloat16 *Th = reinterpret_cast<__nv_bfloat16 *>(b.H);
   tc.D = nullptr; tc.Dh = Th; tc.s_split = 0; tc.s_z = QQ * RT; tc.s_m = RT;
-  // M1 fused into the Tc GEMM: per-warp partials over 32 consecutive b
-  const bool fuse_m1 = Q % 32 == 0;
-  if (fuse_m1) { tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; }
+  // M1 fused into the Tc GEMM: per-warp partials over 32 consecutive b (in
+  // two segments where a warp's rows cross from one a to the next, 32 not
+  // dividing Q)
+  const bool seg = Q % 32 != 0 && Q >= 32;
+  const bool fuse_m1 = Q % 32 == 0 || seg;
+  const int segQ = seg ? Q : 0;
+  if (fuse_m1) {
+    tc.m1_B = b.Bf; tc.m1_part = b.Mparts; tc.Q = Q; tc.RT = RT; tc.m1_seg = seg;
+  }
   // the factor kernel of each update (about 25 KB of shared memory) runs
   // beside these GEMMs: leave it room
   m3.smem_reserve = tc.smem_reserve = kLdlReserve;
@@ -443,11 +450,11 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   const int ks = tc_gemm_splits(m3.K, b.ksplit, kAlsKAtoms);
   const dim3 gKR(NP, P);
   const dim3 gM((Q + 256 / RT - 1) / (256 / RT), P);   // 32 output octets per CTA
-  // With 32 | Q the M3 pass needs no Khatri-Rao operand: the GEMM contracts b,
+  // With Q >= 32 the M3 pass needs no Khatri-Rao operand: the GEMM contracts b,
   //   Tb[(c, a)][r] = sum_b Xc[(c, a)][b] B[b][r]   (B^T in bf16 as the B operand),
   // and its epilogue reduces every 32 consecutive a with weights A[a][r] in
-  // fp32 (the fused reduction of the Tc pass), so M3[c][r] = sum of Q / 32
-  // partials; Tb itself is never stored.
+  // fp32 (the fused reduction of the Tc pass, segmented where 32 does not
+  // divide Q), so M3[c][r] = a sum of partials; Tb itself is never stored.
   const bool m3_fused = fuse_m1 && b.Bt != nullptr;
   TcStoreArgs m3f{};
   if (m3_fused) {
@@ -455,7 +462,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     m3f.B = b.Bt; m3f.b_inner = Q; m3f.b_rows = (int64_t)P * NP; m3f.b_rows_per_z = NP;
     m3f.M = (int)QQ; m3f.N = RT; m3f.K = Q; m3f.BN = NP; m3f.batch = P; m3f.ksplit = 1;
     m3f.D = nullptr; m3f.Dh = nullptr; m3f.s_split = 0; m3f.s_z = 0; m3f.s_m = 0;
-    m3f.m1_B = b.Af; m3f.m1_part = b.Mparts; m3f.Q = Q; m3f.RT = RT;
+    m3f.m1_B = b.Af; m3f.m1_part = b.Mparts; m3f.Q = Q; m3f.RT = RT; m3f.m1_seg = seg;
     m3f.smem_reserve = kLdlReserve;
     m3f.a_stream = true;
     m3f.katoms = kAlsKAtoms;
@@ -473,7 +480,8 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
       ok = ok && tc_gemm_store(m3f, b.status, st);
       mk(kStAlsGemm, 0);
       mk(kStAlsSolve, 1);
-      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Cf, b.Ct, NP, P, Q, 0, b.GC, b, st);
+      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Cf, b.Ct, NP, P, Q, 0, b.GC, b, st,
+                segQ);
       mk(kStAlsSolve, 0);
       return;
     }
@@ -496,7 +504,8 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     mk(kStAlsGemm, 0);
     if (fuse_m1) {
       mk(kStAlsSolve, 1);
-      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Af, nullptr, 0, P, Q, 1, b.GA, b, st);
+      apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Af, nullptr, 0, P, Q, 1, b.GA, b, st,
+                segQ);
       mk(kStAlsSolve, 0);
     } else {
       mk(kStAlsAux, 1);

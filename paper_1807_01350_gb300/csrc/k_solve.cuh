@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(256)
     als_apply_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
                      int64_t row_stride, const float *__restrict__ Lin, float *__restrict__ F,
                      __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int rows_per_cta,
-                     int normalize, float *__restrict__ Gout) {
+                     int normalize, float *__restrict__ Gout, int segQ) {
   extern __shared__ __align__(16) float Ms[];   // [rows_per_cta][RT]
   __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT], Gp[RT * RT];
   __shared__ float red[8 * RT], part[RT], scale[RT];
@@ -390,6 +390,22 @@ __global__ void __launch_bounds__(256)
   constexpr int TPR = RT / 4;
   for (int e = tid; e < nrows * TPR; e += blockDim.x) {
     const int rr = e / TPR, c4 = e - (e / TPR) * TPR;
+    if (segQ > 0) {
+      // segmented partials m1_part[p][j][2][RT] of the blocks j of 32 rows
+      // (q', i) that hold rows of q: segment 0 if the block starts in q
+      const int q = row0 + rr;
+      const int64_t nblk = ((int64_t)segQ * segQ + 31) / 32;
+      const int64_t first = (int64_t)q * segQ, last = first + segQ - 1;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t j = first / 32; j <= last / 32; ++j) {
+        const int sgm = (32 * j) / segQ == q ? 0 : 1;
+        const float4 v = *reinterpret_cast<const float4 *>(
+            M + (((int64_t)p * nblk + j) * 2 + sgm) * RT + 4 * c4);
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+      }
+      *reinterpret_cast<float4 *>(Ms + rr * RT + 4 * c4) = acc;
+      continue;
+    }
     const float *base = M + ((int64_t)p * Q + row0 + rr) * row_stride + 4 * c4;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     int sp = 0;

@@ -198,6 +198,7 @@ struct TcStoreEpi {
   float *part;
   int Q, RT;
   __nv_bfloat16 *Dh;
+  int seg;   // segmented partials (32 does not divide Q)
   __device__ __forceinline__ bool stores() const { return D != nullptr || Dh != nullptr; }
   __device__ __forceinline__ void store(int z, int split, int m, int n, float v) const {
     const int64_t o = (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n;
@@ -275,7 +276,7 @@ struct Mode1TcEpi {
   int P, Q;
   const float *Bfac = nullptr;   // no fused reduction
   float *part = nullptr;
-  int RT = 0;
+  int RT = 0, seg = 0;
   __device__ __forceinline__ bool stores() const { return true; }
   __device__ __forceinline__ void store(int z, int, int a, int b, float v) const {
     const int k = z / P, p = z - k * P;
@@ -510,10 +511,34 @@ __global__ void __launch_bounds__(192, 1)
             const int mb = m0 + quad * 32;   // 32 rows of one a when 32 divides Q
             if (mb < sh.M && n < sh.N) {
               const int b0 = mb % epi.Q;
-              const float *bf = epi.Bfac + ((int64_t)z * epi.Q + b0) * epi.RT + n;
-              float acc = 0.f;
-              for (int i = 0; i < 32; ++i) acc = fmaf(stg[i * 33 + lane], bf[i * epi.RT], acc);
-              epi.part[((int64_t)z * (sh.M / 32) + mb / 32) * epi.RT + n] = acc;
+              if (!epi.seg) {
+                const float *bf = epi.Bfac + ((int64_t)z * epi.Q + b0) * epi.RT + n;
+                float acc = 0.f;
+                for (int i = 0; i < 32; ++i) acc = fmaf(stg[i * 33 + lane], bf[i * epi.RT], acc);
+                epi.part[((int64_t)z * (sh.M / 32) + mb / 32) * epi.RT + n] = acc;
+              } else {
+                // rows [0, Q - b0) belong to the block's first m / Q, the rest
+                // (Q >= 32: at most one more) to the next
+                const float *bf = epi.Bfac + (int64_t)z * epi.Q * epi.RT + n;
+                const int nv = sh.M - mb < 32 ? sh.M - mb : 32;
+                const int cut = epi.Q - b0;   // the same for the whole warp
+                float a0 = 0.f, a1 = 0.f;
+                if (cut >= 32 && nv == 32) {   // most blocks: one segment
+                  const float *w = bf + b0 * epi.RT;
+#pragma unroll
+                  for (int i = 0; i < 32; ++i) a0 = fmaf(stg[i * 33 + lane], w[i * epi.RT], a0);
+                } else {
+                  const int n0 = cut < nv ? cut : nv;
+                  for (int i = 0; i < n0; ++i)
+                    a0 = fmaf(stg[i * 33 + lane], bf[(b0 + i) * epi.RT], a0);
+                  for (int i = n0; i < nv; ++i)
+                    a1 = fmaf(stg[i * 33 + lane], bf[(b0 + i - epi.Q) * epi.RT], a1);
+                }
+                const int64_t nblk = (sh.M + 31) / 32;
+                float *pp = epi.part + (((int64_t)z * nblk + mb / 32) * 2) * epi.RT + n;
+                pp[0] = a0;
+                pp[epi.RT] = a1;
+              }
             }
           }
           __syncwarp();
@@ -804,9 +829,11 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   // the split count is fixed by the caller's K atoms (it sets the summation)
   const int katoms0 = g.katoms == 2 ? 2 : 1;
   const int ks = tc_gemm_splits(g.K, g.ksplit, katoms0);
-  if (g.m1_part && (g.BN != 32 || g.Q % 32 || ks > 1)) return false;
+  const bool seg = g.m1_part && g.m1_seg;
+  if (g.m1_part && (g.BN != 32 || ks > 1 || (seg ? g.Q < 32 : g.Q % 32 != 0))) return false;
   if (ks > 1 && (g.N > g.BN)) return false;
-  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT, g.Dh};
+  TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT, g.Dh,
+                 seg ? 1 : 0};
   auto launch = [&](const TuneChoice &c) {
     TcShape sh{};
     sh.M = g.M; sh.N = g.N; sh.K = g.K; sh.BN = g.BN;

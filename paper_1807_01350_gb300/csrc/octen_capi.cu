@@ -2,6 +2,7 @@
 // the order of the stages of one online update (the loop body of the paper's
 // Algorithm 1: compress, X_p = Y_p + Z_p, CP of every replica, factor match,
 // lift of A, B and the new rows of C).
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdlib>
@@ -513,7 +514,7 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     ok = x->alloc(x->Xa, P * Q * Q * Q) && x->alloc(x->Xc, P * Q * Q * Q) &&
          x->alloc(x->KR, P * kAlsNP * Q * Q) && x->alloc(x->Ctb, P * kAlsNP * Q) &&
          x->alloc(x->Btb, P * kAlsNP * Q) &&
-         x->alloc(x->Mparts, nparts * P * Q * RT);
+         x->alloc(x->Mparts, std::max(nparts * Q, 2 * ((Q * Q + 31) / 32)) * P * RT);
     x->als_tc = ok;
   }
   void *ut = nullptr, *vt = nullptr;

@@ -112,6 +112,10 @@ struct TcStoreArgs {
   const float *m1_B = nullptr;
   float *m1_part = nullptr;
   int Q = 0, RT = 0;
+  // with 32 not dividing Q (Q >= 32) a warp's 32 rows may span two values of
+  // m / Q: m1_seg writes both segments, m1_part[z][m / 32][2][n] (segment 0 the
+  // rows of the block's first m / Q)
+  bool m1_seg = false;
   // shared memory (bytes) to leave free on every SM for a kernel that runs
   // beside this GEMM (fewer pipeline stages)
   int smem_reserve = 0;
