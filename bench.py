@@ -17,6 +17,8 @@ the slowest rank's time is reported.
 from __future__ import annotations
 
 import argparse
+import contextlib
+import gc
 import json
 import os
 import statistics
@@ -217,6 +219,19 @@ def max_over_ranks(x: float, world: int, device) -> float:
     return float(t.item())
 
 
+@contextlib.contextmanager
+def no_gc():
+    """The interpreter's cycle collector stays off inside a timed region (a
+    collection pass can stall the host for tens of milliseconds, which would be
+    charged to the library); garbage is collected before it starts."""
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.enable()
+
+
 def whole_job_rate(units_per_rank: float, seconds_max: float, world: int) -> float:
     """Units processed by all ranks divided by the slowest rank's time."""
     return world * units_per_rank / seconds_max
@@ -245,7 +260,7 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
     launches0 = pkg.launch_count()
     tc0 = pkg.tc_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk, no_gc():
         torch.cuda.synchronize()
         ev0.record(stream)
         for s in range(steps):
@@ -307,13 +322,15 @@ def run_e2e(g, d, wl, prec, k, steps, warmup, rank, world):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for s in range(steps):
-        g.append_ptr(hostX[s % 2].data_ptr(), t, hostW[s].data_ptr())
-        kk = g.factors_into(Ah, Bh, Ch)
-        d2h += (wl.I + wl.J + kk) * wl.R * 4
-    torch.cuda.synchronize()
-    sec = max_over_ranks(time.perf_counter() - t0, world, torch.device("cuda"))
+    with no_gc():
+        t0 = time.perf_counter()
+        for s in range(steps):
+            g.append_ptr(hostX[s % 2].data_ptr(), t, hostW[s].data_ptr())
+            kk = g.factors_into(Ah, Bh, Ch)
+            d2h += (wl.I + wl.J + kk) * wl.R * 4
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+    sec = max_over_ranks(sec, world, torch.device("cuda"))
     return {"value": round(whole_job_rate(steps * t, sec, world), 3), "unit": "slices/s",
             "h2d_bytes_per_step": int(xb + wb), "d2h_bytes_per_step": int(d2h / steps),
             "ms_per_step": round(1e3 * sec / steps, 3)}
@@ -623,7 +640,7 @@ def main_uneven(args):
     for s in range(warm):
         pkg.append_many(ctxs, [b[s % 2] for b in batches], [w[s % 2] for w in ws])
     torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
+    with ClockSampler(0) as clk, no_gc():
         t0 = time.perf_counter()
         for s in range(steps):
             pkg.append_many(ctxs, [b[s % 2] for b in batches], [w[s % 2] for w in ws])
@@ -747,7 +764,7 @@ def main_nmode(args):
     torch.cuda.synchronize()
     l0 = pkg.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    with ClockSampler(0) as clk, no_gc():
         e0.record()
         for s in range(steps):
             g.append(batches[s % nb], Wd[1 + s % nb])
@@ -821,7 +838,7 @@ def main_replay(args, wl):
            f32(W0), f32(A0), f32(B0), f32(C0))
     window = 1000   # appends per timed window
     k, b, total_ms, windows = t_old, 0, 0.0, []
-    with ClockSampler(0) as clk:
+    with ClockSampler(0) as clk, no_gc():
         while k + t <= K:
             n = min(window, (K - k) // t)
             X = slice_batch_torch(A, B_, C, k, k + n * t, wl.noise, args.seed, dev, dt)
