@@ -431,6 +431,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   // Tc is kept in bf16 (half the bytes; it fits the L2 for the M2 pass)
   __nv_bfloat16 *Th = reinterpret_cast<__nv_bfloat16 *>(b.H);
   tc.D = nullptr; tc.Dh = Th; tc.s_split = 0; tc.s_z = QQ * RT; tc.s_m = RT;
+  tc.d_keep = true;   // Tc is read again by the M2 reduction
   // M1 fused into the Tc GEMM: per-warp partials over 32 consecutive b (in
   // two segments where a warp's rows cross from one a to the next, 32 not
   // dividing Q)

@@ -87,6 +87,19 @@ __device__ __forceinline__ void tma_load_2d_policy(void *dst, const CUtensorMap 
 }
 
 // L2 policy that evicts the lines it brings in first (operands read once).
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// 16-byte global store with an L2 cache policy attached.
+__device__ __forceinline__ void st_global_v4_policy(void *ptr, uint4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr),
+               "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -198,7 +211,8 @@ struct TcStoreEpi {
   float *part;
   int Q, RT;
   __nv_bfloat16 *Dh;
-  int seg;   // segmented partials (32 does not divide Q)
+  int seg;    // segmented partials (32 does not divide Q)
+  int keep;   // bf16 rows stored with an L2 evict-last policy (read again soon)
   __device__ __forceinline__ bool stores() const { return D != nullptr || Dh != nullptr; }
   __device__ __forceinline__ void store(int z, int split, int m, int n, float v) const {
     const int64_t o = (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n;
@@ -208,7 +222,8 @@ struct TcStoreEpi {
   // 8 bf16 values of row m from column n (n % 8 == 0; strides multiples of 8)
   __device__ __forceinline__ void store_bf16x8(int z, int split, int m, int n, uint4 v) const {
     const int64_t o = (int64_t)split * s_split + (int64_t)z * s_z + (int64_t)m * s_m + n;
-    *reinterpret_cast<uint4 *>(Dh + o) = v;
+    if (keep) st_global_v4_policy(Dh + o, v, policy_evict_last());
+    else *reinterpret_cast<uint4 *>(Dh + o) = v;
   }
 };
 
@@ -833,7 +848,7 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   if (g.m1_part && (g.BN != 32 || ks > 1 || (seg ? g.Q < 32 : g.Q % 32 != 0))) return false;
   if (ks > 1 && (g.N > g.BN)) return false;
   TcStoreEpi epi{g.D, ks > 1 ? g.s_split : 0, g.s_z, g.s_m, g.m1_B, g.m1_part, g.Q, g.RT, g.Dh,
-                 seg ? 1 : 0};
+                 seg ? 1 : 0, g.d_keep ? 1 : 0};
   auto launch = [&](const TuneChoice &c) {
     TcShape sh{};
     sh.M = g.M; sh.N = g.N; sh.K = g.K; sh.BN = g.BN;

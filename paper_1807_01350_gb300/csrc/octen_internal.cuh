@@ -116,6 +116,8 @@ struct TcStoreArgs {
   // m / Q: m1_seg writes both segments, m1_part[z][m / 32][2][n] (segment 0 the
   // rows of the block's first m / Q)
   bool m1_seg = false;
+  // the bf16 output Dh is read again soon: stored with an L2 evict-last policy
+  bool d_keep = false;
   // shared memory (bytes) to leave free on every SM for a kernel that runs
   // beside this GEMM (fewer pipeline stages)
   int smem_reserve = 0;
