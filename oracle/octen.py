@@ -6,7 +6,7 @@ throughout; library primitives (matmul, tensordot, Cholesky, pinv) serve as
 single steps, with no blocking, fusion or reordering beyond what each step's
 definition states.
 
-Readings of the paper that this file follows (each also listed in the design doc):
+Readings of the paper that this file follows:
 
 * Eq. 2's garbled "(+) Z_p (.) W'_p(k, q)" is the update X_p = Y_p + Z_p with
   Z_p = X_new x1 U_p^T x2 V_p^T x3 W_p^T (only summaries are stored).

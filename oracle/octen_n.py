@@ -10,7 +10,7 @@ matched on their anchor rows in every non-temporal mode, and every
 non-temporal factor is lifted as in Eq. 7 with its own stacked projection, the
 new rows of the time factor as in the 3-mode case.
 
-Readings (also in DESIGN.md): the same as the 3-mode oracle's, mode by mode;
+Readings: the same as the 3-mode oracle's, mode by mode;
 one Q and one S for all modes; the CP sweep updates the time factor first,
 then the non-temporal factors in mode order (each normalised to unit l2),
 with a final time-factor update; the match similarity is the sum over the

@@ -5,7 +5,7 @@ lifted factors, fit).
 Tolerances.  FP32: summaries within 1e-5 relative Frobenius error per
 replica (fp32 FFMA accumulation over J and I terms); replica factors and the
 lifted factors within 1e-3 (the lift operators are fp32 Cholesky solves whose
-error grows with cond(U^T U), see DESIGN.md); fit within 1e-4; factor-match
+error grows with cond(U^T U)); fit within 1e-4; factor-match
 score against the oracle's factors >= 0.999.  BF16: the mode-2 product is
 rounded to bf16 before the mode-1 contraction, a relative error of about
 2^-9 / sqrt(3) ~ 1.1e-3 per element that the two later contractions average but
