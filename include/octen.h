@@ -294,6 +294,12 @@ octen_status octen_n_get_replica_factors(const octen_nctx *ctx, int which, float
 /* Rows of the time factor so far. */
 int64_t octen_n_rows(const octen_nctx *ctx);
 
+/* Fitness of the current factors on the K = octen_n_rows() slices X_all
+ * (K x I_1 x ... x I_{N-1}, fp32, device or host): 1 - ||X - [[A_1, ...,
+ * A_{N-1}, C]]||_F / ||X||_F (Sec. "Evaluation Measures"), the residual formed
+ * element by element with fp64 sums. */
+octen_status octen_n_fit(octen_nctx *ctx, const float *X_all, int64_t K, double *fit_out);
+
 /* Stage timers of the N-mode update (measurement aid): with timing on, every
  * append records CUDA events around compress, warm_start, als, align, lift
  * and c_solve; same conventions as octen_stage_times. */

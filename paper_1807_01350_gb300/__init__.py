@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
         L.octen_n_get_replica_factors.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         L.octen_n_rows.argtypes = [vp]
         L.octen_n_rows.restype = i64
+        L.octen_n_fit.argtypes = [vp, f32p, i64, ctypes.POINTER(ctypes.c_double)]
         L.octen_n_destroy.argtypes = [vp]
         L.octen_n_destroy.restype = None
         L.octen_n_last_error.argtypes = [vp]
@@ -113,7 +114,7 @@ def lib() -> ctypes.CDLL:
         L.octen_n_stage_times.argtypes = [vp, vp, vp]
         for name in ("octen_n_create", "octen_n_init", "octen_n_append", "octen_n_get_factors",
                      "octen_n_get_replicas", "octen_n_get_replica_factors",
-                     "octen_n_set_timing", "octen_n_stage_times"):
+                     "octen_n_set_timing", "octen_n_stage_times", "octen_n_fit"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("octen_create", "octen_init", "octen_append", "octen_append_many",
                      "octen_get_factors",
@@ -372,6 +373,14 @@ class OctenN:
         k = ctypes.c_int64()
         self._check(self._lib.octen_n_get_factors(self._h, ap, C.ctypes.data, ctypes.byref(k)))
         return As, C
+
+    def fit(self, X_all) -> float:
+        """Fitness of the current factors on all slices so far (octen_n_fit)."""
+        keep: list = []
+        out = ctypes.c_double()
+        self._check(self._lib.octen_n_fit(self._h, _f32(X_all, keep), int(X_all.shape[0]),
+                                          ctypes.byref(out)))
+        return float(out.value)
 
     def replicas(self):
         Y = np.empty((self.P,) + (self.Q,) * self.N, np.float32)

@@ -541,6 +541,86 @@ void n_align(const NAlignInput &in, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
+// Fitness (Sec. "Evaluation Measures"): per slice k the sums of X_k^2 and of
+// (X_k - sum_r C[k][r] A_1[:, r] o ... o A_nm[:, r])^2, the residual formed
+// element by element in fp64 (no cancellation against ||X||^2).  grid
+// (blocks per slice, slices), 256 threads; partial[k][block][2] doubles.
+// ---------------------------------------------------------------------------
+struct NFitArgs {
+  const float *X;                  // nk slices, [k][i_1]...[i_nm]
+  const float *A[kMaxNModes];      // I_n x R
+  const float *C;                  // nk x R (the chunk's rows)
+  int64_t dims[kMaxNModes];
+  int64_t E;                       // elements per slice
+  int nm, R;
+  double *partial;
+};
+
+__global__ void __launch_bounds__(256) n_fit_kernel(NFitArgs a) {
+  __shared__ double red[2][8];
+  const int k = blockIdx.y, tid = threadIdx.x;
+  const float *x = a.X + (int64_t)k * a.E;
+  const float *c = a.C + (int64_t)k * a.R;
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < a.E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t idx[kMaxNModes];
+    int64_t rem = e;
+    for (int n = a.nm - 1; n >= 0; --n) {
+      idx[n] = rem % a.dims[n];
+      rem /= a.dims[n];
+    }
+    double model = 0.0;
+    for (int r = 0; r < a.R; ++r) {
+      double pr = c[r];
+      for (int n = 0; n < a.nm; ++n) pr *= (double)a.A[n][idx[n] * a.R + r];
+      model += pr;
+    }
+    const double xv = x[e], d = xv - model;
+    s0 = fma(xv, xv, s0);
+    s1 = fma(d, d, s1);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = s0;
+    red[1][tid >> 5] = s1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      t0 += red[0][w];
+      t1 += red[1][w];
+    }
+    double *pp = a.partial + ((int64_t)k * gridDim.x + blockIdx.x) * 2;
+    pp[0] = t0;
+    pp[1] = t1;
+  }
+}
+
+int n_fit_blocks(int64_t E) {
+  const int64_t b = (E + 256 * 8 - 1) / (256 * 8);
+  return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
+void n_fit_sums(const float *X, int64_t nk, const float *const *A, const float *C,
+                const int64_t *dims, int nm, int R, double *partial, cudaStream_t st) {
+  NFitArgs a{};
+  a.X = X; a.C = C; a.nm = nm; a.R = R; a.partial = partial;
+  a.E = 1;
+  for (int n = 0; n < nm; ++n) {
+    a.A[n] = A[n];
+    a.dims[n] = dims[n];
+    a.E *= dims[n];
+  }
+  n_fit_kernel<<<dim3((unsigned)n_fit_blocks(a.E), (unsigned)nk), 256, 0, st>>>(a);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
 // Compression chain (see the top of the file).
 // ---------------------------------------------------------------------------
 int64_t ncompress_rows_max(int nm, const int64_t *dims, int Q, int64_t t) {

@@ -304,6 +304,12 @@ struct NAlignInput {
 };
 void n_align(const NAlignInput &in, cudaStream_t st);
 
+// Fitness sums of nk slices (see k_nmode.cu): partial[k][block][2] doubles,
+// n_fit_blocks(E) blocks per slice of E elements.
+int n_fit_blocks(int64_t E);
+void n_fit_sums(const float *X, int64_t nk, const float *const *A, const float *C,
+                const int64_t *dims, int nm, int R, double *partial, cudaStream_t st);
+
 // true for device (or managed) memory
 bool is_device_pointer(const void *p);
 

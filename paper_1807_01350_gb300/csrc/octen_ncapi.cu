@@ -6,6 +6,7 @@
 // from the projected previous factors, anchor match in every non-temporal
 // mode, lift of every non-temporal factor (Eq. 7) and the new rows of the time
 // factor.  fp32 throughout.
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 #include <string>
@@ -461,6 +462,45 @@ octen_status octen_n_get_replica_factors(const octen_nctx *cx, int which, float 
 }
 
 int64_t octen_n_rows(const octen_nctx *x) { return x ? x->K : 0; }
+
+octen_status octen_n_fit(octen_nctx *x, const float *X_all, int64_t K, double *fit_out) {
+  if (!x || !X_all || !fit_out) return OCTEN_EINVAL;
+  if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_n_fit before octen_n_init");
+  if (K != x->K || K > 65535)
+    return x->fail(OCTEN_EINVAL, "octen_n_fit: K=%lld, rows=%lld", (long long)K, (long long)x->K);
+  const int nb = n_fit_blocks(x->slice);
+  const bool dev = is_device_pointer(X_all);
+  const int64_t chunk = dev ? K : 16;   // host slices are staged chunk by chunk
+  double *part = nullptr;
+  if (cudaMalloc(&part, (size_t)chunk * nb * 2 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return x->fail(OCTEN_ENOMEM, "fit scratch");
+  }
+  std::vector<double> h((size_t)chunk * nb * 2);
+  double t0 = 0.0, t1 = 0.0;
+  octen_status s = OCTEN_OK;
+  for (int64_t k0 = 0; k0 < K && s == OCTEN_OK; k0 += chunk) {
+    const int64_t n = K - k0 < chunk ? K - k0 : chunk;
+    const float *Xd = dev ? X_all + k0 * x->slice
+                          : x->stage_in(X_all + k0 * x->slice, (size_t)n * x->slice * 4, 0);
+    if (!Xd) {
+      s = x->fail(OCTEN_ENOMEM, "staging X_all");
+      break;
+    }
+    n_fit_sums(Xd, n, x->A, x->C + k0 * x->cfg.R, x->dims, x->nm, x->cfg.R, part, x->st);
+    cudaMemcpyAsync(h.data(), part, (size_t)n * nb * 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                    x->st);
+    s = x->sync_check("fit");
+    for (int64_t i = 0; i < n * nb && s == OCTEN_OK; ++i) {
+      t0 += h[2 * i];
+      t1 += h[2 * i + 1];
+    }
+  }
+  cudaFree(part);
+  if (s != OCTEN_OK) return s;
+  *fit_out = t0 > 0.0 ? 1.0 - sqrt(t1) / sqrt(t0) : 0.0;
+  return OCTEN_OK;
+}
 
 int octen_n_stage_count(void) { return kNStages; }
 

@@ -70,7 +70,7 @@ def run_gpu(pkg, case, d, host=False):
         k += t
         As, C = g.factors()
         out.append(dict(Y=g.replicas(), A=As, C=C, raw=g.replica_factors(0),
-                        hat=g.replica_factors(1)))
+                        hat=g.replica_factors(1), fit=g.fit(conv(d["X"][:k]))))
     return g, out
 
 
@@ -98,9 +98,12 @@ def check(case, d, gpu, ref):
             e = rel(gs["A"][n], rs["A"][n])
             assert e < TOL["F"], ("A", b, n, e)
         assert rel(gs["C"], rs["C"]) < TOL["F"], ("C", b, rel(gs["C"], rs["C"]))
-        f_gpu = octen_n.fit_n(d["X"][:k], gs["A"], gs["C"])
+        f_gpu = octen_n.fit_n(d["X"][:k], [np.asarray(a, np.float64) for a in gs["A"]],
+                              np.asarray(gs["C"], np.float64))
         f_ref = octen_n.fit_n(d["X"][:k], rs["A"], rs["C"])
         assert abs(f_gpu - f_ref) < TOL["fit"], ("fit", b, f_gpu, f_ref)
+        # the library's own fit of its factors (octen_n_fit, fp64 sums)
+        assert abs(gs["fit"] - f_gpu) < 1e-9, ("octen_n_fit", b, gs["fit"], f_gpu)
         assert fms(tuple(gs["A"]) + (gs["C"],), tuple(rs["A"]) + (rs["C"],)) > TOL["fms"]
 
 
