@@ -300,6 +300,12 @@ int64_t octen_n_rows(const octen_nctx *ctx);
  * element by element with fp64 sums. */
 octen_status octen_n_fit(octen_nctx *ctx, const float *X_all, int64_t K, double *fit_out);
 
+/* Checkpoint and resume of an N-mode context (as octen_save / octen_load:
+ * the projections, lift operators, factors, summaries and G_p; a loaded
+ * context continues the stream bit for bit on the same GPU and build). */
+octen_status octen_n_save(const octen_nctx *ctx, const char *path);
+octen_status octen_n_load(const char *path, void *cuda_stream, octen_nctx **out);
+
 /* Stage timers of the N-mode update (measurement aid): with timing on, every
  * append records CUDA events around compress, warm_start, als, align, lift
  * and c_solve; same conventions as octen_stage_times. */

@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.octen_n_rows.argtypes = [vp]
         L.octen_n_rows.restype = i64
         L.octen_n_fit.argtypes = [vp, f32p, i64, ctypes.POINTER(ctypes.c_double)]
+        L.octen_n_save.argtypes = [vp, ctypes.c_char_p]
+        L.octen_n_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
         L.octen_n_destroy.argtypes = [vp]
         L.octen_n_destroy.restype = None
         L.octen_n_last_error.argtypes = [vp]
@@ -114,7 +116,8 @@ def lib() -> ctypes.CDLL:
         L.octen_n_stage_times.argtypes = [vp, vp, vp]
         for name in ("octen_n_create", "octen_n_init", "octen_n_append", "octen_n_get_factors",
                      "octen_n_get_replicas", "octen_n_get_replica_factors",
-                     "octen_n_set_timing", "octen_n_stage_times", "octen_n_fit"):
+                     "octen_n_set_timing", "octen_n_stage_times", "octen_n_fit",
+                     "octen_n_save", "octen_n_load"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("octen_create", "octen_init", "octen_append", "octen_append_many",
                      "octen_get_factors",
@@ -373,6 +376,31 @@ class OctenN:
         k = ctypes.c_int64()
         self._check(self._lib.octen_n_get_factors(self._h, ap, C.ctypes.data, ctypes.byref(k)))
         return As, C
+
+    def save(self, path: str):
+        """Checkpoint the whole state to `path` (octen_n_save)."""
+        self._check(self._lib.octen_n_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "OctenN":
+        """A context resumed from a checkpoint written by `save`."""
+        L = lib()
+        h = ctypes.c_void_p()
+        st = L.octen_n_load(os.fsencode(path), _stream_handle(stream), ctypes.byref(h))
+        if st != 0:
+            raise OctenError(st, f"octen_n_load({path!r}) failed")
+        self = cls.__new__(cls)
+        self._lib = L
+        self._h = h
+        with open(path, "rb") as f:   # the shape, from the header (magic, then octen_nconfig)
+            f.read(8)
+            cfg = _NConfig.from_buffer_copy(f.read(ctypes.sizeof(_NConfig)))
+        self.cfg = cfg
+        self.N = cfg.N
+        self.dims = [int(cfg.dims[n]) for n in range(cfg.N - 1)]
+        self.R, self.P, self.Q, self.S = cfg.R, cfg.P, cfg.Q, cfg.S
+        self.Qd = cfg.S + cfg.P * (cfg.Q - cfg.S)
+        return self
 
     def fit(self, X_all) -> float:
         """Fitness of the current factors on all slices so far (octen_n_fit)."""

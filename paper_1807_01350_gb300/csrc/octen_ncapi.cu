@@ -463,6 +463,108 @@ octen_status octen_n_get_replica_factors(const octen_nctx *cx, int which, float 
 
 int64_t octen_n_rows(const octen_nctx *x) { return x ? x->K : 0; }
 
+}  // extern "C"
+
+namespace {
+
+// Device arrays that make up the state of an initialised N-mode context, in
+// file order: per non-temporal mode the rounded projection, its replica
+// transpose, its lift operator and the factor; the summaries, G_p and C.
+struct NStateArray {
+  void *p;
+  size_t bytes;
+};
+
+std::vector<NStateArray> nstate_arrays(octen_nctx *x) {
+  const octen_nconfig &c = x->cfg;
+  const size_t P = c.P, Q = c.Q, Qd = x->Qd;
+  std::vector<NStateArray> v;
+  for (int n = 0; n < x->nm; ++n) {
+    const size_t I = (size_t)x->dims[n];
+    v.push_back({x->U32[n], I * Qd * 4});
+    v.push_back({x->Ut[n], P * Q * I * 4});
+    v.push_back({x->L[n], I * Qd * 4});
+    v.push_back({x->A[n], I * c.R * 4});
+  }
+  size_t qn = 1;
+  for (int n = 0; n < x->NN; ++n) qn *= Q;
+  v.push_back({x->Y, P * qn * 4});
+  v.push_back({x->G, P * Q * c.R * 4});
+  v.push_back({x->C, (size_t)x->K * c.R * 4});
+  return v;
+}
+
+const char kNMagic[8] = {'O', 'C', 'T', 'E', 'N', 'N', 'M', '1'};
+
+}  // namespace
+
+extern "C" {
+
+octen_status octen_n_save(const octen_nctx *cx, const char *path) {
+  octen_nctx *x = const_cast<octen_nctx *>(cx);
+  if (!x || !path) return OCTEN_EINVAL;
+  if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_n_save before octen_n_init");
+  if (x->sync_check("save") != OCTEN_OK) return OCTEN_ECUDA;
+  FILE *f = fopen(path, "wb");
+  if (!f) return x->fail(OCTEN_EINVAL, "octen_n_save: cannot open %s", path);
+  int64_t hdr[2 + kMaxNModes] = {x->K, 0};
+  for (int n = 0; n < x->nm; ++n) hdr[2 + n] = x->over[n];
+  bool ok = fwrite(kNMagic, 1, 8, f) == 8 && fwrite(&x->cfg, sizeof x->cfg, 1, f) == 1 &&
+            fwrite(hdr, sizeof hdr, 1, f) == 1;
+  std::vector<char> host;
+  for (const NStateArray &a : nstate_arrays(x)) {
+    if (!ok) break;
+    host.resize(a.bytes);
+    ok = cudaMemcpy(host.data(), a.p, a.bytes, cudaMemcpyDeviceToHost) == cudaSuccess &&
+         fwrite(host.data(), 1, a.bytes, f) == a.bytes;
+  }
+  ok = (fclose(f) == 0) && ok;
+  return ok ? OCTEN_OK : x->fail(OCTEN_ECUDA, "octen_n_save: writing %s failed", path);
+}
+
+octen_status octen_n_load(const char *path, void *cuda_stream, octen_nctx **out) {
+  if (!path || !out) return OCTEN_EINVAL;
+  FILE *f = fopen(path, "rb");
+  if (!f) return OCTEN_EINVAL;
+  char magic[8];
+  octen_nconfig cfg{};
+  int64_t hdr[2 + kMaxNModes];
+  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kNMagic, 8) != 0 ||
+      fread(&cfg, sizeof cfg, 1, f) != 1 || fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] < 1) {
+    fclose(f);
+    return OCTEN_EINVAL;
+  }
+  octen_nctx *x = nullptr;
+  octen_status s = octen_n_create(&cfg, cuda_stream, &x);
+  if (s != OCTEN_OK) {
+    fclose(f);
+    return s;
+  }
+  if (!x->ensure_c(hdr[0])) {
+    fclose(f);
+    delete x;
+    return OCTEN_ENOMEM;
+  }
+  x->K = hdr[0];
+  for (int n = 0; n < x->nm; ++n) x->over[n] = (int)hdr[2 + n];
+  bool ok = true;
+  std::vector<char> host;
+  for (const NStateArray &a : nstate_arrays(x)) {
+    host.resize(a.bytes);
+    ok = fread(host.data(), 1, a.bytes, f) == a.bytes &&
+         cudaMemcpy(a.p, host.data(), a.bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) break;
+  }
+  fclose(f);
+  if (!ok) {
+    delete x;
+    return OCTEN_EINVAL;
+  }
+  x->initialized = true;
+  *out = x;
+  return OCTEN_OK;
+}
+
 octen_status octen_n_fit(octen_nctx *x, const float *X_all, int64_t K, double *fit_out) {
   if (!x || !X_all || !fit_out) return OCTEN_EINVAL;
   if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_n_fit before octen_n_init");
