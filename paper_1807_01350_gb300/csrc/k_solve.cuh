@@ -441,6 +441,51 @@ __global__ void __launch_bounds__(256)
     }
     ldl_substitute<RT>(y, Lc, Lr, rf);
   }
+  if (normalize && Gout) {
+    // one reduction serves both: the Gram of the unnormalised rows (per CTA,
+    // then over the cluster) gives the column norms on its diagonal, and the
+    // Gram of the normalised factor is that Gram scaled by 1/(n_r n_s)
+    __syncthreads();   // every row of Ms has been read
+    if (own) {
+      float4 *mr = reinterpret_cast<float4 *>(Ms + tid * RT);
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4)
+        mr[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
+    }
+    __syncthreads();
+    smem_gram<RT>(Ms, nrows, Gp);
+    cluster_barrier();   // every CTA's partial Gram is in place
+    if (tid < RT) {
+      float tot = 0.f;
+      for (uint32_t c = 0; c < ncta; ++c) tot += ld_cluster(Gp + tid * (RT + 1), c);
+      const float n = sqrtf(tot);
+      scale[tid] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
+    }
+    __syncthreads();   // scale visible CTA-wide
+    const int e0 = (int)(crank * (RT * RT) / ncta), e1 = (int)((crank + 1) * (RT * RT) / ncta);
+    for (int e = e0 + tid; e < e1; e += blockDim.x) {
+      float g = 0.f;
+      for (uint32_t c = 0; c < ncta; ++c) g += ld_cluster(Gp + e, c);
+      Gout[(int64_t)p * RT * RT + e] = g * scale[e / RT] * scale[e % RT];
+    }
+    cluster_barrier();   // peers are done reading Gp
+#pragma unroll
+    for (int r = 0; r < RT; ++r) y[r] *= scale[r];
+    if (own) {
+      const int q = row0 + tid;
+      float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4)
+        o[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
+      if (Ft) {
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+          Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(y[r]);
+        for (int r = RT; r < NP; ++r) Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(0.f);
+      }
+    }
+    return;
+  }
   if (normalize) {
     // column sums of squares over this CTA's rows, then over the cluster
     float sq[RT];
