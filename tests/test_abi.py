@@ -53,3 +53,21 @@ def test_create_rejects_bad_shapes_before_touching_the_device(built):
     assert pkg.lib().octen_create(ctypes.byref(cfg), None, ctypes.byref(h)) == 1
     cfg = pkg._Config(10, 10, 4, 2, 8, 8, 5, 0)       # S = Q
     assert pkg.lib().octen_create(ctypes.byref(cfg), None, ctypes.byref(h)) == 1
+
+
+def test_nmode_create_rejects_bad_shapes_before_touching_the_device(built):
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+
+    def cfg(N, dims, R=2, P=2, Q=4, S=1, iters=5):
+        d = (ctypes.c_int64 * (pkg.MAX_MODES - 1))(*(list(dims) + [0] * (pkg.MAX_MODES - 1 - len(dims))))
+        return pkg._NConfig(N, R, P, Q, S, iters, d)
+
+    for c in (cfg(2, (10,)),                      # fewer than three modes
+              cfg(7, (4, 4, 4, 4, 4)),            # more than six
+              cfg(4, (10, 10, 10), R=33),          # rank above 32
+              cfg(4, (10, 10, 10), Q=4, S=4),      # S = Q
+              cfg(4, (10, 0, 10)),                 # an empty mode
+              cfg(6, (8, 8, 8, 8, 8), P=64, Q=32)):  # summaries too large
+        assert L.octen_n_create(ctypes.byref(c), None, ctypes.byref(h)) == 1
+    assert L.octen_n_last_error(None) == b"NULL context"
