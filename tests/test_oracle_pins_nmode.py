@@ -123,3 +123,62 @@ def test_four_mode_planted_mistake_fails(monkeypatch):
     o, As, C, X = _exact_update(_rng(74))
     model = np.einsum("ar,br,cr,kr->kabc", *o.A, o.C)   # the fit without the patched helper
     assert np.linalg.norm(X - model) / np.linalg.norm(X) > 1e-3
+
+
+def test_four_mode_mttkrp_is_the_nested_sum():
+    rng = _rng(75)
+    X = rng.standard_normal((3, 2, 4, 3))
+    R = 2
+    Fs = [rng.standard_normal((n, R)) for n in X.shape]
+    for mode in range(4):
+        M = N.mttkrp_n(X, Fs, mode)
+        ref = np.zeros((X.shape[mode], R))
+        for idx in itertools.product(*(range(n) for n in X.shape)):
+            for r in range(R):
+                w = X[idx]
+                for m in range(4):
+                    if m != mode:
+                        w *= Fs[m][idx[m], r]
+                ref[idx[mode], r] += w
+        assert np.allclose(M, ref, rtol=1e-12, atol=1e-12), mode
+
+
+def test_four_mode_match_recovers_a_known_permutation_and_scales():
+    # replica factors = the references permuted, each mode scaled per column
+    # by d_n (signs included); the match must undo the permutation, divide
+    # every mode by its d_n and multiply the time factor by the product
+    rng = _rng(76)
+    R, S, Q = 4, 5, 7
+    refs = [rng.standard_normal((S, R)) for _ in range(3)]
+    perm = np.array([2, 0, 3, 1])                    # reference column s sits at replica column perm[s]
+    inv = np.argsort(perm)
+    d = [rng.uniform(0.5, 2.0, R) * rng.choice([-1.0, 1.0], R) for _ in range(3)]
+    Fs, tails = [], []
+    for n in range(3):
+        tail = rng.standard_normal((Q - S, R))
+        full = np.vstack([refs[n], tail])            # columns in reference order
+        Fs.append((full * d[n])[:, inv])             # scaled, then permuted
+        tails.append(tail)
+    Ctrue = rng.standard_normal((6, R))
+    C = (Ctrue / (d[0] * d[1] * d[2]))[:, inv]
+    Fh, Ch, got = N.align_n(Fs, C, refs, S)
+    assert np.array_equal(got, perm)
+    for n in range(3):
+        assert np.allclose(Fh[n][:S], refs[n], rtol=1e-12, atol=1e-12)
+        assert np.allclose(Fh[n][S:], tails[n], rtol=1e-12, atol=1e-12)
+    assert np.allclose(Ch, Ctrue, rtol=1e-12, atol=1e-12)
+
+
+def test_four_mode_fit_is_the_explicit_residual():
+    rng = _rng(77)
+    As = [rng.standard_normal((n, 2)) for n in (3, 2, 4)]
+    C = rng.standard_normal((3, 2))
+    X = rng.standard_normal((3, 3, 2, 4))
+    num = den = 0.0
+    for k, a, b, c in itertools.product(range(3), range(3), range(2), range(4)):
+        model = sum(C[k, r] * As[0][a, r] * As[1][b, r] * As[2][c, r] for r in range(2))
+        num += (X[k, a, b, c] - model) ** 2
+        den += X[k, a, b, c] ** 2
+    assert abs(N.fit_n(X, As, C) - (1 - np.sqrt(num) / np.sqrt(den))) < 1e-12
+    exact = np.einsum("ar,br,cr,kr->kabc", *As, C)
+    assert abs(N.fit_n(exact, As, C) - 1.0) < 1e-12
