@@ -445,6 +445,25 @@ def _fms(model, ref):
     return float(sim[rows, cols].mean())
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_cores():
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
         if os.environ.get(var, "").isdigit():
@@ -583,7 +602,7 @@ def main():
         smp = OracleSampler(wl, args.seed, args.prec)
         sec = smp.full_append()
         line["cpu_baseline"] = {
-            "value": round(wl.batch / sec, 5), "unit": "slices/s", "cores": cpu_cores(),
+            "value": round(wl.batch / sec, 5), "unit": "slices/s", "cores": cpu_cores(), "cpu_model": cpu_model(),
             "kind": "oracle",
             "sample": f"one whole append of {wl.batch} slices at {wl.name} ({args.prec} inputs) "
                       f"after an init from 1 slice: compression and CP-ALS of all {wl.P} "
@@ -804,7 +823,7 @@ def main_nmode(args):
         "roofline": dict(stage_roof[dominant], kernel=dominant),
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_roofline": stage_roof,
-        "cpu_baseline": {"value": round(t / cpu_sec, 5), "unit": "slices/s", "cores": cpu_cores(),
+        "cpu_baseline": {"value": round(t / cpu_sec, 5), "unit": "slices/s", "cores": cpu_cores(), "cpu_model": cpu_model(),
                          "kind": "oracle",
                          "sample": f"one whole append of {t} slices at {wl.name} after an init "
                                    f"from {t_old} slices ({cpu_sec:.1f} s)"},
@@ -969,7 +988,7 @@ def main_reference(args, wl, world, rank):
             "config": {"workload": wl.name, "I": wl.I, "J": wl.J, "R": wl.R, "P": wl.P,
                        "Q": wl.Q, "S": wl.S, "batch_slices": wl.batch,
                        "als_iters": wl.als_iters},
-            "cpu_baseline": {"value": round(value, 5), "unit": "slices/s", "cores": cpu_cores(),
+            "cpu_baseline": {"value": round(value, 5), "unit": "slices/s", "cores": cpu_cores(), "cpu_model": cpu_model(),
                              "kind": "oracle",
                              "sample": smp.describe(len(reps), t_rep, t_lift)},
             "e2e": {"value": round(value, 5), "unit": "slices/s", "h2d_bytes_per_step": 0,
