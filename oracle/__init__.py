@@ -24,6 +24,7 @@ from .octen_n import (  # noqa: F401
     align_n,
     compress_n,
     cp_als_n,
+    decompose_existing_n,
     fit_n,
     khatri_rao_list,
     mttkrp_n,

@@ -129,6 +129,17 @@ def align_n(Fs: list, C: np.ndarray, refs: list, S: int):
     return Fh, C[:, perm] * scale_c, perm
 
 
+def decompose_existing_n(X_old: np.ndarray, A0s: list, iters: int) -> list:
+    """The existing decomposition when none is supplied (the paper assumes one
+    exists, Sec. "Problem Formulation"): cp_als_n of the existing tensor, whose
+    slices X_old[k] are I_1 x ... x I_{N-1}, in the mode order (i_1, ..., k) of
+    the model X_old[k][i..] = sum_r prod_n A_n[i_n][r] C[k][r], from the guesses
+    A0s.  Returns [A_1, ..., A_{N-1}, C]."""
+    X = np.asarray(X_old, dtype=np.float64)
+    order = list(range(1, X.ndim)) + [0]
+    return cp_als_n(np.transpose(X, order), A0s, iters)
+
+
 def fit_n(X: np.ndarray, As: list, C: np.ndarray) -> float:
     """1 - ||X - [[A_1, ..., A_{N-1}, C]]||_F / ||X||_F, X[k][i_1]...[i_{N-1}]."""
     num = 0.0
@@ -160,8 +171,12 @@ class OctenOracleN:
         W = self._split(np.asarray(W_old, dtype=np.float64))
         self.Y = [compress_n(X_old, [self.U[n][p] for n in range(len(self.dims))], W[p])
                   for p in range(self.P)]
-        self.A = [np.asarray(A, dtype=np.float64).copy() for A in A0s]
-        self.C = np.asarray(C0, dtype=np.float64).copy()
+        if C0 is None:   # A0s are starting guesses: decompose the existing tensor
+            out = decompose_existing_n(X_old, A0s, self.als_iters)
+            self.A, self.C = out[:-1], out[-1]
+        else:
+            self.A = [np.asarray(A, dtype=np.float64).copy() for A in A0s]
+            self.C = np.asarray(C0, dtype=np.float64).copy()
         self.G = [W[p].T @ self.C for p in range(self.P)]
 
     def append(self, X_new, W_new):

@@ -182,3 +182,23 @@ def test_four_mode_fit_is_the_explicit_residual():
     assert abs(N.fit_n(X, As, C) - (1 - np.sqrt(num) / np.sqrt(den))) < 1e-12
     exact = np.einsum("ar,br,cr,kr->kabc", *As, C)
     assert abs(N.fit_n(exact, As, C) - 1.0) < 1e-12
+
+
+def test_four_mode_existing_decomposition_recovers_planted_factors():
+    # noiseless planted 4-mode data: the decomposition of the existing tensor
+    # from perturbed guesses reproduces it (fit 1) and its factors (FMS 1),
+    # directly and through the oracle's init with the time factor omitted
+    rng = _rng(78)
+    dims, K, R = (7, 6, 5), 12, 2
+    As, C, X = _planted4(rng, dims, K, R)
+    out = N.decompose_existing_n(X, [A + 0.05 * rng.standard_normal(A.shape) for A in As], 80)
+    assert N.fit_n(X, out[:-1], out[-1]) > 1 - 1e-9
+    assert fms(out[:2] + [out[-1]], As[:2] + [C]) > 1 - 1e-9
+    # the same through the oracle's init with C0 omitted
+    P, Q, S = 3, 4, 2
+    Qd = S + P * (Q - S)
+    Us = [rng.standard_normal((I, Qd)) for I in dims]
+    W0 = rng.standard_normal((K, Qd))
+    o = N.OctenOracleN(list(dims), R, P, Q, S, 80)
+    o.init(X, Us, W0, [A + 0.05 * rng.standard_normal(A.shape) for A in As], None)
+    assert N.fit_n(X, o.A, o.C) > 1 - 1e-9
