@@ -155,20 +155,25 @@ def stage_work(wl, prec, layouts=False):
 
 def als_gemm_tc_bytes(wl):
     """Algorithmic bytes per tensor-core ALS GEMM launch, averaged over an
-    append.  The Tc GEMM reads the bf16 copy Xa and the bf16 C^T, writes Tc
-    (bf16, rank padded to RT) and the M1 partials (Q / 32 per row, fp32).  With
-    32 | Q the M3 GEMM reads the bf16 copy Xc and the bf16 B^T and writes only
-    its M3 partials (Q / 32 per row); otherwise it reads Xc and the Khatri-Rao
-    operand (rank padded to 32)."""
+    append (als_iters + 1 M3 launches, als_iters Tc launches).  The Tc GEMM
+    reads the bf16 copy Xa and the bf16 C^T and writes Tc (bf16, rank padded
+    to RT).  With Q >= 32 both GEMMs also write their fused partial sums over
+    32 consecutive rows (fp32, RT per block; two segment sums per block when
+    32 does not divide Q) and the M3 GEMM reads the bf16 copy Xc and the bf16
+    B^T.  Below Q = 32 the M3 GEMM reads Xc and the Khatri-Rao operand (rank
+    padded to 32), and the M1 reduction runs as a separate pass."""
     P, Q, R, it = wl.P, wl.Q, wl.R, wl.als_iters
     RT = 8 if R <= 8 else (16 if R <= 16 else 32)
     NP = 32
-    parts = 4.0 * P * Q * (Q // 32) * RT
-    if Q % 32 == 0:
+    QQ = Q * Q
+    if Q >= 32:
+        blocks = QQ // 32 if Q % 32 == 0 else 2 * ((QQ + 31) // 32)
+        parts = 4.0 * P * blocks * RT
         m3 = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q + parts
+        tc = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q + 2.0 * P * QQ * RT + parts
     else:
-        m3 = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q * Q
-    tc = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q + 2.0 * P * Q * Q * RT + (parts if Q % 32 == 0 else 0)
+        m3 = 2.0 * P * Q ** 3 + 2.0 * P * NP * QQ
+        tc = 2.0 * P * Q ** 3 + 2.0 * P * NP * Q + 2.0 * P * QQ * RT
     return ((it + 1) * m3 + it * tc) / (2 * it + 1)
 
 
