@@ -186,7 +186,12 @@ octen_status octen_compress_noalloc(const octen_config *cfg, void *cuda_stream, 
  * writes the full state of an initialised context to a file; octen_load
  * creates a new context on `cuda_stream` from such a file.  A loaded context
  * continues the stream exactly as the saved one would (same results, bit for
- * bit, on the same GPU and library build).  EINVAL on a bad path or file. */
+ * bit, on the same GPU and library build).  EINVAL on a bad path or file: a
+ * missing or short file, another magic, a row count below 1 or above 2^40,
+ * or lift-operator layout flags that the configuration's shapes contradict
+ * (all checked before any device memory is allocated, except the flags,
+ * checked right after the context is created); ENOMEM when the state does
+ * not fit.  *out is set only on success. */
 octen_status octen_save(const octen_ctx *ctx, const char *path);
 octen_status octen_load(const char *path, void *cuda_stream, octen_ctx **out);
 

@@ -450,6 +450,7 @@ void project(octen_ctx *x, const float *Ur, int64_t rows, const float *F, float 
 
 bool ensure_c_capacity(octen_ctx *x, int64_t rows) {
   if (rows <= x->Kcap) return true;
+  if (rows > kCRowsMax) return false;
   int64_t cap = x->Kcap > 0 ? x->Kcap : 64;
   while (cap < rows) cap *= 2;
   float *nc = nullptr;
@@ -905,7 +906,8 @@ octen_status octen_load(const char *path, void *cuda_stream, octen_ctx **out) {
   octen_config cfg{};
   int64_t hdr[4];
   if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 ||
-      fread(&cfg, sizeof cfg, 1, f) != 1 || fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] < 1) {
+      fread(&cfg, sizeof cfg, 1, f) != 1 || fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] < 1 ||
+      hdr[0] > kCRowsMax) {
     fclose(f);
     return OCTEN_EINVAL;
   }
@@ -914,6 +916,13 @@ octen_status octen_load(const char *path, void *cuda_stream, octen_ctx **out) {
   if (s != OCTEN_OK) {
     fclose(f);
     return s;
+  }
+  // the lift operators' layouts follow from the shapes (Qd above or below
+  // the factor's rows); a header that disagrees is not this build's file
+  if (hdr[1] != (x->Qd > cfg.I ? 1 : 0) || hdr[2] != (x->Qd > cfg.J ? 1 : 0)) {
+    fclose(f);
+    delete x;
+    return OCTEN_EINVAL;
   }
   if (!ensure_c_capacity(x, hdr[0])) {
     fclose(f);

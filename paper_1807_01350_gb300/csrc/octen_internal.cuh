@@ -265,6 +265,12 @@ void transpose_f32(const float *in, int64_t rows, int64_t cols, float *out, cuda
 // ---------------------------------------------------------------------------
 constexpr int kMaxNModes = 6;
 
+// Upper bound on the rows of the time factor C a context grows to (its
+// capacity doubles from 64 rows; 2^40 rows of even one fp32 column are beyond
+// any device memory, so the bound only guards the doubling against overflow
+// on a corrupt checkpoint header).
+constexpr int64_t kCRowsMax = int64_t(1) << 40;
+
 // Compression of fp32 slices X[k][i_1]...[i_{nm}] into the summaries
 // Y[p][q_1]...[q_{nm}][c] (accumulated).  Ut[n] = [p][q][i] replica
 // transposes of the projections; Wt = [p][c][k] of the chunk's time rows;

@@ -166,6 +166,7 @@ struct octen_nctx {
 
   bool ensure_c(int64_t rows) {
     if (rows <= Kcap) return true;
+    if (rows > kCRowsMax) return false;
     int64_t cap = Kcap > 0 ? Kcap : 64;
     while (cap < rows) cap *= 2;
     float *nc = nullptr;
@@ -530,7 +531,8 @@ octen_status octen_n_load(const char *path, void *cuda_stream, octen_nctx **out)
   octen_nconfig cfg{};
   int64_t hdr[2 + kMaxNModes];
   if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kNMagic, 8) != 0 ||
-      fread(&cfg, sizeof cfg, 1, f) != 1 || fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] < 1) {
+      fread(&cfg, sizeof cfg, 1, f) != 1 || fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] < 1 ||
+      hdr[0] > kCRowsMax) {
     fclose(f);
     return OCTEN_EINVAL;
   }
@@ -539,6 +541,14 @@ octen_status octen_n_load(const char *path, void *cuda_stream, octen_nctx **out)
   if (s != OCTEN_OK) {
     fclose(f);
     return s;
+  }
+  // the lift operators' layouts follow from the shapes
+  for (int n = 0; n < x->nm; ++n) {
+    if (hdr[2 + n] != (x->Qd > x->dims[n] ? 1 : 0)) {
+      fclose(f);
+      delete x;
+      return OCTEN_EINVAL;
+    }
   }
   if (!x->ensure_c(hdr[0])) {
     fclose(f);

@@ -71,3 +71,46 @@ def test_nmode_create_rejects_bad_shapes_before_touching_the_device(built):
               cfg(6, (8, 8, 8, 8, 8), P=64, Q=32)):  # summaries too large
         assert L.octen_n_create(ctypes.byref(c), None, ctypes.byref(h)) == 1
     assert L.octen_n_last_error(None) == b"NULL context"
+
+
+def _checkpoint(tmp_path, name, magic, cfg, hdr):
+    path = tmp_path / name
+    hdr_arr = (ctypes.c_int64 * len(hdr))(*hdr)
+    path.write_bytes(magic + bytes(cfg) + bytes(hdr_arr))
+    return str(path).encode()
+
+
+def test_load_rejects_bad_checkpoint_headers_before_touching_the_device(built, tmp_path):
+    # every rejection below happens while reading the header, before a
+    # context (and any device memory) exists
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    cfg = pkg._Config(100, 100, 5, 4, 20, 5, 50, 0)
+    assert L.octen_load(str(tmp_path / "missing.bin").encode(), None, ctypes.byref(h)) == 1
+    for name, magic, hdr in (
+            ("magic.bin", b"OCTENXX1", [80, 0, 0, 0]),          # not a checkpoint
+            ("rows0.bin", b"OCTENST1", [0, 0, 0, 0]),           # no rows of C
+            ("rowsneg.bin", b"OCTENST1", [-5, 0, 0, 0]),
+            ("rowsbig.bin", b"OCTENST1", [1 << 62, 0, 0, 0])):  # beyond any device
+        assert L.octen_load(_checkpoint(tmp_path, name, magic, cfg, hdr), None,
+                            ctypes.byref(h)) == 1, name
+    trunc = tmp_path / "short.bin"
+    trunc.write_bytes(b"OCTENST1" + bytes(cfg)[:12])
+    assert L.octen_load(str(trunc).encode(), None, ctypes.byref(h)) == 1
+    assert not h.value
+
+
+def test_nmode_load_rejects_bad_checkpoint_headers_before_touching_the_device(built, tmp_path):
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * (pkg.MAX_MODES - 1))(100, 100, 100, 0, 0)
+    cfg = pkg._NConfig(4, 5, 8, 10, 3, 50, d)
+    rest = [0] * pkg.MAX_MODES
+    assert L.octen_n_load(str(tmp_path / "missing.bin").encode(), None, ctypes.byref(h)) == 1
+    for name, magic, hdr in (
+            ("magic.bin", b"OCTENST1", [30, 0] + rest),          # the 3-mode format
+            ("rows0.bin", b"OCTENNM1", [0, 0] + rest),
+            ("rowsbig.bin", b"OCTENNM1", [1 << 62, 0] + rest)):
+        assert L.octen_n_load(_checkpoint(tmp_path, name, magic, cfg, hdr), None,
+                              ctypes.byref(h)) == 1, name
+    assert not h.value
