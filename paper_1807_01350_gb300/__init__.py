@@ -161,6 +161,37 @@ def _ptr(a, keep: list):
     return a.data_ptr()
 
 
+def _numel(a) -> int:
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _need(a, count: int, what: str, required: bool = True):
+    """The library reads exactly `count` elements behind each array pointer:
+    an array of another size is refused here (EINVAL), before a kernel could
+    read past its end."""
+    if a is None:
+        if required:
+            raise OctenError(1, f"{what} is required")
+        return
+    if _numel(a) != count:
+        raise OctenError(1, f"{what}: {_numel(a)} elements, expected {count}")
+
+
+def _out(a, count: int, what: str):
+    """A destination buffer: contiguous fp32 of exactly `count` elements (a
+    converted copy would receive the result instead of the caller's array)."""
+    if a is None:
+        return
+    _need(a, count, what)
+    if isinstance(a, np.ndarray):
+        ok = a.dtype == np.float32 and a.flags["C_CONTIGUOUS"] and a.flags["WRITEABLE"]
+    else:
+        import torch
+        ok = a.dtype == torch.float32 and a.is_contiguous()
+    if not ok:
+        raise OctenError(1, f"{what}: must be a contiguous, writable float32 array")
+
+
 def _f32(a, keep: list):
     if a is None:
         return None
@@ -208,6 +239,14 @@ class Octen:
         the GPU by CP-ALS of X_old from the starting guesses A0, B0."""
         keep: list = []
         t_old = int(X_old.shape[0])
+        I, J, R, Qd = self.I, self.J, self.R, self.Qd
+        _need(X_old, t_old * I * J, "X_old")
+        _need(U_all, I * Qd, "U_all")
+        _need(V_all, J * Qd, "V_all")
+        _need(W_old, t_old * Qd, "W_old")
+        _need(A0, I * R, "A0")
+        _need(B0, J * R, "B0")
+        _need(C0, t_old * R, "C0", required=False)
         self._check(self._lib.octen_init(
             self._h, _slices(X_old, self.prec, keep), t_old, _f32(U_all, keep),
             _f32(V_all, keep), _f32(W_old, keep), _f32(A0, keep), _f32(B0, keep),
@@ -215,6 +254,9 @@ class Octen:
 
     def append(self, X_new, W_new):
         keep: list = []
+        t = int(X_new.shape[0])
+        _need(X_new, t * self.I * self.J, "X_new")
+        _need(W_new, t * self.Qd, "W_new")
         self._check(self._lib.octen_append(self._h, _slices(X_new, self.prec, keep),
                                            int(X_new.shape[0]), _f32(W_new, keep)))
 
@@ -239,6 +281,9 @@ class Octen:
     def factors_into(self, A, B, C):
         """Copy the factors into caller buffers (torch device tensors allowed)."""
         keep: list = []
+        _out(A, self.I * self.R, "A")
+        _out(B, self.J * self.R, "B")
+        _out(C, self.rows * self.R, "C")
         k = ctypes.c_int64()
         self._check(self._lib.octen_get_factors(self._h, _ptr(A, keep), _ptr(B, keep),
                                                 _ptr(C, keep), ctypes.byref(k)))
@@ -247,6 +292,7 @@ class Octen:
     def fit(self, X_all) -> float:
         keep: list = []
         out = ctypes.c_double()
+        _need(X_all, int(X_all.shape[0]) * self.I * self.J, "X_all")
         self._check(self._lib.octen_fit(self._h, _slices(X_all, self.prec, keep),
                                         int(X_all.shape[0]), ctypes.byref(out)))
         return float(out.value)
@@ -344,11 +390,26 @@ class OctenN:
         if st != 0:
             raise OctenError(st, self._lib.octen_n_last_error(self._h).decode())
 
+    @property
+    def _slice(self) -> int:
+        """Elements of one slice (I_1 x ... x I_{N-1})."""
+        return int(np.prod(self.dims, dtype=np.int64))
+
     def _ptrs(self, arrays, keep):
         return (ctypes.c_void_p * len(arrays))(*[_f32(a, keep) for a in arrays])
 
     def init(self, X_old, Us, W_old, A0s, C0):
         keep: list = []
+        t_old = int(X_old.shape[0])
+        nm = self.N - 1
+        if len(Us) != nm or len(A0s) != nm:
+            raise OctenError(1, f"{nm} projections and {nm} factors expected")
+        _need(X_old, t_old * self._slice, "X_old")
+        for n in range(nm):
+            _need(Us[n], self.dims[n] * self.Qd, f"U_all[{n}]")
+            _need(A0s[n], self.dims[n] * self.R, f"A0[{n}]")
+        _need(W_old, t_old * self.Qd, "W_old")
+        _need(C0, t_old * self.R, "C0", required=False)
         us = self._ptrs(Us, keep)
         a0 = self._ptrs(A0s, keep)
         keep += [us, a0]
@@ -357,6 +418,9 @@ class OctenN:
 
     def append(self, X_new, W_new):
         keep: list = []
+        t = int(X_new.shape[0])
+        _need(X_new, t * self._slice, "X_new")
+        _need(W_new, t * self.Qd, "W_new")
         self._check(self._lib.octen_n_append(self._h, _f32(X_new, keep), int(X_new.shape[0]),
                                              _f32(W_new, keep)))
 
@@ -406,6 +470,7 @@ class OctenN:
         """Fitness of the current factors on all slices so far (octen_n_fit)."""
         keep: list = []
         out = ctypes.c_double()
+        _need(X_all, int(X_all.shape[0]) * self._slice, "X_all")
         self._check(self._lib.octen_n_fit(self._h, _f32(X_all, keep), int(X_all.shape[0]),
                                           ctypes.byref(out)))
         return float(out.value)
@@ -454,6 +519,12 @@ def append_many(streams, batches, ws):
     L = lib()
     keep: list = []
     n = len(streams)
+    if len(batches) != n or len(ws) != n:
+        raise OctenError(1, "one batch and one W_new per stream expected")
+    for i, (g, x, w) in enumerate(zip(streams, batches, ws)):
+        t = int(x.shape[0])
+        _need(x, t * g.I * g.J, f"X_new[{i}]")
+        _need(w, t * g.Qd, f"W_new[{i}]")
     hs = (ctypes.c_void_p * n)(*[s._h.value for s in streams])
     xs = (ctypes.c_void_p * n)(*[_slices(x, s.prec, keep) for x, s in zip(batches, streams)])
     ts = (ctypes.c_int64 * n)(*[int(x.shape[0]) for x in batches])
@@ -469,6 +540,11 @@ def compress(I, J, P, Q, S, X, U_all, V_all, W_all, prec="fp32", R=1, stream=Non
     L = lib()
     cfg = _Config(int(I), int(J), int(R), int(P), int(Q), int(S), 1, PREC[prec])
     keep: list = []
+    t, Qd = int(X.shape[0]), S + P * (Q - S)
+    _need(X, t * I * J, "X")
+    _need(U_all, I * Qd, "U_all")
+    _need(V_all, J * Qd, "V_all")
+    _need(W_all, t * Qd, "W_all")
     Z = np.empty((P, Q, Q, Q), np.float32)
     st = L.octen_compress(ctypes.byref(cfg), _stream_handle(stream), _slices(X, prec, keep),
                           int(X.shape[0]), _f32(U_all, keep), _f32(V_all, keep),
