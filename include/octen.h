@@ -133,7 +133,9 @@ int64_t octen_rows(const octen_ctx *ctx);
 
 /* Fitness of the current factors on K slices X_all (K x I x J, element type
  * as in octen_init): 1 - ||X - [[A, B, C]]||_F / ||X||_F (Sec. "Evaluation
- * Measures", as a fraction), with fp64 reductions.  K must equal octen_rows(). */
+ * Measures", as a fraction), with fp64 reductions.  K must equal octen_rows();
+ * I <= 65535 * 32 (EINVAL otherwise).  Slices are reduced in chunks of at most
+ * 65535 (16 when X_all is host memory, each chunk staged on the stream). */
 octen_status octen_fit(octen_ctx *ctx, const void *X_all, int64_t K, double *fit_out);
 
 /* Copies the current summaries Y_p (P x Q x Q x Q, [p][a][b][c]) out. */

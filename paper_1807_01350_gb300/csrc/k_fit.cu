@@ -91,6 +91,8 @@ __global__ void fit_reduce_kernel(const double *__restrict__ partial, int64_t n,
   }
 }
 
+int64_t fit_rows_max() { return (int64_t)65535 * kFitRows; }
+
 int64_t fit_partial_count(int64_t K, int64_t I, int64_t J) {
   return ((J + kFitCols - 1) / kFitCols) * ((I + kFitRows - 1) / kFitRows) * K;
 }

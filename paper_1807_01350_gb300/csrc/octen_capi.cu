@@ -820,16 +820,20 @@ int64_t octen_rows(const octen_ctx *x) { return x ? x->K : 0; }
 octen_status octen_fit(octen_ctx *x, const void *X_all, int64_t K, double *fit_out) {
   if (!x || !X_all || !fit_out) return OCTEN_EINVAL;
   if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_fit before octen_init");
-  if (K != x->K || K > 65535) return x->fail(OCTEN_EINVAL, "octen_fit: K=%lld, rows=%lld",
-                                             (long long)K, (long long)x->K);
+  if (K != x->K) return x->fail(OCTEN_EINVAL, "octen_fit: K=%lld, rows=%lld",
+                                (long long)K, (long long)x->K);
   const octen_config &c = x->cfg;
+  if (c.I > fit_rows_max())
+    return x->fail(OCTEN_EINVAL, "octen_fit: I=%lld above %lld", (long long)c.I,
+                   (long long)fit_rows_max());
   const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
   const int64_t np = fit_partial_count(1, c.I, c.J);
-  if (!x->grow(x->fitpart, (size_t)np * K * 2 * sizeof(double)))
+  // slices are streamed in chunks (host inputs are staged chunk by chunk;
+  // device inputs in chunks of at most kFitSlicesMax)
+  const int64_t chunk = is_device_ptr(X_all) ? (K < kFitSlicesMax ? K : kFitSlicesMax) : 16;
+  if (!x->grow(x->fitpart, (size_t)np * chunk * 2 * sizeof(double)))
     return x->fail(OCTEN_ENOMEM, "fit scratch");
   double total0 = 0.0, total1 = 0.0;
-  // slices are streamed in chunks (host inputs are staged chunk by chunk)
-  const int64_t chunk = is_device_ptr(X_all) ? K : 16;
   for (int64_t k0 = 0; k0 < K; k0 += chunk) {
     const int64_t n = K - k0 < chunk ? K - k0 : chunk;
     const void *Xd = x->stage_in(static_cast<const char *>(X_all) + k0 * slice, n * slice, 3);

@@ -325,6 +325,10 @@ void fit_sums(const void *X, Elem tx, int64_t K, int64_t I, int64_t J, const flo
               const float *B, const float *C, int R, double *partial, double *out,
               cudaStream_t st);
 int64_t fit_partial_count(int64_t K, int64_t I, int64_t J);
+// Largest K and I one fit_sums / n_fit_sums call takes (grid limits: slices
+// and row tiles are grid dimensions of at most 65535 blocks).
+constexpr int64_t kFitSlicesMax = 65535;
+int64_t fit_rows_max();
 
 }  // namespace octen
 

@@ -578,11 +578,13 @@ octen_status octen_n_load(const char *path, void *cuda_stream, octen_nctx **out)
 octen_status octen_n_fit(octen_nctx *x, const float *X_all, int64_t K, double *fit_out) {
   if (!x || !X_all || !fit_out) return OCTEN_EINVAL;
   if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_n_fit before octen_n_init");
-  if (K != x->K || K > 65535)
+  if (K != x->K)
     return x->fail(OCTEN_EINVAL, "octen_n_fit: K=%lld, rows=%lld", (long long)K, (long long)x->K);
   const int nb = n_fit_blocks(x->slice);
   const bool dev = is_device_pointer(X_all);
-  const int64_t chunk = dev ? K : 16;   // host slices are staged chunk by chunk
+  // host slices are staged chunk by chunk; device slices are taken in chunks
+  // of at most kFitSlicesMax
+  const int64_t chunk = dev ? (K < kFitSlicesMax ? K : kFitSlicesMax) : 16;
   double *part = nullptr;
   if (cudaMalloc(&part, (size_t)chunk * nb * 2 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
