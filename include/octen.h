@@ -62,7 +62,8 @@ typedef enum { OCTEN_FP32 = 0, OCTEN_BF16 = 1, OCTEN_FP8E4M3 = 2 } octen_prec;
 
 /* Shape of one online decomposition (Algorithm 1's REQUIRE line: R, p, Q,
  * shared S; plus the fixed CP-ALS sweep count).  Limits: 1 <= R <= 32,
- * 1 <= S < Q <= 256, P >= 1, I, J >= 1, als_iters >= 1. */
+ * 1 <= S < Q <= 256, 1 <= P <= 65535, 1 <= I, J <= 2^24,
+ * Qd = S + P (Q - S) <= 2^20, als_iters >= 1. */
 typedef struct {
   int64_t I, J;
   int32_t R, P, Q, S;
@@ -86,8 +87,9 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
  * X_old[k][i][j] = sum_r A[i][r] B[j][r] C[k][r]) from the starting guesses A0,
  * B0, with the same sweeps as the replica CP (als_iters sweeps: C, A, B, A and
  * B normalised to unit l2, a final C update); it needs a workspace of about
- * 4 t_old (I + J) R bytes.  The other arrays are required.  May be called once
- * per context (ESTATE otherwise). */
+ * 4 t_old (I + J) R bytes and takes t_old <= 65535, t_old I < 2^31 (EINVAL
+ * otherwise).  The other arrays are required.  May be called once per context
+ * (ESTATE otherwise). */
 octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
                         const float *U_all, const float *V_all, const float *W_old,
                         const float *A0, const float *B0, const float *C0);
@@ -95,7 +97,8 @@ octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
 /* One pass of Algorithm 1's loop for a batch of t >= 1 new slices X_new
  * (t x I x J, element type as in octen_init) with time projections W_new
  * (t x Qd): Y_p += Z_p, CP-ALS of every replica warm-started from U_p^T A,
- * V_p^T B, anchor matching, lift of A and B, t new rows of C.  Limit t <= 64.
+ * V_p^T B, anchor matching, lift of A and B, t new rows of C.  Limit
+ * t <= min(64, 65535 / P) (one mode-1 product per slice and replica).
  * The CP-ALS of the replicas is recorded once as a CUDA graph (on a private
  * stream, at the second append made with the stage timers off) and replayed on
  * the context's stream at every later such append; environment variable
@@ -253,8 +256,9 @@ typedef struct octen_nctx octen_nctx;
 
 #define OCTEN_MAX_MODES 6
 
-/* Limits: 3 <= N <= OCTEN_MAX_MODES, 1 <= R <= 32, 1 <= S < Q <= 256, P >= 1,
- * als_iters >= 1, 1 <= dims[n] <= 2^24 for n < N - 1 (later entries ignored),
+/* Limits: 3 <= N <= OCTEN_MAX_MODES, 1 <= R <= 32, 1 <= S < Q <= 256,
+ * 1 <= P <= 65535, als_iters >= 1, 1 <= dims[n] <= 2^24 for n < N - 1 (later
+ * entries ignored),
  * Q^N <= 2^24 and P Q^N <= 2^28, and the replica CP state of one summary must
  * fit one thread block's shared memory (N Q R-ish floats; X_p itself is read
  * from global memory when it does not fit). */

@@ -249,11 +249,12 @@ namespace {
 octen_status validate(const octen_config *c, std::string &why) {
   char buf[256];
   if (!c) { why = "config is NULL"; return OCTEN_EINVAL; }
-  if (c->I < 1 || c->J < 1 || c->R < 1 || c->R > 32 || c->P < 1 || c->Q < 2 || c->Q > 256 ||
-      c->S < 1 || c->S >= c->Q || c->als_iters < 1 || c->prec < 0 || c->prec > 2) {
+  if (c->I < 1 || c->J < 1 || c->R < 1 || c->R > 32 || c->P < 1 || c->P > kGridYZMax ||
+      c->Q < 2 || c->Q > 256 || c->S < 1 || c->S >= c->Q || c->als_iters < 1 || c->prec < 0 ||
+      c->prec > 2) {
     snprintf(buf, sizeof buf,
              "unsupported config I=%lld J=%lld R=%d P=%d Q=%d S=%d iters=%d prec=%d (limits: "
-             "1<=R<=32, 1<=S<Q<=256, P>=1, iters>=1)",
+             "1<=R<=32, 1<=S<Q<=256, 1<=P<=65535, iters>=1)",
              (long long)c->I, (long long)c->J, c->R, c->P, c->Q, c->S, c->als_iters, c->prec);
     why = buf;
     return OCTEN_EINVAL;
@@ -288,6 +289,14 @@ void set_types(octen_ctx *x) {
 }
 
 constexpr int64_t kChunk = 64;  // slices per compression pass
+
+// Slices per compression pass for this context: kChunk, fewer when the
+// batched mode-1 contraction (one product per slice and replica, the batch a
+// grid dimension) would exceed kGridYZMax products.
+int64_t chunk_slices(const octen_ctx *x) {
+  const int64_t m = kGridYZMax / x->cfg.P;
+  return m < kChunk ? m : kChunk;
+}
 
 // Scratch of one compression pass of t slices.
 octen_status compress_scratch(octen_ctx *x, int64_t t) {
@@ -355,7 +364,7 @@ void compress_finish(octen_ctx *x, int64_t t, const float *Wd, float *Yacc, bool
   x->mark(kStMode3, 0);
 }
 
-// Z_p (+)= compression of t slices (t <= kChunk, device) into Yacc.
+// Z_p (+)= compression of t slices (t <= chunk_slices(x), device) into Yacc.
 octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float *Wd,
                             float *Yacc, bool layouts = false) {
   octen_status s = compress_scratch(x, t);
@@ -404,8 +413,9 @@ octen_status compress_chunk_host(octen_ctx *x, const void *Xh, int64_t t, const 
 
 octen_status compress_all(octen_ctx *x, const void *Xd, int64_t t, const float *Wd, float *Yacc) {
   const size_t slice = (size_t)x->cfg.I * x->cfg.J * elem_size(x->xin);
-  for (int64_t k0 = 0; k0 < t; k0 += kChunk) {
-    const int64_t n = t - k0 < kChunk ? t - k0 : kChunk;
+  const int64_t ck = chunk_slices(x);
+  for (int64_t k0 = 0; k0 < t; k0 += ck) {
+    const int64_t n = t - k0 < ck ? t - k0 : ck;
     octen_status s = compress_chunk(x, static_cast<const char *>(Xd) + k0 * slice, n,
                                     Wd + k0 * x->Qd, Yacc);
     if (s != OCTEN_OK) return s;
@@ -564,6 +574,13 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
                    "octen_init: X_old, U_all, V_all, W_old, A0, B0 are required and t_old >= 1");
   const bool decompose = C0 == nullptr;   // A0, B0 are starting guesses
   const octen_config &c = x->cfg;
+  // the decomposition's per-slice products are a grid dimension, and its
+  // (slice, row) GEMM has t_old * I rows
+  if (decompose && (t_old > kGridYZMax || t_old * c.I > INT32_MAX))
+    return x->fail(OCTEN_EINVAL,
+                   "octen_init: decomposing X_old takes t_old <= %lld and t_old * I < 2^31 "
+                   "(t_old=%lld, I=%lld)",
+                   (long long)kGridYZMax, (long long)t_old, (long long)c.I);
   const int Qd = x->Qd;
   // projections: round once to the operand formats, build the operand layouts
   const float *Ud = static_cast<const float *>(x->stage_in(U_all, (size_t)c.I * Qd * 4, 0));
@@ -584,8 +601,9 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
     s = compress_all(x, X_old, t_old, Wd, x->Y);
     if (s != OCTEN_OK) return s;
   } else {
-    for (int64_t k0 = 0; k0 < t_old; k0 += kChunk) {
-      const int64_t n = t_old - k0 < kChunk ? t_old - k0 : kChunk;
+    const int64_t ck = chunk_slices(x);
+    for (int64_t k0 = 0; k0 < t_old; k0 += ck) {
+      const int64_t n = t_old - k0 < ck ? t_old - k0 : ck;
       const void *Xd = x->stage_in(static_cast<const char *>(X_old) + k0 * slice, n * slice, 2);
       if (!Xd) return x->fail(OCTEN_ENOMEM, "staging X_old");
       s = compress_chunk(x, Xd, n, Wd + k0 * Qd, x->Y);
@@ -674,8 +692,9 @@ void capture_als(octen_ctx *x, AlsBuffers ab) {
 octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
   if (!x) return OCTEN_EINVAL;
   if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_append before octen_init");
-  if (!X_new || !W_new || t < 1 || t > kChunk)
-    return x->fail(OCTEN_EINVAL, "octen_append: need X_new, W_new and 1 <= t <= %d", (int)kChunk);
+  if (!X_new || !W_new || t < 1 || t > chunk_slices(x))
+    return x->fail(OCTEN_EINVAL, "octen_append: need X_new, W_new and 1 <= t <= %d",
+                   (int)chunk_slices(x));
   const octen_config &c = x->cfg;
   const int Qd = x->Qd, RT = x->RT;
   if (!ensure_c_capacity(x, x->K + t)) return x->fail(OCTEN_ENOMEM, "C");
@@ -1026,8 +1045,9 @@ octen_status octen_compress(const octen_config *cfg, void *cuda_stream, const vo
   if (is_device_ptr(X)) {
     s = compress_all(&x, X, t, Wd, Zd);
   } else {
-    for (int64_t k0 = 0; k0 < t && s == OCTEN_OK; k0 += kChunk) {
-      const int64_t n = t - k0 < kChunk ? t - k0 : kChunk;
+    const int64_t ck = chunk_slices(&x);
+    for (int64_t k0 = 0; k0 < t && s == OCTEN_OK; k0 += ck) {
+      const int64_t n = t - k0 < ck ? t - k0 : ck;
       const void *Xd = x.stage_in(static_cast<const char *>(X) + k0 * slice, n * slice, 2);
       if (!Xd) return OCTEN_ENOMEM;
       s = compress_chunk(&x, Xd, n, Wd + k0 * Qd, Zd);

@@ -325,9 +325,12 @@ void fit_sums(const void *X, Elem tx, int64_t K, int64_t I, int64_t J, const flo
               const float *B, const float *C, int R, double *partial, double *out,
               cudaStream_t st);
 int64_t fit_partial_count(int64_t K, int64_t I, int64_t J);
+// Largest y or z extent of a launch grid.
+constexpr int64_t kGridYZMax = 65535;
+
 // Largest K and I one fit_sums / n_fit_sums call takes (grid limits: slices
-// and row tiles are grid dimensions of at most 65535 blocks).
-constexpr int64_t kFitSlicesMax = 65535;
+// and row tiles are grid dimensions of at most kGridYZMax blocks).
+constexpr int64_t kFitSlicesMax = kGridYZMax;
 int64_t fit_rows_max();
 
 }  // namespace octen

@@ -211,11 +211,12 @@ namespace {
 octen_status nvalidate(const octen_nconfig *c, std::string &why) {
   char buf[320];
   if (!c) { why = "config is NULL"; return OCTEN_EINVAL; }
-  if (c->N < 3 || c->N > kMaxNModes || c->R < 1 || c->R > 32 || c->P < 1 || c->Q < 2 ||
-      c->Q > 256 || c->S < 1 || c->S >= c->Q || c->als_iters < 1) {
+  if (c->N < 3 || c->N > kMaxNModes || c->R < 1 || c->R > 32 || c->P < 1 ||
+      c->P > kGridYZMax || c->Q < 2 || c->Q > 256 || c->S < 1 || c->S >= c->Q ||
+      c->als_iters < 1) {
     snprintf(buf, sizeof buf,
              "unsupported config N=%d R=%d P=%d Q=%d S=%d iters=%d (limits: 3<=N<=%d, "
-             "1<=R<=32, 1<=S<Q<=256, P>=1, iters>=1)",
+             "1<=R<=32, 1<=S<Q<=256, 1<=P<=65535, iters>=1)",
              c->N, c->R, c->P, c->Q, c->S, c->als_iters, kMaxNModes);
     why = buf;
     return OCTEN_EINVAL;

@@ -114,3 +114,16 @@ def test_nmode_load_rejects_bad_checkpoint_headers_before_touching_the_device(bu
         assert L.octen_n_load(_checkpoint(tmp_path, name, magic, cfg, hdr), None,
                               ctypes.byref(h)) == 1, name
     assert not h.value
+
+
+def test_create_rejects_replica_counts_beyond_the_launch_grid(built):
+    # P is a grid dimension of the replica kernels (at most 65535 blocks)
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    cfg = pkg._Config(1000, 1000, 2, 65536, 3, 2, 5, 0)
+    assert L.octen_create(ctypes.byref(cfg), None, ctypes.byref(h)) == 1
+    assert not h.value
+    d = (ctypes.c_int64 * (pkg.MAX_MODES - 1))(10, 10, 0, 0, 0)
+    ncfg = pkg._NConfig(3, 2, 65536, 2, 1, 5, d)
+    assert L.octen_n_create(ctypes.byref(ncfg), None, ctypes.byref(h)) == 1
+    assert not h.value
