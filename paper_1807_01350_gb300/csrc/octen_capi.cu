@@ -522,8 +522,10 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     const int want = (4 * 152 + mt * c.P - 1) / (mt * c.P);
     x->als_ks = als_tc_splits(c.P, c.Q, want < 1 ? 1 : want);
     const size_t nparts = (size_t)(x->als_ks > (c.Q / 32) ? x->als_ks : (c.Q / 32));
+    // the Khatri-Rao operand of the M3 pass exists only below Q = 32 (from 32
+    // on, the M3 GEMM contracts b against B^T and reduces a in its epilogue)
     ok = x->alloc(x->Xa, P * Q * Q * Q) && x->alloc(x->Xc, P * Q * Q * Q) &&
-         x->alloc(x->KR, P * kAlsNP * Q * Q) && x->alloc(x->Ctb, P * kAlsNP * Q) &&
+         (c.Q >= 32 || x->alloc(x->KR, P * kAlsNP * Q * Q)) && x->alloc(x->Ctb, P * kAlsNP * Q) &&
          x->alloc(x->Btb, P * kAlsNP * Q) &&
          x->alloc(x->Mparts, std::max(nparts * Q, 2 * ((Q * Q + 31) / 32)) * P * RT);
     x->als_tc = ok;
