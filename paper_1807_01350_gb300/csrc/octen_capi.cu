@@ -943,7 +943,7 @@ octen_status octen_load(const char *path, void *cuda_stream, octen_ctx **out) {
     return s;
   }
   // the lift operators' layouts follow from the shapes (Qd above or below
-  // the factor's rows); a header that disagrees is not this build's file
+  // the factor's rows); a header that disagrees was not written by octen_save
   if (hdr[1] != (x->Qd > cfg.I ? 1 : 0) || hdr[2] != (x->Qd > cfg.J ? 1 : 0)) {
     fclose(f);
     delete x;
