@@ -228,6 +228,34 @@ def test_align_greedy_matches_bruteforce_on_separated_columns():
         assert np.array_equal(p, np.array(best)), trial
 
 
+def test_align_ties_and_degenerate_scales_follow_the_reading():
+    # Orthonormal anchor references; replica column r points at reference
+    # column sigma(r), with two replica columns on the same reference column:
+    # sim[r, s] = 2 where sigma(r) = s, else 0.  The greedy rule (largest
+    # similarity, ties to the lowest s, then the lowest r) then gives, by hand:
+    # s = 0 <- r = 3, s = 1 <- r = 0 (r = 1 ties and loses), s = 3 <- r = 2,
+    # and the left-over s = 2 <- r = 1 at similarity 0.  Column 1's anchor block
+    # is orthogonal to reference column 2, so its least-squares scale is 0 and
+    # the column stays unscaled.
+    Q, S, R = 7, 4, 4
+    E = np.eye(S)
+    sigma = [1, 1, 3, 0]
+    At = np.zeros((Q, R))
+    Bt = np.zeros((Q, R))
+    for r, s in enumerate(sigma):
+        At[:S, r] = 2.0 * E[:, s]
+        Bt[:S, r] = -3.0 * E[:, s]
+    At[S:] = np.arange((Q - S) * R, dtype=float).reshape(Q - S, R)
+    Bt[S:] = 1.0
+    Ct = np.arange(3 * R, dtype=float).reshape(3, R) + 1.0
+    Ah, Bh, Ch, perm, d_a, d_b = oracle.align(At, Bt, Ct, E, E, S)
+    assert perm.tolist() == [3, 0, 1, 2]
+    assert d_a.tolist() == [2.0, 2.0, 1.0, 2.0]
+    assert d_b.tolist() == [-3.0, -3.0, 1.0, -3.0]
+    assert np.array_equal(Ah, At[:, perm] / d_a)
+    assert np.array_equal(Ch, Ct[:, perm] * (d_a * d_b))
+
+
 # ---------------------------------------------------------------- lifting
 def _lift_case(I, P, Q, S, R, seed):
     rng = np.random.default_rng(seed)
