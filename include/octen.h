@@ -171,9 +171,14 @@ octen_status octen_compress(const octen_config *cfg, void *cuda_stream, const vo
  *    (host buffers are rejected with OCTEN_EINVAL: staging them would
  *    allocate);
  *  - all scratch lives in one static device array of 64 MiB that every GPU
- *    loading the library holds until the process exits; slices are processed
- *    in chunks that fit it, and a shape whose projections alone do not fit is
- *    rejected with OCTEN_EINVAL and a message on stderr;
+ *    loading the library holds until the process exits: the transposed
+ *    projections (P*Q*I + Qd*J operand elements) plus, per slice of a pass,
+ *    its mode-2 and mode-1 products (P*Q*I operand elements and P*Q*Q fp32;
+ *    in fp8 mode also the I*J e4m3 slice and its scale).  Slices are processed
+ *    in passes that fit (at most 64 slices and at most 65535 / P per pass); a
+ *    shape is rejected with OCTEN_EINVAL and a message on stderr when its
+ *    projections plus the scratch of one slice exceed 64 MiB, and so is a
+ *    configuration outside octen_create's limits;
  *  - the first call on a device looks up the array's address on that device
  *    (cudaGetSymbolAddress) and caches it: make that first call before any
  *    stream capture;

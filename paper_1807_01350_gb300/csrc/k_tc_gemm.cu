@@ -86,7 +86,8 @@ __device__ __forceinline__ void tma_load_2d_policy(void *dst, const CUtensorMap 
       : "memory");
 }
 
-// L2 policy that evicts the lines it brings in first (operands read once).
+// L2 policy that keeps the lines it touches in the L2 as long as it can (an
+// output that the next kernel reads again).
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));

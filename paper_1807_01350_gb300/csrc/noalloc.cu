@@ -66,10 +66,12 @@ extern "C" octen_status octen_compress_noalloc(const octen_config *cfg, void *cu
                                                const float *V_all, const float *W_all,
                                                float *Z) {
   if (!cfg || !X || !U_all || !V_all || !W_all || !Z || t < 1) return OCTEN_EINVAL;
-  const octen_config &c = *cfg;
-  if (c.I < 1 || c.J < 1 || c.P < 1 || c.Q < 2 || c.Q > 256 || c.S < 1 || c.S >= c.Q ||
-      c.prec < 0 || c.prec > 2)
+  std::string why;
+  if (validate_config(cfg, why) != OCTEN_OK) {
+    fprintf(stderr, "octen_compress_noalloc: %s\n", why.c_str());
     return OCTEN_EINVAL;
+  }
+  const octen_config &c = *cfg;
   const int Qd = c.S + c.P * (c.Q - c.S);
   const Elem tx = c.prec == OCTEN_FP32 ? Elem::F32 : Elem::BF16;
   const Elem tu = c.prec == OCTEN_FP32 ? Elem::F32 : Elem::BF16;
@@ -86,17 +88,20 @@ extern "C" octen_status octen_compress_noalloc(const octen_config *cfg, void *cu
   const size_t per_slice_T2 = (size_t)c.P * c.Q * c.Q * sizeof(float);
   const size_t per_slice_X8 = fp8 ? (size_t)c.I * c.J : 0;
   const size_t per_slice = per_slice_T + per_slice_T2 + per_slice_X8 + (fp8 ? 4 : 0);
+  // slices per pass: as many as the scratch holds, at most kMaxChunk, and at
+  // most kGridYZMax / P (the batched mode-1 product has one GEMM per slice
+  // and replica on a grid dimension)
+  constexpr size_t kSlack = 4 * 256;   // alignment of the four per-pass buffers
   int64_t chunk = 0;
-  if (fixed < kNoAllocScratchBytes) {
-    const size_t room = kNoAllocScratchBytes - fixed - 4 * 256;   // alignment slack
-    chunk = (int64_t)(room / per_slice);
-  }
+  if (fixed + kSlack < kNoAllocScratchBytes)
+    chunk = (int64_t)((kNoAllocScratchBytes - fixed - kSlack) / per_slice);
   if (chunk > kMaxChunk) chunk = kMaxChunk;
+  if (chunk > kGridYZMax / c.P) chunk = kGridYZMax / c.P;
   if (chunk > t) chunk = t;
   if (chunk < 1) {
     fprintf(stderr,
             "octen_compress_noalloc: shape needs %zu bytes of scratch for the projections plus "
-            "%zu per slice; the static scratch holds %zu bytes (use octen_compress)\n",
+            "%zu for one slice; the static scratch holds %zu bytes (use octen_compress)\n",
             fixed, per_slice, kNoAllocScratchBytes);
     return OCTEN_EINVAL;
   }
@@ -160,6 +165,12 @@ extern "C" octen_status octen_compress_noalloc(const octen_config *cfg, void *cu
   if (cudaMemcpyAsync(&flags, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
+    return OCTEN_ECUDA;
+  }
+  // a launch refused above (a grid or resource limit) leaves Z incomplete
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "octen_compress_noalloc: %s\n", cudaGetErrorString(e));
     return OCTEN_ECUDA;
   }
   if (flags & kDevTimeout) return OCTEN_ETIMEOUT;

@@ -244,9 +244,9 @@ struct octen_ctx {
   }
 };
 
-namespace {
+namespace octen {
 
-octen_status validate(const octen_config *c, std::string &why) {
+octen_status validate_config(const octen_config *c, std::string &why) {
   char buf[256];
   if (!c) { why = "config is NULL"; return OCTEN_EINVAL; }
   if (c->I < 1 || c->J < 1 || c->R < 1 || c->R > 32 || c->P < 1 || c->P > kGridYZMax ||
@@ -266,6 +266,10 @@ octen_status validate(const octen_config *c, std::string &why) {
   }
   return OCTEN_OK;
 }
+
+}  // namespace octen
+
+namespace {
 
 // OCTEN_GEMM=simt keeps the large contractions on the SIMT kernels (used to
 // cross-check the tensor-core kernels against an independent implementation).
@@ -489,7 +493,7 @@ extern "C" {
 octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx **out) {
   if (!out) return OCTEN_EINVAL;
   std::string why;
-  octen_status s = validate(cfg, why);
+  octen_status s = validate_config(cfg, why);
   if (s != OCTEN_OK) {
     fprintf(stderr, "octen_create: %s\n", why.c_str());
     return s;
@@ -1005,7 +1009,7 @@ octen_status octen_compress(const octen_config *cfg, void *cuda_stream, const vo
                             const float *U_all, const float *V_all, const float *W_all,
                             float *Z) {
   std::string why;
-  if (validate(cfg, why) != OCTEN_OK || !X || !U_all || !V_all || !W_all || !Z || t < 1)
+  if (validate_config(cfg, why) != OCTEN_OK || !X || !U_all || !V_all || !W_all || !Z || t < 1)
     return OCTEN_EINVAL;
   // a light context: projections, scratch and a summary buffer only
   octen_ctx x;

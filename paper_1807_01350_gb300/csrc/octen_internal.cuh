@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <string>
 
 #include "../../include/octen.h"
 
@@ -318,6 +319,10 @@ void n_fit_sums(const float *X, int64_t nk, const float *const *A, const float *
 
 // true for device (or managed) memory
 bool is_device_pointer(const void *p);
+
+// Shape and precision limits of a 3-mode configuration (the limits octen_create
+// states); EINVAL with the reason in `why`.
+octen_status validate_config(const octen_config *c, std::string &why);
 
 // Fit: sums of ||X_k||^2 and ||X_k - A diag(C[k]) B^T||^2 over all slices,
 // written to out[0], out[1] (fp64).  partial: ceil(J/256)*ceil(I/32)*K*2 doubles.

@@ -118,3 +118,43 @@ def test_clock_record_without_samples_says_so():
     finally:
         os.remove(path)
     assert s["reasons"] == ["unsampled"] and s["sm_mhz"] is None
+
+
+def test_mode3_is_charged_the_method_bytes_with_the_copies_beside():
+    wl = WORKLOADS["c4"]
+    pk = dict(hbm=6690.8, bf16=1892.4, bf16_sus=1718.1, src="measured")
+    tcs = ("mode2", "mode1", "als_gemm")
+    r = bench.roofline_for("mode3", 0.69, wl, "bf16", pk, None, tc_stages=tcs)
+    y = 16 * 256 ** 3 * 4
+    t2 = 16 * 16 * 256 * 256 * 4
+    # the scope table's bytes of the summary update: Y read and written, T2 read
+    assert r["achieved"] == pytest.approx((2 * y + t2) / 0.69e-3 / 1e9, rel=1e-3)
+    assert (2 * y + t2) / 1e9 == pytest.approx(2.22, abs=0.01)
+    assert r["copy_bytes"] == 2 * 16 * 256 ** 3 * 2
+    assert r["frac_incl_copies"] > r["frac"]
+    # without the tensor-core ALS there are no copies to report
+    r32 = bench.roofline_for("mode3", 0.69, wl, "fp32", pk, None, tc_stages=())
+    assert "copy_bytes" not in r32
+
+
+def test_compression_roofline_of_the_4000_squared_batch():
+    wl = WORKLOADS["c4"]
+    pk = dict(hbm=6690.8, bf16=1942.7, bf16_sus=1714.2, src="measured")
+    tcs = ("mode2", "mode1", "als_gemm")
+    comp = {s: {"ms_per_launch": ms} for s, ms in (("mode2", 1.27), ("mode1", 0.19),
+                                                    ("mode3", 0.69))}
+    c = bench.compression_at_roofline(wl, "bf16", pk, comp, tcs)
+    # flops per slice 2 I J Qd + 2 P Q^2 I + 2 P Q^3 = 1.25e11, 16 slices at the
+    # burst bf16 peak: the scope table's 1027 us per batch
+    assert c["flops_per_batch"] / 16 == pytest.approx(1.246e11, rel=1e-3)
+    assert c["flops_only_at_burst_peak_ms"] == pytest.approx(1.027, abs=0.002)
+    # per stage the slower bound: mode 2 at the sustained tensor peak; mode 1
+    # reads its 557 MB of mode-2 output slightly slower than it multiplies;
+    # mode 3 at the HBM bandwidth for its 2.22 GB
+    w = bench.stage_work(wl, "bf16")
+    assert w["mode1"][1] / 6690.8e9 > w["mode1"][0] / 1714.2e12
+    want = 1e3 * (w["mode2"][0] / 1714.2e12 + w["mode1"][1] / 6690.8e9 +
+                  w["mode3"][1] / 6690.8e9)
+    assert c["at_roofline_ms"] == pytest.approx(want, rel=1e-3)
+    assert c["measured_ms"] == pytest.approx(2.15)
+    assert c["frac"] == pytest.approx(want / 2.15, rel=1e-3)

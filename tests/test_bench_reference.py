@@ -5,6 +5,9 @@ import json
 import os
 import subprocess
 import sys
+import time
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CMD = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c1",
@@ -13,7 +16,10 @@ CMD = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "-
 
 def _run(env_extra):
     env = dict(os.environ, **env_extra)
-    return subprocess.run(CMD, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    t0 = time.perf_counter()
+    r = subprocess.run(CMD, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    r.wall = time.perf_counter() - t0
+    return r
 
 
 def test_reference_arm_prints_one_contract_line():
@@ -28,6 +34,13 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert cb["sample"]
+    # a step is one replica piece: the timed steps fit inside the run itself,
+    # and the sample says how many distinct replicas they covered
+    assert d["ms_per_step"] * d["steps"] / 1e3 <= r.wall
+    assert "2 distinct replicas" in cb["sample"]
+    P, t = d["config"]["P"], d["config"]["batch_slices"]
+    assert d["extrapolated_append_ms"] > P * d["ms_per_step"]
+    assert d["value"] == pytest.approx(t / (d["extrapolated_append_ms"] / 1e3), rel=1e-3)
     assert d["e2e"] == {"value": d["value"], "unit": "slices/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 

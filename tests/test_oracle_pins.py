@@ -438,6 +438,4 @@ def test_existing_decomposition_recovers_planted_factors():
     Ah, Bh, Ch = oracle.decompose_existing(X, A0, B0, 60)
     assert oracle.fit(X, Ah, Bh, Ch) > 1 - 1e-9
     assert fms((Ah, Bh, Ch), (A, B, C)) > 1 - 1e-9
-    # the mode order matters: the same guesses on the (k, i, j) order fail to
-    # fit, the shapes do not even agree
     assert Ah.shape == (I, R) and Bh.shape == (J, R) and Ch.shape == (K, R)
