@@ -74,7 +74,12 @@ typedef struct {
 /* Creates a context and allocates its device state (summaries P x Q^3 fp32,
  * factors, lift operators).  `cuda_stream` is a cudaStream_t or NULL for the
  * legacy default stream.  Returns EINVAL on limits above, ENOMEM on
- * allocation failure.  *out is set only on success. */
+ * allocation failure.  *out is set only on success.  If the environment
+ * variable OCTEN_DEVICE_MEMORY_LIMIT holds a byte count when the context is
+ * created, the context never holds more device memory than that (its state,
+ * its scratch and the init-time decomposition workspace; the lift operators'
+ * transient factorisation workspace at init is not counted): an allocation
+ * past the limit fails with ENOMEM like a refused cudaMalloc. */
 octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx **out);
 
 /* Existing summaries and decomposition (Sec. "Problem Formulation" (a)):
@@ -133,6 +138,11 @@ octen_status octen_get_factors(const octen_ctx *ctx, float *A, float *B, float *
 
 /* Number of rows of C so far. */
 int64_t octen_rows(const octen_ctx *ctx);
+
+/* Bytes of device memory the context holds now (state and scratch; the
+ * figure OCTEN_DEVICE_MEMORY_LIMIT is compared with).  Not in the paper: a
+ * read-out for callers that budget device memory.  0 for NULL. */
+uint64_t octen_device_bytes(const octen_ctx *ctx);
 
 /* Fitness of the current factors on K slices X_all (K x I x J, element type
  * as in octen_init): 1 - ||X - [[A, B, C]]||_F / ||X||_F (Sec. "Evaluation

@@ -68,6 +68,8 @@ def lib() -> ctypes.CDLL:
         L.octen_get_factors.argtypes = [vp, f32p, f32p, f32p, ctypes.POINTER(i64)]
         L.octen_rows.argtypes = [vp]
         L.octen_rows.restype = i64
+        L.octen_device_bytes.argtypes = [vp]
+        L.octen_device_bytes.restype = ctypes.c_uint64
         L.octen_fit.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
         L.octen_get_replicas.argtypes = [vp, f32p]
         L.octen_get_replica_factors.argtypes = [vp, ctypes.c_int, f32p, f32p, f32p, vp, vp]
@@ -267,6 +269,11 @@ class Octen:
     @property
     def rows(self) -> int:
         return int(self._lib.octen_rows(self._h))
+
+    @property
+    def device_bytes(self) -> int:
+        """Bytes of device memory the context holds (octen_device_bytes)."""
+        return int(self._lib.octen_device_bytes(self._h))
 
     def factors(self):
         K = self.rows

@@ -56,13 +56,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; false on timeout or when another role raised the abort flag.
+// Bounded wait; false after `budget` clock cycles or when another role raised
+// the abort flag.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
-                                          volatile int *abort_flag) {
+                                          volatile int *abort_flag, long long budget) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitBudget) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }
@@ -195,6 +196,8 @@ struct TcShape {
   int ksplit;           // > 1: blockIdx.x is the K split (a single N tile)
   int a_stream;         // A is read once: load it with an L2 evict-first policy
   int katoms;           // 128-byte K atoms per pipeline stage (1 or 2)
+  long long wait_budget;   // clock cycles a pipeline wait may take before the CTA
+                           // gives up (the drains after a give-up keep kWaitBudget)
 };
 
 // Plain store: D[split * s_split + z * s_z + m * s_m + n] (split-K partials), in
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(192, 1)
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = it % stages;
         const uint32_t ph = (it / stages) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, sh.wait_budget)) {
           *abort_flag = 1;
           atomicOr(status, kDevTimeout);
           aborted = true;
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(192, 1)
       int z, m0, n0, split, kb0, nk;
       decode(tile, z, m0, n0, split, kb0, nk);
       const uint32_t buf = local & 1u, use = local >> 1;
-      if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u, abort_flag)) {
+      if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u, abort_flag, sh.wait_budget)) {
         *abort_flag = 1;
         atomicOr(status, kDevTimeout);
         break;
@@ -441,7 +444,7 @@ __global__ void __launch_bounds__(192, 1)
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = it % stages;
         const uint32_t ph = (it / stages) & 1u;
-        if (!mbar_wait(&full[s], ph, abort_flag)) {
+        if (!mbar_wait(&full[s], ph, abort_flag, sh.wait_budget)) {
           *abort_flag = 1;
           atomicOr(status, kDevTimeout);
           aborted = true;
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(192, 1)
       int z, m0, n0, split, kb0, nk;
       decode(tile, z, m0, n0, split, kb0, nk);
       const uint32_t buf = local & 1u, use = local >> 1;
-      const bool ok = mbar_wait(&acc_full[buf], use & 1u, abort_flag);
+      const bool ok = mbar_wait(&acc_full[buf], use & 1u, abort_flag, sh.wait_budget);
       if (!__all_sync(0xffffffffu, ok && !*abort_flag)) {
         if (lane == 0) {
           *abort_flag = 1;
@@ -642,9 +645,24 @@ int sm_count() {
   return n;
 }
 
+// Clock budget of the pipeline waits: kWaitBudget (about 2 s), or the cycle
+// count in OCTEN_WAIT_BUDGET_CYCLES (between 1 and kWaitBudget), a debug setting
+// read at every launch with which a test makes the waits run out before their
+// data lands, so that the timeout path (abort, drain, status word) runs
+// without anything on the device hanging.
+long long wait_budget_cycles() {
+  const char *v = getenv("OCTEN_WAIT_BUDGET_CYCLES");
+  if (!v || !*v) return kWaitBudget;
+  char *end = nullptr;
+  const long long n = strtoll(v, &end, 10);
+  if (end == v || n < 1) return kWaitBudget;
+  return n < kWaitBudget ? n : kWaitBudget;
+}
+
 template <int KIND, class Epi>
 bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
                const Epi &epi, int *status, cudaStream_t st, int smem_reserve = 0) {
+  sh.wait_budget = wait_budget_cycles();
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
   if (sh.katoms != 2) sh.katoms = 1;   // kernels exist for 1 and 2 atoms per stage

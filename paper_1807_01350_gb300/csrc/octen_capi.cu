@@ -190,29 +190,51 @@ struct octen_ctx {
     return s;
   }
 
+  // Device memory the context holds (its state and scratch buffers), and the
+  // most it may hold: OCTEN_DEVICE_MEMORY_LIMIT bytes when that is set at
+  // create, else unbounded.  An allocation past the limit fails like a
+  // refused cudaMalloc (ENOMEM).
+  size_t held = 0;
+  size_t limit = SIZE_MAX;
+
+  bool dev_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes > limit || held > limit - bytes) return false;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    held += bytes;
+    return true;
+  }
+  void dev_free(void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    held -= bytes;
+  }
+
   template <class T>
   bool alloc(T *&ptr, size_t count) {
     void *p = nullptr;
-    if (cudaMalloc(&p, count * sizeof(T) + 16) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    owned.push_back({p, count * sizeof(T)});
+    if (!dev_malloc(&p, count * sizeof(T) + 16)) return false;
+    owned.push_back({p, count * sizeof(T) + 16});
     ptr = static_cast<T *>(p);
     return true;
   }
 
+  // Scratch of at least `bytes` in b; a refused allocation (device or limit)
+  // is detected before the smaller buffer is released.
   bool grow(DevBuf &b, size_t bytes) {
     if (b.bytes >= bytes) return true;
+    const size_t old = b.p ? b.bytes + 16 : 0;
+    const size_t want = bytes + 16;
+    if (want > limit || held - old > limit - want) return false;
     cudaStreamSynchronize(st);
-    cudaFree(b.p);
+    dev_free(b.p, old);
     b.p = nullptr;
     b.bytes = 0;
-    if (cudaMalloc(&b.p, bytes + 16) != cudaSuccess) {
-      cudaGetLastError();
-      b.p = nullptr;
-      return false;
-    }
+    if (!dev_malloc(&b.p, want)) return false;
     b.bytes = bytes;
     return true;
   }
@@ -270,6 +292,16 @@ octen_status validate_config(const octen_config *c, std::string &why) {
 }  // namespace octen
 
 namespace {
+
+// OCTEN_DEVICE_MEMORY_LIMIT: bytes of device memory a context created now may
+// hold (unset, empty or not a number: no limit).
+size_t device_memory_limit() {
+  const char *v = getenv("OCTEN_DEVICE_MEMORY_LIMIT");
+  if (!v || !*v) return SIZE_MAX;
+  char *end = nullptr;
+  const unsigned long long n = strtoull(v, &end, 10);
+  return end == v ? SIZE_MAX : (size_t)n;
+}
 
 // OCTEN_GEMM=simt keeps the large contractions on the SIMT kernels (used to
 // cross-check the tensor-core kernels against an independent implementation).
@@ -468,18 +500,16 @@ bool ensure_c_capacity(octen_ctx *x, int64_t rows) {
   int64_t cap = x->Kcap > 0 ? x->Kcap : 64;
   while (cap < rows) cap *= 2;
   float *nc = nullptr;
-  if (cudaMalloc(&nc, (size_t)cap * x->cfg.R * sizeof(float)) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
+  const size_t bytes = (size_t)cap * x->cfg.R * sizeof(float);
+  if (!x->dev_malloc(reinterpret_cast<void **>(&nc), bytes)) return false;
   if (x->C) {
     cudaMemcpyAsync(nc, x->C, (size_t)x->K * x->cfg.R * sizeof(float), cudaMemcpyDeviceToDevice,
                     x->st);
     cudaStreamSynchronize(x->st);
     for (auto &b : x->owned)
-      if (b.p == x->C) { cudaFree(b.p); b.p = nc; b.bytes = (size_t)cap * x->cfg.R * sizeof(float); }
+      if (b.p == x->C) { x->dev_free(b.p, b.bytes); b.p = nc; b.bytes = bytes; }
   } else {
-    x->owned.push_back({nc, (size_t)cap * x->cfg.R * sizeof(float)});
+    x->owned.push_back({nc, bytes});
   }
   x->C = nc;
   x->Kcap = cap;
@@ -499,6 +529,7 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     return s;
   }
   octen_ctx *x = new octen_ctx();
+  x->limit = device_memory_limit();
   x->cfg = *cfg;
   x->Qd = cfg->S + cfg->P * (cfg->Q - cfg->S);
   x->RT = round_rt(cfg->R);
@@ -536,10 +567,10 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
   }
   void *ut = nullptr, *vt = nullptr;
   if (ok) {
-    ok = cudaMalloc(&ut, P * Q * c.I * elem_size(x->tu)) == cudaSuccess &&
-         cudaMalloc(&vt, Qd * c.J * elem_size(x->tv)) == cudaSuccess;
-    if (ut) x->owned.push_back({ut, 0});
-    if (vt) x->owned.push_back({vt, 0});
+    const size_t ub = P * Q * c.I * elem_size(x->tu), vb = Qd * c.J * elem_size(x->tv);
+    ok = x->dev_malloc(&ut, ub) && x->dev_malloc(&vt, vb);
+    if (ut) x->owned.push_back({ut, ub});
+    if (vt) x->owned.push_back({vt, vb});
     x->Ut_rep = ut;
     x->Vt = vt;
   }
@@ -626,10 +657,8 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
     if (!Xd || !A0d || !B0d) return x->fail(OCTEN_ENOMEM, "staging X_old, A0, B0");
     float *work = nullptr;
     const size_t wf = dense_cp_work_floats(t_old, c.I, c.J, x->RT);
-    if (cudaMalloc(&work, wf * sizeof(float)) != cudaSuccess) {
-      cudaGetLastError();
+    if (!x->dev_malloc(reinterpret_cast<void **>(&work), wf * sizeof(float)))
       return x->fail(OCTEN_ENOMEM, "dense CP-ALS workspace (%zu bytes)", wf * sizeof(float));
-    }
     DenseCpArgs a{};
     a.X = Xd; a.xt = x->xin; a.K = t_old; a.I = c.I; a.J = c.J; a.R = c.R;
     a.iters = c.als_iters; a.A0 = A0d; a.B0 = B0d;
@@ -638,7 +667,7 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
     a.status = x->dstatus; a.st = x->st;
     dense_cp(a, x->RT);
     s = x->sync_check("init decomposition");
-    cudaFree(work);
+    x->dev_free(work, wf * sizeof(float));
     if (s != OCTEN_OK) return s;
   } else {
     cudaMemcpyAsync(x->A, A0, (size_t)c.I * c.R * 4, cudaMemcpyDefault, x->st);
@@ -842,6 +871,8 @@ octen_status octen_get_factors(const octen_ctx *cx, float *A, float *B, float *C
 
 int64_t octen_rows(const octen_ctx *x) { return x ? x->K : 0; }
 
+uint64_t octen_device_bytes(const octen_ctx *x) { return x ? (uint64_t)x->held : 0; }
+
 octen_status octen_fit(octen_ctx *x, const void *X_all, int64_t K, double *fit_out) {
   if (!x || !X_all || !fit_out) return OCTEN_EINVAL;
   if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_fit before octen_init");
@@ -1013,6 +1044,7 @@ octen_status octen_compress(const octen_config *cfg, void *cuda_stream, const vo
     return OCTEN_EINVAL;
   // a light context: projections, scratch and a summary buffer only
   octen_ctx x;
+  x.limit = device_memory_limit();
   x.cfg = *cfg;
   x.Qd = cfg->S + cfg->P * (cfg->Q - cfg->S);
   x.RT = round_rt(cfg->R);
@@ -1025,10 +1057,10 @@ octen_status octen_compress(const octen_config *cfg, void *cuda_stream, const vo
             x.alloc(x.dstatus, 1) && x.alloc(Zd, nz);
   void *ut = nullptr, *vt = nullptr;
   if (ok) {
-    ok = cudaMalloc(&ut, (size_t)c.P * c.Q * c.I * elem_size(x.tu)) == cudaSuccess &&
-         cudaMalloc(&vt, Qd * c.J * elem_size(x.tv)) == cudaSuccess;
-    if (ut) x.owned.push_back({ut, 0});
-    if (vt) x.owned.push_back({vt, 0});
+    const size_t ub = (size_t)c.P * c.Q * c.I * elem_size(x.tu), vb = Qd * c.J * elem_size(x.tv);
+    ok = x.dev_malloc(&ut, ub) && x.dev_malloc(&vt, vb);
+    if (ut) x.owned.push_back({ut, ub});
+    if (vt) x.owned.push_back({vt, vb});
   }
   if (!ok) { cudaGetLastError(); return OCTEN_ENOMEM; }
   x.Ut_rep = ut;
