@@ -683,6 +683,10 @@ def main_uneven(args):
     is one append on every stream through octen_append_many (all enqueued
     before any is waited for).  Compared with the same n updates in FP32, one
     after another (octen_append per stream)."""
+    # one hardware work queue per stream (the default of 8 queues would make
+    # the 64 streams share queues and wait on one another's launches); read
+    # when the CUDA context is created, so set before the first CUDA call
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
 
     from paper_1807_01350_gb300 import build as B

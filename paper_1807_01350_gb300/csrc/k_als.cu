@@ -176,22 +176,26 @@ __global__ void __launch_bounds__(256)
 //   Tc[(a,b)][r] = sum_c Xa[(a,b)][c] C[c][r]
 //   M1[a][r] = sum_b Tc[(a,b)][r] B[b][r],  M2[b][r] = sum_a Tc[(a,b)][r] A[a][r]
 // ---------------------------------------------------------------------------
-__global__ void bf16_layouts_kernel(const float *__restrict__ Y, int Q,
+// With Qp > Q the copies are those of X_p zero-padded to Qp x Qp x Qp (every
+// index in [0, Qp), zero where one is >= Q): Xa[p][(a,b)][c] with (a,b) = a Qp
+// + b, Xc[p][c][(a,b)].  grid (ceil(Qp / 32), ceil(Qp^2 / 32), P), 32 x 8 threads.
+__global__ void bf16_layouts_kernel(const float *__restrict__ Y, int Q, int Qp,
                                     __nv_bfloat16 *__restrict__ Xa,
                                     __nv_bfloat16 *__restrict__ Xc) {
   __shared__ float tile[32][33];
   const int p = blockIdx.z;
-  const int64_t QQ = (int64_t)Q * Q;
+  const int64_t QQ = (int64_t)Q * Q, QQp = (int64_t)Qp * Qp;
   const int64_t ab0 = (int64_t)blockIdx.y * 32;
   const int c0 = blockIdx.x * 32;
   const float *y = Y + (int64_t)p * QQ * Q;
   for (int yy = threadIdx.y; yy < 32; yy += 8) {
     const int64_t ab = ab0 + yy;
     const int c = c0 + threadIdx.x;
+    const int a = (int)(ab / Qp), b = (int)(ab - (int64_t)a * Qp);
     float v = 0.f;
-    if (ab < QQ && c < Q) {
-      v = y[ab * Q + c];
-      Xa[(int64_t)p * QQ * Q + ab * Q + c] = __float2bfloat16_rn(v);
+    if (ab < QQp && c < Qp) {
+      if (a < Q && b < Q && c < Q) v = y[((int64_t)a * Q + b) * Q + c];
+      Xa[(int64_t)p * QQp * Qp + ab * Qp + c] = __float2bfloat16_rn(v);
     }
     tile[yy][threadIdx.x] = v;
   }
@@ -199,8 +203,9 @@ __global__ void bf16_layouts_kernel(const float *__restrict__ Y, int Q,
   for (int yy = threadIdx.y; yy < 32; yy += 8) {
     const int c = c0 + yy;
     const int64_t ab = ab0 + threadIdx.x;
-    if (ab < QQ && c < Q)
-      Xc[(int64_t)p * QQ * Q + (int64_t)c * QQ + ab] = __float2bfloat16_rn(tile[threadIdx.x][yy]);
+    if (ab < QQp && c < Qp)
+      Xc[(int64_t)p * QQp * Qp + (int64_t)c * QQp + ab] =
+          __float2bfloat16_rn(tile[threadIdx.x][yy]);
   }
 }
 
@@ -411,10 +416,11 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
                        cudaStream_t st, const Marker &mk) {
   const int NP = kAlsNP;
   const int64_t QQ = (int64_t)Q * Q;
+  if (b.wait_first) cudaStreamWaitEvent(st, b.wait_first, 0);
   if (!b.layouts_ready) {
     mk(kStAlsAux, 1);
     bf16_layouts_kernel<<<dim3((Q + 31) / 32, (unsigned)((QQ + 31) / 32), P), dim3(32, 8), 0,
-                          st>>>(Y, Q, b.Xa, b.Xc);
+                          st>>>(Y, Q, Q, b.Xa, b.Xc);
     count_launch();
     mk(kStAlsAux, 0);
   }
@@ -448,6 +454,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   // stays in the L2 for the M2 pass
   m3.a_stream = tc.a_stream = true;
   m3.katoms = tc.katoms = kAlsKAtoms;
+  m3.max_ctas = tc.max_ctas = b.max_ctas;
   const int ks = tc_gemm_splits(m3.K, b.ksplit, kAlsKAtoms);
   const dim3 gKR(NP, P);
   const dim3 gM((Q + 256 / RT - 1) / (256 / RT), P);   // 32 output octets per CTA
@@ -467,6 +474,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     m3f.smem_reserve = kLdlReserve;
     m3f.a_stream = true;
     m3f.katoms = kAlsKAtoms;
+    m3f.max_ctas = b.max_ctas;
     // B^T of the warm start; every later B update writes it from its solve
     mk(kStAlsAux, 1);
     factor_bf16_t_kernel<RT><<<dim3((Q + 255) / 256, P), 256, 0, st>>>(b.Bf, Q, NP, b.Bt);
@@ -474,12 +482,15 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     mk(kStAlsAux, 0);
   }
   bool ok = true;
+  bool first = true;
   auto c_update = [&]() {
     factor_async<RT>(b.GB, b.GA, P, R, b, st);
     if (m3_fused) {
       mk(kStAlsGemm, 1);
       ok = ok && tc_gemm_store(m3f, b.status, st);
       mk(kStAlsGemm, 0);
+      if (first && b.ev_first) cudaEventRecord(b.ev_first, st);
+      first = false;
       mk(kStAlsSolve, 1);
       apply<RT>(b.Mparts, Q / 32, RT, (int64_t)(Q / 32) * RT, b.Cf, b.Ct, NP, P, Q, 0, b.GC, b, st,
                 segQ);
@@ -530,7 +541,68 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   return ok;
 }
 
-bool als_tc_eligible(int Q) { return Q % 8 == 0 && tc_supported(); }
+// The replicas in b.groups contiguous groups, each group's sweeps an
+// independent chain of launches: group 0 on `st`, group g on b.gst[g] (forked
+// from `st` and joined back at the end), each with its own factor stream and
+// events, group g starting after group g - 1's first GEMM.  Every buffer is indexed by
+// replica first with a stride that does not depend on P, so a group is the
+// same buffers offset to its first replica; per replica the launches and their
+// arithmetic are those of one group.
+template <int RT>
+static bool als_run_tc_groups(const float *Y, int P, int Q, int R, int iters, AlsBuffers &b,
+                              cudaStream_t st) {
+  const int G = b.groups;
+  const char *sv = getenv("OCTEN_ALS_GROUP_SPLIT");
+  const bool split_sms = sv && sv[0] == '1';
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t QQ = (int64_t)Q * Q, Q3 = QQ * Q;
+  // per-replica stride of the fused partials: Q^2 / 32 blocks of RT, or two
+  // segment sums per block when 32 does not divide Q
+  const int64_t mparts = (Q % 32 == 0 ? QQ / 32 : 2 * ((QQ + 31) / 32)) * RT;
+  cudaEventRecord(b.gsplit, st);
+  bool ok = true;
+  for (int g = 0; g < G; ++g) {
+    const int p0 = (int)((int64_t)g * P / G), p1 = (int)((int64_t)(g + 1) * P / G);
+    AlsBuffers bg = b;
+    bg.groups = 1;
+    bg.Af = b.Af + (int64_t)p0 * Q * RT;
+    bg.Bf = b.Bf + (int64_t)p0 * Q * RT;
+    bg.Cf = b.Cf + (int64_t)p0 * Q * RT;
+    bg.GA = b.GA + (int64_t)p0 * RT * RT;
+    bg.GB = b.GB + (int64_t)p0 * RT * RT;
+    bg.GC = b.GC + (int64_t)p0 * RT * RT;
+    bg.M = b.M + (int64_t)p0 * Q * RT;
+    // the bf16 Tc occupies the first half of H, [p][(a, b)][r]
+    bg.H = reinterpret_cast<float *>(reinterpret_cast<__nv_bfloat16 *>(b.H) + p0 * QQ * RT);
+    bg.Xa = b.Xa + p0 * Q3;
+    bg.Xc = b.Xc + p0 * Q3;
+    bg.KR = b.KR ? b.KR + (int64_t)p0 * kAlsNP * QQ : nullptr;
+    bg.Ct = b.Ct + (int64_t)p0 * kAlsNP * Q;
+    bg.Bt = b.Bt ? b.Bt + (int64_t)p0 * kAlsNP * Q : nullptr;
+    bg.Mparts = b.Mparts + p0 * mparts;
+    bg.L = b.L + (int64_t)p0 * als_factor_floats(RT);
+    bg.side = g == 0 ? b.side : b.gside[g];
+    bg.ev_fork = g == 0 ? b.ev_fork : b.gev_fork[g];
+    bg.ev_join = g == 0 ? b.ev_join : b.gev_join[g];
+    // every group's GEMMs on all SMs (a group's solves co-reside with the
+    // next group's GEMM CTAs), or OCTEN_ALS_GROUP_SPLIT=1: SMs / groups each
+    bg.max_ctas = split_sms ? (nsm / G > 0 ? nsm / G : 1) : 0;
+    bg.wait_first = g > 0 ? b.gfirst[g - 1] : nullptr;
+    bg.ev_first = g + 1 < G ? b.gfirst[g] : nullptr;
+    cudaStream_t sg = g == 0 ? st : b.gst[g];
+    if (g > 0) cudaStreamWaitEvent(sg, b.gsplit, 0);
+    ok = als_run_tc<RT>(Y + p0 * Q3, p1 - p0, Q, R, iters, bg, sg, Marker{}) && ok;
+    if (g > 0) cudaEventRecord(b.gdone[g], sg);
+  }
+  for (int g = 1; g < G; ++g) cudaStreamWaitEvent(st, b.gdone[g], 0);
+  return ok;
+}
+
+// Q % 8 == 0, or Q >= 32 run zero-padded to the next multiple of 8 (below 32
+// the replicas are small enough for the single-launch or split-K paths)
+bool als_tc_eligible(int Q) { return (Q % 8 == 0 || Q >= 32) && tc_supported(); }
 
 int als_tc_splits(int P, int Q, int desired) {
   (void)P;
@@ -561,7 +633,40 @@ bool als_run(const float *Y, int P, int Q, int R, int RT, int iters, AlsBuffers 
   } else {
     cudaFuncSetAttribute(als_apply_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ap);
   }
+  if (b.use_tc && b.Qp > Q) {
+    // zero-padded replicas: warm starts into the padded factors, the passes at
+    // Qp, the factors back to Q rows (the padding rows stay zero)
+    const int Qp = b.Qp;
+    const size_t rowb = (size_t)Q * RT * sizeof(float), rowp = (size_t)Qp * RT * sizeof(float);
+    mk(kStAlsAux, 1);
+    cudaMemsetAsync(b.Af_pad, 0, rowp * P, st);
+    cudaMemsetAsync(b.Bf_pad, 0, rowp * P, st);
+    cudaMemsetAsync(b.Cf_pad, 0, rowp * P, st);
+    cudaMemcpy2DAsync(b.Af_pad, rowp, b.Af, rowb, rowb, P, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpy2DAsync(b.Bf_pad, rowp, b.Bf, rowb, rowb, P, cudaMemcpyDeviceToDevice, st);
+    const int64_t QQp = (int64_t)Qp * Qp;
+    bf16_layouts_kernel<<<dim3((Qp + 31) / 32, (unsigned)((QQp + 31) / 32), P), dim3(32, 8), 0,
+                          st>>>(Y, Q, Qp, b.Xa, b.Xc);
+    count_launch();
+    mk(kStAlsAux, 0);
+    AlsBuffers bp = b;
+    bp.Af = b.Af_pad; bp.Bf = b.Bf_pad; bp.Cf = b.Cf_pad;
+    bp.Qp = 0;
+    bp.layouts_ready = true;
+    const bool ok = als_run(Y, P, Qp, R, RT, iters, bp, st, mk);
+    mk(kStAlsAux, 1);
+    cudaMemcpy2DAsync(b.Af, rowb, b.Af_pad, rowp, rowb, P, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpy2DAsync(b.Bf, rowb, b.Bf_pad, rowp, rowb, P, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpy2DAsync(b.Cf, rowb, b.Cf_pad, rowp, rowb, P, cudaMemcpyDeviceToDevice, st);
+    mk(kStAlsAux, 0);
+    return ok;
+  }
   if (b.use_tc) {
+    if (b.groups > 1 && !mk.fn && Q >= 32 && P >= b.groups) {
+      if (RT == 8) return als_run_tc_groups<8>(Y, P, Q, R, iters, b, st);
+      if (RT == 16) return als_run_tc_groups<16>(Y, P, Q, R, iters, b, st);
+      return als_run_tc_groups<32>(Y, P, Q, R, iters, b, st);
+    }
     if (RT == 8) return als_run_tc<8>(Y, P, Q, R, iters, b, st, mk);
     if (RT == 16) return als_run_tc<16>(Y, P, Q, R, iters, b, st, mk);
     return als_run_tc<32>(Y, P, Q, R, iters, b, st, mk);

@@ -377,6 +377,95 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// The same product for A stored with m contiguous (sAm == 1, sAk a multiple of
+// 4, A 16-byte aligned): the projected factors U_all^T F and the lift L e.  A
+// CTA of 256 threads covers 128 rows; each K step of 32 stages A as As[k][m]
+// from 16-byte loads (a warp reads 512 contiguous bytes of one k row) and B as
+// Bs[k][n]; thread t owns rows 4 (t % 32) .. + 3 and columns 4 (t / 32) .. + 3,
+// read as one 16-byte shared load each per k.  The next step's loads are
+// issued into registers before the current step is multiplied.  Every output
+// is the sequential fp32 sum over its K range in k order, as in
+// gemm_skinny_kernel (same splits, same partials), so the two agree bit for bit.
+constexpr int kMcThreads = 256;
+
+__global__ void __launch_bounds__(kMcThreads)
+    gemm_skinny_mc_kernel(const float *__restrict__ A, int64_t sAk, const float *__restrict__ B,
+                          int64_t sBn, int64_t sBk, int M, int N, int K, int kc, float *D,
+                          int64_t sDm, int64_t sDn, float alpha, float beta,
+                          float *__restrict__ part) {
+  __shared__ __align__(16) float As[kSkBK][kSkBM];
+  __shared__ __align__(16) float Bs[kSkBK][32];
+  const int tid = threadIdx.x, rq = tid & 31, cq = tid >> 5;
+  const int m0 = blockIdx.x * kSkBM;
+  const int k_begin = blockIdx.y * kc;
+  const int k_end = min(K, k_begin + kc);
+  // loader roles: A float4 (row kk = tid / 32 + 8 j, rows 4 (tid % 32) ..), B (kk, n = tid % 32)
+  const int lm = m0 + 4 * rq;
+  float4 ra[4];
+  float rb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + cq + 8 * j;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < k_end) {
+        const float *src = A + (int64_t)k * sAk + lm;
+        if (lm + 3 < M) {
+          v = __ldg(reinterpret_cast<const float4 *>(src));
+        } else {
+          if (lm < M) v.x = __ldg(src);
+          if (lm + 1 < M) v.y = __ldg(src + 1);
+          if (lm + 2 < M) v.z = __ldg(src + 2);
+        }
+      }
+      ra[j] = v;
+      rb[j] = (k < k_end && rq < N) ? __ldg(B + (int64_t)k * sBk + (int64_t)rq * sBn) : 0.f;
+    }
+  };
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+  if (k_begin < k_end) load(k_begin);
+  for (int k0 = k_begin; k0 < k_end; k0 += kSkBK) {
+    __syncthreads();   // the previous step's tiles are consumed
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      *reinterpret_cast<float4 *>(&As[cq + 8 * j][4 * rq]) = ra[j];
+      Bs[cq + 8 * j][rq] = rb[j];
+    }
+    __syncthreads();
+    if (k0 + kSkBK < k_end) load(k0 + kSkBK);
+#pragma unroll 8
+    for (int kk = 0; kk < kSkBK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4 *>(&As[kk][4 * rq]);
+      const float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][4 * cq]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(av[i], bv[c], acc[i][c]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = lm + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int n = 4 * cq + c;
+      if (n >= N) continue;
+      if (part) {
+        part[((int64_t)blockIdx.y * M + m) * N + n] = acc[i][c];
+      } else {
+        float *d = D + (int64_t)m * sDm + (int64_t)n * sDn;
+        *d = beta == 0.f ? alpha * acc[i][c] : fmaf(beta, *d, alpha * acc[i][c]);
+      }
+    }
+  }
+}
+
 static void gemm_skinny(const GemmArgs &g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return;
   const int tiles_m = (g.M + kSkBM - 1) / kSkBM;
@@ -396,6 +485,22 @@ static void gemm_skinny(const GemmArgs &g, cudaStream_t st) {
   const float *A = static_cast<const float *>(g.A);
   const float *B = static_cast<const float *>(g.B);
   const dim3 grid((unsigned)tiles_m, (unsigned)splits, (unsigned)g.batch);
+  const bool mc = g.batch == 1 && g.sAm == 1 && g.sAk % 4 == 0 &&
+                  (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  if (mc) {
+    float *part = splits >= 2 ? g.split_scratch : nullptr;
+    gemm_skinny_mc_kernel<<<grid, kMcThreads, 0, st>>>(A, g.sAk, B, g.sBn, g.sBk, g.M, g.N, g.K,
+                                                       splits >= 2 ? kc : (g.K < 1 ? 1 : g.K),
+                                                       g.D, g.sDm, g.sDn, g.alpha, g.beta, part);
+    count_launch();
+    if (splits >= 2) {
+      const int64_t MN = (int64_t)g.M * g.N;
+      splitk_reduce_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(
+          g.split_scratch, splits, g.M, g.N, g.D, g.sDm, g.sDn, g.alpha, g.beta);
+      count_launch();
+    }
+    return;
+  }
   if (splits >= 2) {
     gemm_skinny_kernel<<<grid, 128, 0, st>>>(A, g.sAm, g.sAk, B, g.sBn, g.sBk, g.M, g.N, g.K, kc,
                                              nullptr, 0, 0, 1.f, 0.f, g.split_scratch, 0, 0, 0);

@@ -661,7 +661,8 @@ long long wait_budget_cycles() {
 
 template <int KIND, class Epi>
 bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
-               const Epi &epi, int *status, cudaStream_t st, int smem_reserve = 0) {
+               const Epi &epi, int *status, cudaStream_t st, int smem_reserve = 0,
+               int max_ctas = 0) {
   sh.wait_budget = wait_budget_cycles();
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
@@ -686,7 +687,7 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
   cfg.blockDim = dim3(192);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  const int slots = sm_count();
+  const int slots = max_ctas > 0 && max_ctas < sm_count() ? max_ctas : sm_count();
   const int grid_items = (int)(items < slots ? items : slots);
   cfg.gridDim = dim3(grid_items);
   if (cudaLaunchKernelEx(&cfg, kern, ma, mb, sh, epi, batch, status) != cudaSuccess) {
@@ -876,7 +877,7 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
     sh.a_stream = g.a_stream ? 1 : 0;
     sh.katoms = c.katoms;
     sh.ksplit = ks;
-    return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve);
+    return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve, g.max_ctas);
   };
   // with split-K the other atom count is a candidate only if it cuts K at the
   // same places (the splits set the summation)
@@ -887,8 +888,8 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
   };
   const TuneChoice cand[] = {{katoms0, g.BN}, {katoms1, g.BN}};
   const int ncand = ks > 1 && split_elems(katoms0) != split_elems(katoms1) ? 1 : 2;
-  const std::array<int64_t, 8> key{1, g.M, g.N, g.K, g.batch, ks, g.Dh != nullptr,
-                                   g.m1_part != nullptr};
+  const std::array<int64_t, 8> key{1 + 16 * (int64_t)g.max_ctas, g.M, g.N, g.K, g.batch, ks,
+                                   g.Dh != nullptr, g.m1_part != nullptr};
   return launch(tuned(key, cand, ncand, st, launch));
 }
 

@@ -76,14 +76,23 @@ struct octen_ctx {
   float *GA = nullptr, *GB = nullptr, *GC = nullptr;
   float *splitk = nullptr;                 // split-K partials of the small GEMMs
   static constexpr size_t kSplitkFloats = size_t(4) << 20;
-  // tensor-core ALS (bf16 / e4m3 modes with Q % 8 == 0)
+  // tensor-core ALS (bf16 / e4m3 modes with Q % 8 == 0, or Q >= 32 zero-padded
+  // to als_qp, the next multiple of 8, with factors Apad, Bpad, Cpad)
   bool als_tc = false;
   int als_ks = 1;
+  int als_qp = 0;
+  float *Apad = nullptr, *Bpad = nullptr, *Cpad = nullptr;
   __nv_bfloat16 *Xa = nullptr, *Xc = nullptr, *KR = nullptr, *Ctb = nullptr, *Btb = nullptr;
   float *Mparts = nullptr;
   // replica CP-ALS: the factor of each update runs on als_side beside its MTTKRP
   cudaStream_t als_side = nullptr;
   cudaEvent_t als_fork = nullptr, als_join = nullptr;
+  // replica groups of the tensor-core CP-ALS (see AlsBuffers::groups): group
+  // g > 0 runs on grp_st[g] with its factor kernels on grp_side[g]
+  int als_groups = 1;
+  cudaStream_t grp_st[kMaxAlsGroups] = {}, grp_side[kMaxAlsGroups] = {};
+  cudaEvent_t grp_fork[kMaxAlsGroups] = {}, grp_join[kMaxAlsGroups] = {};
+  cudaEvent_t grp_split = nullptr, grp_done[kMaxAlsGroups] = {}, grp_first[kMaxAlsGroups] = {};
   float *Lfac = nullptr;
   bool layouts_ready = false;   // Xa / Xc hold bf16(Y) from the last mode-3 pass
   int *perm = nullptr;
@@ -91,18 +100,62 @@ struct octen_ctx {
   int *dstatus = nullptr;
   double *dfit = nullptr;
 
-  // The replica CP-ALS of an append (about 200 launches on fixed buffers) runs
-  // as one CUDA graph: captured on a private stream at the second append with
-  // the stage timers off (the first one runs eagerly, so that the GEMM
-  // autotuner has timed its shapes), replayed on the context's stream afterwards.
-  // OCTEN_GRAPH=0 keeps the launches eager.
+  // Everything of an append after its mode-2 contraction (mode 1, mode 3, the
+  // warm start, the replica CP-ALS, the match, the lift, the new rows of C and
+  // the G_p update: about 200 launches on fixed buffers) runs as one CUDA
+  // graph, recorded on a private stream per batch size (the first append runs
+  // eagerly, so that the GEMM autotuner has timed its shapes) and replayed on
+  // the context's stream.  The batch's W rows reach it through Wfix and the
+  // new C rows leave it through Cnew_fix.  A graph is valid for the scratch
+  // buffers it was recorded with: any reallocation bumps `gen` and drops the
+  // graphs.  OCTEN_GRAPH=0 keeps the launches eager.
+  struct TailGraph {
+    int64_t t = 0;
+    cudaGraph_t graph = nullptr;     // kept: octen_append_many's step graph clones it
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0, tc = 0;
+  };
+  static constexpr int kTailGraphs = 4;     // batch sizes kept at once
+  static constexpr int kMaxCaptures = 16;   // recordings per generation of buffers
   bool use_graph = true;
-  bool als_graph_tried = false;
   cudaStream_t cap_st = nullptr;
-  cudaGraphExec_t als_exec = nullptr;
-  int64_t als_graph_launches = 0, als_graph_tc = 0;
-  bool als_graph_layouts = false;   // the graph was recorded with Xa / Xc given
+  TailGraph tails[kTailGraphs];
+  int next_tail = 0, captures = 0;
+  uint64_t gen = 0;                 // bumped whenever a scratch buffer is reallocated
+  float *Wfix = nullptr;            // chunk_slices x Qd: the batch's W rows
+  float *Cnew_fix = nullptr;        // chunk_slices x R: the batch's new C rows
   int64_t appends = 0;              // appends enqueued so far
+
+  void drop_graphs() {
+    for (TailGraph &g : tails) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+      g = TailGraph{};
+    }
+    captures = 0;
+  }
+
+  // One step of octen_append_many led by this context (the first of the
+  // call) as one graph: per context a child graph with its head (W rows into
+  // Wfix, quantisation, mode 2), a clone of its tail graph and the copy of
+  // the new C rows.  The graph is built for the contexts' ids, buffer
+  // generations and batch sizes; later steps with the same key only update
+  // the heads (new slices) and the C copies (new row offsets).
+  struct StepGraph {
+    std::vector<int64_t> key;
+    cudaGraph_t graph = nullptr;     // kept: its nodes name the ones updated per step
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> head, cmem;
+    int64_t launches = 0, tc = 0;   // kernels of the tails, counted per launch
+  } step;
+  uint64_t id = 0;                  // unique per context in the process
+  cudaEvent_t step_ev = nullptr;    // this context's stream reached the step
+  cudaEvent_t step_done = nullptr;  // the step graph this context led has run
+  void drop_step() {
+    if (step.exec) cudaGraphExecDestroy(step.exec);
+    if (step.graph) cudaGraphDestroy(step.graph);
+    step = StepGraph{};
+  }
 
   // per-batch scratch, grown on demand
   DevBuf Tbuf, T2buf, Wbuf, X8buf, xscale, stage[4], fitpart;
@@ -158,7 +211,10 @@ struct octen_ctx {
 
   ~octen_ctx() {
     cudaStreamSynchronize(st);
-    if (als_exec) cudaGraphExecDestroy(als_exec);
+    drop_graphs();
+    drop_step();
+    if (step_ev) cudaEventDestroy(step_ev);
+    if (step_done) cudaEventDestroy(step_done);
     if (cap_st) cudaStreamDestroy(cap_st);
     if (als_side) {
       cudaStreamSynchronize(als_side);
@@ -166,6 +222,16 @@ struct octen_ctx {
     }
     if (als_fork) cudaEventDestroy(als_fork);
     if (als_join) cudaEventDestroy(als_join);
+    for (int g = 0; g < kMaxAlsGroups; ++g) {
+      for (cudaStream_t s2 : {grp_st[g], grp_side[g]})
+        if (s2) {
+          cudaStreamSynchronize(s2);
+          cudaStreamDestroy(s2);
+        }
+      for (cudaEvent_t e : {grp_fork[g], grp_join[g], grp_done[g], grp_first[g]})
+        if (e) cudaEventDestroy(e);
+    }
+    if (grp_split) cudaEventDestroy(grp_split);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
     if (copy_st) {
       cudaStreamSynchronize(copy_st);
@@ -231,6 +297,10 @@ struct octen_ctx {
     const size_t want = bytes + 16;
     if (want > limit || held - old > limit - want) return false;
     cudaStreamSynchronize(st);
+    if (b.p) {
+      drop_graphs();   // recorded with the old address
+      ++gen;
+    }
     dev_free(b.p, old);
     b.p = nullptr;
     b.bytes = 0;
@@ -301,6 +371,17 @@ size_t device_memory_limit() {
   char *end = nullptr;
   const unsigned long long n = strtoull(v, &end, 10);
   return end == v ? SIZE_MAX : (size_t)n;
+}
+
+// Replica groups of the tensor-core CP-ALS: OCTEN_ALS_GROUPS (1 to
+// kMaxAlsGroups, at most P), else 1.
+int als_groups_wanted(int P) {
+  int g = 1;
+  const char *v = getenv("OCTEN_ALS_GROUPS");
+  if (v && *v) g = atoi(v);
+  if (g < 1) g = 1;
+  if (g > kMaxAlsGroups) g = kMaxAlsGroups;
+  return g > P ? P : g;
 }
 
 // OCTEN_GEMM=simt keeps the large contractions on the SIMT kernels (used to
@@ -393,7 +474,8 @@ void compress_finish(octen_ctx *x, int64_t t, const float *Wd, float *Yacc, bool
   }
   x->mark(kStMode1, 0);
   x->mark(kStMode3, 1);
-  const bool want = layouts && x->als_tc;
+  // (the padded ALS builds its own zero-padded copies)
+  const bool want = layouts && x->als_tc && x->als_qp == 0;
   x->layouts_ready =
       mode3_accumulate(static_cast<float *>(x->T2buf.p), Wd, Yacc, t, c.P, c.Q, c.S, x->Qd, x->st,
                        want ? x->Xa : nullptr, want ? x->Xc : nullptr);
@@ -410,17 +492,14 @@ octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float
   return OCTEN_OK;
 }
 
-// The same for t host slices: they are copied into staging slot 2 in up to
-// kCopyChunks pieces on copy_st, and the mode-2 contraction of each piece
-// starts as soon as it has arrived.  The caller ensures 16-byte aligned piece
-// offsets (I J a multiple of 16), which the tensor-map operands need.
-octen_status compress_chunk_host(octen_ctx *x, const void *Xh, int64_t t, const float *Wd,
-                                 float *Yacc, bool layouts) {
+// Quantisation and mode-2 contraction of t host slices: they are copied into
+// staging slot 2 (already sized by the caller) in up to kCopyChunks pieces on
+// copy_st, and the contraction of each piece starts as soon as it has arrived.
+// The caller ensures 16-byte aligned piece offsets (I J a multiple of 16),
+// which the tensor-map operands need.
+octen_status compress_mode2_host(octen_ctx *x, const void *Xh, int64_t t) {
   const octen_config &c = x->cfg;
   const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
-  octen_status s = compress_scratch(x, t);
-  if (s != OCTEN_OK) return s;
-  if (!x->grow(x->stage[2], t * slice)) return x->fail(OCTEN_ENOMEM, "staging the batch");
   // the staging slot is free once the stream's earlier work is done
   cudaEventRecord(x->copy_ready, x->st);
   cudaStreamWaitEvent(x->copy_st, x->copy_ready, 0);
@@ -443,7 +522,6 @@ octen_status compress_chunk_host(octen_ctx *x, const void *Xh, int64_t t, const 
     cudaStreamWaitEvent(x->st, x->copy_ev[nc], 0);
     compress_mode2(x, x->stage[2].p, k0, n);
   }
-  compress_finish(x, t, Wd, Yacc, layouts);
   return OCTEN_OK;
 }
 
@@ -529,6 +607,8 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     return s;
   }
   octen_ctx *x = new octen_ctx();
+  static std::atomic<uint64_t> ids{0};
+  x->id = ++ids;
   x->limit = device_memory_limit();
   x->cfg = *cfg;
   x->Qd = cfg->S + cfg->P * (cfg->Q - cfg->S);
@@ -545,24 +625,31 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
             x->alloc(x->At, P * Q * RT) && x->alloc(x->Bt, P * Q * RT) &&
             x->alloc(x->Ct, P * Q * RT) && x->alloc(x->Ah, P * Q * RT) &&
             x->alloc(x->Bh, P * Q * RT) && x->alloc(x->Ch, P * Q * RT) &&
-            x->alloc(x->M, P * Q * RT) && x->alloc(x->H, P * Q * Q * RT) &&
+            x->alloc(x->M, P * ((Q + 7) / 8 * 8) * RT) && x->alloc(x->H, P * Q * Q * RT) &&
             x->alloc(x->perm, P * c.R) && x->alloc(x->scales, P * 2 * c.R) &&
             x->alloc(x->align_scratch, align_scratch_doubles(c.P, x->RT)) &&
             x->alloc(x->dstatus, 1) && x->alloc(x->dfit, 2) && x->alloc(x->GA, P * RT * RT) &&
             x->alloc(x->GB, P * RT * RT) && x->alloc(x->GC, P * RT * RT) &&
             x->alloc(x->Lfac, P * (size_t)als_factor_floats(x->RT)) &&
-            x->alloc(x->splitk, octen_ctx::kSplitkFloats);
+            x->alloc(x->splitk, octen_ctx::kSplitkFloats) &&
+            x->alloc(x->Wfix, (size_t)chunk_slices(x) * Qd) &&
+            x->alloc(x->Cnew_fix, (size_t)chunk_slices(x) * c.R);
   if (ok && x->use_tc && als_tc_eligible(c.Q)) {
+    // Q not a multiple of 8: the tensor-core passes run on X_p zero-padded to Qp
+    const size_t Qp = (Q + 7) / 8 * 8;
+    x->als_qp = Qp == Q ? 0 : (int)Qp;
     const int mt = (c.Q + 127) / 128;
     const int want = (4 * 152 + mt * c.P - 1) / (mt * c.P);
     x->als_ks = als_tc_splits(c.P, c.Q, want < 1 ? 1 : want);
-    const size_t nparts = (size_t)(x->als_ks > (c.Q / 32) ? x->als_ks : (c.Q / 32));
+    const size_t nparts = (size_t)(x->als_ks > (int)(Qp / 32) ? x->als_ks : (int)(Qp / 32));
     // the Khatri-Rao operand of the M3 pass exists only below Q = 32 (from 32
     // on, the M3 GEMM contracts b against B^T and reduces a in its epilogue)
-    ok = x->alloc(x->Xa, P * Q * Q * Q) && x->alloc(x->Xc, P * Q * Q * Q) &&
-         (c.Q >= 32 || x->alloc(x->KR, P * kAlsNP * Q * Q)) && x->alloc(x->Ctb, P * kAlsNP * Q) &&
-         x->alloc(x->Btb, P * kAlsNP * Q) &&
-         x->alloc(x->Mparts, std::max(nparts * Q, 2 * ((Q * Q + 31) / 32)) * P * RT);
+    ok = x->alloc(x->Xa, P * Qp * Qp * Qp) && x->alloc(x->Xc, P * Qp * Qp * Qp) &&
+         (c.Q >= 32 || x->alloc(x->KR, P * kAlsNP * Q * Q)) &&
+         x->alloc(x->Ctb, P * kAlsNP * Qp) && x->alloc(x->Btb, P * kAlsNP * Qp) &&
+         x->alloc(x->Mparts, std::max(nparts * Qp, 2 * ((Qp * Qp + 31) / 32)) * P * RT) &&
+         (Qp == Q || (x->alloc(x->Apad, P * Qp * RT) && x->alloc(x->Bpad, P * Qp * RT) &&
+                      x->alloc(x->Cpad, P * Qp * RT)));
     x->als_tc = ok;
   }
   void *ut = nullptr, *vt = nullptr;
@@ -584,6 +671,20 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
     ok = cudaStreamCreateWithFlags(&x->als_side, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&x->als_fork, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&x->als_join, cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (ok && x->als_tc && c.Q >= 32) {
+    x->als_groups = als_groups_wanted(c.P);
+    if (x->als_groups > 1)
+      ok = cudaEventCreateWithFlags(&x->grp_split, cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 0; g + 1 < x->als_groups && ok; ++g)
+      ok = cudaEventCreateWithFlags(&x->grp_first[g], cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 1; g < x->als_groups && ok; ++g) {
+      ok = cudaStreamCreateWithFlags(&x->grp_st[g], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaStreamCreateWithFlags(&x->grp_side[g], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&x->grp_fork[g], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&x->grp_join[g], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&x->grp_done[g], cudaEventDisableTiming) == cudaSuccess;
+    }
   }
   if (!ok) {
     cudaGetLastError();
@@ -690,74 +791,8 @@ octen_status octen_init(octen_ctx *x, const void *X_old, int64_t t_old, const fl
 
 namespace {
 
-// Records the replica CP-ALS of an append into x->als_exec (left null if a
-// launch is refused or the capture fails; the eager path is used then).
-void capture_als(octen_ctx *x, AlsBuffers ab) {
-  const octen_config &c = x->cfg;
-  x->als_graph_tried = true;
-  if (!x->cap_st && cudaStreamCreateWithFlags(&x->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    x->cap_st = nullptr;
-    return;
-  }
-  const uint64_t l0 = octen_launch_count(), t0 = octen_tc_launch_count();
-  if (cudaStreamBeginCapture(x->cap_st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-    cudaGetLastError();
-    return;
-  }
-  const bool ok = als_run(x->Y, c.P, c.Q, c.R, x->RT, c.als_iters, ab, x->cap_st, Marker{});
-  cudaGraph_t g = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(x->cap_st, &g);
-  const int64_t dl = (int64_t)(octen_launch_count() - l0);
-  const int64_t dt = (int64_t)(octen_tc_launch_count() - t0);
-  adjust_launch_counts(-dl, -dt);   // recorded, not run
-  if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&x->als_exec, g, 0) == cudaSuccess) {
-    x->als_graph_launches = dl;
-    x->als_graph_tc = dt;
-    x->als_graph_layouts = ab.layouts_ready;
-  } else {
-    x->als_exec = nullptr;
-  }
-  if (g) cudaGraphDestroy(g);
-  cudaGetLastError();
-}
-
-// Enqueues one append on the context's stream (no final synchronisation; K is
-// advanced by the caller once the stream has finished without error).
-octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
-  if (!x) return OCTEN_EINVAL;
-  if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_append before octen_init");
-  if (!X_new || !W_new || t < 1 || t > chunk_slices(x))
-    return x->fail(OCTEN_EINVAL, "octen_append: need X_new, W_new and 1 <= t <= %d",
-                   (int)chunk_slices(x));
-  const octen_config &c = x->cfg;
-  const int Qd = x->Qd, RT = x->RT;
-  if (!ensure_c_capacity(x, x->K + t)) return x->fail(OCTEN_ENOMEM, "C");
-  // the append's scratch is allocated before its first kernel, so that a
-  // refused allocation leaves the context unchanged
-  const size_t cs = (size_t)Qd * c.R + t * c.R + t * Qd + t * t;
-  if (!x->grow(x->Wbuf, cs * sizeof(float))) return x->fail(OCTEN_ENOMEM, "C solve scratch");
-  const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
-  const float *Wd = static_cast<const float *>(x->stage_in(W_new, (size_t)t * Qd * 4, 1));
-  if (!Wd) return x->fail(OCTEN_ENOMEM, "staging W_new");
-  // 1. compress the batch and update the summaries (host slices arrive in
-  // pieces that overlap the mode-2 contraction of the ones before)
-  octen_status s;
-  if (!is_device_ptr(X_new) && t >= 2 && (c.I * c.J) % 16 == 0 && x->copy_st) {
-    s = compress_chunk_host(x, X_new, t, Wd, x->Y, true);
-  } else {
-    const void *Xd = x->stage_in(X_new, t * slice, 2);
-    if (!Xd) return x->fail(OCTEN_ENOMEM, "staging the batch");
-    s = compress_chunk(x, Xd, t, Wd, x->Y, true);
-  }
-  if (s != OCTEN_OK) return s;
-  // 2. CP of every summary, warm-started from the projected previous factors
-  x->mark(kStWarm, 1);
-  project(x, x->U32, c.I, x->A, x->PA);
-  project(x, x->V32, c.J, x->B, x->PB);
-  warm_start(x->PA, c.P, c.Q, c.S, c.R, RT, x->At, x->GA, x->st);
-  warm_start(x->PB, c.P, c.Q, c.S, c.R, RT, x->Bt, x->GB, x->st);
-  x->mark(kStWarm, 0);
+// The replica buffers of the CP-ALS of an append.
+AlsBuffers als_buffers(octen_ctx *x) {
   AlsBuffers ab;
   ab.Af = x->At; ab.Bf = x->Bt; ab.Cf = x->Ct; ab.GA = x->GA; ab.GB = x->GB; ab.GC = x->GC;
   ab.M = x->M; ab.H = x->H; ab.status = x->dstatus;
@@ -766,47 +801,358 @@ octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const fl
   ab.Mparts = x->Mparts; ab.ksplit = x->als_ks;
   ab.side = x->als_side; ab.ev_fork = x->als_fork; ab.ev_join = x->als_join; ab.L = x->Lfac;
   ab.layouts_ready = x->layouts_ready;
-  Marker mk;
-  if (x->timing) { mk.fn = &octen_ctx::mark_cb; mk.arg = x; }
-  bool replayed = false;
-  if (!x->timing && x->use_graph) {
-    if (!x->als_exec && !x->als_graph_tried && x->appends > 0) capture_als(x, ab);
-    if (x->als_exec && x->als_graph_layouts == ab.layouts_ready) {
-      if (cudaGraphLaunch(x->als_exec, x->st) == cudaSuccess) {
-        adjust_launch_counts(x->als_graph_launches, x->als_graph_tc);
-        replayed = true;
-      } else {
-        cudaGetLastError();
-      }
-    }
+  ab.groups = x->als_groups;
+  for (int g = 0; g < kMaxAlsGroups; ++g) {
+    ab.gst[g] = x->grp_st[g]; ab.gside[g] = x->grp_side[g];
+    ab.gev_fork[g] = x->grp_fork[g]; ab.gev_join[g] = x->grp_join[g];
+    ab.gdone[g] = x->grp_done[g];
+    ab.gfirst[g] = x->grp_first[g];
   }
-  if (!replayed && !als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st, mk)) {
-    // a tensor-core launch was refused: redo the CP from the warm start on SIMT
-    cudaGetLastError();
-    x->als_tc = false;
-    ab.use_tc = false;
-    warm_start(x->PA, c.P, c.Q, c.S, c.R, RT, x->At, x->GA, x->st);
-    warm_start(x->PB, c.P, c.Q, c.S, c.R, RT, x->Bt, x->GB, x->st);
-    als_run(x->Y, c.P, c.Q, c.R, RT, c.als_iters, ab, x->st, mk);
-  }
-  // 3. anchor match against u^T A_prev, v^T B_prev
+  ab.gsplit = x->grp_split;
+  ab.Qp = x->als_qp;
+  ab.Af_pad = x->Apad; ab.Bf_pad = x->Bpad; ab.Cf_pad = x->Cpad;
+  return ab;
+}
+
+// Mode 1 and mode 3 of the batch (after its mode 2), then the CP of every
+// summary warm-started from the projected previous factors.  Returns false if
+// a tensor-core launch of the CP was refused (nothing after the warm start is
+// then enqueued).
+bool tail_front(octen_ctx *x, int64_t t, const Marker &mk) {
+  const octen_config &c = x->cfg;
+  compress_finish(x, t, x->Wfix, x->Y, true);
+  x->mark(kStWarm, 1);
+  project(x, x->U32, c.I, x->A, x->PA);
+  project(x, x->V32, c.J, x->B, x->PB);
+  warm_start(x->PA, c.P, c.Q, c.S, c.R, x->RT, x->At, x->GA, x->st);
+  warm_start(x->PB, c.P, c.Q, c.S, c.R, x->RT, x->Bt, x->GB, x->st);
+  x->mark(kStWarm, 0);
+  AlsBuffers ab = als_buffers(x);
+  return als_run(x->Y, c.P, c.Q, c.R, x->RT, c.als_iters, ab, x->st, mk);
+}
+
+// Anchor match against u^T A_prev, v^T B_prev, lift of A and B, the new rows
+// of C (into Cnew_fix) and the G_p update.
+void tail_back(octen_ctx *x, int64_t t) {
+  const octen_config &c = x->cfg;
   x->mark(kStAlign, 1);
-  align_replicas(x->At, x->Bt, x->Ct, x->PA, x->PB, c.P, c.Q, c.S, c.R, RT, x->Ah, x->Bh,
+  align_replicas(x->At, x->Bt, x->Ct, x->PA, x->PB, c.P, c.Q, c.S, c.R, x->RT, x->Ah, x->Bh,
                  x->Ch, x->perm, x->scales, x->align_scratch, x->st);
   x->mark(kStAlign, 0);
-  // 4. lift A and B, solve the new rows of C, update G_p
   x->mark(kStLift, 1);
   lift_mode(x, x->Ah, x->PA, x->La, x->a_over, c.I, x->A);
   lift_mode(x, x->Bh, x->PB, x->Lb, x->b_over, c.J, x->B);
   x->mark(kStLift, 0);
-  float *C_new = x->C + x->K * c.R;
   x->mark(kStCsolve, 1);
-  solve_c_new(Wd, x->Ch, x->G, t, c.P, c.Q, c.S, Qd, c.R, RT, static_cast<float *>(x->Wbuf.p),
-              x->splitk, octen_ctx::kSplitkFloats, C_new, x->dstatus, x->st);
-  update_g(Wd, C_new, t, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
+  solve_c_new(x->Wfix, x->Ch, x->G, t, c.P, c.Q, c.S, x->Qd, c.R, x->RT,
+              static_cast<float *>(x->Wbuf.p), x->splitk, octen_ctx::kSplitkFloats, x->Cnew_fix,
+              x->dstatus, x->st);
+  update_g(x->Wfix, x->Cnew_fix, t, c.P, c.Q, c.S, x->Qd, c.R, x->G, x->st);
   x->mark(kStCsolve, 0);
+}
+
+// Records the tail of a t-slice append (tail_front + tail_back) as a graph in
+// a free slot of x->tails; nullptr if a launch was refused or the recording
+// failed (the eager path runs then).  Every function of the tail enqueues on
+// x->st, which points at the private capture stream while recording.
+octen_ctx::TailGraph *capture_tail(octen_ctx *x, int64_t t) {
+  if (x->captures >= octen_ctx::kMaxCaptures) return nullptr;
+  ++x->captures;
+  if (!x->cap_st && cudaStreamCreateWithFlags(&x->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    x->cap_st = nullptr;
+    return nullptr;
+  }
+  const uint64_t l0 = octen_launch_count(), t0 = octen_tc_launch_count();
+  if (cudaStreamBeginCapture(x->cap_st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaStream_t home = x->st;
+  x->st = x->cap_st;
+  const bool ok = tail_front(x, t, Marker{});
+  if (ok) tail_back(x, t);
+  x->st = home;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(x->cap_st, &g);
+  const int64_t dl = (int64_t)(octen_launch_count() - l0);
+  const int64_t dt = (int64_t)(octen_tc_launch_count() - t0);
+  adjust_launch_counts(-dl, -dt);   // recorded, not run
+  octen_ctx::TailGraph *slot = nullptr;
+  if (ok && e == cudaSuccess && g) {
+    octen_ctx::TailGraph &tg = x->tails[x->next_tail];
+    if (tg.exec) cudaGraphExecDestroy(tg.exec);
+    if (tg.graph) cudaGraphDestroy(tg.graph);
+    tg = octen_ctx::TailGraph{};
+    if (cudaGraphInstantiate(&tg.exec, g, 0) == cudaSuccess) {
+      tg.t = t;
+      tg.graph = g;
+      g = nullptr;
+      tg.launches = dl;
+      tg.tc = dt;
+      slot = &tg;
+      x->next_tail = (x->next_tail + 1) % octen_ctx::kTailGraphs;
+    } else {
+      tg.exec = nullptr;
+    }
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return slot;
+}
+
+// The tail of an append on x->st: the recorded graph for this batch size when
+// there is one (recorded now if needed), else launch by launch.
+void tail_enqueue(octen_ctx *x, int64_t t) {
+  const octen_config &c = x->cfg;
+  if (!x->timing && x->use_graph) {
+    octen_ctx::TailGraph *tg = nullptr;
+    for (octen_ctx::TailGraph &g : x->tails)
+      if (g.exec && g.t == t) tg = &g;
+    if (!tg && x->appends > 0) tg = capture_tail(x, t);
+    if (tg && cudaGraphLaunch(tg->exec, x->st) == cudaSuccess) {
+      adjust_launch_counts(tg->launches, tg->tc);
+      return;
+    }
+    cudaGetLastError();
+  }
+  Marker mk;
+  if (x->timing) { mk.fn = &octen_ctx::mark_cb; mk.arg = x; }
+  if (!tail_front(x, t, mk)) {
+    // a tensor-core launch was refused: redo the CP from the warm start on SIMT
+    cudaGetLastError();
+    x->als_tc = false;
+    x->drop_graphs();
+    AlsBuffers ab = als_buffers(x);
+    ab.use_tc = false;
+    warm_start(x->PA, c.P, c.Q, c.S, c.R, x->RT, x->At, x->GA, x->st);
+    warm_start(x->PB, c.P, c.Q, c.S, c.R, x->RT, x->Bt, x->GB, x->st);
+    als_run(x->Y, c.P, c.Q, c.R, x->RT, c.als_iters, ab, x->st, mk);
+  }
+  tail_back(x, t);
+}
+
+// Whether an append of t slices from X_new copies the host slices in pieces
+// (each piece's mode-2 contraction starting as it lands).
+bool host_pieces(const octen_ctx *x, const void *X_new, int64_t t) {
+  return !is_device_ptr(X_new) && t >= 2 && (x->cfg.I * x->cfg.J) % 16 == 0 && x->copy_st;
+}
+
+// Checks an append's arguments and makes every allocation it needs, before
+// any of its work is enqueued (a refused allocation leaves the context as it
+// was).
+octen_status append_prepare(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
+  if (!x) return OCTEN_EINVAL;
+  if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_append before octen_init");
+  if (!X_new || !W_new || t < 1 || t > chunk_slices(x))
+    return x->fail(OCTEN_EINVAL, "octen_append: need X_new, W_new and 1 <= t <= %d",
+                   (int)chunk_slices(x));
+  const octen_config &c = x->cfg;
+  const int Qd = x->Qd;
+  if (!ensure_c_capacity(x, x->K + t)) return x->fail(OCTEN_ENOMEM, "C");
+  const size_t cs = (size_t)Qd * c.R + t * c.R + t * Qd + t * t;
+  if (!x->grow(x->Wbuf, cs * sizeof(float))) return x->fail(OCTEN_ENOMEM, "C solve scratch");
+  octen_status s = compress_scratch(x, t);
+  if (s != OCTEN_OK) return s;
+  const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
+  if (!is_device_ptr(X_new) && !x->grow(x->stage[2], t * slice))
+    return x->fail(OCTEN_ENOMEM, "staging the batch");
+  if (!is_device_ptr(W_new) && !x->grow(x->stage[1], (size_t)t * Qd * 4))
+    return x->fail(OCTEN_ENOMEM, "staging W_new");
+  return OCTEN_OK;
+}
+
+// The head of a prepared append on x->st: the batch's W rows into Wfix, the
+// quantisation (fp8) and the mode-2 contraction.
+octen_status append_head(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
+  const octen_config &c = x->cfg;
+  const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
+  const float *Wd = static_cast<const float *>(x->stage_in(W_new, (size_t)t * x->Qd * 4, 1));
+  if (!Wd) return x->fail(OCTEN_ECUDA, "staging W_new");
+  cudaMemcpyAsync(x->Wfix, Wd, (size_t)t * x->Qd * sizeof(float), cudaMemcpyDeviceToDevice,
+                  x->st);
+  if (host_pieces(x, X_new, t)) return compress_mode2_host(x, X_new, t);
+  const void *Xd = x->stage_in(X_new, t * slice, 2);
+  if (!Xd) return x->fail(OCTEN_ECUDA, "staging the batch");
+  compress_mode2(x, Xd, 0, t);
+  return OCTEN_OK;
+}
+
+// Enqueues one prepared append on the context's stream (no final
+// synchronisation; K is advanced by the caller once the stream has finished
+// without error): the head, then the rest of the update (Y_p += Z_p, CP of
+// every summary, anchor match, lift of A and B, the new rows of C and the
+// G_p update), then the new rows into C.
+octen_status append_launch(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
+  octen_status s = append_head(x, X_new, t, W_new);
+  if (s != OCTEN_OK) return s;
+  tail_enqueue(x, t);
+  cudaMemcpyAsync(x->C + x->K * x->cfg.R, x->Cnew_fix, (size_t)t * x->cfg.R * sizeof(float),
+                  cudaMemcpyDeviceToDevice, x->st);
   ++x->appends;
   return OCTEN_OK;
+}
+
+octen_status append_enqueue(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
+  const octen_status s = append_prepare(x, X_new, t, W_new);
+  return s != OCTEN_OK ? s : append_launch(x, X_new, t, W_new);
+}
+
+// The recorded tail of a t-slice append, if there is one.
+octen_ctx::TailGraph *find_tail(octen_ctx *x, int64_t t) {
+  for (octen_ctx::TailGraph &g : x->tails)
+    if (g.exec && g.graph && g.t == t) return &g;
+  return nullptr;
+}
+
+// The head of a prepared append of device arrays recorded as a graph on the
+// context's capture stream (nullptr on failure).  Its kernels are not
+// counted: they run when the step graph runs.
+cudaGraph_t capture_head(octen_ctx *x, const void *X, int64_t t, const float *W,
+                         int64_t &launches, int64_t &tc) {
+  if (!x->cap_st && cudaStreamCreateWithFlags(&x->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    x->cap_st = nullptr;
+    return nullptr;
+  }
+  const uint64_t l0 = octen_launch_count(), t0 = octen_tc_launch_count();
+  if (cudaStreamBeginCapture(x->cap_st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaStream_t home = x->st;
+  x->st = x->cap_st;
+  const octen_status s = append_head(x, X, t, W);
+  x->st = home;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(x->cap_st, &g);
+  launches = (int64_t)(octen_launch_count() - l0);
+  tc = (int64_t)(octen_tc_launch_count() - t0);
+  adjust_launch_counts(-launches, -tc);
+  if (s != OCTEN_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return nullptr;
+  }
+  return g;
+}
+
+// One step of octen_append_many as a single graph launch (see
+// octen_ctx::StepGraph), after every context has been prepared.  Returns false,
+// with nothing enqueued, when the step does not qualify (a context timing its
+// stages or without graphs, host arrays, a context given twice, a batch size
+// without a recorded tail) or the graph cannot be built; the caller then
+// enqueues the appends one by one.
+bool step_graph_launch(octen_ctx *const *ctxs, int n, const void *const *X, const int64_t *t,
+                       const float *const *W) {
+  octen_ctx *L = ctxs[0];
+  std::vector<int64_t> key;
+  key.reserve(3 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    octen_ctx *x = ctxs[i];
+    if (x->timing || !x->use_graph || !is_device_ptr(X[i]) || !is_device_ptr(W[i]) ||
+        !find_tail(x, t[i]))
+      return false;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == x) return false;
+    key.push_back((int64_t)x->id);
+    key.push_back((int64_t)x->gen);
+    key.push_back(t[i]);
+  }
+  for (int i = 0; i < n; ++i) {
+    octen_ctx *x = ctxs[i];
+    if ((!x->step_ev && cudaEventCreateWithFlags(&x->step_ev, cudaEventDisableTiming) != cudaSuccess) ||
+        (!x->step_done &&
+         cudaEventCreateWithFlags(&x->step_done, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  int64_t head_l = 0, head_tc = 0;
+  bool fresh = L->step.exec == nullptr || L->step.key != key;
+  if (!fresh) {
+    // same contexts and shapes: new slices into the heads, new row offsets
+    // into the C copies
+    for (int i = 0; i < n && !fresh; ++i) {
+      octen_ctx *x = ctxs[i];
+      int64_t hl = 0, htc = 0;
+      cudaGraph_t hg = capture_head(x, X[i], t[i], W[i], hl, htc);
+      const bool ok =
+          hg && cudaGraphExecChildGraphNodeSetParams(L->step.exec, L->step.head[i], hg) ==
+                    cudaSuccess &&
+          cudaGraphExecMemcpyNodeSetParams1D(
+              L->step.exec, L->step.cmem[i], x->C + x->K * x->cfg.R, x->Cnew_fix,
+              (size_t)t[i] * x->cfg.R * sizeof(float), cudaMemcpyDeviceToDevice) == cudaSuccess;
+      if (hg) cudaGraphDestroy(hg);
+      if (!ok) {
+        cudaGetLastError();
+        fresh = true;
+      }
+      head_l += hl;
+      head_tc += htc;
+    }
+  }
+  if (fresh) {
+    L->drop_step();
+    head_l = head_tc = 0;
+    cudaGraph_t sg = nullptr;
+    if (cudaGraphCreate(&sg, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    bool ok = true;
+    octen_ctx::StepGraph st;
+    for (int i = 0; i < n && ok; ++i) {
+      octen_ctx *x = ctxs[i];
+      int64_t hl = 0, htc = 0;
+      cudaGraph_t hg = capture_head(x, X[i], t[i], W[i], hl, htc);
+      octen_ctx::TailGraph *tg = find_tail(x, t[i]);
+      cudaGraphNode_t hn = nullptr, tn = nullptr, cn = nullptr;
+      ok = hg && tg && cudaGraphAddChildGraphNode(&hn, sg, nullptr, 0, hg) == cudaSuccess &&
+           cudaGraphAddChildGraphNode(&tn, sg, &hn, 1, tg->graph) == cudaSuccess &&
+           cudaGraphAddMemcpyNode1D(&cn, sg, &tn, 1, x->C + x->K * x->cfg.R, x->Cnew_fix,
+                                    (size_t)t[i] * x->cfg.R * sizeof(float),
+                                    cudaMemcpyDeviceToDevice) == cudaSuccess;
+      if (hg) cudaGraphDestroy(hg);
+      if (ok) {
+        st.head.push_back(hn);
+        st.cmem.push_back(cn);
+        st.launches += tg->launches;
+        st.tc += tg->tc;
+        head_l += hl;
+        head_tc += htc;
+      }
+    }
+    if (ok && cudaGraphInstantiate(&st.exec, sg, 0) != cudaSuccess) {
+      st.exec = nullptr;
+      ok = false;
+    }
+    if (!ok) {
+      cudaGraphDestroy(sg);
+      cudaGetLastError();
+      return false;
+    }
+    st.graph = sg;
+    st.key = key;
+    L->step = std::move(st);
+  }
+  // after the work already on every context's stream; before its next work
+  for (int i = 0; i < n; ++i) {
+    cudaEventRecord(ctxs[i]->step_ev, ctxs[i]->st);
+    cudaStreamWaitEvent(L->st, ctxs[i]->step_ev, 0);
+  }
+  if (cudaGraphLaunch(L->step.exec, L->st) != cudaSuccess) {
+    cudaGetLastError();
+    L->drop_step();
+    return false;
+  }
+  cudaEventRecord(L->step_done, L->st);
+  for (int i = 0; i < n; ++i) {
+    if (ctxs[i] != L) cudaStreamWaitEvent(ctxs[i]->st, L->step_done, 0);
+    ++ctxs[i]->appends;
+  }
+  adjust_launch_counts(L->step.launches + head_l, L->step.tc + head_tc);
+  return true;
 }
 
 // After a failed enqueue: nothing the call issued may still read the caller's
@@ -838,13 +1184,25 @@ octen_status octen_append_many(octen_ctx *const *ctxs, int n, const void *const 
                                const int64_t *t, const float *const *W_new) {
   if (!ctxs || !X_new || !t || !W_new || n < 1) return OCTEN_EINVAL;
   octen_status first = OCTEN_OK;
-  std::vector<char> enqueued(n, 0);
+  std::vector<char> ready(n, 0), enqueued(n, 0);
   for (int i = 0; i < n; ++i) {
-    const octen_status s = append_enqueue(ctxs[i], X_new[i], t[i], W_new[i]);
-    enqueued[i] = s == OCTEN_OK;
-    if (s != OCTEN_OK) {
-      drain(ctxs[i]);
-      if (first == OCTEN_OK) first = s;
+    const octen_status s = append_prepare(ctxs[i], X_new[i], t[i], W_new[i]);
+    ready[i] = s == OCTEN_OK;
+    if (s != OCTEN_OK && first == OCTEN_OK) first = s;
+  }
+  // every context prepared: the whole step as one graph launch when it qualifies
+  bool all = first == OCTEN_OK;
+  if (all && step_graph_launch(ctxs, n, X_new, t, W_new)) {
+    for (int i = 0; i < n; ++i) enqueued[i] = 1;
+  } else {
+    for (int i = 0; i < n; ++i) {
+      if (!ready[i]) continue;
+      const octen_status s = append_launch(ctxs[i], X_new[i], t[i], W_new[i]);
+      enqueued[i] = s == OCTEN_OK;
+      if (s != OCTEN_OK) {
+        drain(ctxs[i]);
+        if (first == OCTEN_OK) first = s;
+      }
     }
   }
   for (int i = 0; i < n; ++i) {

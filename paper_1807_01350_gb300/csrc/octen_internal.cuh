@@ -128,6 +128,9 @@ struct TcStoreArgs {
   // 128-byte K atoms per pipeline stage: 2 halves the barrier round trips and
   // commits per byte for the narrow (N = 32) GEMMs
   int katoms = 1;
+  // at most this many CTAs (0: one per SM), so that another GEMM can run on
+  // the other SMs at the same time
+  int max_ctas = 0;
 };
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st);
 // the split count tc_gemm_store will use
@@ -158,6 +161,7 @@ void quantize_e4m3(const __nv_bfloat16 *X, int64_t t, int64_t IJ, __nv_fp8_e4m3 
 // (RT = R rounded up to 8, padded columns zero).
 // ---------------------------------------------------------------------------
 constexpr int kAlsNP = 32;   // padded rank rows of the tensor-core ALS operands
+constexpr int kMaxAlsGroups = 4;   // replica groups of the tensor-core CP-ALS
 
 struct AlsBuffers {
   float *Af, *Bf, *Cf;   // current factors, P x Q x RT
@@ -181,6 +185,30 @@ struct AlsBuffers {
   cudaStream_t side = nullptr;                  // non-blocking
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   float *L = nullptr;                           // P x als_factor_floats(RT)
+  // GEMM grid cap of this group's passes (0: one CTA per SM)
+  int max_ctas = 0;
+  // Q not a multiple of 8 (Q >= 32): the tensor-core passes run on X_p
+  // zero-padded to Qp = the next multiple of 8 (the TMA row pitch of the bf16
+  // copies), with factors Af_pad, Bf_pad, Cf_pad (P x Qp x RT, the rows past Q
+  // zero, and zero after every update since their MTTKRP rows are zero), and
+  // Xa, Xc, Ct, Bt, Mparts, M and the bf16 Tc sized for Qp.  0: no padding.
+  int Qp = 0;
+  float *Af_pad = nullptr, *Bf_pad = nullptr, *Cf_pad = nullptr;
+  // Replica groups (tensor-core path, 32 <= Q): the replicas are split into
+  // `groups` contiguous groups whose sweeps run as independent chains, group g
+  // on gst[g] (group 0 on the caller's stream) with its factor kernels on
+  // gside[g], each GEMM on at most SMs / groups CTAs, so that one group's
+  // solves and reductions overlap another group's GEMMs.  Per replica the
+  // arithmetic is the same as with one group.
+  int groups = 1;
+  cudaStream_t gst[kMaxAlsGroups] = {}, gside[kMaxAlsGroups] = {};
+  cudaEvent_t gev_fork[kMaxAlsGroups] = {}, gev_join[kMaxAlsGroups] = {};
+  cudaEvent_t gsplit = nullptr, gdone[kMaxAlsGroups] = {};
+  // staggered start: group g's first launch waits for group g - 1's first
+  // GEMM (gfirst[g - 1]), so that the groups' GEMMs and solves alternate
+  // instead of running in lockstep
+  cudaEvent_t gfirst[kMaxAlsGroups] = {};
+  cudaEvent_t wait_first = nullptr, ev_first = nullptr;   // per group, set by the runner
 };
 int als_factor_floats(int RT);
 // Returns false if a tensor-core launch was refused (the caller then reruns

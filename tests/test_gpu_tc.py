@@ -181,3 +181,55 @@ def test_host_batches_copied_in_pieces_equal_device_batches(pkg, prec):
     for a, b in zip(*out):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("Q", [32, 40])
+def test_replica_groups_give_bit_identical_results(pkg, Q, monkeypatch):
+    """The tensor-core CP-ALS run as independent chains over groups of
+    replicas (OCTEN_ALS_GROUPS, each group's GEMMs on a share of the SMs)
+    gives the single chain's results bit for bit: per replica the launches
+    and their summation order are the same.  Q = 40 takes the segmented
+    partial sums (32 does not divide Q); three appends cover the eager first
+    append and the graph replays."""
+    from tests.test_gpu_parity import run_gpu
+
+    case = Case(160, 144, 6, 5, Q, 8, 24, (16, 8, 16), 10, prec="bf16", seed=28)
+    d = case.make()
+    runs = {}
+    for groups in ("1", "2", "3"):
+        monkeypatch.setenv("OCTEN_ALS_GROUPS", groups)
+        g, states = run_gpu(pkg, case, d)
+        g.close()
+        runs[groups] = states
+    for groups in ("2", "3"):
+        for a, b in zip(runs["1"], runs[groups]):
+            for key in ("Y", "A", "B", "C"):
+                assert np.array_equal(a[key], b[key]), (groups, key)
+            for u, v in zip(a["raw"], b["raw"]):
+                assert np.array_equal(u, v), groups
+
+
+@pytest.mark.parametrize("Q", [36, 45])
+def test_padded_replicas_run_the_tensor_core_als(pkg, Q, monkeypatch):
+    """Q not a multiple of 8 (the bf16 row pitch the TMA loads need): the
+    replica CP-ALS runs on tcgen05 with X_p zero-padded to the next multiple
+    of 8, and the update matches the oracle at the bf16 tolerances and the
+    SIMT path (OCTEN_GEMM=simt) closely."""
+    from tests.test_gpu_parity import check_update, run_gpu
+
+    case = Case(160, 144, 6, 3, Q, 6, 24, (16, 8), 10, prec="bf16", seed=29)
+    d = case.make()
+    _, ref = case.oracle_run(d)
+    n0 = pkg.tc_launch_count()
+    g, tc = run_gpu(pkg, case, d)
+    g.close()
+    # per append: mode 2, mode 1, and two GEMMs per sweep plus the final C update
+    assert pkg.tc_launch_count() - n0 >= len(case.batches) * (2 + 2 * case.iters + 1)
+    check_update(case, d, tc, ref)
+    monkeypatch.setenv("OCTEN_GEMM", "simt")
+    h, simt = run_gpu(pkg, case, d)
+    h.close()
+    for a, b in zip(tc, simt):
+        assert abs(a["fit"] - b["fit"]) < 1e-3
+        for key in ("A", "B", "C"):
+            assert rel(a[key], b[key]) < 5e-2, key
