@@ -2,6 +2,8 @@
 // layout/precision conversion of the projection matrices, per-slice e4m3
 // quantisation of the slice batch, and the time-mode contraction fused with the
 // summary update X_p = Y_p + Z_p (Eq. 2, Algorithm 1's second step).
+#include <cstdlib>
+
 #include "octen_internal.cuh"
 
 namespace octen {
@@ -165,9 +167,8 @@ __global__ void __launch_bounds__(256)
 // With Xa / Xc given it also writes the bf16 copies of the updated X_p that
 // the tensor-core CP-ALS reads, Xa[p][(a,b)][c] and Xc[p][c][(a,b)] (the
 // latter through a [c][row] block in shared memory, 16-byte stores).
-constexpr int kRG = 8;
-
-__global__ void __launch_bounds__(256)
+template <int kRG>
+__global__ void __launch_bounds__(256, kRG == 4 ? 3 : 2)
     mode3_stream_kernel(const float *__restrict__ T2, const float *__restrict__ W,
                         float *__restrict__ Y, int t, int Q, int S, int Qd,
                         __nv_bfloat16 *__restrict__ Xa, __nv_bfloat16 *__restrict__ Xc) {
@@ -264,34 +265,53 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Rows of Y per thread of the streaming mode-3 kernel: 8, or 4
+// (OCTEN_MODE3_ROWS=4: half the registers, twice the resident CTAs).  Every
+// element's arithmetic is the same either way.
+static int mode3_rows() {
+  const char *v = getenv("OCTEN_MODE3_ROWS");
+  return v && v[0] == '4' ? 4 : 8;
+}
+
+template <int RG>
+static bool mode3_stream(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
+                         int S, int Qd, cudaStream_t st, __nv_bfloat16 *Xa,
+                         __nv_bfloat16 *Xc) {
+  const int64_t QQ = (int64_t)Q * Q;
+  const int tp = (int)((t + 3) & ~int64_t(3));
+  const int ncg = Q / 4;
+  const int lanes = 256 / ncg;
+  const int rows_blk = lanes * RG;
+  const bool layouts = Xa != nullptr && Xc != nullptr;
+  const size_t smem = ((size_t)tp * Q + (size_t)rows_blk * tp) * sizeof(float) +
+                      (layouts ? (size_t)Q * (rows_blk + 1) * sizeof(__nv_bfloat16) : 0);
+  if (smem > 200 * 1024) return false;
+  cudaFuncSetAttribute(mode3_stream_kernel<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       200 * 1024);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mode3_stream_kernel<RG>, 256, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t nblk = (QQ + rows_blk - 1) / rows_blk;
+  int64_t gx = ((int64_t)sms * per_sm + P - 1) / P;   // one wave over all replicas
+  if (gx > nblk) gx = nblk;
+  if (gx < 1) gx = 1;
+  mode3_stream_kernel<RG><<<dim3((unsigned)gx, P), 256, smem, st>>>(
+      T2, W, Y, (int)t, Q, S, Qd, layouts ? Xa : nullptr, layouts ? Xc : nullptr);
+  count_launch();
+  return true;
+}
+
 bool mode3_accumulate(const float *T2, const float *W, float *Y, int64_t t, int P, int Q,
                       int S, int Qd, cudaStream_t st, __nv_bfloat16 *Xa, __nv_bfloat16 *Xc) {
   const int64_t QQ = (int64_t)Q * Q;
   if (Q % 4 == 0 && Q <= 1024) {
-    const int tp = (int)((t + 3) & ~int64_t(3));
-    const int ncg = Q / 4;
-    const int lanes = 256 / ncg;
-    const int rows_blk = lanes * kRG;
     const bool layouts = Xa != nullptr && Xc != nullptr;
-    const size_t smem = ((size_t)tp * Q + (size_t)rows_blk * tp) * sizeof(float) +
-                        (layouts ? (size_t)Q * (rows_blk + 1) * sizeof(__nv_bfloat16) : 0);
-    if (smem <= 200 * 1024) {
-      cudaFuncSetAttribute(mode3_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           200 * 1024);
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mode3_stream_kernel, 256, smem);
-      if (per_sm < 1) per_sm = 1;
-      const int64_t nblk = (QQ + rows_blk - 1) / rows_blk;
-      int64_t gx = ((int64_t)sms * per_sm + P - 1) / P;   // one wave over all replicas
-      if (gx > nblk) gx = nblk;
-      if (gx < 1) gx = 1;
-      mode3_stream_kernel<<<dim3((unsigned)gx, P), 256, smem, st>>>(
-          T2, W, Y, (int)t, Q, S, Qd, layouts ? Xa : nullptr, layouts ? Xc : nullptr);
-      count_launch();
-      return layouts;
-    }
+    const bool ran = mode3_rows() == 4
+                         ? mode3_stream<4>(T2, W, Y, t, P, Q, S, Qd, st, Xa, Xc)
+                         : mode3_stream<8>(T2, W, Y, t, P, Q, S, Qd, st, Xa, Xc);
+    if (ran) return layouts;
   }
   const size_t smem = ((size_t)t * Q + (size_t)t * kRows) * sizeof(float);
   cudaFuncSetAttribute(mode3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -82,6 +82,10 @@ struct octen_ctx {
   int als_ks = 1;
   int als_qp = 0;
   float *Apad = nullptr, *Bpad = nullptr, *Cpad = nullptr;
+  // CTAs of the replica-ALS GEMMs (0: one per SM).  octen_append_many gives
+  // each of its contexts a share of the SMs, so that the GEMMs of several
+  // contexts run side by side instead of one after another.
+  int als_ctas = 0;
   __nv_bfloat16 *Xa = nullptr, *Xc = nullptr, *KR = nullptr, *Ctb = nullptr, *Btb = nullptr;
   float *Mparts = nullptr;
   // replica CP-ALS: the factor of each update runs on als_side beside its MTTKRP
@@ -810,6 +814,7 @@ AlsBuffers als_buffers(octen_ctx *x) {
   }
   ab.gsplit = x->grp_split;
   ab.Qp = x->als_qp;
+  ab.max_ctas = x->als_ctas;
   ab.Af_pad = x->Apad; ab.Bf_pad = x->Bpad; ab.Cf_pad = x->Cpad;
   return ab;
 }
@@ -1185,6 +1190,25 @@ octen_status octen_append_many(octen_ctx *const *ctxs, int n, const void *const 
   if (!ctxs || !X_new || !t || !W_new || n < 1) return OCTEN_EINVAL;
   octen_status first = OCTEN_OK;
   std::vector<char> ready(n, 0), enqueued(n, 0);
+  // the ALS GEMMs of each context on a share of the SMs: 1 / min(n, 8) of
+  // them, or OCTEN_MANY_CTAS CTAs (0: all)
+  {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int share = n > 1 ? nsm / (n < 8 ? n : 8) : 0;
+    const char *v = getenv("OCTEN_MANY_CTAS");
+    if (v && *v) share = atoi(v);
+    if (share < 0 || share >= nsm) share = 0;
+    for (int i = 0; i < n; ++i) {
+      octen_ctx *x = ctxs[i];
+      if (x && x->als_ctas != share) {
+        x->als_ctas = share;
+        x->drop_graphs();   // recorded with the old grid
+        ++x->gen;
+      }
+    }
+  }
   for (int i = 0; i < n; ++i) {
     const octen_status s = append_prepare(ctxs[i], X_new[i], t[i], W_new[i]);
     ready[i] = s == OCTEN_OK;

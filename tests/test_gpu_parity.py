@@ -282,3 +282,48 @@ def test_init_decomposition_matches_oracle(pkg, prec):
     assert abs(g.fit(slices(d["X"][:k + 10], case.prec))
                - oracle.fit(d["X"][:k + 10], o.A, o.B, o.C)) < tol["fit"]
     g.close()
+
+
+def test_append_many_steps_as_one_graph_equal_single_appends(pkg):
+    """Four octen_append_many steps over uneven streams (small replicas on the
+    single-launch CP-ALS, Q = 40 on the tensor cores, Q = 36 zero-padded to 40):
+    once every stream has a recorded tail (from the third step) a step is one
+    graph launch, with each context's ALS GEMMs on a share of the SMs.  Every
+    stream equals the same appends made one by one with octen_append, bit for
+    bit, and its launches are counted."""
+    cases = [Case(96, 80, 4, 3, 20, 4, 8, (6,) * 4, 6, prec="bf16", seed=130),
+             Case(160, 144, 6, 3, 40, 6, 8, (8,) * 4, 6, prec="bf16", seed=131),
+             Case(128, 112, 5, 2, 36, 5, 8, (5,) * 4, 6, prec="bf16", seed=132)]
+    datas = [c.make() for c in cases]
+    streams = [torch.cuda.Stream() for _ in cases]
+
+    def start(case, d, stream):
+        g = pkg.Octen(case.I, case.J, case.R, case.P, case.Q, case.S, case.iters, case.prec,
+                      stream=stream)
+        g.init(slices(d["X"][:case.t_old], case.prec), dev(d["U"]), dev(d["V"]), dev(d["W"][0]),
+               dev(d["A0"]), dev(d["B0"]), dev(d["C0"]))
+        return g
+
+    def batch(c, d, b):
+        k = c.t_old + sum(c.batches[:b])
+        return slices(d["X"][k:k + c.batches[b]], c.prec), dev(d["W"][b + 1])
+
+    many = [start(c, d, s) for c, d, s in zip(cases, datas, streams)]
+    counts = []
+    for b in range(4):
+        xs, ws = zip(*[batch(c, d, b) for c, d in zip(cases, datas)])
+        n0 = pkg.launch_count()
+        pkg.append_many(many, list(xs), list(ws))
+        counts.append(pkg.launch_count() - n0)
+    # the graph steps run (and count) the same kernels as the eager ones
+    assert counts[2] == counts[3] and counts[3] > 0
+    for c, d, g in zip(cases, datas, many):
+        single = start(c, d, None)
+        for b in range(4):
+            single.append(*batch(c, d, b))
+        assert g.rows == single.rows == c.t_old + sum(c.batches)
+        for a, s in zip(g.factors(), single.factors()):
+            assert np.array_equal(a, s)
+        assert np.array_equal(g.replicas(), single.replicas())
+        single.close()
+        g.close()
