@@ -121,6 +121,30 @@ octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
  * returns. */
 octen_status octen_append(octen_ctx *ctx, const void *X_new, int64_t t, const float *W_new);
 
+/* octen_append without waiting for it: the append is enqueued on the
+ * context's stream and the call returns at once with a ticket for it (not in
+ * the paper: a serving interface, so that the host-to-device copy of the next
+ * batch overlaps the update of this one).  Arguments as in octen_append; the
+ * caller keeps X_new and W_new unchanged until octen_wait of the ticket has
+ * returned.  A_out (I x R), B_out (J x R) and C_new_out (t x R), each may be
+ * NULL, receive the factors after this append and its new rows of C once it
+ * has run (pinned host memory keeps the copies asynchronous).  Host slices
+ * are copied in pieces into one of two staging buffers used in turn, so the
+ * copy of a batch waits only for the mode-2 contraction of the append two
+ * before it.  At most 8 appends are in flight: a ninth waits for the oldest
+ * first.  K advances when the append is enqueued.  EINVAL, ESTATE and ENOMEM
+ * are returned before anything is enqueued, as in octen_append; device-side
+ * failures (ENUMERIC, ETIMEOUT) are returned by octen_wait, after which the
+ * context is to be discarded or restored from a checkpoint. */
+octen_status octen_append_async(octen_ctx *ctx, const void *X_new, int64_t t,
+                                const float *W_new, float *A_out, float *B_out,
+                                float *C_new_out, int64_t *ticket);
+
+/* Waits until the append of `ticket` (and every one before it) has run and
+ * returns its status (OK for a ticket already waited for; EINVAL for a ticket
+ * not issued).  Not in the paper (see octen_append_async). */
+octen_status octen_wait(octen_ctx *ctx, int64_t ticket);
+
 /* One append on each of n independent decompositions (many streams with
  * uneven shapes, ranks and batch sizes): the work of every context is enqueued
  * on that context's own stream before any of them is waited for, so streams

@@ -65,6 +65,9 @@ def lib() -> ctypes.CDLL:
         L.octen_init.argtypes = [vp, vp, i64, f32p, f32p, f32p, f32p, f32p, f32p]
         L.octen_append.argtypes = [vp, vp, i64, f32p]
         L.octen_append_many.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.octen_append_async.argtypes = [vp, vp, i64, f32p, f32p, f32p, f32p,
+                                         ctypes.POINTER(i64)]
+        L.octen_wait.argtypes = [vp, i64]
         L.octen_get_factors.argtypes = [vp, f32p, f32p, f32p, ctypes.POINTER(i64)]
         L.octen_rows.argtypes = [vp]
         L.octen_rows.restype = i64
@@ -122,6 +125,7 @@ def lib() -> ctypes.CDLL:
                      "octen_n_save", "octen_n_load"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("octen_create", "octen_init", "octen_append", "octen_append_many",
+                     "octen_append_async", "octen_wait",
                      "octen_get_factors",
                      "octen_fit", "octen_get_replicas", "octen_get_replica_factors",
                      "octen_compress", "octen_compress_noalloc", "octen_set_timing",
@@ -192,6 +196,20 @@ def _out(a, count: int, what: str):
         ok = a.dtype == torch.float32 and a.is_contiguous()
     if not ok:
         raise OctenError(1, f"{what}: must be a contiguous, writable float32 array")
+
+
+def _as_is(a, dtype: str, what: str):
+    """An array the library reads after the call returns: it must be passed
+    as it is (contiguous, of the element type the library reads), since a
+    converted copy would be freed before the library reads it."""
+    if isinstance(a, np.ndarray):
+        ok = a.dtype == np.dtype(dtype) if dtype != "bfloat16" else False
+        ok = ok and a.flags["C_CONTIGUOUS"]
+    else:
+        import torch
+        ok = a.dtype == getattr(torch, dtype) and a.is_contiguous()
+    if not ok:
+        raise OctenError(1, f"{what}: must be a contiguous {dtype} array")
 
 
 def _f32(a, keep: list):
@@ -265,6 +283,34 @@ class Octen:
     def append_ptr(self, x_ptr: int, t: int, w_ptr: int):
         """Append from raw pointers (device or host) already in the right types."""
         self._check(self._lib.octen_append(self._h, x_ptr, int(t), w_ptr))
+
+    def append_async(self, X_new, W_new, A_out=None, B_out=None, C_new_out=None) -> int:
+        """octen_append_async: enqueue an append and return its ticket.  X_new
+        must already be in the precision's element type (fp32, or bf16 for the
+        bf16 / fp8 modes) and stay alive and unchanged, with W_new, until
+        wait(ticket); the optional fp32 outputs receive A, B and the new rows
+        of C once the append has run."""
+        t = int(X_new.shape[0])
+        _need(X_new, t * self.I * self.J, "X_new")
+        _need(W_new, t * self.Qd, "W_new")
+        _as_is(X_new, "float32" if self.prec == "fp32" else "bfloat16", "X_new")
+        _as_is(W_new, "float32", "W_new")
+        _out(A_out, self.I * self.R, "A_out")
+        _out(B_out, self.J * self.R, "B_out")
+        _out(C_new_out, t * self.R, "C_new_out")
+        return self.append_async_ptr(_ptr(X_new, []), t, _ptr(W_new, []), _ptr(A_out, []),
+                                     _ptr(B_out, []), _ptr(C_new_out, []))
+
+    def append_async_ptr(self, x_ptr, t, w_ptr, a_ptr=None, b_ptr=None, c_ptr=None) -> int:
+        """octen_append_async from raw pointers; returns the ticket."""
+        tk = ctypes.c_int64()
+        self._check(self._lib.octen_append_async(self._h, x_ptr, int(t), w_ptr, a_ptr, b_ptr,
+                                                 c_ptr, ctypes.byref(tk)))
+        return int(tk.value)
+
+    def wait(self, ticket: int):
+        """octen_wait: block until the append of `ticket` has run."""
+        self._check(self._lib.octen_wait(self._h, int(ticket)))
 
     @property
     def rows(self) -> int:

@@ -165,10 +165,24 @@ struct octen_ctx {
   DevBuf Tbuf, T2buf, Wbuf, X8buf, xscale, stage[4], fitpart;
 
   // host slices of an append are copied in chunks on copy_st, so that the
-  // mode-2 contraction of one chunk runs while the next is in flight
+  // mode-2 contraction of one chunk runs while the next is in flight.  Two
+  // staging slots are used in turn, each free again once the mode-2
+  // contraction of the append that filled it has run (xslot_free), so that
+  // the copy of a batch need not wait for the rest of the previous append.
   static constexpr int kCopyChunks = 8;
   cudaStream_t copy_st = nullptr;
   cudaEvent_t copy_ev[kCopyChunks] = {}, copy_ready = nullptr;
+  DevBuf xstage[2];
+  cudaEvent_t xslot_free[2] = {};
+  int xslot = 0;
+
+  // appends enqueued without waiting (octen_append_async / octen_wait): a
+  // ring of tickets, each with the event recorded after its append and the
+  // device status word copied to pinned host memory just before it
+  static constexpr int kTickets = 8;
+  cudaEvent_t ticket_ev[kTickets] = {};
+  int *ticket_status = nullptr;              // pinned, kTickets
+  int64_t next_ticket = 0, done_ticket = 0;  // issued; known complete
 
   // stage timers (CUDA events on the context's stream)
   bool timing = false;
@@ -246,8 +260,13 @@ struct octen_ctx {
     if (copy_ready) cudaEventDestroy(copy_ready);
     for (auto &b : owned) cudaFree(b.p);
     DevBuf *extra[] = {&Tbuf, &T2buf, &Wbuf, &X8buf, &xscale, &stage[0], &stage[1], &stage[2],
-                       &stage[3], &fitpart};
+                       &stage[3], &fitpart, &xstage[0], &xstage[1]};
     for (DevBuf *b : extra) cudaFree(b->p);
+    for (cudaEvent_t e : xslot_free)
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ticket_ev)
+      if (e) cudaEventDestroy(e);
+    if (ticket_status) cudaFreeHost(ticket_status);
   }
 
   octen_status fail(octen_status s, const char *fmt, ...) {
@@ -504,15 +523,15 @@ octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float
 octen_status compress_mode2_host(octen_ctx *x, const void *Xh, int64_t t) {
   const octen_config &c = x->cfg;
   const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
-  // the staging slot is free once the stream's earlier work is done
-  cudaEventRecord(x->copy_ready, x->st);
-  cudaStreamWaitEvent(x->copy_st, x->copy_ready, 0);
+  // the slot is free once the mode-2 contraction of its previous batch has run
+  DevBuf &stg = x->xstage[x->xslot];
+  cudaStreamWaitEvent(x->copy_st, x->xslot_free[x->xslot], 0);
   const int64_t per = (t + octen_ctx::kCopyChunks - 1) / octen_ctx::kCopyChunks;
   const int64_t step = per < 2 ? 2 : per;
   int nc = 0;
   for (int64_t k0 = 0; k0 < t; k0 += step, ++nc) {
     const int64_t n = t - k0 < step ? t - k0 : step;
-    if (cudaMemcpyAsync(static_cast<char *>(x->stage[2].p) + k0 * slice,
+    if (cudaMemcpyAsync(static_cast<char *>(stg.p) + k0 * slice,
                         static_cast<const char *>(Xh) + k0 * slice, n * slice,
                         cudaMemcpyHostToDevice, x->copy_st) != cudaSuccess) {
       cudaStreamSynchronize(x->copy_st);   // no copy of the caller's buffer stays in flight
@@ -524,8 +543,10 @@ octen_status compress_mode2_host(octen_ctx *x, const void *Xh, int64_t t) {
   for (int64_t k0 = 0; k0 < t; k0 += step, ++nc) {
     const int64_t n = t - k0 < step ? t - k0 : step;
     cudaStreamWaitEvent(x->st, x->copy_ev[nc], 0);
-    compress_mode2(x, x->stage[2].p, k0, n);
+    compress_mode2(x, stg.p, k0, n);
   }
+  cudaEventRecord(x->xslot_free[x->xslot], x->st);
+  x->xslot ^= 1;
   return OCTEN_OK;
 }
 
@@ -670,6 +691,13 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
          cudaEventCreateWithFlags(&x->copy_ready, cudaEventDisableTiming) == cudaSuccess;
     for (cudaEvent_t &e : x->copy_ev)
       ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    for (cudaEvent_t &e : x->xslot_free)
+      ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    for (cudaEvent_t &e : x->ticket_ev)
+      ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaHostAlloc(reinterpret_cast<void **>(&x->ticket_status),
+                             octen_ctx::kTickets * sizeof(int), cudaHostAllocDefault) ==
+                   cudaSuccess;
   }
   if (ok) {
     ok = cudaStreamCreateWithFlags(&x->als_side, cudaStreamNonBlocking) == cudaSuccess &&
@@ -960,8 +988,12 @@ octen_status append_prepare(octen_ctx *x, const void *X_new, int64_t t, const fl
   octen_status s = compress_scratch(x, t);
   if (s != OCTEN_OK) return s;
   const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
-  if (!is_device_ptr(X_new) && !x->grow(x->stage[2], t * slice))
+  if (host_pieces(x, X_new, t)) {
+    if (!x->grow(x->xstage[x->xslot], t * slice))
+      return x->fail(OCTEN_ENOMEM, "staging the batch");
+  } else if (!is_device_ptr(X_new) && !x->grow(x->stage[2], t * slice)) {
     return x->fail(OCTEN_ENOMEM, "staging the batch");
+  }
   if (!is_device_ptr(W_new) && !x->grow(x->stage[1], (size_t)t * Qd * 4))
     return x->fail(OCTEN_ENOMEM, "staging W_new");
   return OCTEN_OK;
@@ -1180,8 +1212,51 @@ octen_status octen_append(octen_ctx *x, const void *X_new, int64_t t, const floa
     return s;
   }
   s = x->sync_check("append");
+  x->done_ticket = x->next_ticket;   // every asynchronous append before it has run too
   if (s != OCTEN_OK) return s;
   x->K += t;
+  return OCTEN_OK;
+}
+
+octen_status octen_wait(octen_ctx *x, int64_t ticket) {
+  if (!x || ticket < 0 || ticket >= x->next_ticket) return OCTEN_EINVAL;
+  if (ticket < x->done_ticket) return OCTEN_OK;
+  const int slot = (int)(ticket % octen_ctx::kTickets);
+  cudaError_t e = cudaEventSynchronize(x->ticket_ev[slot]);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return x->fail(OCTEN_ECUDA, "wait: %s", cudaGetErrorString(e));
+  const int flags = x->ticket_status[slot];
+  x->done_ticket = ticket + 1;
+  if (flags & kDevTimeout) return x->fail(OCTEN_ETIMEOUT, "append: a device wait ran out");
+  if (flags) return x->fail(OCTEN_ENUMERIC, "append: a Cholesky pivot was not positive");
+  return OCTEN_OK;
+}
+
+octen_status octen_append_async(octen_ctx *x, const void *X_new, int64_t t, const float *W_new,
+                                float *A_out, float *B_out, float *C_new_out,
+                                int64_t *ticket) {
+  if (!x || !ticket) return OCTEN_EINVAL;
+  // at most kTickets appends in flight: the oldest is waited for first
+  if (x->next_ticket - x->done_ticket >= octen_ctx::kTickets) {
+    const octen_status s = octen_wait(x, x->done_ticket);
+    if (s != OCTEN_OK) return s;
+  }
+  octen_status s = append_prepare(x, X_new, t, W_new);
+  if (s == OCTEN_OK) s = append_launch(x, X_new, t, W_new);
+  if (s != OCTEN_OK) {
+    drain(x);
+    return s;
+  }
+  const octen_config &c = x->cfg;
+  if (A_out) cudaMemcpyAsync(A_out, x->A, (size_t)c.I * c.R * 4, cudaMemcpyDefault, x->st);
+  if (B_out) cudaMemcpyAsync(B_out, x->B, (size_t)c.J * c.R * 4, cudaMemcpyDefault, x->st);
+  if (C_new_out)
+    cudaMemcpyAsync(C_new_out, x->C + x->K * c.R, (size_t)t * c.R * 4, cudaMemcpyDefault, x->st);
+  const int slot = (int)(x->next_ticket % octen_ctx::kTickets);
+  cudaMemcpyAsync(x->ticket_status + slot, x->dstatus, sizeof(int), cudaMemcpyDeviceToHost, x->st);
+  cudaEventRecord(x->ticket_ev[slot], x->st);
+  x->K += t;
+  *ticket = x->next_ticket++;
   return OCTEN_OK;
 }
 
