@@ -123,6 +123,97 @@ __global__ void unpad_kernel(const float *__restrict__ Fp, int64_t rows, int R, 
 
 unsigned blocks(int64_t n, int per = 256) { return (unsigned)((n + per - 1) / per); }
 
+// ---------------------------------------------------------------------------
+// N-way form (the higher-order extension, Sec. "Extending to Higher-Order
+// Tensors"): X_old is [k][i_1]...[i_nm], mode 0 the time mode k, mode m >= 1
+// the non-temporal mode i_m.  The mode-n MTTKRP
+//   M[i][r] = sum over every element with index i in mode n of
+//             x * prod_{m != n} F_m[index in mode m][r]
+// is one pass over X_old: CTA (i, split) walks the split's share of the
+// elements of row i (the other modes' indices decoded from one counter, the
+// innermost varying fastest, so a warp reads consecutive elements unless n
+// is the innermost mode), each thread accumulating RT sums; the CTA sums its
+// threads in a fixed order and a second kernel sums the splits in order.
+struct NDenseShape {
+  const float *F[kMaxNModes];   // factors, [rows][RT]
+  int64_t dim[kMaxNModes];      // extent of every mode (mode 0: time)
+  int64_t stride[kMaxNModes];   // element stride of every mode in X_old
+  int NN;
+};
+
+template <int RT>
+__global__ void __launch_bounds__(256)
+    nmttkrp_kernel(const float *__restrict__ X, const NDenseShape sh, int mode, int64_t per,
+                   float *__restrict__ part) {
+  __shared__ float red[8 * RT], out[RT];
+  const int64_t row = blockIdx.x;
+  const int split = blockIdx.y, nsplit = gridDim.y;
+  const int64_t others = [&] {
+    int64_t n = 1;
+    for (int m = 0; m < sh.NN; ++m)
+      if (m != mode) n *= sh.dim[m];
+    return n;
+  }();
+  const int64_t o0 = (int64_t)split * per;
+  const int64_t o1 = o0 + per < others ? o0 + per : others;
+  float acc[RT];
+#pragma unroll
+  for (int r = 0; r < RT; ++r) acc[r] = 0.f;
+  for (int64_t o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
+    int64_t rem = o, off = row * sh.stride[mode];
+    float w[RT];
+#pragma unroll
+    for (int r = 0; r < RT; ++r) w[r] = 1.f;
+    for (int m = sh.NN - 1; m >= 0; --m) {
+      if (m == mode) continue;
+      const int64_t idx = rem % sh.dim[m];
+      rem /= sh.dim[m];
+      off += idx * sh.stride[m];
+      const float4 *f = reinterpret_cast<const float4 *>(sh.F[m] + idx * RT);
+#pragma unroll
+      for (int r4 = 0; r4 < RT / 4; ++r4) {
+        const float4 v = __ldg(f + r4);
+        w[4 * r4] *= v.x; w[4 * r4 + 1] *= v.y; w[4 * r4 + 2] *= v.z; w[4 * r4 + 3] *= v.w;
+      }
+    }
+    const float x = __ldg(X + off);
+#pragma unroll
+    for (int r = 0; r < RT; ++r) acc[r] = fmaf(x, w[r], acc[r]);
+  }
+  block_sum_rows<RT>(acc, red, out);
+  if (threadIdx.x < RT) part[(row * nsplit + split) * RT + threadIdx.x] = out[threadIdx.x];
+}
+
+// M[row][r] = sum over the splits, in order
+template <int RT>
+__global__ void nsplit_sum_kernel(const float *__restrict__ part, int64_t rows, int nsplit,
+                                  float *__restrict__ M) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= rows * RT) return;
+  const int64_t row = e / RT;
+  const int r = (int)(e - row * RT);
+  float s = 0.f;
+  for (int k = 0; k < nsplit; ++k) s += part[(row * nsplit + k) * RT + r];
+  M[e] = s;
+}
+
+// out = elementwise product of the Grams of every mode but `skip1` and `skip2`
+// (RT x RT each; all ones if there is none)
+struct NGrams {
+  const float *G[kMaxNModes];
+};
+
+template <int RT>
+__global__ void gram_product_kernel(const NGrams g, int NN, int skip1, int skip2,
+                                    float *__restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= RT * RT) return;
+  float v = 1.f;
+  for (int m = 0; m < NN; ++m)
+    if (m != skip1 && m != skip2) v *= g.G[m][e];
+  out[e] = v;
+}
+
 template <int RT>
 struct DenseCp {
   const void *X;
@@ -237,7 +328,142 @@ void run_dense(const DenseCpArgs &a) {
   count_launch();
 }
 
+constexpr size_t kNSplitkFloats = size_t(1) << 20;   // Gram split-K scratch
+
+int64_t n_mpart_rows(int64_t maxdim) { return maxdim + 304; }
+
+// The N-way sweeps of the replica CP-ALS reading (time mode first, then every
+// non-temporal mode in order, normalised; a final time update), each update
+// F_n = M_n (Hadamard product of the other modes' Grams)^-1 with the fp64
+// L D L^T of the replica solve.
+template <int RT>
+struct DenseCpN {
+  const float *X;
+  int NN, R;
+  int64_t dim[kMaxNModes], stride[kMaxNModes], total;
+  float *F[kMaxNModes], *G[kMaxNModes];
+  float *M, *Hp, *L, *part, *mpart, *splitk;
+  int *status;
+  cudaStream_t st;
+
+  void gram(const float *Fm, int64_t rows, float *Gm) const {
+    GemmArgs g{};
+    g.A = Fm; g.ta = Elem::F32; g.sAm = 1; g.sAk = RT;
+    g.B = Fm; g.tb = Elem::F32; g.sBn = 1; g.sBk = RT;
+    g.D = Gm; g.sDm = RT; g.sDn = 1;
+    g.M = RT; g.N = RT; g.K = (int)rows; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
+    g.split_scratch = splitk; g.split_scratch_floats = kNSplitkFloats;
+    gemm_strided(g, st);
+  }
+  void mttkrp(int mode) const {
+    NDenseShape sh{};
+    for (int m = 0; m < NN; ++m) {
+      sh.F[m] = F[m];
+      sh.dim[m] = dim[m];
+      sh.stride[m] = stride[m];
+    }
+    sh.NN = NN;
+    const int64_t rows = dim[mode], others = total / rows;
+    int64_t nsplit = (304 + rows - 1) / rows;          // about two CTAs per SM
+    if (nsplit > others / 256) nsplit = others / 256;  // at least a CTA's worth each
+    if (nsplit < 1) nsplit = 1;
+    const int64_t per = (others + nsplit - 1) / nsplit;
+    nmttkrp_kernel<RT><<<dim3((unsigned)rows, (unsigned)nsplit), 256, 0, st>>>(X, sh, mode, per,
+                                                                              mpart);
+    count_launch();
+    nsplit_sum_kernel<RT><<<blocks(rows * RT), 256, 0, st>>>(mpart, rows, (int)nsplit, M);
+    count_launch();
+  }
+  void update(int mode, bool normalize) const {
+    mttkrp(mode);
+    const int last = mode == NN - 1 ? NN - 2 : NN - 1;
+    NGrams gs{};
+    for (int m = 0; m < NN; ++m) gs.G[m] = G[m];
+    gram_product_kernel<RT><<<blocks(RT * RT), 256, 0, st>>>(gs, NN, mode, last, Hp);
+    count_launch();
+    dense_factor_kernel<RT><<<1, 128, 0, st>>>(Hp, G[last], R, L, status);
+    count_launch();
+    const int64_t rows = dim[mode];
+    const unsigned nb = blocks(rows);
+    dense_rows_kernel<RT><<<nb, 256, 0, st>>>(M, nullptr, R, (int)rows, L, F[mode],
+                                              normalize ? part : nullptr);
+    count_launch();
+    if (normalize) {
+      dense_scale_kernel<RT><<<blocks(rows * RT), 256, 0, st>>>(F[mode], (int)rows, part,
+                                                               (int)nb);
+      count_launch();
+    }
+    gram(F[mode], rows, G[mode]);
+  }
+  void unit_columns(const float *F0, int m) const {
+    const int64_t rows = dim[m];
+    const unsigned nb = blocks(rows);
+    dense_rows_kernel<RT><<<nb, 256, 0, st>>>(nullptr, F0, R, (int)rows, nullptr, F[m], part);
+    count_launch();
+    dense_scale_kernel<RT><<<blocks(rows * RT), 256, 0, st>>>(F[m], (int)rows, part, (int)nb);
+    count_launch();
+    gram(F[m], rows, G[m]);
+  }
+};
+
+template <int RT>
+void run_dense_n(const DenseCpNArgs &a) {
+  DenseCpN<RT> d{};
+  d.X = a.X; d.NN = a.NN; d.R = a.R; d.status = a.status; d.st = a.st;
+  int64_t maxdim = 1;
+  d.total = 1;
+  for (int m = 0; m < a.NN; ++m) {
+    d.dim[m] = a.dims[m];
+    d.total *= a.dims[m];
+    if (a.dims[m] > maxdim) maxdim = a.dims[m];
+  }
+  int64_t str = 1;
+  for (int m = a.NN - 1; m >= 0; --m) {
+    d.stride[m] = str;
+    str *= a.dims[m];
+  }
+  float *w = a.work;
+  for (int m = 0; m < a.NN; ++m) { d.F[m] = w; w += a.dims[m] * RT; }
+  for (int m = 0; m < a.NN; ++m) { d.G[m] = w; w += RT * RT; }
+  d.Hp = w; w += RT * RT;
+  d.M = w; w += maxdim * RT;
+  d.L = w; w += factor_floats<RT>();
+  d.part = w; w += ((maxdim + 255) / 256) * RT;
+  d.mpart = w; w += n_mpart_rows(maxdim) * RT;
+  d.splitk = w;
+  for (int m = 1; m < a.NN; ++m) d.unit_columns(a.A0[m - 1], m);
+  for (int it = 0; it < a.iters; ++it) {
+    d.update(0, false);
+    for (int m = 1; m < a.NN; ++m) d.update(m, true);
+  }
+  d.update(0, false);
+  for (int m = 1; m < a.NN; ++m) {
+    unpad_kernel<<<blocks(a.dims[m] * a.R), 256, 0, a.st>>>(d.F[m], a.dims[m], a.R, RT,
+                                                            a.A_out[m - 1]);
+    count_launch();
+  }
+  unpad_kernel<<<blocks(a.dims[0] * a.R), 256, 0, a.st>>>(d.F[0], a.dims[0], a.R, RT, a.C_out);
+  count_launch();
+}
+
 }  // namespace
+
+size_t dense_cp_n_work_floats(int NN, const int64_t *dims, int RT) {
+  int64_t maxdim = 1, sum = 0;
+  for (int m = 0; m < NN; ++m) {
+    sum += dims[m];
+    if (dims[m] > maxdim) maxdim = dims[m];
+  }
+  return (size_t)(sum * RT + (NN + 1) * RT * RT + maxdim * RT + 2 * RT * RT + RT +
+                  ((maxdim + 255) / 256) * RT + n_mpart_rows(maxdim) * RT) +
+         kNSplitkFloats;
+}
+
+void dense_cp_n(const DenseCpNArgs &a, int RT) {
+  if (RT == 8) run_dense_n<8>(a);
+  else if (RT == 16) run_dense_n<16>(a);
+  else run_dense_n<32>(a);
+}
 
 size_t dense_cp_work_floats(int64_t K, int64_t I, int64_t J, int RT) {
   const int64_t mx = I > J ? (I > K ? I : K) : (J > K ? J : K);

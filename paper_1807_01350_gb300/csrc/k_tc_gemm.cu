@@ -662,7 +662,7 @@ long long wait_budget_cycles() {
 template <int KIND, class Epi>
 bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
                const Epi &epi, int *status, cudaStream_t st, int smem_reserve = 0,
-               int max_ctas = 0) {
+               int max_ctas = 0, int max_stages = 0) {
   sh.wait_budget = wait_budget_cycles();
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
@@ -674,6 +674,7 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
   const int64_t room = 220 * 1024 - (int64_t)stage_bytes - smem_reserve;
   sh.stages = room > 0 ? static_cast<int>(room / (int64_t)per_stage) : 0;
   if (sh.stages > 8) sh.stages = 8;
+  if (max_stages >= 2 && sh.stages > max_stages) sh.stages = max_stages;
   if (sh.stages < 2) return false;
   const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 5) * 8 + 16 + stage_bytes;
   auto kern = sh.katoms == 2 ? tc_gemm_kernel<KIND, Epi, 2> : tc_gemm_kernel<KIND, Epi, 1>;
@@ -711,6 +712,7 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
 // launches.  OCTEN_AUTOTUNE=0 keeps the defaults.
 struct TuneChoice {
   int katoms, BN;
+  int stages = 0;   // pipeline stages at most (0: as many as fit)
 };
 
 std::mutex g_tune_mu;
@@ -748,7 +750,7 @@ TuneChoice tuned(const std::array<int64_t, 8> &key, const TuneChoice *cand, int 
   // kernel beside the GEMM, would slow whichever candidate it overlaps), in
   // two rounds over the candidates, keeping each candidate's best
   cudaDeviceSynchronize();
-  constexpr int kMaxCand = 4;
+  constexpr int kMaxCand = 6;
   float cand_ms[kMaxCand];
   bool runs[kMaxCand];
   for (int c = 0; c < ncand && c < kMaxCand; ++c) {
@@ -786,9 +788,12 @@ TuneChoice tuned(const std::array<int64_t, 8> &key, const TuneChoice *cand, int 
     fprintf(stderr, "octen autotune key");
     for (int64_t v : key) fprintf(stderr, " %lld", (long long)v);
     for (int c = 0; c < ncand && c < kMaxCand; ++c)
-      fprintf(stderr, " | katoms %d BN %d: %.4f ms%s", cand[c].katoms, cand[c].BN,
-              runs[c] ? cand_ms[c] / 2 : -1.f, cand[c].katoms == best.katoms &&
-              cand[c].BN == best.BN ? " *" : "");
+      fprintf(stderr, " | katoms %d BN %d stages %d: %.4f ms%s", cand[c].katoms, cand[c].BN,
+              cand[c].stages, runs[c] ? cand_ms[c] / 2 : -1.f,
+              cand[c].katoms == best.katoms && cand[c].BN == best.BN &&
+                      cand[c].stages == best.stages
+                  ? " *"
+                  : "");
     fprintf(stderr, "\n");
   }
   adjust_launch_counts(-(int64_t)(octen_launch_count() - l0),
@@ -838,7 +843,7 @@ bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st) {
 
 bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
   if (a.te != Elem::BF16) return false;
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mb128;
   const int BN = (a.Q + 31) / 32 * 32;
   if (BN > 256) return false;
   const int64_t rowsA = static_cast<int64_t>(a.P) * a.Q;
@@ -846,14 +851,24 @@ bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st) {
   if (rowsB > (1 << 30)) return false;
   if (!make_map(&ma, a.Ut, false, a.I, rowsA, kBM) || !make_map(&mb, a.T, false, a.I, rowsB, BN))
     return false;
-  TcShape sh{};
-  sh.ksplit = 1;
-  sh.M = a.Q; sh.N = a.Q; sh.K = static_cast<int>(a.I); sh.BN = BN;
-  sh.zdiv = a.P;                   // z = k * P + p
-  sh.a_hi = 0; sh.a_lo = a.Q;      // A rows: p * Q
-  sh.b_hi = a.P * a.Q; sh.b_lo = a.Q;   // B rows: (k * P + p) * Q
+  const bool two_n = BN > 128 && make_map(&mb128, a.T, false, a.I, rowsB, 128);
   Mode1TcEpi epi{a.T2, a.t, a.P, a.Q};
-  return launch_tc<0>(ma, mb, sh, static_cast<int>(a.t * a.P), epi, status, st);
+  auto launch = [&](const TuneChoice &c) {
+    TcShape sh{};
+    sh.ksplit = 1;
+    sh.M = a.Q; sh.N = a.Q; sh.K = static_cast<int>(a.I); sh.BN = c.BN;
+    sh.zdiv = a.P;                   // z = k * P + p
+    sh.a_hi = 0; sh.a_lo = a.Q;      // A rows: p * Q
+    sh.b_hi = a.P * a.Q; sh.b_lo = a.Q;   // B rows: (k * P + p) * Q
+    sh.katoms = c.katoms;
+    return launch_tc<0>(ma, c.BN == 128 && two_n ? mb128 : mb, sh, static_cast<int>(a.t * a.P),
+                        epi, status, st, 0, 0, c.stages);
+  };
+  // the N tile (one or two tiles of the Q columns) and the K atoms per stage
+  // leave every output's K order unchanged
+  const TuneChoice cand[] = {{1, BN}, {2, BN}, {1, 128}, {2, 128}};
+  const std::array<int64_t, 8> key{3, a.t, a.I, a.P, a.Q, 0, 0, 0};
+  return launch(tuned(key, cand, two_n ? 4 : 2, st, launch));
 }
 
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
@@ -877,7 +892,8 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
     sh.a_stream = g.a_stream ? 1 : 0;
     sh.katoms = c.katoms;
     sh.ksplit = ks;
-    return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve, g.max_ctas);
+    return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve, g.max_ctas,
+                        c.stages);
   };
   // with split-K the other atom count is a candidate only if it cuts K at the
   // same places (the splits set the summation)
@@ -886,8 +902,12 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
     const int nk = (g.K + 64 * k - 1) / (64 * k);
     return ((nk + ks - 1) / ks) * 64 * k;
   };
-  const TuneChoice cand[] = {{katoms0, g.BN}, {katoms1, g.BN}};
-  const int ncand = ks > 1 && split_elems(katoms0) != split_elems(katoms1) ? 1 : 2;
+  // pipeline depth: as many stages as fit, or three (fewer bytes in flight
+  // per SM, more room beside the GEMM)
+  const bool other_atoms = !(ks > 1 && split_elems(katoms0) != split_elems(katoms1));
+  TuneChoice cand[4] = {{katoms0, g.BN, 0}, {katoms0, g.BN, 3}, {katoms1, g.BN, 0},
+                        {katoms1, g.BN, 3}};
+  const int ncand = other_atoms ? 4 : 2;
   const std::array<int64_t, 8> key{1 + 16 * (int64_t)g.max_ctas, g.M, g.N, g.K, g.batch, ks,
                                    g.Dh != nullptr, g.m1_part != nullptr};
   return launch(tuned(key, cand, ncand, st, launch));

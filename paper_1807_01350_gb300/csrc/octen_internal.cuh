@@ -251,6 +251,26 @@ struct DenseCpArgs {
 size_t dense_cp_work_floats(int64_t K, int64_t I, int64_t J, int RT);
 void dense_cp(const DenseCpArgs &a, int RT);
 
+// Dense N-way CP-ALS of the existing tensor X ([k][i_1]...[i_{NN-1}], fp32;
+// dims[0] = K, dims[m] = I_m) from the guesses A0[m - 1] (I_m x R): `iters`
+// sweeps as in the N-mode replica CP-ALS (time mode, then every non-temporal
+// mode normalised to unit l2, a final time update), results into A_out[m - 1]
+// (I_m x R) and C_out (K x R).  `work` holds dense_cp_n_work_floats floats.
+struct DenseCpNArgs {
+  const float *X;
+  int NN;
+  const int64_t *dims;
+  int R, iters;
+  const float *const *A0;
+  float *const *A_out;
+  float *C_out;
+  float *work;
+  int *status;
+  cudaStream_t st;
+};
+size_t dense_cp_n_work_floats(int NN, const int64_t *dims, int RT);
+void dense_cp_n(const DenseCpNArgs &a, int RT);
+
 // doubles of scratch align_replicas needs
 size_t align_scratch_doubles(int P, int RT);
 

@@ -321,8 +321,10 @@ octen_status octen_n_init(octen_nctx *x, const float *X_old, int64_t t_old,
                           const float *const *A0, const float *C0) {
   if (!x) return OCTEN_EINVAL;
   if (x->initialized) return x->fail(OCTEN_ESTATE, "octen_n_init called twice");
-  if (!X_old || !U_all || !W_old || !A0 || !C0 || t_old < 1)
-    return x->fail(OCTEN_EINVAL, "octen_n_init: X_old, U_all, W_old, A0, C0 are required, t_old >= 1");
+  if (!X_old || !U_all || !W_old || !A0 || t_old < 1)
+    return x->fail(OCTEN_EINVAL, "octen_n_init: X_old, U_all, W_old, A0 are required, t_old >= 1");
+  if (!C0 && t_old > (int64_t)1 << 31)
+    return x->fail(OCTEN_EINVAL, "octen_n_init: decomposing X_old takes t_old < 2^31");
   for (int n = 0; n < x->nm; ++n)
     if (!U_all[n] || !A0[n]) return x->fail(OCTEN_EINVAL, "octen_n_init: U_all[%d] or A0[%d] is NULL", n, n);
   const octen_nconfig &c = x->cfg;
@@ -346,7 +348,39 @@ octen_status octen_n_init(octen_nctx *x, const float *X_old, int64_t t_old,
     if (!xdev) cudaStreamSynchronize(x->st);   // the staging slot is reused
   }
   if (!x->ensure_c(t_old)) return x->fail(OCTEN_ENOMEM, "C");
-  cudaMemcpyAsync(x->C, C0, (size_t)t_old * c.R * 4, cudaMemcpyDefault, x->st);
+  if (C0) {
+    cudaMemcpyAsync(x->C, C0, (size_t)t_old * c.R * 4, cudaMemcpyDefault, x->st);
+  } else {
+    // the existing decomposition: N-way CP-ALS of X_old from the guesses A0
+    // (already in x->A), results into x->A and x->C
+    s = x->sync_check("init summaries");
+    if (s != OCTEN_OK) return s;
+    const float *Xd = xdev ? X_old : x->stage_in(X_old, (size_t)t_old * x->slice * 4, 0);
+    if (!Xd) return x->fail(OCTEN_ENOMEM, "staging X_old");
+    int64_t dims[kMaxNModes];
+    dims[0] = t_old;
+    for (int n = 0; n < x->nm; ++n) dims[n + 1] = x->dims[n];
+    const size_t wf = dense_cp_n_work_floats(x->NN, dims, x->RT);
+    float *work = nullptr;
+    if (cudaMalloc(&work, wf * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return x->fail(OCTEN_ENOMEM, "N-way CP-ALS workspace (%zu bytes)", wf * sizeof(float));
+    }
+    const float *a0[kMaxNModes];
+    float *aout[kMaxNModes];
+    for (int n = 0; n < x->nm; ++n) {
+      a0[n] = x->A[n];
+      aout[n] = x->A[n];
+    }
+    DenseCpNArgs a{};
+    a.X = Xd; a.NN = x->NN; a.dims = dims; a.R = c.R; a.iters = c.als_iters;
+    a.A0 = a0; a.A_out = aout; a.C_out = x->C; a.work = work; a.status = x->dstatus;
+    a.st = x->st;
+    dense_cp_n(a, x->RT);
+    s = x->sync_check("init decomposition");
+    cudaFree(work);
+    if (s != OCTEN_OK) return s;
+  }
   update_g(Wd, x->C, t_old, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
   s = x->sync_check("init summaries");
   if (s != OCTEN_OK) return s;

@@ -170,3 +170,39 @@ def test_nmode_checkpoint_resume_is_bit_identical(pkg, tmp_path):
     assert np.array_equal(C_a, C_b) and np.array_equal(Y_a, Y_b)
     for a, b in zip(A_a, A_b):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["n3", "n4", "n5"])
+def test_nmode_init_decomposition_matches_oracle(pkg, name):
+    """octen_n_init without C0: the existing decomposition is the N-way CP-ALS
+    of X_old on the GPU (one pass over X_old per mode per sweep) from the
+    guesses A0; it and the update that follows match the oracle doing the same
+    (octen_n.decompose_existing_n), at the fp32 tolerances."""
+    case = CASES[name]
+    d = case.make()
+    X_old = d["X"][:case.t_old]
+    g = pkg.OctenN(case.dims, case.R, case.P, case.Q, case.S, case.iters)
+    g.init(dev(X_old), [dev(u) for u in d["U"]], dev(d["W"][0]), [dev(a) for a in d["A0"]],
+           None)
+    As, C = g.factors()
+    ref = octen_n.decompose_existing_n(X_old, d["A0"], case.iters)
+    for n in range(case.N - 1):
+        assert rel(As[n], ref[n]) < TOL["F"], (n, rel(As[n], ref[n]))
+    assert rel(C, ref[-1]) < TOL["F"], rel(C, ref[-1])
+    f_gpu = octen_n.fit_n(X_old, [np.asarray(a, np.float64) for a in As],
+                          np.asarray(C, np.float64))
+    f_ref = octen_n.fit_n(X_old, ref[:-1], ref[-1])
+    assert abs(f_gpu - f_ref) < TOL["fit"], (f_gpu, f_ref)
+    assert f_ref > 0.98
+    # the update from there
+    o = octen_n.OctenOracleN(list(case.dims), case.R, case.P, case.Q, case.S, case.iters)
+    o.init(X_old, d["U"], d["W"][0], d["A0"], None)
+    k, t = case.t_old, case.batches[0]
+    o.append(d["X"][k:k + t], d["W"][1])
+    g.append(dev(d["X"][k:k + t]), dev(d["W"][1]))
+    As, C = g.factors()
+    g.close()
+    for n in range(case.N - 1):
+        assert rel(As[n], o.A[n]) < TOL["F"], (n, rel(As[n], o.A[n]))
+    assert rel(C, o.C) < TOL["F"]
+    assert fms(tuple(As) + (C,), tuple(o.A) + (o.C,)) > TOL["fms"]
