@@ -286,9 +286,15 @@ octen_status octen_reset_stage_times(octen_ctx *ctx);
  * projection; the new rows of the time factor are solved as in the 3-mode
  * update.  With N = 3 this is the 3-mode update in fp32.
  *
- * fp32 throughout.  Slices are laid out [k][i_1]...[i_{N-1}], summaries
- * [p][q_1]...[q_{N-1}][c].  Pointers may be device or host memory (host
- * inputs are staged on the context's stream).  Same status codes and
+ * Precision (prec): OCTEN_FP32 computes everything in fp32.  OCTEN_BF16 takes
+ * bf16 slices, rounds every U_all[n] to bf16 once (the rounded values are the
+ * matrices from then on), and runs the first contraction of the compression
+ * (every slice against all P Q columns of the innermost mode's projection,
+ * the one pass that reads the slices) in bf16 with fp32 accumulation, on the
+ * tensor cores when I_{N-1} is a multiple of 8; the rest of the update is
+ * fp32.  Slices are laid out [k][i_1]...[i_{N-1}] (fp32 or bf16 by prec),
+ * summaries [p][q_1]...[q_{N-1}][c].  Pointers may be device or host memory
+ * (host inputs are staged on the context's stream).  Same status codes and
  * threading rules as the 3-mode calls.
  * ------------------------------------------------------------------------ */
 typedef struct octen_nctx octen_nctx;
@@ -306,24 +312,31 @@ typedef struct {
   int32_t R, P, Q, S;
   int32_t als_iters;
   int64_t dims[OCTEN_MAX_MODES - 1];
+  int32_t prec; /* OCTEN_FP32 or OCTEN_BF16 */
 } octen_nconfig;
 
 /* Creates a context (summaries, projections, factors, scratch on the device).
  * EINVAL on the limits above, ENOMEM on allocation failure. */
 octen_status octen_n_create(const octen_nconfig *cfg, void *cuda_stream, octen_nctx **out);
 
-/* Existing summaries and decomposition: compresses X_old (t_old slices) with
- * U_all[n] (n < N - 1, each I_n x Qd) and W_old (t_old x Qd), takes A0[n]
- * (I_n x R) and C0 (t_old x R) as the existing factors (all required), forms
- * G_p = W_old,p^T C0 and the lift operators of every non-temporal mode.  Once
- * per context (ESTATE otherwise). */
-octen_status octen_n_init(octen_nctx *ctx, const float *X_old, int64_t t_old,
+/* Existing summaries and decomposition: compresses X_old (t_old slices, element
+ * type by prec) with U_all[n] (n < N - 1, each I_n x Qd) and W_old
+ * (t_old x Qd), takes A0[n] (I_n x R) and C0 (t_old x R) as the existing
+ * factors, forms G_p = W_old,p^T C0 and the lift operators of every
+ * non-temporal mode.  With C0 == NULL the existing decomposition is computed
+ * instead: the N-way CP-ALS of X_old (model X_old[k][i_1]..[i_{N-1}] =
+ * sum_r prod_n A_n[i_n][r] C[k][r]) from the starting guesses A0, with the
+ * sweeps of the replica CP (als_iters sweeps: the time factor, then every
+ * non-temporal factor normalised to unit l2, a final time-factor update); it
+ * needs a workspace of about 4 R (t_old + sum_n I_n) bytes plus 4 MB.  The
+ * other arrays are required.  Once per context (ESTATE otherwise). */
+octen_status octen_n_init(octen_nctx *ctx, const void *X_old, int64_t t_old,
                           const float *const *U_all, const float *W_old,
                           const float *const *A0, const float *C0);
 
-/* One update with t new slices (1 <= t <= 64) and their time projections
- * W_new (t x Qd). */
-octen_status octen_n_append(octen_nctx *ctx, const float *X_new, int64_t t,
+/* One update with t new slices (1 <= t <= 64, element type by prec) and their
+ * time projections W_new (t x Qd). */
+octen_status octen_n_append(octen_nctx *ctx, const void *X_new, int64_t t,
                             const float *W_new);
 
 /* Copies A[n] (I_n x R, n < N - 1) and C (K x R); A, any A[n] and C may be
@@ -345,10 +358,10 @@ octen_status octen_n_get_replica_factors(const octen_nctx *ctx, int which, float
 int64_t octen_n_rows(const octen_nctx *ctx);
 
 /* Fitness of the current factors on the K = octen_n_rows() slices X_all
- * (K x I_1 x ... x I_{N-1}, fp32, device or host): 1 - ||X - [[A_1, ...,
- * A_{N-1}, C]]||_F / ||X||_F (Sec. "Evaluation Measures"), the residual formed
- * element by element with fp64 sums. */
-octen_status octen_n_fit(octen_nctx *ctx, const float *X_all, int64_t K, double *fit_out);
+ * (K x I_1 x ... x I_{N-1}, element type by prec, device or host):
+ * 1 - ||X - [[A_1, ..., A_{N-1}, C]]||_F / ||X||_F (Sec. "Evaluation
+ * Measures"), the residual formed element by element with fp64 sums. */
+octen_status octen_n_fit(octen_nctx *ctx, const void *X_all, int64_t K, double *fit_out);
 
 /* Checkpoint and resume of an N-mode context (as octen_save / octen_load:
  * the projections, lift operators, factors, summaries and G_p; a loaded

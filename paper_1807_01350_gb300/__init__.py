@@ -35,7 +35,7 @@ MAX_MODES = 6
 class _NConfig(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("R", ctypes.c_int32), ("P", ctypes.c_int32),
                 ("Q", ctypes.c_int32), ("S", ctypes.c_int32), ("als_iters", ctypes.c_int32),
-                ("dims", ctypes.c_int64 * (MAX_MODES - 1))]
+                ("dims", ctypes.c_int64 * (MAX_MODES - 1)), ("prec", ctypes.c_int32)]
 
 
 class _Config(ctypes.Structure):
@@ -419,17 +419,21 @@ class Octen:
 
 class OctenN:
     """One online CP decomposition of an N-mode tensor growing in its last
-    (time) mode, fp32 (octen_n_* in include/octen.h).  dims are the N - 1
-    non-temporal sizes; slices are [k][i_1]...[i_{N-1}]."""
+    (time) mode (octen_n_* in include/octen.h), fp32 or bf16 slices.  dims are
+    the N - 1 non-temporal sizes; slices are [k][i_1]...[i_{N-1}]."""
 
-    def __init__(self, dims, R, P, Q, S, als_iters, stream=None):
+    def __init__(self, dims, R, P, Q, S, als_iters, prec="fp32", stream=None):
         self._lib = lib()
+        if prec not in ("fp32", "bf16"):
+            raise OctenError(1, f"N-mode precision {prec!r}: fp32 or bf16")
+        self.prec = prec
         self.dims = [int(d) for d in dims]
         self.N = len(self.dims) + 1
         if not 3 <= self.N <= MAX_MODES:
             raise OctenError(1, f"N = {self.N} modes: 3 <= N <= {MAX_MODES}")
         dd = (ctypes.c_int64 * (MAX_MODES - 1))(*(self.dims + [0] * (MAX_MODES - self.N)))
-        self.cfg = _NConfig(self.N, int(R), int(P), int(Q), int(S), int(als_iters), dd)
+        self.cfg = _NConfig(self.N, int(R), int(P), int(Q), int(S), int(als_iters), dd,
+                            PREC[prec])
         self.R, self.P, self.Q, self.S = R, P, Q, S
         self.Qd = S + P * (Q - S)
         h = ctypes.c_void_p()
@@ -466,16 +470,17 @@ class OctenN:
         us = self._ptrs(Us, keep)
         a0 = self._ptrs(A0s, keep)
         keep += [us, a0]
-        self._check(self._lib.octen_n_init(self._h, _f32(X_old, keep), int(X_old.shape[0]), us,
-                                           _f32(W_old, keep), a0, _f32(C0, keep)))
+        self._check(self._lib.octen_n_init(self._h, _slices(X_old, self.prec, keep),
+                                           int(X_old.shape[0]), us, _f32(W_old, keep), a0,
+                                           _f32(C0, keep)))
 
     def append(self, X_new, W_new):
         keep: list = []
         t = int(X_new.shape[0])
         _need(X_new, t * self._slice, "X_new")
         _need(W_new, t * self.Qd, "W_new")
-        self._check(self._lib.octen_n_append(self._h, _f32(X_new, keep), int(X_new.shape[0]),
-                                             _f32(W_new, keep)))
+        self._check(self._lib.octen_n_append(self._h, _slices(X_new, self.prec, keep),
+                                             int(X_new.shape[0]), _f32(W_new, keep)))
 
     def append_ptr(self, x_ptr: int, t: int, w_ptr: int):
         """Append from raw fp32 pointers (device or host)."""
@@ -513,6 +518,7 @@ class OctenN:
             f.read(8)
             cfg = _NConfig.from_buffer_copy(f.read(ctypes.sizeof(_NConfig)))
         self.cfg = cfg
+        self.prec = {v: k for k, v in PREC.items()}[cfg.prec]
         self.N = cfg.N
         self.dims = [int(cfg.dims[n]) for n in range(cfg.N - 1)]
         self.R, self.P, self.Q, self.S = cfg.R, cfg.P, cfg.Q, cfg.S
@@ -524,8 +530,8 @@ class OctenN:
         keep: list = []
         out = ctypes.c_double()
         _need(X_all, int(X_all.shape[0]) * self._slice, "X_all")
-        self._check(self._lib.octen_n_fit(self._h, _f32(X_all, keep), int(X_all.shape[0]),
-                                          ctypes.byref(out)))
+        self._check(self._lib.octen_n_fit(self._h, _slices(X_all, self.prec, keep),
+                                          int(X_all.shape[0]), ctypes.byref(out)))
         return float(out.value)
 
     def replicas(self):

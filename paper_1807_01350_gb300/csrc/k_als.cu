@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256)
   if (row < Q) {
     const __nv_bfloat16 *t = Tc + (int64_t)p * Q * Q * RT + r;
     const float *f = Fac + (int64_t)p * Q * RT + r;
-#pragma unroll 4
+#pragma unroll 8
     for (int k = sl; k < Q; k += 8) {
       const int64_t ab = KIND == 1 ? (int64_t)row * Q + k : (int64_t)k * Q + row;
       const uint4 raw = *reinterpret_cast<const uint4 *>(t + ab * RT);

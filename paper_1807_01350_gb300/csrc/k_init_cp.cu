@@ -141,9 +141,9 @@ struct NDenseShape {
   int NN;
 };
 
-template <int RT>
+template <int RT, Elem XT>
 __global__ void __launch_bounds__(256)
-    nmttkrp_kernel(const float *__restrict__ X, const NDenseShape sh, int mode, int64_t per,
+    nmttkrp_kernel(const void *__restrict__ X, const NDenseShape sh, int mode, int64_t per,
                    float *__restrict__ part) {
   __shared__ float red[8 * RT], out[RT];
   const int64_t row = blockIdx.x;
@@ -176,7 +176,9 @@ __global__ void __launch_bounds__(256)
         w[4 * r4] *= v.x; w[4 * r4 + 1] *= v.y; w[4 * r4 + 2] *= v.z; w[4 * r4 + 3] *= v.w;
       }
     }
-    const float x = __ldg(X + off);
+    const float x = XT == Elem::BF16
+                        ? __bfloat162float(static_cast<const __nv_bfloat16 *>(X)[off])
+                        : __ldg(static_cast<const float *>(X) + off);
 #pragma unroll
     for (int r = 0; r < RT; ++r) acc[r] = fmaf(x, w[r], acc[r]);
   }
@@ -338,7 +340,8 @@ int64_t n_mpart_rows(int64_t maxdim) { return maxdim + 304; }
 // L D L^T of the replica solve.
 template <int RT>
 struct DenseCpN {
-  const float *X;
+  const void *X;
+  Elem xt;
   int NN, R;
   int64_t dim[kMaxNModes], stride[kMaxNModes], total;
   float *F[kMaxNModes], *G[kMaxNModes];
@@ -368,8 +371,11 @@ struct DenseCpN {
     if (nsplit > others / 256) nsplit = others / 256;  // at least a CTA's worth each
     if (nsplit < 1) nsplit = 1;
     const int64_t per = (others + nsplit - 1) / nsplit;
-    nmttkrp_kernel<RT><<<dim3((unsigned)rows, (unsigned)nsplit), 256, 0, st>>>(X, sh, mode, per,
-                                                                              mpart);
+    const dim3 grid((unsigned)rows, (unsigned)nsplit);
+    if (xt == Elem::BF16)
+      nmttkrp_kernel<RT, Elem::BF16><<<grid, 256, 0, st>>>(X, sh, mode, per, mpart);
+    else
+      nmttkrp_kernel<RT, Elem::F32><<<grid, 256, 0, st>>>(X, sh, mode, per, mpart);
     count_launch();
     nsplit_sum_kernel<RT><<<blocks(rows * RT), 256, 0, st>>>(mpart, rows, (int)nsplit, M);
     count_launch();
@@ -409,7 +415,7 @@ struct DenseCpN {
 template <int RT>
 void run_dense_n(const DenseCpNArgs &a) {
   DenseCpN<RT> d{};
-  d.X = a.X; d.NN = a.NN; d.R = a.R; d.status = a.status; d.st = a.st;
+  d.X = a.X; d.xt = a.xt; d.NN = a.NN; d.R = a.R; d.status = a.status; d.st = a.st;
   int64_t maxdim = 1;
   d.total = 1;
   for (int m = 0; m < a.NN; ++m) {

@@ -547,7 +547,8 @@ void n_align(const NAlignInput &in, cudaStream_t st) {
 // (blocks per slice, slices), 256 threads; partial[k][block][2] doubles.
 // ---------------------------------------------------------------------------
 struct NFitArgs {
-  const float *X;                  // nk slices, [k][i_1]...[i_nm]
+  const void *X;                   // nk slices, [k][i_1]...[i_nm], fp32 or bf16
+  int xbf16;
   const float *A[kMaxNModes];      // I_n x R
   const float *C;                  // nk x R (the chunk's rows)
   int64_t dims[kMaxNModes];
@@ -559,7 +560,8 @@ struct NFitArgs {
 __global__ void __launch_bounds__(256) n_fit_kernel(NFitArgs a) {
   __shared__ double red[2][8];
   const int k = blockIdx.y, tid = threadIdx.x;
-  const float *x = a.X + (int64_t)k * a.E;
+  const float *x = static_cast<const float *>(a.X) + (int64_t)k * a.E;
+  const __nv_bfloat16 *xh = static_cast<const __nv_bfloat16 *>(a.X) + (int64_t)k * a.E;
   const float *c = a.C + (int64_t)k * a.R;
   double s0 = 0.0, s1 = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < a.E;
@@ -576,7 +578,8 @@ __global__ void __launch_bounds__(256) n_fit_kernel(NFitArgs a) {
       for (int n = 0; n < a.nm; ++n) pr *= (double)a.A[n][idx[n] * a.R + r];
       model += pr;
     }
-    const double xv = x[e], d = xv - model;
+    const double xv = a.xbf16 ? (double)__bfloat162float(xh[e]) : (double)x[e];
+    const double d = xv - model;
     s0 = fma(xv, xv, s0);
     s1 = fma(d, d, s1);
   }
@@ -606,10 +609,10 @@ int n_fit_blocks(int64_t E) {
   return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
-void n_fit_sums(const float *X, int64_t nk, const float *const *A, const float *C,
+void n_fit_sums(const void *X, Elem xt, int64_t nk, const float *const *A, const float *C,
                 const int64_t *dims, int nm, int R, double *partial, cudaStream_t st) {
   NFitArgs a{};
-  a.X = X; a.C = C; a.nm = nm; a.R = R; a.partial = partial;
+  a.X = X; a.xbf16 = xt == Elem::BF16; a.C = C; a.nm = nm; a.R = R; a.partial = partial;
   a.E = 1;
   for (int n = 0; n < nm; ++n) {
     a.A[n] = A[n];
@@ -651,16 +654,32 @@ int64_t ncompress_buf_floats(int nm, const int64_t *dims, int P, int Q, int64_t 
   return best * P;
 }
 
-void ncompress_chunk(const NCompressInput &c, const float *X, int64_t t, const float *Wt,
-                     float *Y, cudaStream_t st) {
+void ncompress_chunk(const NCompressInput &c, const void *X, Elem xt, int64_t t,
+                     const float *Wt, float *Y, cudaStream_t st, const void *Ut16,
+                     int *status) {
   const int nm = c.nm, P = c.P, Q = c.Q;
-  // 1. innermost mode, all replicas at once
+  // 1. innermost mode, all replicas at once: bufA[(p, q)][row] = sum_i
+  // X[row][i] Ut[(p, q)][i].  bf16 slices: on the tensor cores as the product
+  // Ut . X^T (A = Ut, B = the slice rows, both K-major; the [(p, q)][row]
+  // output is row-major in the GEMM's own terms), else on the SIMT kernels.
   int64_t rows = t;
   for (int n = 0; n + 1 < nm; ++n) rows *= c.dims[n];
   const int64_t Il = c.dims[nm - 1];
-  {
+  bool done = false;
+  if (xt == Elem::BF16 && Ut16 && rows <= (int64_t(1) << 30)) {
+    TcStoreArgs g{};
+    g.A = Ut16; g.a_inner = Il; g.a_rows = (int64_t)P * Q; g.a_rows_per_z = 0;
+    g.B = X; g.b_inner = Il; g.b_rows = rows; g.b_rows_per_z = 0;
+    g.M = P * Q; g.N = (int)rows; g.K = (int)Il; g.BN = rows >= 256 ? 256 : 128;
+    g.batch = 1; g.ksplit = 1;
+    g.D = c.bufA; g.s_split = 0; g.s_z = 0; g.s_m = rows;
+    g.katoms = 1;
+    done = tc_gemm_store(g, status, st);
+    if (!done) cudaGetLastError();
+  }
+  if (!done) {
     GemmArgs g{};
-    g.A = X; g.ta = Elem::F32; g.sAm = Il; g.sAk = 1;
+    g.A = X; g.ta = xt; g.sAm = Il; g.sAk = 1;
     g.B = c.Ut[nm - 1]; g.tb = Elem::F32; g.sBn = Il; g.sBk = 1;
     g.D = c.bufA; g.sDm = 1; g.sDn = rows;
     g.M = (int)rows; g.N = P * Q; g.K = (int)Il; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;

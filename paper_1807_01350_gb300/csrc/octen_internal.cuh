@@ -251,13 +251,14 @@ struct DenseCpArgs {
 size_t dense_cp_work_floats(int64_t K, int64_t I, int64_t J, int RT);
 void dense_cp(const DenseCpArgs &a, int RT);
 
-// Dense N-way CP-ALS of the existing tensor X ([k][i_1]...[i_{NN-1}], fp32;
+// Dense N-way CP-ALS of the existing tensor X ([k][i_1]...[i_{NN-1}], fp32 or bf16;
 // dims[0] = K, dims[m] = I_m) from the guesses A0[m - 1] (I_m x R): `iters`
 // sweeps as in the N-mode replica CP-ALS (time mode, then every non-temporal
 // mode normalised to unit l2, a final time update), results into A_out[m - 1]
 // (I_m x R) and C_out (K x R).  `work` holds dense_cp_n_work_floats floats.
 struct DenseCpNArgs {
-  const float *X;
+  const void *X;
+  Elem xt;
   int NN;
   const int64_t *dims;
   int R, iters;
@@ -330,8 +331,12 @@ struct NCompressInput {
   const float *const *Ut;
   float *bufA, *bufB;
 };
-void ncompress_chunk(const NCompressInput &c, const float *X, int64_t t, const float *Wt,
-                     float *Y, cudaStream_t st);
+// X is fp32 or bf16 (xt); with bf16 slices the first contraction runs on the
+// tensor cores when Ut16 (the innermost mode's replica transpose in bf16) is
+// given and the rows meet the TMA rules, else on the SIMT kernels.
+void ncompress_chunk(const NCompressInput &c, const void *X, Elem xt, int64_t t,
+                     const float *Wt, float *Y, cudaStream_t st, const void *Ut16 = nullptr,
+                     int *status = nullptr);
 int64_t ncompress_rows_max(int nm, const int64_t *dims, int Q, int64_t t);
 int64_t ncompress_buf_floats(int nm, const int64_t *dims, int P, int Q, int64_t t);
 
@@ -362,7 +367,7 @@ void n_align(const NAlignInput &in, cudaStream_t st);
 // Fitness sums of nk slices (see k_nmode.cu): partial[k][block][2] doubles,
 // n_fit_blocks(E) blocks per slice of E elements.
 int n_fit_blocks(int64_t E);
-void n_fit_sums(const float *X, int64_t nk, const float *const *A, const float *C,
+void n_fit_sums(const void *X, Elem xt, int64_t nk, const float *const *A, const float *C,
                 const int64_t *dims, int nm, int R, double *partial, cudaStream_t st);
 
 // true for device (or managed) memory

@@ -5,7 +5,8 @@
 // batch into every replica's N-way summary, CP of every summary warm-started
 // from the projected previous factors, anchor match in every non-temporal
 // mode, lift of every non-temporal factor (Eq. 7) and the new rows of the time
-// factor.  fp32 throughout.
+// factor.  fp32, or bf16 slices and projections with the slice-reading first
+// contraction of the compression in bf16 (fp32 accumulation).
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -37,7 +38,9 @@ struct octen_nctx {
   octen_nconfig cfg{};
   int nm = 0, NN = 0, Qd = 0, RT = 8;
   int64_t dims[kMaxNModes] = {};
-  int64_t slice = 1;      // floats per slice
+  int64_t slice = 1;      // elements per slice
+  Elem xin = Elem::F32;   // slice element type (OCTEN_FP32 or OCTEN_BF16)
+  void *Ut16 = nullptr;   // bf16 replica transpose of the innermost mode (bf16 mode)
   int64_t tchunk = 1;     // slices per compression pass
   cudaStream_t st = nullptr;
   bool initialized = false;
@@ -125,7 +128,8 @@ struct octen_nctx {
   }
 
   // device view of a caller buffer (copied into staging slot `slot` if host)
-  const float *stage_in(const float *p, size_t bytes, int slot) {
+  template <class T>
+  const T *stage_in(const T *p, size_t bytes, int slot) {
     if (is_device_pointer(p)) return p;
     if (stg_bytes[slot] < bytes) {
       cudaStreamSynchronize(st);
@@ -141,7 +145,7 @@ struct octen_nctx {
     }
     if (cudaMemcpyAsync(stg[slot], p, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return nullptr;
-    return static_cast<const float *>(stg[slot]);
+    return static_cast<const T *>(stg[slot]);
   }
 
   octen_status sync_check(const char *what) {
@@ -185,12 +189,17 @@ struct octen_nctx {
   }
 
   // Y_p += compression of t slices (device X, device W rows t x Qd)
-  void compress(const float *X, int64_t t, const float *W) {
+  size_t slice_bytes() const { return (size_t)slice * elem_size(xin); }
+  const void *slice_at(const void *X, int64_t k) const {
+    return static_cast<const char *>(X) + k * slice_bytes();
+  }
+
+  void compress(const void *X, int64_t t, const float *W) {
     NCompressInput c{nm, cfg.P, cfg.Q, dims, Ut, bufA, bufB};
     for (int64_t k0 = 0; k0 < t; k0 += tchunk) {
       const int64_t n = t - k0 < tchunk ? t - k0 : tchunk;
       make_replica_transpose(W + k0 * Qd, n, cfg.P, cfg.Q, cfg.S, Qd, Wt, Elem::F32, st);
-      ncompress_chunk(c, X + k0 * slice, n, Wt, Y, st);
+      ncompress_chunk(c, slice_at(X, k0), xin, n, Wt, Y, st, Ut16, dstatus);
     }
   }
 
@@ -213,11 +222,11 @@ octen_status nvalidate(const octen_nconfig *c, std::string &why) {
   if (!c) { why = "config is NULL"; return OCTEN_EINVAL; }
   if (c->N < 3 || c->N > kMaxNModes || c->R < 1 || c->R > 32 || c->P < 1 ||
       c->P > kGridYZMax || c->Q < 2 || c->Q > 256 || c->S < 1 || c->S >= c->Q ||
-      c->als_iters < 1) {
+      c->als_iters < 1 || (c->prec != OCTEN_FP32 && c->prec != OCTEN_BF16)) {
     snprintf(buf, sizeof buf,
-             "unsupported config N=%d R=%d P=%d Q=%d S=%d iters=%d (limits: 3<=N<=%d, "
-             "1<=R<=32, 1<=S<Q<=256, 1<=P<=65535, iters>=1)",
-             c->N, c->R, c->P, c->Q, c->S, c->als_iters, kMaxNModes);
+             "unsupported config N=%d R=%d P=%d Q=%d S=%d iters=%d prec=%d (limits: "
+             "3<=N<=%d, 1<=R<=32, 1<=S<Q<=256, 1<=P<=65535, iters>=1, prec fp32 or bf16)",
+             c->N, c->R, c->P, c->Q, c->S, c->als_iters, c->prec, kMaxNModes);
     why = buf;
     return OCTEN_EINVAL;
   }
@@ -273,6 +282,7 @@ octen_status octen_n_create(const octen_nconfig *cfg, void *cuda_stream, octen_n
   }
   x->Qd = cfg->S + cfg->P * (cfg->Q - cfg->S);
   x->RT = nround_rt(cfg->R);
+  x->xin = cfg->prec == OCTEN_BF16 ? Elem::BF16 : Elem::F32;
   x->st = static_cast<cudaStream_t>(cuda_stream);
   const int64_t r1 = ncompress_rows_max(x->nm, x->dims, cfg->Q, 1);
   const int64_t b1 = ncompress_buf_floats(x->nm, x->dims, cfg->P, cfg->Q, 1);
@@ -300,6 +310,11 @@ octen_status octen_n_create(const octen_nconfig *cfg, void *cuda_stream, octen_n
        x->alloc(x->csolve, Qd * c.R + kNBatchMax * (c.R + Qd + kNBatchMax)) &&
        x->alloc(x->splitk, octen_nctx::kSplitkFloats) && x->alloc(x->perm, P * c.R) &&
        x->alloc(x->scales, P * x->nm * c.R) && x->alloc(x->dstatus, 1);
+  if (ok && x->xin == Elem::BF16) {
+    __nv_bfloat16 *u16 = nullptr;
+    ok = x->alloc(u16, P * Q * (size_t)x->dims[x->nm - 1]);
+    x->Ut16 = u16;
+  }
   if (!ok) {
     cudaGetLastError();
     delete x;
@@ -316,7 +331,7 @@ octen_status octen_n_create(const octen_nconfig *cfg, void *cuda_stream, octen_n
   return OCTEN_OK;
 }
 
-octen_status octen_n_init(octen_nctx *x, const float *X_old, int64_t t_old,
+octen_status octen_n_init(octen_nctx *x, const void *X_old, int64_t t_old,
                           const float *const *U_all, const float *W_old,
                           const float *const *A0, const float *C0) {
   if (!x) return OCTEN_EINVAL;
@@ -330,8 +345,20 @@ octen_status octen_n_init(octen_nctx *x, const float *X_old, int64_t t_old,
   const octen_nconfig &c = x->cfg;
   const int Qd = x->Qd;
   for (int n = 0; n < x->nm; ++n) {
-    cudaMemcpyAsync(x->U32[n], U_all[n], (size_t)x->dims[n] * Qd * 4, cudaMemcpyDefault, x->st);
+    // bf16 mode: the projections are rounded to bf16 once (through L[n],
+    // free until the lift operators are built); the rounded values are the
+    // matrices from then on
+    if (x->xin == Elem::BF16) {
+      cudaMemcpyAsync(x->L[n], U_all[n], (size_t)x->dims[n] * Qd * 4, cudaMemcpyDefault, x->st);
+      round_copy(x->L[n], x->U32[n], x->dims[n] * Qd, Elem::BF16, x->st);
+    } else {
+      cudaMemcpyAsync(x->U32[n], U_all[n], (size_t)x->dims[n] * Qd * 4, cudaMemcpyDefault,
+                      x->st);
+    }
     make_replica_transpose(x->U32[n], x->dims[n], c.P, c.Q, c.S, Qd, x->Ut[n], Elem::F32, x->st);
+    if (x->xin == Elem::BF16 && n == x->nm - 1)
+      make_replica_transpose(x->U32[n], x->dims[n], c.P, c.Q, c.S, Qd, x->Ut16, Elem::BF16,
+                             x->st);
     cudaMemcpyAsync(x->A[n], A0[n], (size_t)x->dims[n] * c.R * 4, cudaMemcpyDefault, x->st);
   }
   octen_status s = x->sync_check("projection setup");
@@ -341,8 +368,8 @@ octen_status octen_n_init(octen_nctx *x, const float *X_old, int64_t t_old,
   const bool xdev = is_device_pointer(X_old);
   for (int64_t k0 = 0; k0 < t_old; k0 += x->tchunk) {
     const int64_t n = t_old - k0 < x->tchunk ? t_old - k0 : x->tchunk;
-    const float *Xd = xdev ? X_old + k0 * x->slice
-                           : x->stage_in(X_old + k0 * x->slice, (size_t)n * x->slice * 4, 0);
+    const void *Xd = xdev ? x->slice_at(X_old, k0)
+                          : x->stage_in(x->slice_at(X_old, k0), n * x->slice_bytes(), 0);
     if (!Xd) return x->fail(OCTEN_ENOMEM, "staging X_old");
     x->compress(Xd, n, Wd + k0 * Qd);
     if (!xdev) cudaStreamSynchronize(x->st);   // the staging slot is reused
@@ -355,7 +382,7 @@ octen_status octen_n_init(octen_nctx *x, const float *X_old, int64_t t_old,
     // (already in x->A), results into x->A and x->C
     s = x->sync_check("init summaries");
     if (s != OCTEN_OK) return s;
-    const float *Xd = xdev ? X_old : x->stage_in(X_old, (size_t)t_old * x->slice * 4, 0);
+    const void *Xd = xdev ? X_old : x->stage_in(X_old, t_old * x->slice_bytes(), 0);
     if (!Xd) return x->fail(OCTEN_ENOMEM, "staging X_old");
     int64_t dims[kMaxNModes];
     dims[0] = t_old;
@@ -373,7 +400,7 @@ octen_status octen_n_init(octen_nctx *x, const float *X_old, int64_t t_old,
       aout[n] = x->A[n];
     }
     DenseCpNArgs a{};
-    a.X = Xd; a.NN = x->NN; a.dims = dims; a.R = c.R; a.iters = c.als_iters;
+    a.X = Xd; a.xt = x->xin; a.NN = x->NN; a.dims = dims; a.R = c.R; a.iters = c.als_iters;
     a.A0 = a0; a.A_out = aout; a.C_out = x->C; a.work = work; a.status = x->dstatus;
     a.st = x->st;
     dense_cp_n(a, x->RT);
@@ -395,7 +422,7 @@ octen_status octen_n_init(octen_nctx *x, const float *X_old, int64_t t_old,
   return OCTEN_OK;
 }
 
-octen_status octen_n_append(octen_nctx *x, const float *X_new, int64_t t, const float *W_new) {
+octen_status octen_n_append(octen_nctx *x, const void *X_new, int64_t t, const float *W_new) {
   if (!x) return OCTEN_EINVAL;
   if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_n_append before octen_n_init");
   if (!X_new || !W_new || t < 1 || t > kNBatchMax)
@@ -404,7 +431,7 @@ octen_status octen_n_append(octen_nctx *x, const float *X_new, int64_t t, const 
   const octen_nconfig &c = x->cfg;
   const int Qd = x->Qd, RT = x->RT, nm = x->nm;
   if (!x->ensure_c(x->K + t)) return x->fail(OCTEN_ENOMEM, "C");
-  const float *Xd = x->stage_in(X_new, (size_t)t * x->slice * 4, 0);
+  const void *Xd = x->stage_in(X_new, t * x->slice_bytes(), 0);
   const float *Wd = x->stage_in(W_new, (size_t)t * Qd * 4, 1);
   if (!Xd || !Wd) return x->fail(OCTEN_ENOMEM, "staging the batch");
   // 1. compress the batch into the summaries
@@ -522,6 +549,8 @@ std::vector<NStateArray> nstate_arrays(octen_nctx *x) {
     v.push_back({x->L[n], I * Qd * 4});
     v.push_back({x->A[n], I * c.R * 4});
   }
+  if (x->Ut16)
+    v.push_back({x->Ut16, P * Q * (size_t)x->dims[x->nm - 1] * sizeof(__nv_bfloat16)});
   size_t qn = 1;
   for (int n = 0; n < x->NN; ++n) qn *= Q;
   v.push_back({x->Y, P * qn * 4});
@@ -610,7 +639,7 @@ octen_status octen_n_load(const char *path, void *cuda_stream, octen_nctx **out)
   return OCTEN_OK;
 }
 
-octen_status octen_n_fit(octen_nctx *x, const float *X_all, int64_t K, double *fit_out) {
+octen_status octen_n_fit(octen_nctx *x, const void *X_all, int64_t K, double *fit_out) {
   if (!x || !X_all || !fit_out) return OCTEN_EINVAL;
   if (!x->initialized) return x->fail(OCTEN_ESTATE, "octen_n_fit before octen_n_init");
   if (K != x->K)
@@ -630,13 +659,14 @@ octen_status octen_n_fit(octen_nctx *x, const float *X_all, int64_t K, double *f
   octen_status s = OCTEN_OK;
   for (int64_t k0 = 0; k0 < K && s == OCTEN_OK; k0 += chunk) {
     const int64_t n = K - k0 < chunk ? K - k0 : chunk;
-    const float *Xd = dev ? X_all + k0 * x->slice
-                          : x->stage_in(X_all + k0 * x->slice, (size_t)n * x->slice * 4, 0);
+    const void *Xd = dev ? x->slice_at(X_all, k0)
+                         : x->stage_in(x->slice_at(X_all, k0), n * x->slice_bytes(), 0);
     if (!Xd) {
       s = x->fail(OCTEN_ENOMEM, "staging X_all");
       break;
     }
-    n_fit_sums(Xd, n, x->A, x->C + k0 * x->cfg.R, x->dims, x->nm, x->cfg.R, part, x->st);
+    n_fit_sums(Xd, x->xin, n, x->A, x->C + k0 * x->cfg.R, x->dims, x->nm, x->cfg.R, part,
+               x->st);
     cudaMemcpyAsync(h.data(), part, (size_t)n * nb * 2 * sizeof(double), cudaMemcpyDeviceToHost,
                     x->st);
     s = x->sync_check("fit");

@@ -206,3 +206,63 @@ def test_nmode_init_decomposition_matches_oracle(pkg, name):
         assert rel(As[n], o.A[n]) < TOL["F"], (n, rel(As[n], o.A[n]))
     assert rel(C, o.C) < TOL["F"]
     assert fms(tuple(As) + (C,), tuple(o.A) + (o.C,)) > TOL["fms"]
+
+
+def _bf16_case(case):
+    """The case's inputs with the slices and every projection rounded to bf16
+    (what a bf16 context receives and keeps)."""
+    from synth import round_to
+
+    d = case.make()
+    d["X"] = round_to(d["X"], "bf16")
+    d["U"] = [round_to(u, "bf16") for u in d["U"]]
+    return d
+
+
+def _bf16(a):
+    return dev(a).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("dims", [(40, 36, 32), (30, 28, 21)])
+def test_nmode_bf16_update_parity(pkg, dims):
+    """bf16 slices (N = 4): the slice-reading first contraction of the
+    compression runs in bf16 with fp32 accumulation, on tcgen05 when the
+    innermost size is a multiple of 8 (32) and on the SIMT kernels otherwise
+    (21).  bf16 products are exact in fp32, so against the oracle run on the
+    same bf16-rounded slices and projections the fp32 tolerances hold."""
+    case = NCase(dims, 4, 4, 8, 3, 10, (10, 4), 40, seed=22)
+    d = _bf16_case(case)
+    _, ref = case.oracle_run(d)
+    n_tc = pkg.tc_launch_count()
+    g = pkg.OctenN(case.dims, case.R, case.P, case.Q, case.S, case.iters, prec="bf16")
+    g.init(_bf16(d["X"][:case.t_old]), [dev(u) for u in d["U"]], dev(d["W"][0]),
+           [dev(a) for a in d["A0"]], dev(d["C0"]))
+    k = case.t_old
+    gpu = []
+    for b, t in enumerate(case.batches):
+        g.append(_bf16(d["X"][k:k + t]), dev(d["W"][b + 1]))
+        k += t
+        As, C = g.factors()
+        gpu.append(dict(Y=g.replicas(), A=As, C=C, raw=g.replica_factors(0),
+                        hat=g.replica_factors(1), fit=g.fit(_bf16(d["X"][:k]))))
+    g.close()
+    if dims[-1] % 8 == 0:
+        assert pkg.tc_launch_count() > n_tc, "the first contraction should run on tcgen05"
+    check(case, d, gpu, ref)
+
+
+def test_nmode_bf16_init_decomposition_matches_oracle(pkg):
+    """A bf16 context initialised without C0: the N-way CP-ALS of the bf16
+    slices matches the oracle's decomposition of the same values."""
+    case = CASES["n4"]
+    d = _bf16_case(case)
+    X_old = d["X"][:case.t_old]
+    g = pkg.OctenN(case.dims, case.R, case.P, case.Q, case.S, case.iters, prec="bf16")
+    g.init(_bf16(X_old), [dev(u) for u in d["U"]], dev(d["W"][0]), [dev(a) for a in d["A0"]],
+           None)
+    As, C = g.factors()
+    g.close()
+    ref = octen_n.decompose_existing_n(X_old, d["A0"], case.iters)
+    for n in range(case.N - 1):
+        assert rel(As[n], ref[n]) < TOL["F"], (n, rel(As[n], ref[n]))
+    assert rel(C, ref[-1]) < TOL["F"]
