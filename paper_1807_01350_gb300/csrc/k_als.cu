@@ -254,6 +254,8 @@ __global__ void __launch_bounds__(256)
   constexpr int OCT = RT / 8;            // column octets per output row
   constexpr int ROWS = 32 / OCT;         // output rows per CTA
   __shared__ float4 part[8][32][2];
+  pdl_trigger();
+  pdl_wait();   // the factor is the previous kernel's
   const int p = blockIdx.y;
   const int j = threadIdx.x & 31, sl = threadIdx.x >> 5;
   const int row = blockIdx.x * ROWS + j / OCT, r = 8 * (j % OCT);
@@ -310,6 +312,37 @@ __global__ void __launch_bounds__(256)
 
 static int block_for(int Q) { return ((Q + 31) / 32) * 32; }
 
+// K atoms per stage the ALS GEMMs start from (the autotuner also tries the
+// others): kAlsKAtoms, or OCTEN_ALS_KATOMS (1, 2 or 4), a debug setting that
+// pins the configuration a profiler capture sees when the autotuner is off.
+static int als_katoms() {
+  const char *v = getenv("OCTEN_ALS_KATOMS");
+  if (v && (v[0] == '1' || v[0] == '2' || v[0] == '4') && v[1] == 0) return v[0] - '0';
+  return kAlsKAtoms;
+}
+
+// The M1 / M2 reduction, as a programmatic dependent of the previous kernel
+// when `pdl` is set.
+template <int RT, int KIND>
+static void mred(dim3 grid, const __nv_bfloat16 *Tc, const float *Fac, int Q, float *M, bool pdl,
+                 cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  if (pdl) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  if (cudaLaunchKernelEx(&cfg, tc_mred_kernel<RT, KIND>, Tc, Fac, Q, M) != cudaSuccess) {
+    cudaGetLastError();
+    tc_mred_kernel<RT, KIND><<<grid, 256, 0, st>>>(Tc, Fac, Q, M);
+  }
+}
+
 int als_factor_floats(int RT) {
   return RT == 8 ? factor_floats<8>() : (RT == 16 ? factor_floats<16>() : factor_floats<32>());
 }
@@ -344,7 +377,7 @@ static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_
   const int rows = ((Q + cl - 1) / cl + 7) / 8 * 8;
   cl = (Q + rows - 1) / rows;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   cfg.gridDim = dim3(P * cl);
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = (size_t)rows * RT * sizeof(float);
@@ -353,8 +386,10 @@ static void apply(const float *M, int nsplit, int64_t split_stride, int64_t row_
   attr[0].val.clusterDim.x = cl;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = b.pdl ? 2 : 1;
   if (cudaLaunchKernelEx(&cfg, als_apply_kernel<RT>, M, nsplit, split_stride, row_stride,
                          (const float *)b.L, F, Ft, NP, Q, rows, normalize, Gout,
                          segQ) != cudaSuccess) {
@@ -453,8 +488,10 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
   // the bf16 copies of X_p stream through once per pass (evict-first), so Tc
   // stays in the L2 for the M2 pass
   m3.a_stream = tc.a_stream = true;
-  m3.katoms = tc.katoms = kAlsKAtoms;
+  m3.katoms = kAlsKAtoms;   // split-K: the split count below follows these atoms
+  tc.katoms = als_katoms();
   m3.max_ctas = tc.max_ctas = b.max_ctas;
+  m3.pdl = tc.pdl = b.pdl;
   const int ks = tc_gemm_splits(m3.K, b.ksplit, kAlsKAtoms);
   const dim3 gKR(NP, P);
   const dim3 gM((Q + 256 / RT - 1) / (256 / RT), P);   // 32 output octets per CTA
@@ -473,8 +510,9 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     m3f.m1_B = b.Af; m3f.m1_part = b.Mparts; m3f.Q = Q; m3f.RT = RT; m3f.m1_seg = seg;
     m3f.smem_reserve = kLdlReserve;
     m3f.a_stream = true;
-    m3f.katoms = kAlsKAtoms;
+    m3f.katoms = als_katoms();
     m3f.max_ctas = b.max_ctas;
+    m3f.pdl = b.pdl;
     // B^T of the warm start; every later B update writes it from its solve
     mk(kStAlsAux, 1);
     factor_bf16_t_kernel<RT><<<dim3((Q + 255) / 256, P), 256, 0, st>>>(b.Bf, Q, NP, b.Bt);
@@ -521,7 +559,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
       mk(kStAlsSolve, 0);
     } else {
       mk(kStAlsAux, 1);
-      tc_mred_kernel<RT, 1><<<gM, 256, 0, st>>>(Th, b.Bf, Q, b.M);
+      mred<RT, 1>(gM, Th, b.Bf, Q, b.M, b.pdl, st);
       count_launch();
       mk(kStAlsAux, 0);
       mk(kStAlsSolve, 1);
@@ -530,7 +568,7 @@ static bool als_run_tc(const float *Y, int P, int Q, int R, int iters, AlsBuffer
     }
     factor_async<RT>(b.GA, b.GC, P, R, b, st);
     mk(kStAlsAux, 1);
-    tc_mred_kernel<RT, 2><<<gM, 256, 0, st>>>(Th, b.Af, Q, b.M);
+    mred<RT, 2>(gM, Th, b.Af, Q, b.M, b.pdl, st);
     count_launch();
     mk(kStAlsAux, 0);
     mk(kStAlsSolve, 1);

@@ -372,6 +372,8 @@ __global__ void __launch_bounds__(256)
   extern __shared__ __align__(16) float Ms[];   // [rows_per_cta][RT]
   __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT], Gp[RT * RT];
   __shared__ float red[8 * RT], part[RT], scale[RT];
+  pdl_trigger();
+  pdl_wait();   // the MTTKRP partials are the previous kernel's
   const int tid = threadIdx.x;
   const uint32_t ncta = cluster_size(), crank = cluster_rank();
   const int p = blockIdx.x / ncta;

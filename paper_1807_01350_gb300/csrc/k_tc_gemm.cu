@@ -195,7 +195,7 @@ struct TcShape {
   int a_hi, a_lo, b_hi, b_lo;
   int ksplit;           // > 1: blockIdx.x is the K split (a single N tile)
   int a_stream;         // A is read once: load it with an L2 evict-first policy
-  int katoms;           // 128-byte K atoms per pipeline stage (1 or 2)
+  int katoms;           // 128-byte K atoms per pipeline stage (1, 2 or 4)
   long long wait_budget;   // clock cycles a pipeline wait may take before the CTA
                            // gives up (the drains after a give-up keep kWaitBudget)
 };
@@ -368,6 +368,10 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+  // everything above is setup: the operands and outputs of the update are
+  // touched only once the previous kernel of the chain has completed
+  pdl_trigger();
+  pdl_wait();
 
   // work item -> (z, m0, n0 or split, first K block, K blocks)
   auto decode = [&](int tile, int &z, int &m0, int &n0, int &split, int &kb0, int &nk) {
@@ -662,11 +666,11 @@ long long wait_budget_cycles() {
 template <int KIND, class Epi>
 bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int batch,
                const Epi &epi, int *status, cudaStream_t st, int smem_reserve = 0,
-               int max_ctas = 0, int max_stages = 0) {
+               int max_ctas = 0, int max_stages = 0, bool pdl = false) {
   sh.wait_budget = wait_budget_cycles();
   sh.tmem_cols = pow2_at_least(2 * sh.BN);       // two accumulators
   if (sh.tmem_cols > 512) return false;
-  if (sh.katoms != 2) sh.katoms = 1;   // kernels exist for 1 and 2 atoms per stage
+  if (sh.katoms != 2 && sh.katoms != 4) sh.katoms = 1;   // kernels for 1, 2 and 4 atoms
   const size_t per_stage = static_cast<size_t>(kBM + sh.BN) * kRowBytes * sh.katoms;
   const size_t stage_bytes = Epi::kRowMajor ? 4 * 32 * 33 * sizeof(float) + 16
                              : Epi::kSeg   ? 4 * 32 * 32 * sizeof(__nv_bfloat16) + 16
@@ -677,7 +681,9 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
   if (max_stages >= 2 && sh.stages > max_stages) sh.stages = max_stages;
   if (sh.stages < 2) return false;
   const size_t smem = 1024 + per_stage * sh.stages + (2 * sh.stages + 5) * 8 + 16 + stage_bytes;
-  auto kern = sh.katoms == 2 ? tc_gemm_kernel<KIND, Epi, 2> : tc_gemm_kernel<KIND, Epi, 1>;
+  auto kern = sh.katoms == 4   ? tc_gemm_kernel<KIND, Epi, 4>
+              : sh.katoms == 2 ? tc_gemm_kernel<KIND, Epi, 2>
+                               : tc_gemm_kernel<KIND, Epi, 1>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return false;
@@ -688,6 +694,13 @@ bool launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcShape sh, int bat
   cfg.blockDim = dim3(192);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (pdl) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
   const int slots = max_ctas > 0 && max_ctas < sm_count() ? max_ctas : sm_count();
   const int grid_items = (int)(items < slots ? items : slots);
   cfg.gridDim = dim3(grid_items);
@@ -878,7 +891,7 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
       !make_map(&mb, g.B, false, g.b_inner, g.b_rows, g.BN))
     return false;
   // the split count is fixed by the caller's K atoms (it sets the summation)
-  const int katoms0 = g.katoms == 2 ? 2 : 1;
+  const int katoms0 = g.katoms == 2 || g.katoms == 4 ? g.katoms : 1;
   const int ks = tc_gemm_splits(g.K, g.ksplit, katoms0);
   const bool seg = g.m1_part && g.m1_seg;
   if (g.m1_part && (g.BN != 32 || ks > 1 || (seg ? g.Q < 32 : g.Q % 32 != 0))) return false;
@@ -893,21 +906,22 @@ bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st) {
     sh.katoms = c.katoms;
     sh.ksplit = ks;
     return launch_tc<0>(ma, mb, sh, g.batch, epi, status, st, g.smem_reserve, g.max_ctas,
-                        c.stages);
+                        c.stages, g.pdl);
   };
-  // with split-K the other atom count is a candidate only if it cuts K at the
-  // same places (the splits set the summation)
-  const int katoms1 = katoms0 == 2 ? 1 : 2;
+  // candidates: the caller's K atoms per stage with as many pipeline stages
+  // as fit or three (fewer bytes in flight per SM, more room beside the
+  // GEMM), and the other atom counts (1, 2, 4: with four, a tile's rows of
+  // K = 256 arrive as whole 512-byte rows); with split-K another atom count
+  // only if it cuts K at the same places (the splits set the summation)
   auto split_elems = [&](int k) {
     const int nk = (g.K + 64 * k - 1) / (64 * k);
     return ((nk + ks - 1) / ks) * 64 * k;
   };
-  // pipeline depth: as many stages as fit, or three (fewer bytes in flight
-  // per SM, more room beside the GEMM)
-  const bool other_atoms = !(ks > 1 && split_elems(katoms0) != split_elems(katoms1));
-  TuneChoice cand[4] = {{katoms0, g.BN, 0}, {katoms0, g.BN, 3}, {katoms1, g.BN, 0},
-                        {katoms1, g.BN, 3}};
-  const int ncand = other_atoms ? 4 : 2;
+  TuneChoice cand[5] = {{katoms0, g.BN, 0}, {katoms0, g.BN, 3}};
+  int ncand = 2;
+  for (int k : {1, 2, 4})
+    if (k != katoms0 && (ks == 1 || split_elems(k) == split_elems(katoms0)))
+      cand[ncand++] = TuneChoice{k, g.BN, 0};
   const std::array<int64_t, 8> key{1 + 16 * (int64_t)g.max_ctas, g.M, g.N, g.K, g.batch, ks,
                                    g.Dh != nullptr, g.m1_part != nullptr};
   return launch(tuned(key, cand, ncand, st, launch));

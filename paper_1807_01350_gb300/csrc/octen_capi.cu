@@ -407,6 +407,14 @@ int als_groups_wanted(int P) {
   return g > P ? P : g;
 }
 
+// The replica CP-ALS chain as programmatic dependent launches: OCTEN_PDL=1
+// (off by default: at 4000^2 it measured 1435 against 1642 slices/s, the
+// early-launched kernels waiting resident on the SMs beside the running ones).
+bool pdl_wanted() {
+  const char *v = getenv("OCTEN_PDL");
+  return v && v[0] == '1';
+}
+
 // OCTEN_GEMM=simt keeps the large contractions on the SIMT kernels (used to
 // cross-check the tensor-core kernels against an independent implementation).
 bool tc_wanted() {
@@ -843,6 +851,7 @@ AlsBuffers als_buffers(octen_ctx *x) {
   ab.gsplit = x->grp_split;
   ab.Qp = x->als_qp;
   ab.max_ctas = x->als_ctas;
+  ab.pdl = pdl_wanted();
   ab.Af_pad = x->Apad; ab.Bf_pad = x->Bpad; ab.Cf_pad = x->Cpad;
   return ab;
 }

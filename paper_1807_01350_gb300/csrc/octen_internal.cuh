@@ -24,6 +24,19 @@ enum class Elem : int { F32 = 0, BF16 = 1, E4M3 = 2 };
 
 inline size_t elem_size(Elem e) { return e == Elem::F32 ? 4 : (e == Elem::BF16 ? 2 : 1); }
 
+// Programmatic dependent launch inside the replica CP-ALS chain: a kernel
+// launched with cudaLaunchAttributeProgrammaticStreamSerialization may start
+// while its predecessor on the stream is still running.  pdl_trigger lets the
+// next kernel of the chain launch early (its CTAs then do their setup beside
+// this one); pdl_wait blocks until the predecessor has completed and its
+// writes are visible.  Every kernel of the chain calls both before it touches
+// any data of the update, so the chain's order of reads and writes is the
+// stream's.  Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Counts every kernel launch issued through the launch helpers below.
 void count_launch();
 // Adds to the launch counters (negative: launches that did not do the work).
@@ -131,6 +144,8 @@ struct TcStoreArgs {
   // at most this many CTAs (0: one per SM), so that another GEMM can run on
   // the other SMs at the same time
   int max_ctas = 0;
+  // launched as a programmatic dependent of the previous kernel on the stream
+  bool pdl = false;
 };
 bool tc_gemm_store(const TcStoreArgs &g, int *status, cudaStream_t st);
 // the split count tc_gemm_store will use
@@ -187,6 +202,9 @@ struct AlsBuffers {
   float *L = nullptr;                           // P x als_factor_floats(RT)
   // GEMM grid cap of this group's passes (0: one CTA per SM)
   int max_ctas = 0;
+  // the chain's GEMMs, solves and reductions launched as programmatic
+  // dependents of their predecessors (OCTEN_PDL=0: ordinary launches)
+  bool pdl = false;
   // Q not a multiple of 8 (Q >= 32): the tensor-core passes run on X_p
   // zero-padded to Qp = the next multiple of 8 (the TMA row pitch of the bf16
   // copies), with factors Af_pad, Bf_pad, Cf_pad (P x Qp x RT, the rows past Q
