@@ -305,6 +305,7 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
         torch.distributed.barrier()
     launches0 = pkg.launch_count()
     tc0 = pkg.tc_launch_count()
+    fb0 = pkg.tc_fallback_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk, no_gc():
         torch.cuda.synchronize()
@@ -316,6 +317,7 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
         torch.cuda.synchronize()
     launches = pkg.launch_count() - launches0
     tc_launches = pkg.tc_launch_count() - tc0
+    tc_fallbacks = pkg.tc_fallback_count() - fb0
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     if world > 1:
         torch.distributed.barrier()
@@ -335,7 +337,8 @@ def run_stream(args, wl, prec, steps, warmup, rank, world, time_e2e):
     if tc_launches >= (2 + 2 * wl.als_iters + 1) * steps:
         tc_stages = tc_stages + ("als_gemm",)
     out = dict(ms=ms, steps=steps, slices=steps * t, stages=stages, stage_steps=nbd, fit=fit,
-               launches=launches, tc_launches=tc_launches, tc_stages=tc_stages,
+               launches=launches, tc_launches=tc_launches, tc_fallbacks=tc_fallbacks,
+               tc_stages=tc_stages,
                clocks=clk.summary())
     if time_e2e:
         out["e2e"] = run_e2e(g, d, wl, prec, k, steps, warmup, rank, world)
@@ -679,6 +682,7 @@ def main():
         "clocks": main_run["clocks"],
         "gpu_launches": main_run["launches"],
         "tcgen05_launches": main_run["tc_launches"],
+        "tcgen05_fallbacks": main_run["tc_fallbacks"],
         "roofline": roof,
         "stage_ms_per_step": {k: round(v[0] / main_run["stage_steps"], 3)
                               for k, v in timed.items()},

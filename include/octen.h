@@ -104,10 +104,13 @@ octen_status octen_init(octen_ctx *ctx, const void *X_old, int64_t t_old,
  * (t x Qd): Y_p += Z_p, CP-ALS of every replica warm-started from U_p^T A,
  * V_p^T B, anchor matching, lift of A and B, t new rows of C.  Limit
  * t <= min(64, 65535 / P) (one mode-1 product per slice and replica).
- * The CP-ALS of the replicas is recorded once as a CUDA graph (on a private
- * stream, at the second append made with the stage timers off) and replayed on
- * the context's stream at every later such append; environment variable
- * OCTEN_GRAPH=0 issues its launches one by one instead.  The first call for
+ * Everything after the batch's mode-2 contraction (mode 1, mode 3, the warm
+ * start, the replica CP-ALS, the match, the lift, the new rows of C) is
+ * recorded once per batch size as a CUDA graph (on a private stream, at the
+ * second append made with the stage timers off) and replayed on the context's
+ * stream at every later such append; a reallocated scratch buffer drops the
+ * recordings; environment variable OCTEN_GRAPH=0 issues the launches one by
+ * one instead.  The first call for
  * each tensor-core GEMM shape times its candidate tile configurations (only
  * ones that give bit-identical results) and keeps the fastest for the process;
  * OCTEN_AUTOTUNE=0 keeps the defaults.  Host slices are copied in pieces on a
@@ -146,12 +149,20 @@ octen_status octen_append_async(octen_ctx *ctx, const void *X_new, int64_t t,
 octen_status octen_wait(octen_ctx *ctx, int64_t ticket);
 
 /* One append on each of n independent decompositions (many streams with
- * uneven shapes, ranks and batch sizes): the work of every context is enqueued
- * on that context's own stream before any of them is waited for, so streams
- * created on different CUDA streams run concurrently.  Arguments per stream as
- * in octen_append.  Every context whose work was enqueued without error is
- * advanced; the first error is returned (details via octen_last_error of that
- * context). */
+ * uneven shapes, ranks and batch sizes).  Every context is first prepared
+ * (arguments checked, every allocation made).  Once each context has recorded
+ * the tail of an append of its batch size (from its second append on) and
+ * every array is device memory, the whole step is one CUDA graph launch: per
+ * context a branch with its head (W rows, quantisation, mode 2), a clone of
+ * its recorded tail and the copy of its new C rows, the branches independent;
+ * the graph is built once for the contexts and batch sizes and later steps
+ * only update its heads and copies.  Otherwise the appends are enqueued one by
+ * one, each on its context's stream, before any of them is waited for.  The
+ * contexts' CP-ALS GEMMs run on 1 / min(n, 8) of the SMs each (environment
+ * variable OCTEN_MANY_CTAS: that many CTAs; 0 all), so that several contexts'
+ * GEMMs run side by side.  Arguments per stream as in octen_append.  Every
+ * context whose work was enqueued without error is advanced; the first error
+ * is returned (details via octen_last_error of that context). */
 octen_status octen_append_many(octen_ctx *const *ctxs, int n, const void *const *X_new,
                                const int64_t *t, const float *const *W_new);
 
@@ -255,6 +266,13 @@ const char *octen_status_name(octen_status s);
  * for e4m3; otherwise the SIMT kernels run). */
 uint64_t octen_launch_count(void);
 uint64_t octen_tc_launch_count(void);
+
+/* Tensor-core contractions that were wanted (bf16 / e4m3 operands on sm_103)
+ * but refused, an operand row pitch off the TMA rules or a resource limit,
+ * so that the SIMT kernels ran instead.  The first one in a process is also
+ * reported on stderr.  Not in the paper: a guard against a slow path passing
+ * unnoticed. */
+uint64_t octen_tc_fallback_count(void);
 
 /* Stage timers (measurement aid, not part of the method).  With timing on,
  * every append records CUDA events on the context's stream around each

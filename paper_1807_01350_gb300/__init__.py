@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         L.octen_launch_count.restype = ctypes.c_uint64
         L.octen_tc_launch_count.argtypes = []
         L.octen_tc_launch_count.restype = ctypes.c_uint64
+        L.octen_tc_fallback_count.argtypes = []
+        L.octen_tc_fallback_count.restype = ctypes.c_uint64
         L.octen_stage_count.argtypes = []
         L.octen_stage_count.restype = ctypes.c_int
         L.octen_stage_name.argtypes = [ctypes.c_int]
@@ -143,6 +145,11 @@ def launch_count() -> int:
 
 def tc_launch_count() -> int:
     return int(lib().octen_tc_launch_count())
+
+
+def tc_fallback_count() -> int:
+    """Wanted tensor-core contractions that ran on the SIMT kernels instead."""
+    return int(lib().octen_tc_fallback_count())
 
 
 def _stream_handle(stream) -> int | None:

@@ -151,12 +151,14 @@ extern "C" octen_status octen_compress_noalloc(const octen_config *cfg, void *cu
     }
     if (!(use_tc && mode2_tc(m2, status, st))) {
       cudaGetLastError();
+      if (use_tc) count_tc_fallback("mode-2 contraction");
       mode2_simt(m2, st);
     }
     Mode1Args m1{};
     m1.Ut = Ut; m1.T = T; m1.te = tmid; m1.T2 = T2; m1.t = n; m1.I = c.I; m1.P = c.P; m1.Q = c.Q;
     if (!(use_tc && mode1_tc(m1, status, st))) {
       cudaGetLastError();
+      if (use_tc) count_tc_fallback("mode-1 contraction");
       mode1_simt(m1, st);
     }
     mode3_accumulate(T2, W_all + k0 * Qd, Z, n, c.P, c.Q, c.S, Qd, st);

@@ -17,8 +17,20 @@ using namespace octen;
 namespace octen {
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_tc_launches{0};
+static std::atomic<uint64_t> g_tc_fallbacks{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_tc_launch() { g_tc_launches.fetch_add(1, std::memory_order_relaxed); }
+// A tensor-core contraction that was wanted (bf16 / e4m3 operands on sm_103)
+// but refused (an operand pitch off the TMA rules, a resource limit): the
+// SIMT kernels run instead.  Counted, and reported once per process on stderr
+// so that a slow path does not pass unnoticed.
+void count_tc_fallback(const char *what) {
+  if (g_tc_fallbacks.fetch_add(1, std::memory_order_relaxed) == 0)
+    fprintf(stderr,
+            "octen: a tensor-core launch (%s) was refused; the SIMT kernels run instead "
+            "(octen_tc_fallback_count() counts these)\n",
+            what);
+}
 bool is_device_pointer(const void *p) {
   if (p == nullptr) return false;
   cudaPointerAttributes a{};
@@ -484,6 +496,7 @@ void compress_mode2(octen_ctx *x, const void *Xd, int64_t k0, int64_t n) {
   x->mark(kStMode2, 1);
   if (!(x->use_tc && mode2_tc(m2, x->dstatus, x->st))) {
     cudaGetLastError();
+    if (x->use_tc) count_tc_fallback("mode-2 contraction");
     mode2_simt(m2, x->st);
   }
   x->mark(kStMode2, 0);
@@ -501,6 +514,7 @@ void compress_finish(octen_ctx *x, int64_t t, const float *Wd, float *Yacc, bool
   x->mark(kStMode1, 1);
   if (!(x->use_tc && mode1_tc(m1, x->dstatus, x->st))) {
     cudaGetLastError();
+    if (x->use_tc) count_tc_fallback("mode-1 contraction");
     mode1_simt(m1, x->st);
   }
   x->mark(kStMode1, 0);
@@ -963,6 +977,7 @@ void tail_enqueue(octen_ctx *x, int64_t t) {
   if (!tail_front(x, t, mk)) {
     // a tensor-core launch was refused: redo the CP from the warm start on SIMT
     cudaGetLastError();
+    count_tc_fallback("replica CP-ALS GEMM");
     x->als_tc = false;
     x->drop_graphs();
     AlsBuffers ab = als_buffers(x);
@@ -1585,6 +1600,8 @@ const char *octen_status_name(octen_status s) {
 uint64_t octen_launch_count(void) { return g_launches.load(); }
 
 uint64_t octen_tc_launch_count(void) { return g_tc_launches.load(); }
+
+uint64_t octen_tc_fallback_count(void) { return g_tc_fallbacks.load(); }
 
 static const char *kStageNames[kNumStages] = {"quantize", "mode2", "mode1", "mode3",
                                               "warm_start", "als_gemm", "als_aux", "als_solve",

@@ -108,6 +108,8 @@ bool tc_supported();
 bool mode2_tc(const Mode2Args &a, int *status, cudaStream_t st);
 bool mode1_tc(const Mode1Args &a, int *status, cudaStream_t st);
 void count_tc_launch();
+// a wanted tensor-core launch that was refused (the SIMT kernels ran instead)
+void count_tc_fallback(const char *what);
 
 // Generic bf16 tcgen05 GEMM with a plain fp32 store, used by the replica ALS:
 //   D[split][z](m, n) = sum_{k in split} A[z * a_rows_per_z + m][k] * B[z * b_rows_per_z + n][k]

@@ -109,3 +109,26 @@ def test_n_mode_sizes(lib):
     _raises(lambda: g.append(z(t, 5, 4), z(t, Qd)), "X_new")
     _raises(lambda: g.append(z(t, *d), z(t, Qd - 1)), "W_new")
     _raises(lambda: g.fit(z(t, 5, 4, 2)), "X_all")
+
+
+def test_async_append_takes_arrays_as_they_are(lib):
+    """octen_append_async reads its inputs after the call returns, so the
+    binding refuses arrays it would have to convert (a converted copy would be
+    freed first): wrong element type or non-contiguous.  Refused before the
+    library is called (EINVAL)."""
+    g = _octen(lib, prec="fp32")
+    I, J, Qd, t = g.I, g.J, g.Qd, 3
+    x64 = np.zeros((t, I, J), np.float64)
+    _raises(lambda: g.append_async(x64, np.zeros((t, Qd), np.float32)), "X_new")
+    xT = np.zeros((t, J, I), np.float32).transpose(0, 2, 1)
+    _raises(lambda: g.append_async(xT, np.zeros((t, Qd), np.float32)), "X_new")
+    w64 = np.zeros((t, Qd), np.float64)
+    _raises(lambda: g.append_async(np.zeros((t, I, J), np.float32), w64), "W_new")
+    bf = _octen(lib, prec="bf16")
+    # a bf16 context takes bf16 slices; numpy has no bf16, so numpy is refused
+    _raises(lambda: bf.append_async(np.zeros((t, I, J), np.float32),
+                                    np.zeros((t, bf.Qd), np.float32)), "X_new")
+    # right types: the call reaches the library, which has no context here
+    with pytest.raises(pkg.OctenError) as e:
+        g.append_async(np.zeros((t, I, J), np.float32), np.zeros((t, Qd), np.float32))
+    assert e.value.status == 1 and "X_new" not in str(e.value)

@@ -233,3 +233,24 @@ def test_padded_replicas_run_the_tensor_core_als(pkg, Q, monkeypatch):
         assert abs(a["fit"] - b["fit"]) < 1e-3
         for key in ("A", "B", "C"):
             assert rel(a[key], b[key]) < 5e-2, key
+
+
+def test_refused_tensor_core_launches_are_counted(pkg):
+    """A bf16 compression whose operand rows meet the TMA pitch rule runs both
+    contractions on tcgen05 with no fallback; one whose slice rows are 150
+    bf16 (300 bytes, not a multiple of 16) runs mode 2 on the SIMT kernels,
+    and that refused launch is counted (the first of a process is also
+    reported on stderr); the result is right either way."""
+    for (I, J), want_fallback in (((152, 144), False), ((152, 150), True)):
+        P, Q, S, t = 3, 24, 4, 5
+        case = Case(I, J, 4, P, Q, S, t, (), 1, prec="bf16", seed=26)
+        d = case.make()
+        f0 = pkg.tc_fallback_count()
+        Z = pkg.compress(I, J, P, Q, S, dev(d["X"], torch.bfloat16), dev(d["U"]), dev(d["V"]),
+                         dev(d["W"][0]), prec="bf16")
+        assert (pkg.tc_fallback_count() > f0) == want_fallback, (J, pkg.tc_fallback_count(), f0)
+        for p in range(P):
+            ref = oracle.compress(d["X"], oracle.replica_block(d["U"], p, Q, S),
+                                  oracle.replica_block(d["V"], p, Q, S),
+                                  oracle.replica_block(d["W"][0], p, Q, S))
+            assert rel(Z[p], ref) < TOL_Y["bf16"]
