@@ -354,47 +354,20 @@ __device__ __forceinline__ float ld_cluster(const float *p, uint32_t rank) {
   return v;
 }
 
-// F_p = M_p (L D L^T)^-1 for rows [rank * rows_per_cta, ...) of replica p,
-// M_p the sum of `nsplit` partial MTTKRPs (row q of split s at M + s *
-// split_stride + (p * Q + q) * row_stride).  A cluster of CTAs shares a
-// replica (grid P * cluster size); with `normalize` the column norms are summed
-// over the cluster through distributed shared memory and the columns scaled to
-// unit l2.  Writes F_p and, if Ft is given, a bf16 copy transposed to [NP][Q]
-// (rows >= R zero) for the tensor-core passes; with Gout the Gram F_p^T F_p
-// (each CTA's rows, then the partials summed over the cluster in rank order).
-// 256 threads; dynamic smem rows_per_cta * RT floats.
+// Rows [row0, row0 + nrows) of M_p summed over `nsplit` partial MTTKRPs into
+// Ms (nrows x RT): row q of split s at M + s * split_stride + (p * Q + q) *
+// row_stride, or with segQ > 0 the segmented partials m1_part[p][j][2][RT] of
+// the blocks j of 32 rows (q', i) that hold rows of q (segment 0 if the block
+// starts in q).  RT / 4 threads per row, a float4 of columns each.
 template <int RT>
-__global__ void __launch_bounds__(256)
-    als_apply_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
-                     int64_t row_stride, const float *__restrict__ Lin, float *__restrict__ F,
-                     __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int rows_per_cta,
-                     int normalize, float *__restrict__ Gout, int segQ) {
-  extern __shared__ __align__(16) float Ms[];   // [rows_per_cta][RT]
-  __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT], Gp[RT * RT];
-  __shared__ float red[8 * RT], part[RT], scale[RT];
-  pdl_trigger();
-  pdl_wait();   // the MTTKRP partials are the previous kernel's
-  const int tid = threadIdx.x;
-  const uint32_t ncta = cluster_size(), crank = cluster_rank();
-  const int p = blockIdx.x / ncta;
-  const int row0 = crank * rows_per_cta;
-  const int nrows = Q - row0 < rows_per_cta ? (Q - row0 > 0 ? Q - row0 : 0) : rows_per_cta;
-  {
-    const float4 *li = reinterpret_cast<const float4 *>(Lin + (int64_t)p * factor_floats<RT>());
-    float4 *lc = reinterpret_cast<float4 *>(Lc), *lr = reinterpret_cast<float4 *>(Lr);
-    for (int e = tid; e < RT * RT / 4; e += blockDim.x) {
-      lc[e] = li[e];
-      lr[e] = li[RT * RT / 4 + e];
-    }
-    if (tid < RT) rf[tid] = Lin[(int64_t)p * factor_floats<RT>() + 2 * RT * RT + tid];
-  }
-  // rows of M: RT / 4 threads per row, each a float4 of columns summed over the splits
+__device__ __forceinline__ void sum_partial_rows(const float *__restrict__ M, int nsplit,
+                                                 int64_t split_stride, int64_t row_stride,
+                                                 int segQ, int p, int Q, int row0, int nrows,
+                                                 float *Ms) {
   constexpr int TPR = RT / 4;
-  for (int e = tid; e < nrows * TPR; e += blockDim.x) {
+  for (int e = threadIdx.x; e < nrows * TPR; e += blockDim.x) {
     const int rr = e / TPR, c4 = e - (e / TPR) * TPR;
     if (segQ > 0) {
-      // segmented partials m1_part[p][j][2][RT] of the blocks j of 32 rows
-      // (q', i) that hold rows of q: segment 0 if the block starts in q
       const int q = row0 + rr;
       const int64_t nblk = ((int64_t)segQ * segQ + 31) / 32;
       const int64_t first = (int64_t)q * segQ, last = first + segQ - 1;
@@ -427,15 +400,17 @@ __global__ void __launch_bounds__(256)
     }
     *reinterpret_cast<float4 *>(Ms + rr * RT + 4 * c4) = acc;
   }
-  __syncthreads();
+}
 
-  // f = M row solved against L D L^T: forward with L, scale by 1/D, backward with L^T
-  const bool own = tid < nrows;
-  float y[RT];
+// y = row `threadIdx.x` of Ms solved against L D L^T (zero for threads past
+// the CTA's rows).
+template <int RT>
+__device__ __forceinline__ void solve_own_row(const float *Ms, bool own, const float *Lc,
+                                              const float *Lr, const float *rf, float (&y)[RT]) {
 #pragma unroll
   for (int r = 0; r < RT; ++r) y[r] = 0.f;
   if (own) {
-    const float4 *mr = reinterpret_cast<const float4 *>(Ms + tid * RT);
+    const float4 *mr = reinterpret_cast<const float4 *>(Ms + threadIdx.x * RT);
 #pragma unroll
     for (int r4 = 0; r4 < RT / 4; ++r4) {
       const float4 v = mr[r4];
@@ -443,49 +418,109 @@ __global__ void __launch_bounds__(256)
     }
     ldl_substitute<RT>(y, Lc, Lr, rf);
   }
-  if (normalize && Gout) {
-    // one reduction serves both: the Gram of the unnormalised rows (per CTA,
-    // then over the cluster) gives the column norms on its diagonal, and the
-    // Gram of the normalised factor is that Gram scaled by 1/(n_r n_s)
-    __syncthreads();   // every row of Ms has been read
-    if (own) {
-      float4 *mr = reinterpret_cast<float4 *>(Ms + tid * RT);
+}
+
+template <int RT>
+__device__ __forceinline__ void store_row(float *dst, const float (&y)[RT]) {
+  float4 *o = reinterpret_cast<float4 *>(dst);
 #pragma unroll
-      for (int r4 = 0; r4 < RT / 4; ++r4)
-        mr[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
+  for (int r4 = 0; r4 < RT / 4; ++r4)
+    o[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
+}
+
+// Column norms and Gram of the solved rows over the cluster.  One reduction
+// serves both: the Gram of the unnormalised rows (per CTA into Gp, then summed
+// over the cluster in rank order) has the squared column norms on its
+// diagonal, and the Gram of the normalised factor is that Gram scaled by
+// 1 / (n_r n_s).  On return scale[r] = 1 / n_r (1 for a zero column) and this
+// CTA's share of the normalised Gram, entries [e0, e1) with e0 = rank * RT^2 /
+// size, is in Gout_p; peers may still be reading Gp, so the caller closes with
+// a cluster barrier before Gp is written again or the CTA exits.
+template <int RT>
+__device__ __forceinline__ void cluster_gram_scale(const float (&y)[RT], bool own, float *Ms,
+                                                   int nrows, float *Gp, float *scale,
+                                                   float *__restrict__ Gout_p, uint32_t crank,
+                                                   uint32_t ncta) {
+  const int tid = threadIdx.x;
+  __syncthreads();   // every row of Ms has been read
+  if (own) store_row<RT>(Ms + tid * RT, y);
+  __syncthreads();
+  smem_gram<RT>(Ms, nrows, Gp);
+  cluster_barrier();   // every CTA's partial Gram is in place
+  if (tid < RT) {
+    float tot = 0.f;
+    for (uint32_t c = 0; c < ncta; ++c) tot += ld_cluster(Gp + tid * (RT + 1), c);
+    const float n = sqrtf(tot);
+    scale[tid] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
+  }
+  __syncthreads();   // scale visible CTA-wide
+  const int e0 = (int)(crank * (RT * RT) / ncta), e1 = (int)((crank + 1) * (RT * RT) / ncta);
+  for (int e = e0 + tid; e < e1; e += blockDim.x) {
+    float g = 0.f;
+    for (uint32_t c = 0; c < ncta; ++c) g += ld_cluster(Gp + e, c);
+    Gout_p[e] = g * scale[e / RT] * scale[e % RT];
+  }
+}
+
+// Row q of F_p (and, with Ft, column q of its bf16 transpose [NP][Q], rows >= RT zero).
+template <int RT>
+__device__ __forceinline__ void store_factor_row(const float (&y)[RT], float *__restrict__ F,
+                                                 __nv_bfloat16 *__restrict__ Ft, int NP, int p,
+                                                 int Q, int q) {
+  store_row<RT>(F + ((int64_t)p * Q + q) * RT, y);
+  if (Ft) {
+#pragma unroll
+    for (int r = 0; r < RT; ++r) Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(y[r]);
+    for (int r = RT; r < NP; ++r) Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(0.f);
+  }
+}
+
+// F_p = M_p (L D L^T)^-1 for rows [rank * rows_per_cta, ...) of replica p,
+// M_p the sum of `nsplit` partial MTTKRPs (sum_partial_rows).  A cluster of
+// CTAs shares a replica (grid P * cluster size); with `normalize` the column
+// norms are summed over the cluster through distributed shared memory and the
+// columns scaled to unit l2.  Writes F_p and, if Ft is given, a bf16 copy
+// transposed to [NP][Q] (rows >= R zero) for the tensor-core passes; with Gout
+// the Gram F_p^T F_p (each CTA's rows, then the partials summed over the
+// cluster in rank order).  256 threads; dynamic smem rows_per_cta * RT floats.
+template <int RT>
+__global__ void __launch_bounds__(256)
+    als_apply_kernel(const float *__restrict__ M, int nsplit, int64_t split_stride,
+                     int64_t row_stride, const float *__restrict__ Lin, float *__restrict__ F,
+                     __nv_bfloat16 *__restrict__ Ft, int NP, int Q, int rows_per_cta,
+                     int normalize, float *__restrict__ Gout, int segQ) {
+  extern __shared__ __align__(16) float Ms[];   // [rows_per_cta][RT]
+  __shared__ __align__(16) float Lc[RT * RT], Lr[RT * RT], rf[RT], Gp[RT * RT];
+  __shared__ float red[8 * RT], part[RT], scale[RT];
+  pdl_trigger();
+  pdl_wait();   // the MTTKRP partials are the previous kernel's
+  const int tid = threadIdx.x;
+  const uint32_t ncta = cluster_size(), crank = cluster_rank();
+  const int p = blockIdx.x / ncta;
+  const int row0 = crank * rows_per_cta;
+  const int nrows = Q - row0 < rows_per_cta ? (Q - row0 > 0 ? Q - row0 : 0) : rows_per_cta;
+  {
+    const float4 *li = reinterpret_cast<const float4 *>(Lin + (int64_t)p * factor_floats<RT>());
+    float4 *lc = reinterpret_cast<float4 *>(Lc), *lr = reinterpret_cast<float4 *>(Lr);
+    for (int e = tid; e < RT * RT / 4; e += blockDim.x) {
+      lc[e] = li[e];
+      lr[e] = li[RT * RT / 4 + e];
     }
-    __syncthreads();
-    smem_gram<RT>(Ms, nrows, Gp);
-    cluster_barrier();   // every CTA's partial Gram is in place
-    if (tid < RT) {
-      float tot = 0.f;
-      for (uint32_t c = 0; c < ncta; ++c) tot += ld_cluster(Gp + tid * (RT + 1), c);
-      const float n = sqrtf(tot);
-      scale[tid] = n > 0.f ? 1.f / n : 1.f;   // reciprocal norm per column
-    }
-    __syncthreads();   // scale visible CTA-wide
-    const int e0 = (int)(crank * (RT * RT) / ncta), e1 = (int)((crank + 1) * (RT * RT) / ncta);
-    for (int e = e0 + tid; e < e1; e += blockDim.x) {
-      float g = 0.f;
-      for (uint32_t c = 0; c < ncta; ++c) g += ld_cluster(Gp + e, c);
-      Gout[(int64_t)p * RT * RT + e] = g * scale[e / RT] * scale[e % RT];
-    }
+    if (tid < RT) rf[tid] = Lin[(int64_t)p * factor_floats<RT>() + 2 * RT * RT + tid];
+  }
+  sum_partial_rows<RT>(M, nsplit, split_stride, row_stride, segQ, p, Q, row0, nrows, Ms);
+  __syncthreads();
+
+  // f = M row solved against L D L^T: forward with L, scale by 1/D, backward with L^T
+  const bool own = tid < nrows;
+  float y[RT];
+  solve_own_row<RT>(Ms, own, Lc, Lr, rf, y);
+  if (normalize && Gout) {
+    cluster_gram_scale<RT>(y, own, Ms, nrows, Gp, scale, Gout + (int64_t)p * RT * RT, crank, ncta);
     cluster_barrier();   // peers are done reading Gp
 #pragma unroll
     for (int r = 0; r < RT; ++r) y[r] *= scale[r];
-    if (own) {
-      const int q = row0 + tid;
-      float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
-#pragma unroll
-      for (int r4 = 0; r4 < RT / 4; ++r4)
-        o[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
-      if (Ft) {
-#pragma unroll
-        for (int r = 0; r < RT; ++r)
-          Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(y[r]);
-        for (int r = RT; r < NP; ++r) Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(0.f);
-      }
-    }
+    if (own) store_factor_row<RT>(y, F, Ft, NP, p, Q, row0 + tid);
     return;
   }
   if (normalize) {
@@ -505,27 +540,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int r = 0; r < RT; ++r) y[r] *= scale[r];
   }
-  if (own) {
-    const int q = row0 + tid;
-    float4 *o = reinterpret_cast<float4 *>(F + ((int64_t)p * Q + q) * RT);
-#pragma unroll
-    for (int r4 = 0; r4 < RT / 4; ++r4)
-      o[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
-    if (Ft) {
-#pragma unroll
-      for (int r = 0; r < RT; ++r)
-        Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(y[r]);
-      for (int r = RT; r < NP; ++r) Ft[((int64_t)p * NP + r) * Q + q] = __float2bfloat16_rn(0.f);
-    }
-  }
+  if (own) store_factor_row<RT>(y, F, Ft, NP, p, Q, row0 + tid);
   if (Gout) {
     __syncthreads();   // every row of Ms has been read
-    if (own) {
-      float4 *mr = reinterpret_cast<float4 *>(Ms + tid * RT);
-#pragma unroll
-      for (int r4 = 0; r4 < RT / 4; ++r4)
-        mr[r4] = make_float4(y[4 * r4], y[4 * r4 + 1], y[4 * r4 + 2], y[4 * r4 + 3]);
-    }
+    if (own) store_row<RT>(Ms + tid * RT, y);
     __syncthreads();
     smem_gram<RT>(Ms, nrows, Gp);
     cluster_barrier();   // every CTA's partial Gram is in place
