@@ -361,14 +361,18 @@ def run_e2e(g, d, wl, prec, k, steps, warmup, rank, world):
     serving loop runs them: step s enqueues its batch with octen_append_async
     (the library copies it from pinned host memory in pieces and copies A, B
     and the new rows of C back into pinned host buffers when the append has
-    run), then waits for step s - 1.  Every step's time thus includes its
-    host-to-device copy and its device-to-host read, and the copy of one batch
-    overlaps the update of the one before.  The synchronous form (octen_append
-    then octen_get_factors every step, nothing overlapped) is timed beside it."""
+    run), then waits for step s - 2, two appends in flight.  Every step's time
+    thus includes its host-to-device copy and its device-to-host read, and
+    the copy of one batch overlaps the updates before it.  Each step has its
+    own input and output buffers until it has been waited for (three sets in
+    turn).  The synchronous form (octen_append then octen_get_factors every
+    step, nothing overlapped) is timed beside it."""
     import torch
 
     t = wl.batch
+    depth = 2
     hostX = [d["X"][k + i * t:k + (i + 1) * t].to("cpu").pin_memory() for i in range(2)]
+    hostX.append(hostX[0].clone().pin_memory())
     hostW = [d["W"][1 + warmup + i].to("cpu").pin_memory() for i in range(steps)]
     K_end = k + (warmup + 2 * steps) * t
     Ah = torch.empty((wl.I, wl.R), dtype=torch.float32).pin_memory()
@@ -376,7 +380,8 @@ def run_e2e(g, d, wl, prec, k, steps, warmup, rank, world):
     Ch = torch.empty((K_end, wl.R), dtype=torch.float32).pin_memory()
     outs = [(torch.empty((wl.I, wl.R), dtype=torch.float32).pin_memory(),
              torch.empty((wl.J, wl.R), dtype=torch.float32).pin_memory(),
-             torch.empty((t, wl.R), dtype=torch.float32).pin_memory()) for _ in range(2)]
+             torch.empty((t, wl.R), dtype=torch.float32).pin_memory())
+            for _ in range(depth + 1)]
     xb = hostX[0].numel() * hostX[0].element_size()
     wb = hostW[0].numel() * 4
     ptrs = lambda o: [a.data_ptr() for a in o]
@@ -391,14 +396,14 @@ def run_e2e(g, d, wl, prec, k, steps, warmup, rank, world):
         torch.distributed.barrier()
     with no_gc():
         t0 = time.perf_counter()
-        prev = None
+        tickets = []
         for s in range(steps):
-            tk = g.append_async_ptr(hostX[s % 2].data_ptr(), t, hostW[s].data_ptr(),
-                                    *ptrs(outs[s % 2]))
-            if prev is not None:
-                g.wait(prev)
-            prev = tk
-        g.wait(prev)
+            tickets.append(g.append_async_ptr(hostX[s % 3].data_ptr(), t, hostW[s].data_ptr(),
+                                              *ptrs(outs[s % 3])))
+            if len(tickets) > depth:
+                g.wait(tickets[-1 - depth])
+        for tk in tickets[-depth:]:
+            g.wait(tk)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
     sec = max_over_ranks(sec, world, torch.device("cuda"))
@@ -417,7 +422,7 @@ def run_e2e(g, d, wl, prec, k, steps, warmup, rank, world):
     return {"value": round(whole_job_rate(steps * t, sec, world), 3), "unit": "slices/s",
             "h2d_bytes_per_step": int(xb + wb), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": round(1e3 * sec / steps, 3),
-            "api": "octen_append_async from pinned host batches, step s waiting for step s-1; "
+            "api": "octen_append_async from pinned host batches, step s waiting for step s-2; "
                    "A, B and the new C rows copied back into pinned host buffers every step",
             "sync": {"value": round(whole_job_rate(steps * t, sec_sync, world), 3),
                      "ms_per_step": round(1e3 * sec_sync / steps, 3),

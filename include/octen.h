@@ -135,7 +135,11 @@ octen_status octen_append(octen_ctx *ctx, const void *X_new, int64_t t, const fl
  * are copied in pieces into one of two staging buffers used in turn, so the
  * copy of a batch waits only for the mode-2 contraction of the append two
  * before it.  At most 8 appends are in flight: a ninth waits for the oldest
- * first.  K advances when the append is enqueued.  EINVAL, ESTATE and ENOMEM
+ * first.  K advances when the append is enqueued.  The call does not wait for
+ * the device: when C outgrows its buffer (room for 1024 rows, doubled as
+ * needed) the rows so far are copied into a larger one on the stream, and the
+ * old buffer is freed at the next synchronising call or octen_wait of the
+ * latest ticket.  EINVAL, ESTATE and ENOMEM
  * are returned before anything is enqueued, as in octen_append; device-side
  * failures (ENUMERIC, ETIMEOUT) are returned by octen_wait, after which the
  * context is to be discarded or restored from a checkpoint. */

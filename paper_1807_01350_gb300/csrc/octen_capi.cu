@@ -271,6 +271,7 @@ struct octen_ctx {
       if (e) cudaEventDestroy(e);
     if (copy_ready) cudaEventDestroy(copy_ready);
     for (auto &b : owned) cudaFree(b.p);
+    for (auto &r : retired) cudaFree(r.first);
     DevBuf *extra[] = {&Tbuf, &T2buf, &Wbuf, &X8buf, &xscale, &stage[0], &stage[1], &stage[2],
                        &stage[3], &fitpart, &xstage[0], &xstage[1]};
     for (DevBuf *b : extra) cudaFree(b->p);
@@ -313,6 +314,14 @@ struct octen_ctx {
     if (!p) return;
     cudaFree(p);
     held -= bytes;
+  }
+  // Buffers replaced while enqueued work may still read them (the old C after
+  // it grows): held until the context's streams are next known to be idle,
+  // then freed (cudaFree would wait for the device).
+  std::vector<std::pair<void *, size_t>> retired;
+  void free_retired() {
+    for (auto &r : retired) dev_free(r.first, r.second);
+    retired.clear();
   }
 
   template <class T>
@@ -357,6 +366,7 @@ struct octen_ctx {
   octen_status sync_check(const char *what) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) free_retired();
     if (e == cudaSuccess && !pending.empty()) flush_timers();
     if (e != cudaSuccess) return fail(OCTEN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
     int flags = 0;
@@ -619,10 +629,14 @@ void project(octen_ctx *x, const float *Ur, int64_t rows, const float *F, float 
   gemm_strided(g, x->st);
 }
 
+// Room for `rows` rows of C (capacity doubling from 1024 rows).  Growing
+// enqueues the copy of the rows so far on x->st and retires the old buffer
+// rather than synchronising: appends already enqueued write their rows into
+// the old C before the copy runs, and the next append's rows go to the new one.
 bool ensure_c_capacity(octen_ctx *x, int64_t rows) {
   if (rows <= x->Kcap) return true;
   if (rows > kCRowsMax) return false;
-  int64_t cap = x->Kcap > 0 ? x->Kcap : 64;
+  int64_t cap = x->Kcap > 0 ? x->Kcap : 1024;
   while (cap < rows) cap *= 2;
   float *nc = nullptr;
   const size_t bytes = (size_t)cap * x->cfg.R * sizeof(float);
@@ -630,9 +644,12 @@ bool ensure_c_capacity(octen_ctx *x, int64_t rows) {
   if (x->C) {
     cudaMemcpyAsync(nc, x->C, (size_t)x->K * x->cfg.R * sizeof(float), cudaMemcpyDeviceToDevice,
                     x->st);
-    cudaStreamSynchronize(x->st);
     for (auto &b : x->owned)
-      if (b.p == x->C) { x->dev_free(b.p, b.bytes); b.p = nc; b.bytes = bytes; }
+      if (b.p == x->C) {
+        x->retired.push_back({b.p, b.bytes});
+        b.p = nc;
+        b.bytes = bytes;
+      }
   } else {
     x->owned.push_back({nc, bytes});
   }
@@ -1251,6 +1268,7 @@ octen_status octen_wait(octen_ctx *x, int64_t ticket) {
   if (e != cudaSuccess) return x->fail(OCTEN_ECUDA, "wait: %s", cudaGetErrorString(e));
   const int flags = x->ticket_status[slot];
   x->done_ticket = ticket + 1;
+  if (x->done_ticket == x->next_ticket) x->free_retired();   // nothing of the context in flight
   if (flags & kDevTimeout) return x->fail(OCTEN_ETIMEOUT, "append: a device wait ran out");
   if (flags) return x->fail(OCTEN_ENUMERIC, "append: a Cholesky pivot was not positive");
   return OCTEN_OK;
