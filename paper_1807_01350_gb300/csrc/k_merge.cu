@@ -228,40 +228,81 @@ __global__ void c_rhs_cols_kernel(const float *__restrict__ Ch, const float *__r
   E[idx] = v;
 }
 
+// Reciprocal square root of a Cholesky pivot.  ok is cleared unless d is
+// positive, normal and finite.  For d in [2^-100, 2^100]: the fp32 value of d
+// assembled from its bits (mantissa truncated to 23 bits), rsqrt.approx of it
+// (relative error < 2^-22), widened to fp64 from its bits, and one Newton step
+// for 1 / sqrt(d), y <- y + y (1 - d y^2) / 2, which squares the relative error
+// (< 2^-42).  Outside that range the fp64 square root and division are used.
+__device__ __forceinline__ double pivot_rsqrt(double d, bool &ok) {
+  const int hi = __double2hiint(d);
+  const unsigned lo = static_cast<unsigned>(__double2loint(d));
+  const int be = (hi >> 20) & 0x7ff;
+  if (hi < 0 || be == 0 || be == 0x7ff) {
+    ok = false;
+    return 0.0;
+  }
+  if (be < 1023 - 100 || be > 1023 + 100) return 1.0 / sqrt(d);
+  const float f = __int_as_float(((be - 1023 + 127) << 23) | ((hi & 0xfffff) << 3) |
+                                 static_cast<int>(lo >> 29));
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+  const int yb = __float_as_int(y);
+  const int ye = (yb >> 23) & 0xff;
+  const int ym = yb & 0x7fffff;
+  const double y0 = __hiloint2double(((ye - 127 + 1023) << 20) | (ym >> 3), ym << 29);
+  const double e = fma(-d * y0, y0, 1.0);
+  return fma(0.5 * y0, e, y0);
+}
+
+// Gram (t x t, t <= 64) = L L^T by right-looking Cholesky in fp64 (the pivot
+// column scaled by the reciprocal square root of the pivot, then the trailing
+// lower triangle updated by all threads), then L L^T X = rhs for the R
+// columns of rhs, forward and backward by columns with the updates of the
+// remaining rows in parallel.  A pivot that is not positive: the diagonal is
+// loaded by 1e-12 trace / t and the factorisation repeated once; if that fails
+// as well, status gets kDevCholesky and C_new = 0.
 __global__ void __launch_bounds__(256)
     c_solve_kernel(const float *__restrict__ Gram, const float *__restrict__ rhs, int t, int R,
                    float *__restrict__ C_new, int *status) {
   __shared__ double L[64 * 64];
   __shared__ double X[64 * 32];
+  __shared__ double rinv[64];
   __shared__ int ok_s;
-  for (int e = threadIdx.x; e < t * t; e += blockDim.x) L[e] = Gram[e];
-  for (int e = threadIdx.x; e < t * R; e += blockDim.x) X[e] = rhs[e];
-  if (threadIdx.x == 0) ok_s = 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < t * t; e += nt) L[e] = Gram[e];
+  for (int e = tid; e < t * R; e += nt) X[e] = rhs[e];
+  if (tid == 0) ok_s = 1;
   __syncthreads();
   for (int attempt = 0; attempt < 2; ++attempt) {
     for (int j = 0; j < t; ++j) {
-      if (threadIdx.x == 0) {
-        double d = L[j * t + j];
-        for (int k = 0; k < j; ++k) d -= L[j * t + k] * L[j * t + k];
-        if (d > 0.0) L[j * t + j] = sqrt(d);
-        else ok_s = 0;
+      if (tid == 0) {
+        bool ok = true;
+        const double d = L[j * t + j];
+        const double y = pivot_rsqrt(d, ok);
+        if (ok) {
+          L[j * t + j] = d * y;
+          rinv[j] = y;
+        } else {
+          ok_s = 0;
+        }
       }
       __syncthreads();
       if (!ok_s) break;
-      const int i = j + 1 + threadIdx.x;
-      if (i < t) {
-        double s = L[i * t + j];
-        for (int k = 0; k < j; ++k) s -= L[i * t + k] * L[j * t + k];
-        L[i * t + j] = s / L[j * t + j];
+      for (int i = j + 1 + tid; i < t; i += nt) L[i * t + j] *= rinv[j];
+      __syncthreads();
+      const int m = t - j - 1;   // trailing block rows / columns j + 1 ..
+      for (int e = tid; e < m * m; e += nt) {
+        const int i = j + 1 + e / m, k = j + 1 + e % m;
+        if (k <= i) L[i * t + k] = fma(-L[i * t + j], L[k * t + j], L[i * t + k]);
       }
       __syncthreads();
     }
     if (ok_s || attempt == 1) break;
-    // reload, add 1e-12 * trace / t to the diagonal and retry once
     __syncthreads();
-    for (int e = threadIdx.x; e < t * t; e += blockDim.x) L[e] = Gram[e];
+    for (int e = tid; e < t * t; e += nt) L[e] = Gram[e];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       double tr = 0.0;
       for (int k = 0; k < t; ++k) tr += L[k * t + k];
       for (int k = 0; k < t; ++k) L[k * t + k] += 1e-12 * tr / t;
@@ -270,24 +311,33 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
   }
   if (!ok_s) {
-    if (threadIdx.x == 0) atomicOr(status, kDevCholesky);
-    for (int e = threadIdx.x; e < t * R; e += blockDim.x) C_new[e] = 0.f;
+    if (tid == 0) atomicOr(status, kDevCholesky);
+    for (int e = tid; e < t * R; e += nt) C_new[e] = 0.f;
     return;
   }
-  const int r = threadIdx.x;
-  if (r < R) {
-    for (int i = 0; i < t; ++i) {
-      double s = X[i * R + r];
-      for (int k = 0; k < i; ++k) s -= L[i * t + k] * X[k * R + r];
-      X[i * R + r] = s / L[i * t + i];
+  // L z = rhs: z_k = b_k / L_kk, then b_i -= L_ik z_k below it
+  for (int k = 0; k < t; ++k) {
+    for (int r = tid; r < R; r += nt) X[k * R + r] *= rinv[k];
+    __syncthreads();
+    const int n = (t - k - 1) * R;
+    for (int e = tid; e < n; e += nt) {
+      const int i = k + 1 + e / R, r = e % R;
+      X[i * R + r] = fma(-L[i * t + k], X[k * R + r], X[i * R + r]);
     }
-    for (int i = t - 1; i >= 0; --i) {
-      double s = X[i * R + r];
-      for (int k = i + 1; k < t; ++k) s -= L[k * t + i] * X[k * R + r];
-      X[i * R + r] = s / L[i * t + i];
-    }
-    for (int i = 0; i < t; ++i) C_new[i * R + r] = (float)X[i * R + r];
+    __syncthreads();
   }
+  // L^T x = z: x_k = z_k / L_kk, then z_i -= L_ki x_k above it
+  for (int k = t - 1; k >= 0; --k) {
+    for (int r = tid; r < R; r += nt) X[k * R + r] *= rinv[k];
+    __syncthreads();
+    const int n = k * R;
+    for (int e = tid; e < n; e += nt) {
+      const int i = e / R, r = e % R;
+      X[i * R + r] = fma(-L[k * t + i], X[k * R + r], X[i * R + r]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < t * R; e += nt) C_new[e] = (float)X[e];
 }
 
 __global__ void scale_columns_kernel(const float *__restrict__ in, int64_t rows, int cols,

@@ -87,6 +87,10 @@ struct octen_ctx {
   float *M = nullptr, *H = nullptr, *csolve = nullptr;
   float *GA = nullptr, *GB = nullptr, *GC = nullptr;
   float *splitk = nullptr;                 // split-K partials of the small GEMMs
+  // the B-side halves of the warm start and the lift run on als_side beside
+  // the A-side halves, with their own split-K and right-hand-side scratch
+  float *splitk2 = nullptr, *e2 = nullptr;
+  cudaEvent_t pair_fork = nullptr, pair_join = nullptr;
   static constexpr size_t kSplitkFloats = size_t(4) << 20;
   // tensor-core ALS (bf16 / e4m3 modes with Q % 8 == 0, or Q >= 32 zero-padded
   // to als_qp, the next multiple of 8, with factors Apad, Bpad, Cpad)
@@ -252,6 +256,8 @@ struct octen_ctx {
     }
     if (als_fork) cudaEventDestroy(als_fork);
     if (als_join) cudaEventDestroy(als_join);
+    if (pair_fork) cudaEventDestroy(pair_fork);
+    if (pair_join) cudaEventDestroy(pair_join);
     for (int g = 0; g < kMaxAlsGroups; ++g) {
       for (cudaStream_t s2 : {grp_st[g], grp_side[g]})
         if (s2) {
@@ -598,10 +604,10 @@ octen_status compress_all(octen_ctx *x, const void *Xd, int64_t t, const float *
 // Qd > rows the stack has full column rank: L = (U Omega U^T)^-1 U, shape
 // rows x Qd (Omega weights the anchor columns by P).  Otherwise the distinct
 // rows have full row rank: L = U (U^T U)^-1, stored transposed (Qd x rows).
-LiftEnv lift_env(octen_ctx *x) {
+LiftEnv lift_env(octen_ctx *x, bool side = false) {
   const octen_config &c = x->cfg;
-  return LiftEnv{x->Qd, c.P, c.Q, c.S, c.R, x->RT, x->st, x->dstatus, x->e, x->splitk,
-                 octen_ctx::kSplitkFloats};
+  return LiftEnv{x->Qd, c.P, c.Q, c.S, c.R, x->RT, side ? x->als_side : x->st, x->dstatus,
+                 side ? x->e2 : x->e, side ? x->splitk2 : x->splitk, octen_ctx::kSplitkFloats};
 }
 
 octen_status build_lift(octen_ctx *x, const float *Ur, int64_t rows, float *L, int &over) {
@@ -613,20 +619,32 @@ octen_status build_lift(octen_ctx *x, const float *Ur, int64_t rows, float *L, i
 // Delta of one global factor: F += Lift * e (Qd x R rhs built from the
 // aligned replica blocks and the projected previous factor PF).
 void lift_mode(octen_ctx *x, const float *Fh, const float *PF, const float *L, int over,
-               int64_t rows, float *F) {
-  lift_apply(lift_env(x), Fh, PF, L, over, rows, F);
+               int64_t rows, float *F, bool side) {
+  lift_apply(lift_env(x, side), Fh, PF, L, over, rows, F);
 }
 
-// PF = U_all^T F (Qd x R)
-void project(octen_ctx *x, const float *Ur, int64_t rows, const float *F, float *PF) {
+// The A- and B-side halves of the warm start and of the lift are independent:
+// the B side goes to als_side between pair_fork and pair_join.
+void pair_fork(octen_ctx *x) {
+  cudaEventRecord(x->pair_fork, x->st);
+  cudaStreamWaitEvent(x->als_side, x->pair_fork, 0);
+}
+void pair_join(octen_ctx *x) {
+  cudaEventRecord(x->pair_join, x->als_side);
+  cudaStreamWaitEvent(x->st, x->pair_join, 0);
+}
+
+// PF = U_all^T F (Qd x R) on stream st with split-K scratch splitk
+void project(octen_ctx *x, const float *Ur, int64_t rows, const float *F, float *PF,
+             cudaStream_t st, float *splitk) {
   const octen_config &c = x->cfg;
   GemmArgs g{};
   g.A = Ur; g.ta = Elem::F32; g.sAm = 1; g.sAk = x->Qd;
   g.B = F; g.tb = Elem::F32; g.sBn = 1; g.sBk = c.R;
   g.D = PF; g.sDm = c.R; g.sDn = 1;
   g.M = x->Qd; g.N = c.R; g.K = (int)rows; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
-  g.split_scratch = x->splitk; g.split_scratch_floats = octen_ctx::kSplitkFloats;
-  gemm_strided(g, x->st);
+  g.split_scratch = splitk; g.split_scratch_floats = octen_ctx::kSplitkFloats;
+  gemm_strided(g, st);
 }
 
 // Room for `rows` rows of C (capacity doubling from 1024 rows).  Growing
@@ -696,6 +714,7 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
             x->alloc(x->GB, P * RT * RT) && x->alloc(x->GC, P * RT * RT) &&
             x->alloc(x->Lfac, P * (size_t)als_factor_floats(x->RT)) &&
             x->alloc(x->splitk, octen_ctx::kSplitkFloats) &&
+            x->alloc(x->splitk2, octen_ctx::kSplitkFloats) && x->alloc(x->e2, Qd * c.R) &&
             x->alloc(x->Wfix, (size_t)chunk_slices(x) * Qd) &&
             x->alloc(x->Cnew_fix, (size_t)chunk_slices(x) * c.R);
   if (ok && x->use_tc && als_tc_eligible(c.Q)) {
@@ -741,7 +760,9 @@ octen_status octen_create(const octen_config *cfg, void *cuda_stream, octen_ctx 
   if (ok) {
     ok = cudaStreamCreateWithFlags(&x->als_side, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&x->als_fork, cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&x->als_join, cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&x->als_join, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x->pair_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x->pair_join, cudaEventDisableTiming) == cudaSuccess;
   }
   if (ok && x->als_tc && c.Q >= 32) {
     x->als_groups = als_groups_wanted(c.P);
@@ -895,10 +916,12 @@ bool tail_front(octen_ctx *x, int64_t t, const Marker &mk) {
   const octen_config &c = x->cfg;
   compress_finish(x, t, x->Wfix, x->Y, true);
   x->mark(kStWarm, 1);
-  project(x, x->U32, c.I, x->A, x->PA);
-  project(x, x->V32, c.J, x->B, x->PB);
+  pair_fork(x);
+  project(x, x->U32, c.I, x->A, x->PA, x->st, x->splitk);
+  project(x, x->V32, c.J, x->B, x->PB, x->als_side, x->splitk2);
   warm_start(x->PA, c.P, c.Q, c.S, c.R, x->RT, x->At, x->GA, x->st);
-  warm_start(x->PB, c.P, c.Q, c.S, c.R, x->RT, x->Bt, x->GB, x->st);
+  warm_start(x->PB, c.P, c.Q, c.S, c.R, x->RT, x->Bt, x->GB, x->als_side);
+  pair_join(x);
   x->mark(kStWarm, 0);
   AlsBuffers ab = als_buffers(x);
   return als_run(x->Y, c.P, c.Q, c.R, x->RT, c.als_iters, ab, x->st, mk);
@@ -913,8 +936,10 @@ void tail_back(octen_ctx *x, int64_t t) {
                  x->Ch, x->perm, x->scales, x->align_scratch, x->st);
   x->mark(kStAlign, 0);
   x->mark(kStLift, 1);
-  lift_mode(x, x->Ah, x->PA, x->La, x->a_over, c.I, x->A);
-  lift_mode(x, x->Bh, x->PB, x->Lb, x->b_over, c.J, x->B);
+  pair_fork(x);
+  lift_mode(x, x->Ah, x->PA, x->La, x->a_over, c.I, x->A, false);
+  lift_mode(x, x->Bh, x->PB, x->Lb, x->b_over, c.J, x->B, true);
+  pair_join(x);
   x->mark(kStLift, 0);
   x->mark(kStCsolve, 1);
   solve_c_new(x->Wfix, x->Ch, x->G, t, c.P, c.Q, c.S, x->Qd, c.R, x->RT,
