@@ -207,25 +207,67 @@ void lift_rhs(const float *Fh, const float *PF, int P, int Q, int S, int R, int 
 // ---------------------------------------------------------------------------
 // New rows of C.  The stacked system (W_new,p^T) C_new = Ch_p - G_p has normal
 // equations (sum_p W_p W_p^T) C_new = sum_p W_p (Ch_p - G_p).  Both sides are
-// reduced over the Qd distinct columns of W_all (anchor columns weighted P),
-// then factored by fp64 Cholesky (t x t, t <= 64) in one CTA.
+// reduced over the Qd distinct columns of W_all (anchor columns weighted P):
+// chunks of kCChunk columns give partial sums, added in chunk order by the
+// solve, which factors the t x t system by fp64 Cholesky (t <= 64) in one CTA.
 // ---------------------------------------------------------------------------
-__global__ void c_rhs_cols_kernel(const float *__restrict__ Ch, const float *__restrict__ G,
-                                  int P, int Q, int S, int R, int RT, int Qd,
-                                  float *__restrict__ E) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)Qd * R) return;
-  const int c = (int)(idx / R), r = (int)(idx % R);
-  float v = 0.f;
-  if (c < S) {
-    for (int p = 0; p < P; ++p)
-      v += Ch[((int64_t)p * Q + c) * RT + r] - G[((int64_t)p * Q + c) * R + r];
-  } else {
-    const int p = (c - S) / (Q - S);
-    const int b = S + (c - S) - p * (Q - S);
-    v = Ch[((int64_t)p * Q + b) * RT + r] - G[((int64_t)p * Q + b) * R + r];
+constexpr int kCChunk = 64;
+
+size_t c_solve_scratch_floats(int64_t t, int Qd, int R) {
+  return (size_t)((Qd + kCChunk - 1) / kCChunk) * (size_t)(t * t + t * R);
+}
+
+// Chunk j of the columns c (grid ceil(Qd / kCChunk), 256 threads):
+//   part[j][k][l]         = sum_c w_c W[k][c] W[l][c]      (w_c = P for c < S, else 1)
+//   part[j][t t + k R + r] = sum_c W[k][c] E[c][r],
+// E[c][r] = sum over the replicas holding column c of Ch_p[b][r] - G_p[b][r]
+// (all P for an anchor column c = b < S, else the one replica p with
+// c = S + p (Q - S) + b - S), each sum in increasing c.
+__global__ void __launch_bounds__(256)
+    c_normal_kernel(const float *__restrict__ W, const float *__restrict__ Ch,
+                    const float *__restrict__ G, int t, int P, int Q, int S, int Qd, int R,
+                    int RT, float *__restrict__ part) {
+  __shared__ float Ws[64][kCChunk + 1];
+  __shared__ float Es[kCChunk][33];
+  const int c0 = blockIdx.x * kCChunk;
+  const int nc = Qd - c0 < kCChunk ? Qd - c0 : kCChunk;
+  for (int e = threadIdx.x; e < t * kCChunk; e += blockDim.x) {
+    const int k = e / kCChunk, cc = e % kCChunk;
+    Ws[k][cc] = cc < nc ? W[(int64_t)k * Qd + c0 + cc] : 0.f;
   }
-  E[idx] = v;
+  for (int e = threadIdx.x; e < kCChunk * R; e += blockDim.x) {
+    const int cc = e / R, r = e % R, c = c0 + cc;
+    float v = 0.f;
+    if (cc < nc) {
+      if (c < S) {
+        for (int p = 0; p < P; ++p)
+          v += Ch[((int64_t)p * Q + c) * RT + r] - G[((int64_t)p * Q + c) * R + r];
+      } else {
+        const int p = (c - S) / (Q - S);
+        const int b = S + (c - S) - p * (Q - S);
+        v = Ch[((int64_t)p * Q + b) * RT + r] - G[((int64_t)p * Q + b) * R + r];
+      }
+    }
+    Es[cc][r] = v;
+  }
+  __syncthreads();
+  float *out = part + (int64_t)blockIdx.x * (t * t + t * R);
+  const float wS = (float)P;
+  for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
+    const int k = e / t, l = e % t;
+    float acc = 0.f;
+    for (int cc = 0; cc < nc; ++cc) {
+      const float w = c0 + cc < S ? wS : 1.f;
+      acc = fmaf(w * Ws[k][cc], Ws[l][cc], acc);
+    }
+    out[e] = acc;
+  }
+  for (int e = threadIdx.x; e < t * R; e += blockDim.x) {
+    const int k = e / R, r = e % R;
+    float acc = 0.f;
+    for (int cc = 0; cc < nc; ++cc) acc = fmaf(Ws[k][cc], Es[cc][r], acc);
+    out[t * t + e] = acc;
+  }
 }
 
 // Reciprocal square root of a Cholesky pivot.  ok is cleared unless d is
@@ -263,15 +305,26 @@ __device__ __forceinline__ double pivot_rsqrt(double d, bool &ok) {
 // loaded by 1e-12 trace / t and the factorisation repeated once; if that fails
 // as well, status gets kDevCholesky and C_new = 0.
 __global__ void __launch_bounds__(256)
-    c_solve_kernel(const float *__restrict__ Gram, const float *__restrict__ rhs, int t, int R,
+    c_solve_kernel(const float *__restrict__ part, int nchunks, int t, int R,
                    float *__restrict__ C_new, int *status) {
   __shared__ double L[64 * 64];
   __shared__ double X[64 * 32];
   __shared__ double rinv[64];
   __shared__ int ok_s;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < t * t; e += nt) L[e] = Gram[e];
-  for (int e = tid; e < t * R; e += nt) X[e] = rhs[e];
+  const int per = t * t + t * R;
+  // the chunks' partial sums, added in chunk order (the system's entries
+  // e < t t, its right-hand side after them)
+  auto entry = [&](int e) {
+    float v = 0.f;
+    for (int j = 0; j < nchunks; ++j) v += part[(int64_t)j * per + e];
+    return v;
+  };
+  for (int e = tid; e < per; e += nt) {
+    const float v = entry(e);
+    if (e < t * t) L[e] = v;
+    else X[e - t * t] = v;
+  }
   if (tid == 0) ok_s = 1;
   __syncthreads();
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -300,7 +353,7 @@ __global__ void __launch_bounds__(256)
     }
     if (ok_s || attempt == 1) break;
     __syncthreads();
-    for (int e = tid; e < t * t; e += nt) L[e] = Gram[e];
+    for (int e = tid; e < t * t; e += nt) L[e] = entry(e);
     __syncthreads();
     if (tid == 0) {
       double tr = 0.0;
@@ -359,33 +412,14 @@ void scale_columns(const float *in, int64_t rows, int cols, int S, float w_share
   count_launch();
 }
 
-// scratch holds E (Qd x R), rhs (t x R), Ww (t x Qd) and Gram (t x t).
+// scratch: c_solve_scratch_floats(t, Qd, R) floats of chunk partials.
 void solve_c_new(const float *W, const float *Ch, const float *G, int64_t t, int P, int Q,
-                 int S, int Qd, int R, int RT, float *scratch, float *splitk,
-                 size_t splitk_floats, float *C_new, int *status, cudaStream_t st) {
-  float *E = scratch;
-  float *rhs = E + (int64_t)Qd * R;
-  float *Ww = rhs + t * R;
-  float *Gram = Ww + t * Qd;
-  const int64_t n = (int64_t)Qd * R;
-  c_rhs_cols_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Ch, G, P, Q, S, R, RT, Qd, E);
+                 int S, int Qd, int R, int RT, float *scratch, float *C_new, int *status,
+                 cudaStream_t st) {
+  const int nchunks = (Qd + kCChunk - 1) / kCChunk;
+  c_normal_kernel<<<nchunks, 256, 0, st>>>(W, Ch, G, (int)t, P, Q, S, Qd, R, RT, scratch);
   count_launch();
-  GemmArgs g{};
-  g.A = W; g.ta = Elem::F32; g.sAm = Qd; g.sAk = 1;
-  g.B = E; g.tb = Elem::F32; g.sBn = 1; g.sBk = R;
-  g.D = rhs; g.sDm = R; g.sDn = 1;
-  g.M = (int)t; g.N = R; g.K = Qd; g.batch = 1; g.alpha = 1.f; g.beta = 0.f;
-  g.split_scratch = splitk; g.split_scratch_floats = splitk_floats;
-  gemm_strided(g, st);
-  scale_columns(W, t, Qd, S, (float)P, Ww, st);
-  GemmArgs h{};
-  h.A = Ww; h.ta = Elem::F32; h.sAm = Qd; h.sAk = 1;
-  h.B = W; h.tb = Elem::F32; h.sBn = Qd; h.sBk = 1;
-  h.D = Gram; h.sDm = t; h.sDn = 1;
-  h.M = (int)t; h.N = (int)t; h.K = Qd; h.batch = 1; h.alpha = 1.f; h.beta = 0.f;
-  h.split_scratch = splitk; h.split_scratch_floats = splitk_floats;
-  gemm_strided(h, st);
-  c_solve_kernel<<<1, 256, 0, st>>>(Gram, rhs, (int)t, R, C_new, status);
+  c_solve_kernel<<<1, 256, 0, st>>>(scratch, nchunks, (int)t, R, C_new, status);
   count_launch();
 }
 

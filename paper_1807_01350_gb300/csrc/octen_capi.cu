@@ -939,14 +939,14 @@ void tail_back(octen_ctx *x, int64_t t) {
   pair_fork(x);
   lift_mode(x, x->Ah, x->PA, x->La, x->a_over, c.I, x->A, false);
   lift_mode(x, x->Bh, x->PB, x->Lb, x->b_over, c.J, x->B, true);
-  pair_join(x);
   x->mark(kStLift, 0);
+  // the new rows of C need only the aligned blocks, G and W: beside the B lift
   x->mark(kStCsolve, 1);
   solve_c_new(x->Wfix, x->Ch, x->G, t, c.P, c.Q, c.S, x->Qd, c.R, x->RT,
-              static_cast<float *>(x->Wbuf.p), x->splitk, octen_ctx::kSplitkFloats, x->Cnew_fix,
-              x->dstatus, x->st);
+              static_cast<float *>(x->Wbuf.p), x->Cnew_fix, x->dstatus, x->st);
   update_g(x->Wfix, x->Cnew_fix, t, c.P, c.Q, c.S, x->Qd, c.R, x->G, x->st);
   x->mark(kStCsolve, 0);
+  pair_join(x);
 }
 
 // Records the tail of a t-slice append (tail_front + tail_back) as a graph in
@@ -1049,7 +1049,7 @@ octen_status append_prepare(octen_ctx *x, const void *X_new, int64_t t, const fl
   const octen_config &c = x->cfg;
   const int Qd = x->Qd;
   if (!ensure_c_capacity(x, x->K + t)) return x->fail(OCTEN_ENOMEM, "C");
-  const size_t cs = (size_t)Qd * c.R + t * c.R + t * Qd + t * t;
+  const size_t cs = c_solve_scratch_floats(t, Qd, c.R);
   if (!x->grow(x->Wbuf, cs * sizeof(float))) return x->fail(OCTEN_ENOMEM, "C solve scratch");
   octen_status s = compress_scratch(x, t);
   if (s != OCTEN_OK) return s;

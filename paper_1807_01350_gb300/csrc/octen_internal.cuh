@@ -299,11 +299,12 @@ size_t align_scratch_doubles(int P, int RT);
 void lift_rhs(const float *Fh, const float *PF, int P, int Q, int S, int R, int RT, int Qd,
               int sum_mode, float *e, cudaStream_t st);
 
-// C_new (t x R) from the stacked W_new,p^T system and G update.
-// scratch: Qd*R + t*R + t*Qd + t*t floats.
+// C_new (t x R, t <= 64) from the stacked W_new,p^T system, and the G update.
+// scratch: c_solve_scratch_floats(t, Qd, R) floats.
+size_t c_solve_scratch_floats(int64_t t, int Qd, int R);
 void solve_c_new(const float *W, const float *Ch, const float *G, int64_t t, int P, int Q,
-                 int S, int Qd, int R, int RT, float *scratch, float *splitk,
-                 size_t splitk_floats, float *C_new, int *status, cudaStream_t st);
+                 int S, int Qd, int R, int RT, float *scratch, float *C_new, int *status,
+                 cudaStream_t st);
 void update_g(const float *W, const float *C_new, int64_t t, int P, int Q, int S, int Qd,
               int R, float *G, cudaStream_t st);
 

@@ -307,7 +307,7 @@ octen_status octen_n_create(const octen_nconfig *cfg, void *cuda_stream, octen_n
   ok = ok && x->alloc(x->Y, P * qn) && x->alloc(x->G, P * Q * c.R) &&
        x->alloc(x->e, Qd * c.R) && x->alloc(x->bufA, buf) && x->alloc(x->bufB, buf) &&
        x->alloc(x->Wt, P * Q * (size_t)x->tchunk) &&
-       x->alloc(x->csolve, Qd * c.R + kNBatchMax * (c.R + Qd + kNBatchMax)) &&
+       x->alloc(x->csolve, c_solve_scratch_floats(kNBatchMax, Qd, c.R)) &&
        x->alloc(x->splitk, octen_nctx::kSplitkFloats) && x->alloc(x->perm, P * c.R) &&
        x->alloc(x->scales, P * x->nm * c.R) && x->alloc(x->dstatus, 1);
   if (ok && x->xin == Elem::BF16) {
@@ -473,8 +473,8 @@ octen_status octen_n_append(octen_nctx *x, const void *X_new, int64_t t, const f
   x->mark(kNLift, 0);
   float *C_new = x->C + x->K * c.R;
   x->mark(kNCsolve, 1);
-  solve_c_new(Wd, x->Fh[nm], x->G, t, c.P, c.Q, c.S, Qd, c.R, RT, x->csolve, x->splitk,
-              octen_nctx::kSplitkFloats, C_new, x->dstatus, x->st);
+  solve_c_new(Wd, x->Fh[nm], x->G, t, c.P, c.Q, c.S, Qd, c.R, RT, x->csolve, C_new, x->dstatus,
+              x->st);
   update_g(Wd, C_new, t, c.P, c.Q, c.S, Qd, c.R, x->G, x->st);
   x->mark(kNCsolve, 0);
   const octen_status s = x->sync_check("append");
