@@ -455,13 +455,17 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
+        // the stage's descriptors once; an MMA's operands lie at byte offsets
+        // within the stage, which add to the 16-byte start-address field
+        // (shared addresses stay below 2^18, so the field does not carry)
+        const uint64_t da = make_desc_sw128(smem_u32(sA + s * a_bytes));
+        const uint64_t db = make_desc_sw128(smem_u32(sB + s * b_bytes));
 #pragma unroll
         for (int at = 0; at < katoms; ++at) {
 #pragma unroll
           for (int kk = 0; kk < kRowBytes / 32; ++kk) {
-            mma_issue<KIND>(d, make_desc_sw128(a0 + at * a_atom + kk * 32),
-                            make_desc_sw128(b0 + at * b_atom + kk * 32), idesc,
+            mma_issue<KIND>(d, da + ((at * a_atom + kk * 32) >> 4),
+                            db + ((at * b_atom + kk * 32) >> 4), idesc,
                             (kb > 0 || at > 0 || kk > 0) ? 1u : 0u);
           }
         }
