@@ -197,8 +197,17 @@ def roofline_for(stage, ms_per_launch, wl, prec, pk, traffic, tc_stages=()):
         bound, peak, unit = "hbm", pk["hbm"], "GB/s"
         achieved = als_gemm_tc_bytes(wl) / sec / 1e9
     elif stage in tc_stages:
-        peak = pk["bf16_sus"] * (2.0 if prec == "fp8" and stage == "mode2" else 1.0)
-        bound, unit, achieved = "tensor", "TFLOP/s", flops / sec / 1e12
+        # the binding one of the two: flops at the sustained tensor peak or
+        # the method's bytes at the copy bandwidth (mode 1 streams the 524 MB
+        # mode-2 product at 4000^2 and is bound by its bytes)
+        tpk = pk["bf16_sus"] * (2.0 if prec == "fp8" and stage == "mode2" else 1.0)
+        t_flops, t_bytes = flops / (tpk * 1e12), nbytes / (pk["hbm"] * 1e9)
+        if t_flops >= t_bytes:
+            bound, peak, unit, achieved = "tensor", tpk, "TFLOP/s", flops / sec / 1e12
+            extra["hbm_frac"] = round(nbytes / sec / 1e9 / pk["hbm"], 4)
+        else:
+            bound, peak, unit, achieved = "hbm", pk["hbm"], "GB/s", nbytes / sec / 1e9
+            extra["tensor_frac"] = round(flops / sec / 1e12 / tpk, 4)
     else:
         bound, peak, unit, achieved = "alu", FP32_ALU_TFLOPS, "TFLOP/s", flops / sec / 1e12
     return dict({"kernel": stage, "bound": bound, "achieved": round(achieved, 3),

@@ -158,3 +158,19 @@ def test_compression_roofline_of_the_4000_squared_batch():
     assert c["at_roofline_ms"] == pytest.approx(want, rel=1e-3)
     assert c["measured_ms"] == pytest.approx(2.15)
     assert c["frac"] == pytest.approx(want / 2.15, rel=1e-3)
+
+
+def test_tensor_core_stages_report_their_binding_bound():
+    """A tensor-core stage is reported against whichever of its two limits
+    binds: mode 2 at 4000^2 by its flops (1.85 TFLOP against 1.07 GB), mode 1
+    by its bytes (0.134 TFLOP against 557 MB: the mode-2 product it streams),
+    each with the other fraction beside it."""
+    wl = WORKLOADS["c4"]
+    pk = {"hbm": 6690.8, "bf16": 1892.4, "bf16_sus": 1718.1, "src": "measured"}
+    m2 = bench.roofline_for("mode2", 1.26, wl, "bf16", pk, None, ("mode2", "mode1"))
+    m1 = bench.roofline_for("mode1", 0.18, wl, "bf16", pk, None, ("mode2", "mode1"))
+    assert m2["bound"] == "tensor" and "hbm_frac" in m2
+    assert m1["bound"] == "hbm" and "tensor_frac" in m1
+    fl, nb = bench.stage_work(wl, "bf16")["mode1"]
+    assert m1["achieved"] == pytest.approx(nb / 0.18e-3 / 1e9, rel=1e-3)
+    assert m1["tensor_frac"] == pytest.approx(fl / 0.18e-3 / 1e12 / 1718.1, rel=1e-3)
