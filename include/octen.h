@@ -132,9 +132,9 @@ octen_status octen_append(octen_ctx *ctx, const void *X_new, int64_t t, const fl
  * returned.  A_out (I x R), B_out (J x R) and C_new_out (t x R), each may be
  * NULL, receive the factors after this append and its new rows of C once it
  * has run (pinned host memory keeps the copies asynchronous).  Host slices
- * are copied in pieces into one of two staging buffers used in turn, so the
- * copy of a batch waits only for the mode-2 contraction of the append two
- * before it.  At most 8 appends are in flight: a ninth waits for the oldest
+ * are copied whole into one of two staging buffers used in turn (the copy
+ * waits only for the mode-2 contraction of the append two before it, and runs
+ * while the appends before it update), then contracted in one piece.  At most 8 appends are in flight: a ninth waits for the oldest
  * first.  K advances when the append is enqueued.  The call does not wait for
  * the device: when C outgrows its buffer (room for 1024 rows, doubled as
  * needed) the rows so far are copied into a larger one on the stream, and the

@@ -554,17 +554,19 @@ octen_status compress_chunk(octen_ctx *x, const void *Xd, int64_t t, const float
 }
 
 // Quantisation and mode-2 contraction of t host slices: they are copied into
-// staging slot 2 (already sized by the caller) in up to kCopyChunks pieces on
-// copy_st, and the contraction of each piece starts as soon as it has arrived.
+// staging slot 2 (already sized by the caller) in up to `pieces` pieces on
+// copy_st, and the contraction of each piece starts as soon as it has arrived
+// (one piece: one contraction of the whole batch once it has all arrived).
 // The caller ensures 16-byte aligned piece offsets (I J a multiple of 16),
 // which the tensor-map operands need.
-octen_status compress_mode2_host(octen_ctx *x, const void *Xh, int64_t t) {
+octen_status compress_mode2_host(octen_ctx *x, const void *Xh, int64_t t, int pieces) {
   const octen_config &c = x->cfg;
   const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
   // the slot is free once the mode-2 contraction of its previous batch has run
   DevBuf &stg = x->xstage[x->xslot];
   cudaStreamWaitEvent(x->copy_st, x->xslot_free[x->xslot], 0);
-  const int64_t per = (t + octen_ctx::kCopyChunks - 1) / octen_ctx::kCopyChunks;
+  const int np = pieces < 1 ? 1 : (pieces > octen_ctx::kCopyChunks ? octen_ctx::kCopyChunks : pieces);
+  const int64_t per = (t + np - 1) / np;
   const int64_t step = per < 2 ? 2 : per;
   int nc = 0;
   for (int64_t k0 = 0; k0 < t; k0 += step, ++nc) {
@@ -1067,14 +1069,15 @@ octen_status append_prepare(octen_ctx *x, const void *X_new, int64_t t, const fl
 
 // The head of a prepared append on x->st: the batch's W rows into Wfix, the
 // quantisation (fp8) and the mode-2 contraction.
-octen_status append_head(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
+octen_status append_head(octen_ctx *x, const void *X_new, int64_t t, const float *W_new,
+                         int pieces) {
   const octen_config &c = x->cfg;
   const size_t slice = (size_t)c.I * c.J * elem_size(x->xin);
   const float *Wd = static_cast<const float *>(x->stage_in(W_new, (size_t)t * x->Qd * 4, 1));
   if (!Wd) return x->fail(OCTEN_ECUDA, "staging W_new");
   cudaMemcpyAsync(x->Wfix, Wd, (size_t)t * x->Qd * sizeof(float), cudaMemcpyDeviceToDevice,
                   x->st);
-  if (host_pieces(x, X_new, t)) return compress_mode2_host(x, X_new, t);
+  if (host_pieces(x, X_new, t)) return compress_mode2_host(x, X_new, t, pieces);
   const void *Xd = x->stage_in(X_new, t * slice, 2);
   if (!Xd) return x->fail(OCTEN_ECUDA, "staging the batch");
   compress_mode2(x, Xd, 0, t);
@@ -1086,8 +1089,9 @@ octen_status append_head(octen_ctx *x, const void *X_new, int64_t t, const float
 // without error): the head, then the rest of the update (Y_p += Z_p, CP of
 // every summary, anchor match, lift of A and B, the new rows of C and the
 // G_p update), then the new rows into C.
-octen_status append_launch(octen_ctx *x, const void *X_new, int64_t t, const float *W_new) {
-  octen_status s = append_head(x, X_new, t, W_new);
+octen_status append_launch(octen_ctx *x, const void *X_new, int64_t t, const float *W_new,
+                           int pieces = octen_ctx::kCopyChunks) {
+  octen_status s = append_head(x, X_new, t, W_new, pieces);
   if (s != OCTEN_OK) return s;
   tail_enqueue(x, t);
   cudaMemcpyAsync(x->C + x->K * x->cfg.R, x->Cnew_fix, (size_t)t * x->cfg.R * sizeof(float),
@@ -1125,7 +1129,7 @@ cudaGraph_t capture_head(octen_ctx *x, const void *X, int64_t t, const float *W,
   }
   cudaStream_t home = x->st;
   x->st = x->cap_st;
-  const octen_status s = append_head(x, X, t, W);
+  const octen_status s = append_head(x, X, t, W, octen_ctx::kCopyChunks);
   x->st = home;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(x->cap_st, &g);
@@ -1309,7 +1313,10 @@ octen_status octen_append_async(octen_ctx *x, const void *X_new, int64_t t, cons
     if (s != OCTEN_OK) return s;
   }
   octen_status s = append_prepare(x, X_new, t, W_new);
-  if (s == OCTEN_OK) s = append_launch(x, X_new, t, W_new);
+  // the copy of a host batch runs while the appends before it update, so it is
+  // one piece and one contraction (the pieces of octen_append overlap the
+  // copy with the contraction inside a single call)
+  if (s == OCTEN_OK) s = append_launch(x, X_new, t, W_new, 1);
   if (s != OCTEN_OK) {
     drain(x);
     return s;
