@@ -211,6 +211,10 @@ __global__ void __launch_bounds__(256)
 // With Xa / Xc given it also writes the bf16 copies of the updated X_p that
 // the tensor-core CP-ALS reads, Xa[p][(a,b)][c] and Xc[p][c][(a,b)] (the
 // latter through a [c][row] block in shared memory, 16-byte stores).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int kRG>
 __global__ void __launch_bounds__(256, 2)
     mode3_stream_kernel(const float *__restrict__ T2, const float *__restrict__ W,
@@ -238,6 +242,19 @@ __global__ void __launch_bounds__(256, 2)
   float *Yp = Y + (int64_t)p * QQ * Q;
   for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     const int64_t row0 = blk * rows_blk;
+    {
+      // this CTA's next block of Y rows (and of T2) into the L2 while this
+      // block computes; every address lies inside the next block's rows
+      const int64_t nrow0 = row0 + (int64_t)gridDim.x * rows_blk;
+      if (nrow0 < QQ) {
+        const int64_t nr = QQ - nrow0 < rows_blk ? QQ - nrow0 : rows_blk;
+        const char *ny = reinterpret_cast<const char *>(Yp + nrow0 * Q);
+        const int64_t lines = nr * Q * (int64_t)sizeof(float) / 128;
+        for (int64_t e = threadIdx.x; e < lines; e += blockDim.x) prefetch_l2(ny + e * 128);
+        for (int k = threadIdx.x; k < t; k += blockDim.x)
+          prefetch_l2(T2 + ((int64_t)p * t + k) * QQ + nrow0);
+      }
+    }
     __syncthreads();   // Ws ready / previous block's Ts consumed
     for (int e = threadIdx.x; e < rows_blk * tp; e += blockDim.x) {
       const int k = e / rows_blk, r = e - (e / rows_blk) * rows_blk;
@@ -313,7 +330,8 @@ __global__ void __launch_bounds__(256, 2)
 // registers and three CTAs per SM, but 0.98 ms against 0.70 ms at 4000^2).
 // Also tried and dropped: the next block of Y rows prefetched into shared
 // memory by a bulk asynchronous copy while the current block is computed
-// (0.83 ms against 0.69 ms at 4000^2).
+// (0.83 ms against 0.69 ms at 4000^2); prefetched into the L2 instead (the
+// prefetch_l2 lines of the kernel), 0.681 against 0.691 - 0.697 ms.
 constexpr int kMode3Rows = 8;
 
 template <int RG>
