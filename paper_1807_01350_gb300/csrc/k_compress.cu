@@ -211,10 +211,6 @@ __global__ void __launch_bounds__(256)
 // With Xa / Xc given it also writes the bf16 copies of the updated X_p that
 // the tensor-core CP-ALS reads, Xa[p][(a,b)][c] and Xc[p][c][(a,b)] (the
 // latter through a [c][row] block in shared memory, 16-byte stores).
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 template <int kRG>
 __global__ void __launch_bounds__(256, 2)
     mode3_stream_kernel(const float *__restrict__ T2, const float *__restrict__ W,

@@ -37,6 +37,11 @@ __device__ __forceinline__ void pdl_trigger() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Brings the 128-byte line holding p into the L2 (a hint: nothing waits on it).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Counts every kernel launch issued through the launch helpers below.
 void count_launch();
 // Adds to the launch counters (negative: launches that did not do the work).
