@@ -247,12 +247,15 @@ def compression_at_roofline(wl, prec, pk, comp, tc_stages):
                     "compute peak and the method's bytes at the HBM bandwidth"}
 
 
-def traffic_from_profiles(stage, prec):
+def traffic_from_profiles(stage, prec, workload):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu capture
+    of that stage, precision and workload shape (profiles/traffic.json), or
+    None where there is none."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        v = d.get(f"{stage}:{prec}")
+        v = d.get(f"{stage}:{prec}:{workload}")
         return None if v is None else v.get("bytes_per_launch")
     except Exception:
         return None
@@ -673,9 +676,9 @@ def main():
     ms_launch = st[dominant][0] / st[dominant][1]
     tcs = main_run["tc_stages"]
     roof = roofline_for(dominant, ms_launch, wl, args.prec, pk,
-                        traffic_from_profiles(dominant, args.prec), tcs)
+                        traffic_from_profiles(dominant, args.prec, wl.name), tcs)
     comp = {s: roofline_for(s, st[s][0] / st[s][1], wl, args.prec, pk,
-                            traffic_from_profiles(s, args.prec), tcs)
+                            traffic_from_profiles(s, args.prec, wl.name), tcs)
             for s in ("quantize", "mode2", "mode1", "mode3", "als_gemm") if st[s][1]}
     # the compression as a whole (quantise, mode 2, mode 1, mode 3)
     compression_roofline = compression_at_roofline(wl, args.prec, pk, comp, tcs)

@@ -174,3 +174,13 @@ def test_tensor_core_stages_report_their_binding_bound():
     fl, nb = bench.stage_work(wl, "bf16")["mode1"]
     assert m1["achieved"] == pytest.approx(nb / 0.18e-3 / 1e9, rel=1e-3)
     assert m1["tensor_frac"] == pytest.approx(fl / 0.18e-3 / 1e12 / 1718.1, rel=1e-3)
+
+
+def test_traffic_is_only_reported_for_the_captured_shape():
+    """The ncu traffic figure belongs to the shape it was captured on: the
+    4000^2 ALS GEMM has one, other workloads and precisions report none."""
+    c4 = WORKLOADS["c4"].name
+    assert bench.traffic_from_profiles("als_gemm", "bf16", c4) > 0
+    assert bench.traffic_from_profiles("als_gemm", "bf16", WORKLOADS["c3"].name) is None
+    assert bench.traffic_from_profiles("als_gemm", "fp8", c4) is None
+    assert bench.traffic_from_profiles("mode2", "bf16", c4) is None
