@@ -356,6 +356,9 @@ constexpr int kLdlReserve = 28 * 1024;
 template <int RT>
 static void factor_async(const float *Gnew, const float *Gother, int P, int R, AlsBuffers &b,
                          cudaStream_t st) {
+  // runs beside the update's GEMM (or M2 reduction): the same on-chip split
+  static const bool shared_split = (prefer_max_shared(als_ldl_kernel<RT>), true);
+  (void)shared_split;
   cudaEventRecord(b.ev_fork, st);
   cudaStreamWaitEvent(b.side, b.ev_fork, 0);
   als_ldl_kernel<RT><<<P, 128, 0, b.side>>>(Gnew, Gother, R, b.L, b.status);

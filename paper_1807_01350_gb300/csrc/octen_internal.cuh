@@ -37,6 +37,19 @@ __device__ __forceinline__ void pdl_trigger() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Asks for the largest shared-memory part of the SMs' on-chip memory when
+// kernel f runs.  An SM holds one split between L1 and shared memory at a
+// time and the tensor-core GEMMs take the largest shared part, so a kernel
+// meant to run beside them (or beside another such kernel) must prefer the
+// same split; with another preference it waits for their CTAs to leave the
+// SMs.  Call once per kernel (the setting persists).
+template <class Kernel>
+inline void prefer_max_shared(Kernel *f) {
+  if (cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    cudaGetLastError();
+}
+
 // Brings the 128-byte line holding p into the L2 (a hint: nothing waits on it).
 __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
